@@ -1,0 +1,209 @@
+"""FP64 CPU oracle for SDP-BSREM (arXiv 2111.07886) — TEST INFRASTRUCTURE.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may
+import this package.  It wraps ``pet_oracle.c`` (plain C, double precision, built with gcc)
+through ctypes and shares no code with the CUDA library.  See the C file's header for the
+passage of the paper each function follows.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pet_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, OpenMP, no FMA contraction so that x86 and Arm
+    round alike)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off",
+                               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class Geom(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("nplanes", ctypes.c_int), ("nviews", ctypes.c_int),
+                ("nbins", ctypes.c_int), ("nsubsets", ctypes.c_int),
+                ("pixel_mm", ctypes.c_double), ("bin_mm", ctypes.c_double),
+                ("sens", ctypes.c_double)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int)] + [
+        (k, ctypes.c_double) for k in ("beta", "gamma_r", "eps", "t", "U", "lambda0", "a",
+                                       "rho", "delta1", "delta2", "nu1", "nu2")] + [
+        ("J0", ctypes.c_int), ("J1", ctypes.c_int), ("precond", ctypes.c_int)]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            dp = ctypes.POINTER(ctypes.c_double)
+            ip = ctypes.POINTER(ctypes.c_int)
+            fp = ctypes.POINTER(ctypes.c_float)
+            gp = ctypes.POINTER(Geom)
+            L.ora_ray_pieces.argtypes = [gp, ctypes.c_int, ctypes.c_int, ip, dp]
+            L.ora_ray_pieces.restype = ctypes.c_int
+            L.ora_subset_size.argtypes = [gp, ctypes.c_int]
+            L.ora_subset_size.restype = ctypes.c_int
+            L.ora_forward.argtypes = [gp, ctypes.c_int, dp, dp]
+            L.ora_back.argtypes = [gp, ctypes.c_int, dp, dp]
+            L.ora_sensitivity.argtypes = [gp, dp]
+            L.ora_rdp_value.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_double, ctypes.c_double]
+            L.ora_rdp_value.restype = ctypes.c_double
+            L.ora_rdp_grad.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_double, ctypes.c_double, dp]
+            L.ora_matlab_gradient.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp]
+            L.ora_nu_from_image.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_double, ctypes.c_double, dp]
+            L.ora_alpha_nesterov.argtypes = [ctypes.c_int, dp]
+            L.ora_alpha_km.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
+            L.ora_objective.argtypes = [gp, ip, fp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
+            L.ora_reconstruct.argtypes = [gp, ip, fp, ctypes.POINTER(Params), dp, ctypes.c_int, dp]
+            _lib = L
+    return _lib
+
+
+def _d(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def geom(n, nplanes, nviews, nbins, nsubsets, pixel_mm=1.0, bin_mm=None, sens=1.0) -> Geom:
+    return Geom(n, nplanes, nviews, nbins, nsubsets, pixel_mm,
+                pixel_mm if bin_mm is None else bin_mm, sens)
+
+
+def geom_from(geometry: dict, sens: float) -> Geom:
+    g = geometry
+    return Geom(g["n"], g["nplanes"], g["nviews"], g["nbins"], g["nsubsets"],
+                g["pixel_mm"], g["bin_mm"], sens)
+
+
+def subset_size(g: Geom, subset: int) -> int:
+    return lib().ora_subset_size(ctypes.byref(g), subset)
+
+
+def ray_pieces(g: Geom, v: int, b: int):
+    """Siddon pieces of ray (v, b): (flat in-plane pixel index, length in pixel units)."""
+    cap = 2 * g.n + 2
+    pix = np.zeros(cap, np.int32)
+    ln = np.zeros(cap, np.float64)
+    k = lib().ora_ray_pieces(ctypes.byref(g), v, b,
+                             pix.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                             ln.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return pix[:k].copy(), ln[:k].copy()
+
+
+def forward(g: Geom, subset: int, f) -> np.ndarray:
+    """y = A_i f, f [P][N][N] -> [P][V_i][n_b] (subset -1: all views, [P][V][n_b])."""
+    f, fp = _d(f)
+    nv = g.nviews if subset < 0 else subset_size(g, subset)
+    y = np.zeros((g.nplanes, nv, g.nbins))
+    lib().ora_forward(ctypes.byref(g), subset, fp, y.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return y
+
+
+def back(g: Geom, subset: int, y) -> np.ndarray:
+    """A_i^T y, y [P][V_i][n_b] -> [P][N][N]."""
+    y, yp = _d(y)
+    out = np.zeros((g.nplanes, g.n, g.n))
+    lib().ora_back(ctypes.byref(g), subset, yp, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return out
+
+
+def sensitivity(g: Geom) -> np.ndarray:
+    """p_j of Eq. pj, [N][N]."""
+    out = np.zeros((g.n, g.n))
+    lib().ora_sensitivity(ctypes.byref(g), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return out
+
+
+def rdp_value(f, gamma_r=2.0, eps=1e-12) -> float:
+    f, fp = _d(f)
+    P, N = (1,) + f.shape if f.ndim == 2 else f.shape[:2]
+    return lib().ora_rdp_value(N, P, fp, gamma_r, eps)
+
+
+def rdp_grad(f, gamma_r=2.0, eps=1e-12) -> np.ndarray:
+    f, fp = _d(f)
+    P, N = (1,) + f.shape if f.ndim == 2 else f.shape[:2]
+    out = np.zeros_like(f)
+    lib().ora_rdp_grad(N, P, fp, gamma_r, eps, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return out
+
+
+def matlab_gradient(f):
+    f, fp = _d(f)
+    P, N = (1,) + f.shape if f.ndim == 2 else f.shape[:2]
+    gx, gy = np.zeros_like(f), np.zeros_like(f)
+    lib().ora_matlab_gradient(N, P, fp, gx.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                              gy.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return gx, gy
+
+
+def nu_from_image(f, nu1, nu2) -> np.ndarray:
+    f, fp = _d(f)
+    P, N = (1,) + f.shape if f.ndim == 2 else f.shape[:2]
+    out = np.zeros_like(f)
+    lib().ora_nu_from_image(N, P, fp, nu1, nu2, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return out
+
+
+def alpha_nesterov(nsub: int) -> np.ndarray:
+    out = np.zeros(nsub)
+    lib().ora_alpha_nesterov(nsub, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return out
+
+
+def alpha_km(nsub: int, rho: float, delta1: float, delta2: float) -> np.ndarray:
+    out = np.zeros(nsub)
+    lib().ora_alpha_km(nsub, rho, delta1, delta2, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return out
+
+
+def objective(g: Geom, counts, gamma, f, beta, gamma_r=2.0, eps=1e-12) -> dict:
+    """Phi(f) and its parts: sum(Af), sum(g ln(Af + gamma)), R(f)."""
+    counts = np.ascontiguousarray(counts, dtype=np.int32)
+    gamma = np.ascontiguousarray(gamma, dtype=np.float32)
+    f, fp = _d(f)
+    out = np.zeros(4)
+    lib().ora_objective(ctypes.byref(g), counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                        gamma.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), fp, beta, gamma_r,
+                        eps, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return dict(sum_af=out[0], sum_glog=out[1], rdp=out[2], phi=out[3])
+
+
+def params_from(p) -> Params:
+    """Oracle parameters from an object with the AlgoParams attribute names."""
+    return Params(p.iterations, p.beta, p.gamma_r, p.eps, p.t, p.U, p.lambda0, p.a, p.rho,
+                  p.delta1, p.delta2, p.nu1, p.nu2, p.J0, p.J1, p.precond)
+
+
+def reconstruct(g: Geom, counts, gamma, params, f0, nsub: int = -1, with_objective=False):
+    """Run SDP-BSREM (Table I) for ``nsub`` subiterations (all T M when -1).
+
+    Returns (f, objective history or None)."""
+    counts = np.ascontiguousarray(counts, dtype=np.int32)
+    gamma = np.ascontiguousarray(gamma, dtype=np.float32)
+    f = np.array(f0, dtype=np.float64, copy=True, order="C")
+    prm = params if isinstance(params, Params) else params_from(params)
+    obj = np.full(prm.iterations + 1, np.nan) if with_objective else None
+    lib().ora_reconstruct(ctypes.byref(g), counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                          gamma.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), ctypes.byref(prm),
+                          f.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), nsub,
+                          obj.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if obj is not None else None)
+    return f, obj

@@ -1,0 +1,452 @@
+/*
+ * FP64 CPU oracle for SDP-BSREM PET reconstruction (arXiv 2111.07886).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, obviously-correct reference
+ * that the CUDA path is checked against.  Only the test-suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load it; the product library never links it, and it
+ * shares no code, header, table or helper with the CUDA sources.
+ *
+ * Everything is double precision.  Each function cites the passage it follows:
+ *   - Poisson data model, fidelity F ................ Sec. II-A, Eqs. model-Poisson, FidelityTerm
+ *   - objective Phi = F + beta R, RDP R ............... Sec. II-A, Eqs. ObjectiveFunction, RDP
+ *   - subset objective Phi_i ......................... Sec. II-B, Eq. SubObjFunc
+ *   - preconditioner S, p_j, clamp P_t .............. Sec. II-B, Eqs. preconditioner, pj, OperatorPt
+ *   - SDP-BSREM loop ................................. Sec. II-C, Table I
+ *   - alpha (Nesterov / KM), mu, nu, lambda_k ......... Sec. III, Eqs. preconditioner:Nesterov,
+ *                                                      preconditioner:KM, nuki; Theorem 2
+ *   - grad F, dR/df_j ................................ Appendix A, Eq. gradRD
+ *
+ * System model: one line per detector bin, parallel beam; A_ij = sens * (length in mm of
+ * ray i inside pixel j), where a pixel is the half-open square [x, x+1) x [y, y+1) in pixel
+ * units (a ray lying on a pixel edge belongs to the pixel on its + side only).  Lengths are
+ * found by Siddon's method: all crossings of the ray with the grid lines are sorted, and each
+ * piece between consecutive crossings is charged to the pixel that contains its midpoint.
+ *
+ * Layouts: images [P][N][N] (x fastest), full sinograms [P][V][n_b], subset sinograms
+ * [P][V_i][n_b] with the subset's views in increasing order.  Subset i (0-based) holds the
+ * views v with v mod M == i.
+ */
+#define _DEFAULT_SOURCE 1
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef struct {
+    int n;           /* image side N */
+    int nplanes;     /* P */
+    int nviews;      /* V */
+    int nbins;       /* n_b */
+    int nsubsets;    /* M */
+    double pixel_mm;
+    double bin_mm;
+    double sens;     /* A_ij = sens * length_mm */
+} ora_geom;
+
+typedef struct {
+    int iterations;
+    double beta, gamma_r, eps, t, U, lambda0, a, rho, delta1, delta2, nu1, nu2;
+    int J0, J1;
+    int precond;     /* 0 BSREM, 1 M1, 2 M2, 3 P1, 4 P2 */
+} ora_params;
+
+/* ---------------------------------------------------------------------------------------
+ * Geometry.  theta_v = v pi / V; cos/sin values within 1e-12 of 0 are set to exactly 0 (and
+ * the other to exactly +-1) so that rays at theta = 0 and pi/2 lie exactly on grid lines.
+ * ------------------------------------------------------------------------------------- */
+static void view_dir(const ora_geom *g, int v, double *c, double *s)
+{
+    double th = (double)v * 3.14159265358979323846 / (double)g->nviews;
+    double cc = cos(th), ss = sin(th);
+    if (fabs(cc) < 1e-12) { cc = 0.0; ss = ss > 0 ? 1.0 : -1.0; }
+    if (fabs(ss) < 1e-12) { ss = 0.0; cc = cc > 0 ? 1.0 : -1.0; }
+    *c = cc; *s = ss;
+}
+
+/* offset of bin b from the centre, in pixel units */
+static double bin_offset(const ora_geom *g, int b)
+{
+    return ((double)b - 0.5 * (double)(g->nbins - 1)) * (g->bin_mm / g->pixel_mm);
+}
+
+int ora_subset_size(const ora_geom *g, int subset)
+{
+    int cnt = 0;
+    for (int v = subset; v < g->nviews; v += g->nsubsets) cnt++;
+    return cnt;
+}
+
+static int cmp_double(const void *a, const void *b)
+{
+    double x = *(const double *)a, y = *(const double *)b;
+    return (x > y) - (x < y);
+}
+
+/*
+ * Siddon's method for ray (v, b): fills pix[] (flat in-plane index iy*N+ix) and len[]
+ * (length in pixel units) and returns the number of pieces.  Buffers need 2N+2 entries.
+ * The ray is P(tau) = r (c, s) + tau (-s, c); the image is [-N/2, N/2]^2 in pixel units.
+ */
+int ora_ray_pieces(const ora_geom *g, int v, int b, int *pix, double *len)
+{
+    const int N = g->n;
+    double c, s;
+    view_dir(g, v, &c, &s);
+    const double r = bin_offset(g, b);
+    const double half = 0.5 * N;
+    double *tau = (double *)malloc(sizeof(double) * (2 * N + 2));
+    int nt = 0;
+    /* crossings with the vertical lines X = k - N/2: X(tau) = r c - tau s */
+    if (s != 0.0)
+        for (int k = 0; k <= N; ++k) tau[nt++] = (r * c - ((double)k - half)) / s;
+    /* crossings with the horizontal lines Y = k - N/2: Y(tau) = r s + tau c */
+    if (c != 0.0)
+        for (int k = 0; k <= N; ++k) tau[nt++] = (((double)k - half) - r * s) / c;
+    qsort(tau, (size_t)nt, sizeof(double), cmp_double);
+    int np = 0;
+    for (int m = 0; m + 1 < nt; ++m) {
+        double ta = tau[m], tb = tau[m + 1];
+        if (!(tb > ta)) continue;
+        double tm = 0.5 * (ta + tb);
+        double X = r * c - tm * s, Y = r * s + tm * c;
+        double fx = floor(X + half), fy = floor(Y + half);
+        if (fx < 0 || fy < 0 || fx >= N || fy >= N) continue;
+        pix[np] = (int)fy * N + (int)fx;
+        len[np] = tb - ta;
+        ++np;
+    }
+    free(tau);
+    return np;
+}
+
+/* views of subset `subset` in increasing order; returns count */
+static int subset_views(const ora_geom *g, int subset, int *views)
+{
+    int cnt = 0;
+    for (int v = subset; v < g->nviews; v += g->nsubsets) views[cnt++] = v;
+    return cnt;
+}
+
+/* Piece table of a list of views: for every ray (u, b), its Siddon pieces. */
+typedef struct { int *pix; double *len; int *cnt; int stride; } piece_table;
+
+static void build_pieces(const ora_geom *g, const int *views, int nv, piece_table *tb)
+{
+    const int N = g->n, NB = g->nbins;
+    tb->stride = 2 * N + 2;
+    tb->pix = (int *)malloc(sizeof(int) * (size_t)nv * NB * tb->stride);
+    tb->len = (double *)malloc(sizeof(double) * (size_t)nv * NB * tb->stride);
+    tb->cnt = (int *)malloc(sizeof(int) * (size_t)nv * NB);
+    #pragma omp parallel for schedule(dynamic)
+    for (int ray = 0; ray < nv * NB; ++ray)
+        tb->cnt[ray] = ora_ray_pieces(g, views[ray / NB], ray % NB,
+                                      tb->pix + (size_t)ray * tb->stride,
+                                      tb->len + (size_t)ray * tb->stride);
+}
+
+static void free_pieces(piece_table *tb) { free(tb->pix); free(tb->len); free(tb->cnt); }
+
+static int view_list(const ora_geom *g, int subset, int *views)
+{
+    if (subset < 0) { for (int v = 0; v < g->nviews; ++v) views[v] = v; return g->nviews; }
+    return subset_views(g, subset, views);
+}
+
+/*
+ * Forward projection of one subset: y = A_i f  (Sec. II-B, the row block A_i of A).
+ * f: [P][N][N]; y: [P][V_i][n_b].  subset = -1 projects all views into [P][V][n_b].
+ */
+void ora_forward(const ora_geom *g, int subset, const double *f, double *y)
+{
+    const int N = g->n, P = g->nplanes, NB = g->nbins;
+    int *views = (int *)malloc(sizeof(int) * g->nviews);
+    const int nv = view_list(g, subset, views);
+    const double scale = g->sens * g->pixel_mm;
+    piece_table tb;
+    build_pieces(g, views, nv, &tb);
+    #pragma omp parallel for schedule(static)
+    for (int p = 0; p < P; ++p) {
+        const double *fp = f + (size_t)p * N * N;
+        for (int ray = 0; ray < nv * NB; ++ray) {
+            const int *pix = tb.pix + (size_t)ray * tb.stride;
+            const double *len = tb.len + (size_t)ray * tb.stride;
+            double acc = 0.0;
+            for (int m = 0; m < tb.cnt[ray]; ++m) acc += len[m] * fp[pix[m]];
+            y[(size_t)p * nv * NB + ray] = scale * acc;
+        }
+    }
+    free_pieces(&tb);
+    free(views);
+}
+
+/*
+ * Back projection of one subset: out = A_i^T y (ray-driven scatter, the plain transpose).
+ * y: [P][V_i][n_b] (or [P][V][n_b] for subset = -1); out: [P][N][N] (overwritten).
+ */
+void ora_back(const ora_geom *g, int subset, const double *y, double *out)
+{
+    const int N = g->n, P = g->nplanes, NB = g->nbins;
+    int *views = (int *)malloc(sizeof(int) * g->nviews);
+    const int nv = view_list(g, subset, views);
+    const double scale = g->sens * g->pixel_mm;
+    piece_table tb;
+    build_pieces(g, views, nv, &tb);
+    memset(out, 0, sizeof(double) * (size_t)P * N * N);
+    /* planes are independent: parallel over planes, each plane scatters serially */
+    #pragma omp parallel for schedule(static)
+    for (int p = 0; p < P; ++p) {
+        double *op = out + (size_t)p * N * N;
+        for (int ray = 0; ray < nv * NB; ++ray) {
+            const double w = y[(size_t)p * nv * NB + ray];
+            const int *pix = tb.pix + (size_t)ray * tb.stride;
+            const double *len = tb.len + (size_t)ray * tb.stride;
+            for (int m = 0; m < tb.cnt[ray]; ++m) op[pix[m]] += scale * len[m] * w;
+        }
+    }
+    free_pieces(&tb);
+    free(views);
+}
+
+/* p_j of Eq. pj: (A^T 1)_j / M, or 1/M where (A^T 1)_j = 0.  p: [N][N] (same every plane). */
+void ora_sensitivity(const ora_geom *g, double *pj)
+{
+    ora_geom g1 = *g;
+    g1.nplanes = 1;
+    const int N = g->n;
+    double *ones = (double *)malloc(sizeof(double) * (size_t)g->nviews * g->nbins);
+    for (size_t k = 0; k < (size_t)g->nviews * g->nbins; ++k) ones[k] = 1.0;
+    ora_back(&g1, -1, ones, pj);
+    for (int j = 0; j < N * N; ++j)
+        pj[j] = pj[j] > 0.0 ? pj[j] / g->nsubsets : 1.0 / g->nsubsets;
+    free(ones);
+}
+
+/* ---------------------------------------------------------------------------------------
+ * RDP (Eq. RDP) and its gradient (Eq. gradRD).  8-point in-plane neighbourhood (Sec. IV-A),
+ * unweighted; neighbours outside the image do not exist.  Sum over ordered pairs (j, k).
+ * ------------------------------------------------------------------------------------- */
+static const int NBR_DX[8] = {-1, 0, 1, -1, 1, -1, 0, 1};
+static const int NBR_DY[8] = {-1, -1, -1, 0, 0, 1, 1, 1};
+
+double ora_rdp_value(int N, int P, const double *f, double gamma_r, double eps)
+{
+    double R = 0.0;
+    for (int p = 0; p < P; ++p) {
+        const double *fp = f + (size_t)p * N * N;
+        for (int iy = 0; iy < N; ++iy)
+            for (int ix = 0; ix < N; ++ix) {
+                double fj = fp[iy * N + ix];
+                for (int k = 0; k < 8; ++k) {
+                    int x = ix + NBR_DX[k], y = iy + NBR_DY[k];
+                    if (x < 0 || y < 0 || x >= N || y >= N) continue;
+                    double fk = fp[y * N + x];
+                    double d = fj - fk;
+                    R += d * d / (fj + fk + gamma_r * fabs(d) + eps);
+                }
+            }
+    }
+    return R;
+}
+
+void ora_rdp_grad(int N, int P, const double *f, double gamma_r, double eps, double *grad)
+{
+    for (int p = 0; p < P; ++p) {
+        const double *fp = f + (size_t)p * N * N;
+        double *gp = grad + (size_t)p * N * N;
+        for (int iy = 0; iy < N; ++iy)
+            for (int ix = 0; ix < N; ++ix) {
+                double fj = fp[iy * N + ix], acc = 0.0;
+                for (int k = 0; k < 8; ++k) {
+                    int x = ix + NBR_DX[k], y = iy + NBR_DY[k];
+                    if (x < 0 || y < 0 || x >= N || y >= N) continue;
+                    double fk = fp[y * N + x];
+                    double d = fj - fk;
+                    double den = fj + fk + gamma_r * fabs(d) + eps;
+                    acc += d * (gamma_r * fabs(d) + fj + 3.0 * fk + 2.0 * eps) / (den * den);
+                }
+                gp[iy * N + ix] = 2.0 * acc;
+            }
+    }
+}
+
+/*
+ * Numerical gradient of mat(f) along x and y (Sec. III, "gradient function in Matlab"):
+ * central differences (f[j+1] - f[j-1]) / 2 inside, one-sided differences at the two edges,
+ * unit spacing, in-plane.  gx along ix, gy along iy.
+ */
+void ora_matlab_gradient(int N, int P, const double *f, double *gx, double *gy)
+{
+    for (int p = 0; p < P; ++p) {
+        const double *fp = f + (size_t)p * N * N;
+        double *ox = gx + (size_t)p * N * N, *oy = gy + (size_t)p * N * N;
+        for (int iy = 0; iy < N; ++iy)
+            for (int ix = 0; ix < N; ++ix) {
+                double dx, dy;
+                if (N == 1) dx = 0.0;
+                else if (ix == 0) dx = fp[iy * N + 1] - fp[iy * N];
+                else if (ix == N - 1) dx = fp[iy * N + N - 1] - fp[iy * N + N - 2];
+                else dx = 0.5 * (fp[iy * N + ix + 1] - fp[iy * N + ix - 1]);
+                if (N == 1) dy = 0.0;
+                else if (iy == 0) dy = fp[N + ix] - fp[ix];
+                else if (iy == N - 1) dy = fp[(N - 1) * N + ix] - fp[(N - 2) * N + ix];
+                else dy = 0.5 * (fp[(iy + 1) * N + ix] - fp[(iy - 1) * N + ix]);
+                ox[iy * N + ix] = dx;
+                oy[iy * N + ix] = dy;
+            }
+    }
+}
+
+/*
+ * nu from f (Sec. III): mu = max(0.01, grad(f) / mean(f)), nu = P_{nu1}^{nu2}(mean(mu) / mu),
+ * with grad(f) = sqrt(gx^2 + gy^2) and means over all q = N^2 P pixels.
+ */
+void ora_nu_from_image(int N, int P, const double *f, double nu1, double nu2, double *nu)
+{
+    size_t q = (size_t)N * N * P;
+    double *gx = (double *)malloc(sizeof(double) * q), *gy = (double *)malloc(sizeof(double) * q);
+    ora_matlab_gradient(N, P, f, gx, gy);
+    double mf = 0.0;
+    for (size_t j = 0; j < q; ++j) mf += f[j];
+    mf /= (double)q;
+    double mmu = 0.0;
+    for (size_t j = 0; j < q; ++j) {
+        double mu = sqrt(gx[j] * gx[j] + gy[j] * gy[j]) / mf;
+        if (mu < 0.01) mu = 0.01;
+        gx[j] = mu;
+        mmu += mu;
+    }
+    mmu /= (double)q;
+    for (size_t j = 0; j < q; ++j) {
+        double v = mmu / gx[j];
+        nu[j] = v < nu1 ? nu1 : (v > nu2 ? nu2 : v);
+    }
+    free(gx); free(gy);
+}
+
+/* ---------------------------------------------------------------------------------------
+ * Scalar schedules (Sec. III).  alpha for subiterations J = 1..nsub in order.
+ * ------------------------------------------------------------------------------------- */
+/* Eq. preconditioner:Nesterov: alpha = 1 + (t_J - 1) / t_{J+1}, t_{J+1} = (1 + sqrt(1 + 4 t_J^2)) / 2,
+   t_1 = 1, the t sequence running on across outer iterations (t_{k+1,1} = t_{k,M+1}). */
+void ora_alpha_nesterov(int nsub, double *alpha)
+{
+    double t = 1.0;
+    for (int J = 0; J < nsub; ++J) {
+        double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+        alpha[J] = 1.0 + (t - 1.0) / tn;
+        t = tn;
+    }
+}
+
+/* Eq. preconditioner:KM: alpha_{k,i} = (rho (kM + i - 1) + delta2) / (kM + i - 1 + delta1). */
+void ora_alpha_km(int nsub, double rho, double delta1, double delta2, double *alpha)
+{
+    for (int J = 1; J <= nsub; ++J)
+        alpha[J - 1] = (rho * (J - 1) + delta2) / ((double)(J - 1) + delta1);
+}
+
+/* ---------------------------------------------------------------------------------------
+ * Objective Phi(f) = <Af, 1> - <ln(Af + gamma), g> + beta R(f)   (Eqs. FidelityTerm,
+ * ObjectiveFunction, RDP).  out[0] = <Af,1>, out[1] = <ln(Af+gamma), g>, out[2] = R, out[3] = Phi.
+ * ------------------------------------------------------------------------------------- */
+void ora_objective(const ora_geom *g, const int *counts, const float *gamma, const double *f,
+                   double beta, double gamma_r, double eps, double *out)
+{
+    size_t nsino = (size_t)g->nplanes * g->nviews * g->nbins;
+    double *y = (double *)malloc(sizeof(double) * nsino);
+    ora_forward(g, -1, f, y);
+    double s1 = 0.0, s2 = 0.0;
+    for (size_t k = 0; k < nsino; ++k) {
+        s1 += y[k];
+        s2 += (double)counts[k] * log(y[k] + (double)gamma[k]);
+    }
+    double R = ora_rdp_value(g->n, g->nplanes, f, gamma_r, eps);
+    out[0] = s1; out[1] = s2; out[2] = R; out[3] = s1 - s2 + beta * R;
+    free(y);
+}
+
+/* ---------------------------------------------------------------------------------------
+ * SDP-BSREM (Table I), run for `nsub` subiterations from (k, i) = (0, 1); nsub < 0 runs all
+ * T M subiterations.  f: [P][N][N] in/out.  obj (optional, length T+1): Phi(f^k) at each
+ * completed outer iteration k = 0..T (only for iterations reached).
+ *
+ * One subiteration, with J = kM + i and the subset I_i = views v == i-1 (mod M):
+ *   grad   = A_i^T (1 - g_i / (A_i f + gamma_i)) + (beta / M) grad R(f)      (Eq. SubObjFunc, App. A)
+ *   S_jj   = f_j / p_j  if f_j < U/2,  (U - f_j) / p_j  otherwise              (Eq. preconditioner)
+ *   nu     = 1 (J <= J0) | P(mean(mu)/mu) from f (J0 < J <= J1) | frozen (J > J1)   (Eq. nuki)
+ *   f~     = f - lambda_k alpha_{k,i} nu_j S_jj grad_j                             (Table I)
+ *   f      = P_t(f~)                                                           (Eq. OperatorPt)
+ * nu is computed from f^{k,i-1}, the iterate the preconditioner is applied to.
+ * ------------------------------------------------------------------------------------- */
+void ora_reconstruct(const ora_geom *g, const int *counts, const float *gamma,
+                     const ora_params *prm, double *f, int nsub, double *obj)
+{
+    const int N = g->n, P = g->nplanes, M = g->nsubsets, NB = g->nbins;
+    const size_t q = (size_t)N * N * P, npix = (size_t)N * N;
+    const int T = prm->iterations;
+    const int total = T * M;
+    if (nsub < 0 || nsub > total) nsub = total;
+    double *pj = (double *)malloc(sizeof(double) * npix);
+    ora_sensitivity(g, pj);
+    double *alpha = (double *)malloc(sizeof(double) * (total > 0 ? total : 1));
+    int kind = prm->precond;
+    if (kind == 1 || kind == 3) ora_alpha_nesterov(total, alpha);
+    else if (kind == 2 || kind == 4) ora_alpha_km(total, prm->rho, prm->delta1, prm->delta2, alpha);
+    else for (int J = 0; J < total; ++J) alpha[J] = 1.0;
+    const int use_nu = (kind == 3 || kind == 4);
+
+    double *nu = (double *)malloc(sizeof(double) * q);
+    double *nu_frozen = (double *)malloc(sizeof(double) * q);
+    int have_frozen = 0;
+    double *grad = (double *)malloc(sizeof(double) * q);
+    double *rgrad = (double *)malloc(sizeof(double) * q);
+    int *views = (int *)malloc(sizeof(int) * g->nviews);
+    double *ysub = (double *)malloc(sizeof(double) * (size_t)P * g->nviews * NB);
+
+    if (obj) { double o[4]; ora_objective(g, counts, gamma, f, prm->beta, prm->gamma_r, prm->eps, o); obj[0] = o[3]; }
+    for (int J = 1; J <= nsub; ++J) {
+        const int k = (J - 1) / M, i = (J - 1) % M + 1;
+        const double lambda = prm->lambda0 / (prm->a * k + 1.0);
+        const int subset = i - 1;
+        const int nv = subset_views(g, subset, views);
+        /* nu^{k,i} (Eq. nuki) from f^{k,i-1} */
+        if (!use_nu || J <= prm->J0) { for (size_t j = 0; j < q; ++j) nu[j] = 1.0; }
+        else if (J <= prm->J1) {
+            ora_nu_from_image(N, P, f, prm->nu1, prm->nu2, nu);
+            if (J == prm->J1) { memcpy(nu_frozen, nu, sizeof(double) * q); have_frozen = 1; }
+        } else {
+            if (!have_frozen) { /* J1 < first dynamic J: nu^{k1,i1} with J_{k1,i1} = J1 <= J0 is 1 */
+                for (size_t j = 0; j < q; ++j) nu_frozen[j] = 1.0;
+                have_frozen = 1;
+            }
+            memcpy(nu, nu_frozen, sizeof(double) * q);
+        }
+        /* data term of grad Phi_i: A_i^T (1 - g_i / (A_i f + gamma_i))  (App. A) */
+        ora_forward(g, subset, f, ysub);
+        for (int p = 0; p < P; ++p)
+            for (int u = 0; u < nv; ++u)
+                for (int b = 0; b < NB; ++b) {
+                    size_t ks = ((size_t)p * nv + u) * NB + b;
+                    size_t kf = ((size_t)p * g->nviews + views[u]) * NB + b;
+                    ysub[ks] = 1.0 - (double)counts[kf] / (ysub[ks] + (double)gamma[kf]);
+                }
+        ora_back(g, subset, ysub, grad);
+        /* penalty term (beta / M) grad R  (Eq. SubObjFunc, Eq. gradRD) */
+        ora_rdp_grad(N, P, f, prm->gamma_r, prm->eps, rgrad);
+        for (size_t j = 0; j < q; ++j) {
+            const double d = grad[j] + prm->beta / M * rgrad[j];
+            const double fj = f[j], pjj = pj[j % npix];
+            const double S = fj < 0.5 * prm->U ? fj / pjj : (prm->U - fj) / pjj;
+            double ft = fj - lambda * alpha[J - 1] * nu[j] * S * d;
+            if (ft <= 0.0) ft = prm->t;
+            else if (ft >= prm->U) ft = prm->U - prm->t;
+            f[j] = ft;
+        }
+        if (obj && i == M) {
+            double o[4];
+            ora_objective(g, counts, gamma, f, prm->beta, prm->gamma_r, prm->eps, o);
+            obj[k + 1] = o[3];
+        }
+    }
+    free(pj); free(alpha); free(nu); free(nu_frozen); free(grad); free(rgrad);
+    free(views); free(ysub);
+}

@@ -1,0 +1,263 @@
+"""Seeded synthetic PET workloads (phantoms, sinograms, algorithm parameters).
+
+This module is the ONLY code shared by the CUDA path and the FP64 oracle, and it holds
+none of the reconstruction method's arithmetic: it draws phantoms from a seeded
+``numpy.random.Generator(PCG64(seed))``, computes their *analytic* line integrals
+(continuous ellipses and ellipsoid cross-sections, not the pixel system matrix), and
+draws Poisson counts.  It follows the data model g = Poisson(A f + gamma) of Sec. II-A
+(Eq. model-Poisson) with a uniform background gamma > 0.
+
+Geometry conventions (shared by both sides as *definitions*, not code):
+  * image N x N pixels of side ``pixel_mm``, centred at the origin; pixel (ix, iy)
+    covers [ix - N/2, ix + 1 - N/2) x [iy - N/2, iy + 1 - N/2) in pixel units; the
+    flat index is iy * N + ix (x fastest); planes are stacked 2-D slices;
+  * view v has angle theta_v = v * pi / V over [0, pi); bin b sits at offset
+    r_b = (b - (n_b - 1) / 2) * bin_mm from the centre; ray (v, b) is the line
+    {X cos(theta) + Y sin(theta) = r_b};
+  * subset i (0-based) holds the views v with v mod M == i (interleaved);
+  * the system matrix is A_ij = sens * (length in mm of ray i inside pixel j), so
+    ``sens`` converts activity x mm into expected counts.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+__all__ = [
+    "Workload", "AlgoParams", "config_2d_128", "config_stacked_256x89",
+    "mixed_2d_scans", "make_scan", "ellipse_phantom_2d", "ellipsoid_phantom_3d",
+    "rasterize", "random_image",
+]
+
+# Preconditioner kinds (Sec. III: BSREM, momentum-only M1/M2, SDP P1/P2).
+PRECOND_BSREM, PRECOND_M1, PRECOND_M2, PRECOND_P1, PRECOND_P2 = 0, 1, 2, 3, 4
+# Arithmetic of the GPU path.
+PREC_FP32, PREC_FP32_KAHAN, PREC_FP64 = 0, 1, 2
+
+
+@dataclasses.dataclass
+class AlgoParams:
+    """Parameters of SDP-BSREM (Table I, Eqs. preconditioner:Nesterov/KM, nuki, Table II)."""
+    iterations: int = 10
+    beta: float = 0.05
+    gamma_r: float = 2.0          # Sec. IV-A: gamma_R = 2
+    eps: float = 1e-12            # Sec. IV-A: epsilon = 1e-12
+    t: float = 1e-4               # Sec. IV-A: t = 1e-4 in P_t
+    U: float = 1000.0             # bound of the box B (Eq. BoundedSet); no value in the paper
+    lambda0: float = 1.0          # Sec. IV-A: lambda_0 = 1
+    a: float = 0.2                # relaxation lambda_k = lambda_0 / (a k + 1)
+    rho: float = 5.0              # KM alpha limit (Eq. preconditioner:KM)
+    delta1: float = 5.0
+    delta2: float = 5.0           # Sec. IV-A: delta_1 = delta_2
+    nu1: float = 0.8
+    nu2: float = 2.2
+    J0: int = 3                   # Sec. IV-A
+    J1: int = 1000                # Sec. IV-A prints "J_2 = 1000"; Eq. nuki uses J_1
+    precond: int = PRECOND_P2
+    precision: int = PREC_FP32_KAHAN
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    n: int
+    nplanes: int
+    pixel_mm: float
+    nviews: int
+    nbins: int
+    bin_mm: float
+    nsubsets: int
+    counts: float                 # expected total counts (signal + background)
+    phantom: str                  # "ellipses2d" | "ellipsoid3d"
+    params: AlgoParams
+    plane_mm: float = 0.0
+    seed: int = 0
+
+    def geometry(self) -> dict:
+        return dict(n=self.n, nplanes=self.nplanes, pixel_mm=self.pixel_mm,
+                    nviews=self.nviews, nbins=self.nbins, bin_mm=self.bin_mm,
+                    nsubsets=self.nsubsets)
+
+
+def config_2d_128(seed: int = 0) -> Workload:
+    """2-D plain method: 128^2 at 4 mm, 180 views x 185 bins, 12 subsets, 1e6 counts,
+    10 iterations; SDP-P2(12) high-count parameters of Table II."""
+    p = AlgoParams(iterations=10, beta=0.05, a=1 / 5, rho=5.0, delta1=5.0, delta2=5.0,
+                   nu1=0.8, nu2=2.2)
+    return Workload("2d_128x128_v180_b185_m12", 128, 1, 4.0, 180, 185, 4.0, 12, 1e6,
+                    "ellipses2d", p, seed=seed)
+
+
+def config_stacked_256x89(seed: int = 0, nplanes: int = 89, iterations: int = 20) -> Workload:
+    """Clinical-size stacked 2-D: 256^2 x 89 at 2.7 mm, 288 views x 357 bins, 24 subsets,
+    5e7 counts per volume, 20 iterations; SDP-P2(24) high-count parameters of Table II."""
+    p = AlgoParams(iterations=iterations, beta=0.02, a=0.45, rho=4.0, delta1=3.0,
+                   delta2=3.0, nu1=0.8, nu2=1.8)
+    return Workload(f"stacked_256x256x{nplanes}_v288_b357_m24", 256, nplanes, 2.7, 288,
+                    357, 2.7, 24, 5e7 * nplanes / 89.0, "ellipsoid3d", p, plane_mm=2.7,
+                    seed=seed)
+
+
+# Table II rows used for the mixed 2-D scans, keyed by subset count (nearest row).
+_TABLE2_P2 = {12: (1 / 5, 5.0, 5.0, 0.8, 2.2), 24: (0.45, 4.0, 3.0, 0.8, 1.8)}
+
+
+def mixed_2d_scans(count: int = 64, seed: int = 0, iterations: int = 10) -> list[Workload]:
+    """Mixed 2-D scans: N in {128, 200, 256, 400} at FOV 512 mm, 120-360 views,
+    n_b = largest odd <= 1.45 N (bin = pixel), counts log-uniform in [1e5, 1e7],
+    12-36 subsets."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for s in range(count):
+        n = int(rng.choice([128, 200, 256, 400]))
+        v = int(rng.integers(120, 361))
+        nb = int(math.floor(1.45 * n))
+        if nb % 2 == 0:
+            nb -= 1
+        m = int(rng.choice([12, 18, 24, 36]))
+        counts = float(10 ** rng.uniform(5, 7))
+        a, rho, d1, n1, n2 = _TABLE2_P2[12 if m < 18 else 24]
+        p = AlgoParams(iterations=iterations, beta=0.05, a=a, rho=rho, delta1=d1,
+                       delta2=d1, nu1=n1, nu2=n2)
+        out.append(Workload(f"mix{s}_{n}_v{v}_b{nb}_m{m}", n, 1, 512.0 / n, v, nb,
+                            512.0 / n, m, counts, "ellipses2d", p,
+                            seed=seed * 1000 + s + 1))
+    return out
+
+
+# ----------------------------------------------------------------------------------
+# Phantoms: lists of ellipses per plane, (cx, cy, ax, ay, phi, value) in mm, additive.
+# ----------------------------------------------------------------------------------
+
+def _overlap(c1, r1, c2, r2) -> bool:
+    return math.hypot(c1[0] - c2[0], c1[1] - c2[1]) < r1 + r2 + 1e-9
+
+
+def ellipse_phantom_2d(n: int, pixel_mm: float, seed: int, n_ellipses: int = 10):
+    """Disk background of value 1 (radius 0.45 FOV) holding ``n_ellipses`` random,
+    non-overlapping ellipses of intensity U[0.5, 4] (the ellipse replaces the background,
+    so it is stored as an additive offset intensity - 1)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    fov = n * pixel_mm
+    rbg = 0.45 * fov
+    shapes = [(0.0, 0.0, rbg, rbg, 0.0, 1.0)]
+    placed = []
+    tries = 0
+    while len(placed) < n_ellipses and tries < 20000:
+        tries += 1
+        ax, ay = rng.uniform(0.04, 0.2, size=2) * rbg
+        rad = 0.7 * rbg * math.sqrt(rng.uniform())
+        ang = rng.uniform(0, 2 * math.pi)
+        c = (rad * math.cos(ang), rad * math.sin(ang))
+        r = max(ax, ay)
+        if math.hypot(*c) + r > 0.95 * rbg:
+            continue
+        if any(_overlap(c, r, c2, r2) for c2, r2 in placed):
+            continue
+        phi = rng.uniform(0, math.pi)
+        val = rng.uniform(0.5, 4.0)
+        placed.append((c, r))
+        shapes.append((c[0], c[1], ax, ay, phi, val - 1.0))
+    return [shapes]
+
+
+def ellipsoid_phantom_3d(n: int, nplanes: int, pixel_mm: float, plane_mm: float, seed: int,
+                         n_spheres: int = 6):
+    """Random ellipsoid body (value 1) holding ``n_spheres`` hot spheres of diameter
+    U[3, 15] mm at contrast 4:1; returns the elliptical cross-section of every plane."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    fov = n * pixel_mm
+    ax, ay = rng.uniform(0.28, 0.38) * fov, rng.uniform(0.2, 0.28) * fov
+    az = rng.uniform(0.5, 0.7) * max(nplanes * plane_mm, 1.0)
+    phi = rng.uniform(0, math.pi)
+    spheres = []
+    tries = 0
+    zext = max(0.5 * (nplanes - 1) * plane_mm, 1.0)
+    while len(spheres) < n_spheres and tries < 20000:
+        tries += 1
+        rad = 0.5 * rng.uniform(3.0, 15.0)
+        c = (rng.uniform(-0.6, 0.6) * ax, rng.uniform(-0.6, 0.6) * ay,
+             rng.uniform(-0.8, 0.8) * zext)
+        if any(math.dist(c, c2) < rad + r2 + 2.0 for c2, r2 in spheres):
+            continue
+        spheres.append((c, rad))
+    planes = []
+    for p in range(nplanes):
+        z = (p - (nplanes - 1) / 2.0) * plane_mm
+        sh = []
+        k2 = 1.0 - (z / az) ** 2
+        if k2 > 0:
+            k = math.sqrt(k2)
+            sh.append((0.0, 0.0, ax * k, ay * k, phi, 1.0))
+        for (cx, cy, cz), rad in spheres:
+            d2 = rad * rad - (z - cz) ** 2
+            if d2 > 0:
+                rr = math.sqrt(d2)
+                sh.append((cx, cy, rr, rr, 0.0, 3.0))
+        planes.append(sh)
+    return planes
+
+
+def analytic_sinogram(planes, nviews: int, nbins: int, bin_mm: float) -> np.ndarray:
+    """Exact line integrals (activity x mm) of the continuous phantom along every ray,
+    [P][V][n_b] float64.  For an ellipse with semi-axes (a, b), rotation phi, centre c,
+    the chord along {X cos t + Y sin t = r} is 2ab sqrt(D^2 - r'^2) / D^2 with
+    D^2 = a^2 cos^2(t - phi) + b^2 sin^2(t - phi) and r' = r - <c, (cos t, sin t)>."""
+    theta = np.arange(nviews) * math.pi / nviews
+    ct, st = np.cos(theta)[:, None], np.sin(theta)[:, None]
+    r = ((np.arange(nbins) - (nbins - 1) / 2.0) * bin_mm)[None, :]
+    out = np.zeros((len(planes), nviews, nbins))
+    for p, shapes in enumerate(planes):
+        for (cx, cy, a, b, phi, val) in shapes:
+            d2 = (a * np.cos(theta - phi)) ** 2 + (b * np.sin(theta - phi)) ** 2
+            d2 = d2[:, None]
+            rp = r - (cx * ct + cy * st)
+            inside = np.clip(d2 - rp * rp, 0.0, None)
+            out[p] += val * 2.0 * a * b * np.sqrt(inside) / d2
+    return out
+
+
+def rasterize(planes, n: int, pixel_mm: float, supersample: int = 4) -> np.ndarray:
+    """Pixel image [P][N][N] of the phantom (partial volume by supersampling)."""
+    s = supersample
+    g = (np.arange(n * s) + 0.5) / s - n / 2.0
+    X, Y = np.meshgrid(g * pixel_mm, g * pixel_mm)
+    out = np.zeros((len(planes), n, n))
+    for p, shapes in enumerate(planes):
+        img = np.zeros_like(X)
+        for (cx, cy, a, b, phi, val) in shapes:
+            dx, dy = X - cx, Y - cy
+            u = dx * math.cos(phi) + dy * math.sin(phi)
+            w = -dx * math.sin(phi) + dy * math.cos(phi)
+            img += val * ((u / a) ** 2 + (w / b) ** 2 <= 1.0)
+        out[p] = img.reshape(n, s, n, s).mean(axis=(1, 3))
+    return out
+
+
+def make_scan(w: Workload) -> dict:
+    """Counts (int32 [P][V][n_b]), background gamma (float32, uniform, 10 % of the mean
+    signal), the projector scale ``sens`` and the phantom, for workload ``w``.
+
+    ``sens`` is chosen so that the expected total counts sum(sens * line integrals)
+    + sum(gamma) equals ``w.counts``."""
+    if w.phantom == "ellipses2d":
+        planes = ellipse_phantom_2d(w.n, w.pixel_mm, w.seed)
+    else:
+        planes = ellipsoid_phantom_3d(w.n, w.nplanes, w.pixel_mm, w.plane_mm, w.seed)
+    sino = analytic_sinogram(planes, w.nviews, w.nbins, w.bin_mm)
+    total_signal = sino.sum()
+    sens = w.counts / (1.1 * total_signal)
+    mean_sig = sens * total_signal / sino.size
+    gamma = np.full(sino.shape, 0.1 * mean_sig, dtype=np.float32)
+    rng = np.random.Generator(np.random.PCG64(w.seed + 7919))
+    lam = sens * sino + gamma.astype(np.float64)
+    counts = rng.poisson(lam).astype(np.int32)
+    return dict(counts=counts, gamma=gamma, sens=float(sens), planes=planes)
+
+
+def random_image(shape, seed: int, lo: float = 0.1, hi: float = 2.0) -> np.ndarray:
+    """Seeded uniform random image / sinogram (test inputs)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.uniform(lo, hi, size=shape)
