@@ -1,0 +1,348 @@
+"""Benchmark: SDP-BSREM ordered-subsets subiterations per second on one GB300.
+
+One step = one whole reconstruction of the clinical-size stacked workload (256 x 256 x 89
+planes at 2.7 mm, 288 views x 357 bins, 24 subsets, 20 iterations of SDP-P2(24), with the
+objective Phi(f^k) after every iteration): 480 subiterations (subset forward projection +
+Poisson ratio, gather backprojection + RDP gradient + nu + preconditioned update + clamp,
+the mu reduction when nu is dynamic) plus 21 objective evaluations, on inputs already
+resident in HBM.  L2 is flushed (a 256 MiB write) before every timed step and each step is
+timed with CUDA events on its stream.  ``value`` = subiterations per second over the job.
+
+``e2e`` repeats the measurement through pet_reconstruct_host from pinned host buffers (counts,
+gamma and f^0 copied in, f^T and the objective history copied out inside the timed call).
+
+``--impl reference`` times the FP64 CPU oracle instead (bounded sample of subiterations of the
+same workload on the host cores).  Multi-GPU: independent replicas, one scan per rank, no
+collective (scans do not exchange data).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2111_07886_gb300 import synth  # noqa: E402
+
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="stacked", choices=["stacked", "2d"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def workload(name: str):
+    return synth.config_stacked_256x89(seed=0) if name == "stacked" else synth.config_2d_128(seed=0)
+
+
+def workload_config(w) -> dict:
+    return {"workload": w.name, "image": [w.nplanes, w.n, w.n], "pixel_mm": w.pixel_mm,
+            "views": w.nviews, "bins": w.nbins, "subsets": w.nsubsets,
+            "iterations": w.params.iterations, "precond": "SDP-P2", "beta": w.params.beta,
+            "counts": w.counts, "subiters_per_step": w.params.iterations * w.nsubsets,
+            "objective_per_iteration": True, "l2": "flushed (256 MiB write) before each step",
+            "global_batch": 1, "parallelism": "replicas"}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ------------------------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() in ("active", "0x1", "1"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------
+# roofline: algorithmic bytes per launch of each kernel kind
+# ------------------------------------------------------------------------------------------
+def algorithmic_bytes(w) -> dict:
+    q = w.n * w.n * w.nplanes                                  # image elements
+    sub_bins = (w.nviews // w.nsubsets) * w.nbins * w.nplanes  # |I_i| (equal subsets here)
+    all_bins = w.nviews * w.nbins * w.nplanes
+    return {
+        # f read, counts + gamma read, ratio w written
+        "forward_ratio": 4 * q + 12 * sub_bins,
+        # w read, f read, 1/p read (one plane), f written
+        "update": 4 * sub_bins + 8 * q + 4 * w.n * w.n,
+        "mu_sum": 4 * q,
+        # f read, counts + gamma read (all views)
+        "obj_forward": 4 * q + 8 * all_bins,
+        "rdp_value": 4 * q,
+    }
+
+
+def load_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary of the same kernel, if current."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return d.get(kernel)
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------------------------------------
+def run_ours(args, rank, world, local):
+    import torch
+    from paper_2111_07886_gb300 import pet
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = workload(args.workload)
+    w.seed = w.seed + rank                 # each replica reconstructs its own scan
+    scan = synth.make_scan(w)
+    g = pet.Geometry.from_dict(w.geometry(), scan["sens"])
+    prm = pet.make_params(w.params)
+    counts = torch.from_numpy(scan["counts"]).to(dev)
+    gamma = torch.from_numpy(scan["gamma"]).to(dev)
+    f0 = torch.ones((w.nplanes, w.n, w.n), dtype=torch.float32, device=dev)
+    img = torch.empty_like(f0)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    subiters = w.params.iterations * w.nsubsets
+
+    def step():
+        img.copy_(f0)
+        return pet.reconstruct(g, counts, gamma, prm, img, objective=True)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    n0 = pet.launch_count()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    t_wall = time.perf_counter()
+    obj = None
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        evs[k][0].record(stream)
+        obj = step()
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall
+    launches = (pet.launch_count() - n0) // args.steps
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(t.item())
+    ms_per_step = ms_max / args.steps
+    value = world * subiters / (ms_per_step / 1e3)
+
+    # per-kernel device time: a second pass with every launch bracketed by events
+    pet.profile_reset()
+    pet.profile_enable(True)
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        step()
+    torch.cuda.synchronize()
+    prof = pet.profile_read()
+    pet.profile_enable(False)
+    byts = algorithmic_bytes(w)
+    tot = sum(v[0] for v in prof.values())
+    shares = {k: {"ms": round(v[0] / max(1, args.steps), 4), "launches_per_step": v[1] // max(1, args.steps),
+                  "share": round(v[0] / tot, 4) if tot else 0.0} for k, v in prof.items() if v[1]}
+    dom = max((k for k in prof if k in byts and prof[k][1]), key=lambda k: prof[k][0])
+    avg_ms = prof[dom][0] / prof[dom][1]
+    peaks = load_peaks()
+    achieved = byts[dom] / (avg_ms / 1e3) / 1e9
+    roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
+            "peak_source": peaks["source"] + " (burst copy)", "unit": "GB/s",
+            "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": ncu_traffic(dom),
+            "algorithmic_bytes_per_launch": byts[dom], "avg_launch_ms": round(avg_ms, 5)}
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    h_counts = torch.from_numpy(scan["counts"]).pin_memory()
+    h_gamma = torch.from_numpy(scan["gamma"]).pin_memory()
+    h_img = torch.ones((w.nplanes, w.n, w.n), dtype=torch.float32).pin_memory()
+    h_f0 = h_img.clone()
+    e2e_steps = max(1, min(args.steps, 3))
+    pet.reconstruct_host(g, h_counts.numpy(), h_gamma.numpy(), prm, h_img.numpy(), objective=True)
+    e2e_ms = 0.0
+    for k in range(e2e_steps):
+        h_img.copy_(h_f0)
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pet.reconstruct_host(g, h_counts.numpy(), h_gamma.numpy(), prm, h_img.numpy(), objective=True)
+        e2e_ms += (time.perf_counter() - t0) * 1e3
+    e2e_ms /= e2e_steps
+    te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
+    e2e = {"value": round(world * subiters / (float(te.item()) / 1e3), 2), "unit": "subiters/s",
+           "h2d_bytes_per_step": int(h_counts.numel() * 4 + h_gamma.numel() * 4 + h_img.numel() * 4),
+           "d2h_bytes_per_step": int(h_img.numel() * 4 + 8 * (w.params.iterations + 1)),
+           "api": "pet_reconstruct_host", "ms_per_step": round(float(te.item()), 3)}
+
+    line = {
+        "metric": "OS subiters/s", "value": round(value, 2), "unit": "subiters/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (Kahan sums) + f64 scalars/objective",
+        "data": "synthetic (seeded random-ellipsoid phantom, analytic projections, Poisson counts)",
+        "config": workload_config(w), "clocks": clk, "gpu_launches": int(launches),
+        "wall_s_timed": round(wall, 3), "roofline": roof, "kernels": shares, "e2e": e2e,
+        "objective_final": obj[-1] if obj else None,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, scan, args.cpu_seconds)
+    return line
+
+
+def cpu_baseline(w, scan, seconds: float) -> dict:
+    """The FP64 oracle, as it stands, on a bounded sample of the same workload: runs
+    ora_reconstruct for a growing number of subiterations until ~`seconds` of CPU time."""
+    import oracle
+    og = oracle.geom_from(w.geometry(), scan["sens"])
+    f0 = np.ones((w.nplanes, w.n, w.n))
+    n = 2
+    while True:
+        t0 = time.perf_counter()
+        oracle.reconstruct(og, scan["counts"], scan["gamma"], w.params, f0, nsub=n)
+        dt = time.perf_counter() - t0
+        if dt >= seconds / 3 or n >= w.params.iterations * w.nsubsets:
+            break
+        n = min(w.params.iterations * w.nsubsets, max(n + 1, int(n * seconds / 3 / max(dt, 1e-3))))
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": round(n / dt, 4), "unit": "subiters/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n} subiterations of {w.name} from f0 = 1 (incl. its sensitivity setup), "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    """The oracle as the reference arm: each step is a bounded sample of subiterations."""
+    w = workload(args.workload)
+    scan = synth.make_scan(w)
+    import oracle
+    og = oracle.geom_from(w.geometry(), scan["sens"])
+    f0 = np.ones((w.nplanes, w.n, w.n))
+    nsub = 4 if args.workload == "stacked" else 24
+    for _ in range(args.warmup):
+        oracle.reconstruct(og, scan["counts"], scan["gamma"], w.params, f0, nsub=1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.reconstruct(og, scan["counts"], scan["gamma"], w.params, f0, nsub=nsub)
+    dt = time.perf_counter() - t0
+    value = args.steps * nsub / dt
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = f"{nsub} subiterations of {w.name} per step from f0 = 1"
+    return {"impl": "reference", "metric": "OS subiters/s", "value": round(value, 4),
+            "unit": "subiters/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(w),
+            "cpu_baseline": {"value": round(value, 4), "unit": "subiters/s", "cores": cores,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(value, 4), "unit": "subiters/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args, rank, world)), flush=True)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local)
+        torch.distributed.init_process_group("nccl")
+    line = run_ours(args, rank, world, local)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,218 @@
+/*
+ * libpet — GB300-native SDP-BSREM PET reconstruction (arXiv 2111.07886), C ABI.
+ *
+ * The library computes penalised-likelihood PET reconstruction with the relative difference
+ * prior (RDP) by BSREM with subiteration-dependent diagonal preconditioners (SDP-BSREM,
+ * Table I).  Every step of the path runs in hand-written CUDA kernels for sm_103a.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Geometry (Sec. II-A, Eq. model-Poisson; one line per detector bin, parallel beam):
+ *   - image: N x N pixels of side pixel_mm, P stacked planes, centred at the origin; pixel
+ *     (ix, iy) is the half-open square [ix - N/2, ix + 1 - N/2) x [iy - N/2, iy + 1 - N/2) in
+ *     pixel units, so a ray lying on a pixel edge belongs to the pixel on its + side only;
+ *   - views theta_v = v pi / V, v = 0..V-1; bins at offsets r_b = (b - (n_b - 1)/2) bin_mm;
+ *     ray (v, b) is the line {x cos theta_v + y sin theta_v = r_b};
+ *   - system matrix A_ij = sens * (length in mm of ray i inside pixel j);
+ *   - ordered subsets (Sec. II-B): subset i (0-based) holds the views v with v mod M == i,
+ *     processed i = 0..M-1 within an iteration; subset projections list the subset's views
+ *     in increasing order.
+ * Layouts (row-major, x fastest):
+ *   - images  float [P][N][N];
+ *   - sinograms: counts int32 [P][V][n_b], background gamma float [P][V][n_b] (gamma > 0);
+ *   - subset projections float [P][V_i][n_b].
+ * Memory: pointers named d_* are device memory owned by the caller (the library never frees
+ *   them); pointers named h_* are host memory owned by the caller.  Handles are owned by the
+ *   library and freed by the matching *_destroy.  `stream` is a cudaStream_t passed as void*
+ *   (NULL = the legacy default stream); device work is enqueued on it and the call returns
+ *   without synchronising unless it says otherwise.
+ * Errors: every call returns a pet_status and never aborts; on failure pet_last_error()
+ *   gives a message for the calling thread.  CUDA failures map to PET_ERR_CUDA.
+ * Precision: PET_PREC_FP32 sums in plain FP32; PET_PREC_FP32_KAHAN adds compensated (Kahan)
+ *   sums along rays and in the backprojection gather; PET_PREC_FP64 runs every kernel in
+ *   double.  In all modes the objective, the global sums behind mean(f) and mean(mu), and the
+ *   step-size scalars are FP64; counts stay exact int32.
+ */
+#ifndef PET_H_
+#define PET_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PET_OK = 0,
+    PET_ERR_INVALID = 1,    /* bad argument, shape, or input value (e.g. gamma <= 0) */
+    PET_ERR_OOM = 2,        /* device or host allocation failed / over budget */
+    PET_ERR_CUDA = 3,       /* a CUDA runtime call failed */
+    PET_ERR_TIMEOUT = 4,    /* a bounded wait ran out */
+    PET_PENDING = 5,        /* serving: request not finished yet */
+    PET_ERR_NOT_FOUND = 6   /* serving: unknown ticket */
+} pet_status;
+
+typedef struct {
+    int n;              /* image side N (pixels) */
+    int nplanes;        /* P stacked 2-D planes */
+    double pixel_mm;    /* pixel side */
+    int nviews;         /* V views over [0, pi) */
+    int nbins;          /* n_b radial bins */
+    double bin_mm;      /* bin spacing */
+    int nsubsets;       /* M ordered subsets, 1 <= M <= V */
+    double sens;        /* A_ij = sens * length_mm (counts per activity per mm), > 0 */
+} pet_geometry_desc;
+
+typedef enum {
+    PET_PRECOND_BSREM = 0,  /* S^{k,i} = S                         (Sec. II-B)           */
+    PET_PRECOND_M1 = 1,     /* alpha Nesterov, nu = 1              (Eq. preconditioner:Nesterov) */
+    PET_PRECOND_M2 = 2,     /* alpha KM, nu = 1                    (Eq. preconditioner:KM) */
+    PET_PRECOND_P1 = 3,     /* alpha Nesterov, nu from Eq. nuki                          */
+    PET_PRECOND_P2 = 4      /* alpha KM, nu from Eq. nuki                                */
+} pet_precond;
+
+typedef enum { PET_PREC_FP32 = 0, PET_PREC_FP32_KAHAN = 1, PET_PREC_FP64 = 2 } pet_precision;
+
+/* Parameters of SDP-BSREM (Table I; Eqs. RDP, preconditioner, OperatorPt,
+ * preconditioner:Nesterov, preconditioner:KM, nuki; relaxation lambda_k of Theorem 2). */
+typedef struct {
+    int iterations;     /* T outer iterations (pet_reconstruct) */
+    double beta;        /* RDP weight beta >= 0 (Eq. ObjectiveFunction) */
+    double gamma_r;     /* RDP edge parameter gamma_R >= 0 (Eq. RDP) */
+    double eps;         /* RDP epsilon > 0 (Eq. RDP) */
+    double t;           /* clamp margin of P_t, 0 < t < U (Eq. OperatorPt) */
+    double U;           /* upper bound of the box B (Eq. BoundedSet) */
+    double lambda0;     /* lambda_k = lambda0 / (a k + 1), lambda0 > 0 */
+    double a;           /* a >= 0 */
+    double rho;         /* KM alpha: (rho (J-1) + delta2) / (J - 1 + delta1) */
+    double delta1;
+    double delta2;
+    double nu1;         /* nu = P_{nu1}^{nu2}(mean(mu) / mu), 0 < nu1 <= nu2 */
+    double nu2;
+    int J0;             /* nu = 1 for J <= J0 */
+    int J1;             /* nu frozen at its J1 value for J > J1 */
+    int precond;        /* pet_precond */
+    int precision;      /* pet_precision */
+} pet_params;
+
+typedef struct pet_geometry pet_geometry;
+typedef struct pet_state pet_state;
+typedef struct pet_server pet_server;
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char *pet_last_error(void);
+
+/* ------------------------------------------------------------------------------------------
+ * Geometry (Sec. II-A/II-B).  Builds the per-view / per-ray walk tables in FP64 on the host,
+ * uploads them, and computes the sensitivity p_j of Eq. pj (one backprojection of ones over all
+ * views) on the device.  Synchronises `stream` before returning.  PET_ERR_INVALID for a bad desc.
+ * ---------------------------------------------------------------------------------------- */
+pet_status pet_geometry_create(const pet_geometry_desc *desc, void *stream, pet_geometry **out);
+void pet_geometry_destroy(pet_geometry *g);
+
+/* Number of views V_i in subset `subset` (0 <= subset < M), or -1 if out of range. */
+int pet_subset_size(const pet_geometry *g, int subset);
+
+/* p_j of Eq. pj: (A^T 1)_j / M, or 1/M where (A^T 1)_j = 0.  d_p: float [N][N] (identical for
+ * every plane).  Copies the FP32 table computed at creation. */
+pet_status pet_sensitivity(const pet_geometry *g, float *d_p, void *stream);
+
+/* ------------------------------------------------------------------------------------------
+ * Projectors (Sec. II-B: the row block A_i of A; App. A: grad F = A^T(1 - g/(Af + gamma))).
+ * pet_forward_subset: d_proj = A_i d_img (no background added); float [P][N][N] ->
+ *   float [P][V_i][n_b].  Ray-driven Siddon line integrals, FP32 with Kahan sums.
+ * pet_back_subset: d_img = A_i^T d_proj; float [P][V_i][n_b] -> float [P][N][N] (overwritten).
+ *   Pixel-driven gather (deterministic, no float atomics), FP32 with Kahan sums.
+ * *_f64 variants: the same in double throughout.
+ * subset = -1 means all views (d_proj then [P][V][n_b]).  Calls on one geometry use its scratch
+ * buffers: do not overlap them on different streams.
+ * ---------------------------------------------------------------------------------------- */
+pet_status pet_forward_subset(const pet_geometry *g, int subset, const float *d_img, float *d_proj,
+                              void *stream);
+pet_status pet_back_subset(const pet_geometry *g, int subset, const float *d_proj, float *d_img,
+                           void *stream);
+pet_status pet_forward_subset_f64(const pet_geometry *g, int subset, const double *d_img,
+                                  double *d_proj, void *stream);
+pet_status pet_back_subset_f64(const pet_geometry *g, int subset, const double *d_proj,
+                               double *d_img, void *stream);
+
+/* ------------------------------------------------------------------------------------------
+ * Reconstruction state (Table I).  pet_state_create copies counts, gamma and the initial image
+ * into library-owned device buffers (reordered by subset, planes innermost), validates that
+ * counts >= 0 and gamma > 0 and finite (PET_ERR_INVALID otherwise), and positions the state at
+ * (k, i) = (0, 1).  The state keeps f, the frozen nu, the scalar schedule and the FP64 global
+ * sums resident across subiterations.  Synchronises `stream`.
+ * pet_subiter: one subiteration f^{k,i} = P_t(f^{k,i-1} - lambda_k S^{k,i}(f^{k,i-1})
+ *   grad Phi_i(f^{k,i-1})), then advances (k, i).  Asynchronous.
+ * pet_state_read_image: d_img = current f as float [P][N][N].
+ * pet_state_objective: *h_phi = Phi(current f) (Eqs. FidelityTerm, ObjectiveFunction), FP64;
+ *   h_parts (optional, 3 doubles) = sum(Af), sum(g ln(Af + gamma)), R(f).  Synchronises.
+ * pet_state_subiters: completed subiterations J.
+ * ---------------------------------------------------------------------------------------- */
+pet_status pet_state_create(const pet_geometry *g, const int32_t *d_counts, const float *d_gamma,
+                            const pet_params *params, const float *d_img_init, void *stream,
+                            pet_state **out);
+pet_status pet_subiter(pet_state *s, void *stream);
+pet_status pet_state_read_image(const pet_state *s, float *d_img, void *stream);
+pet_status pet_state_objective(pet_state *s, double *h_phi, double *h_parts, void *stream);
+int pet_state_subiters(const pet_state *s);
+void pet_state_destroy(pet_state *s);
+
+/* ------------------------------------------------------------------------------------------
+ * Whole reconstruction (Table I, T = params->iterations outer iterations of M subiterations).
+ * d_img_inout: f^0 in, f^T out (float [P][N][N]).  h_objective: NULL, or T+1 doubles receiving
+ * Phi(f^k), k = 0..T.  Synchronises `stream`.
+ * pet_reconstruct_host: the same from host buffers (copies in and out inside the call).
+ * ---------------------------------------------------------------------------------------- */
+pet_status pet_reconstruct(const pet_geometry *g, const int32_t *d_counts, const float *d_gamma,
+                           const pet_params *params, float *d_img_inout, double *h_objective,
+                           void *stream);
+pet_status pet_reconstruct_host(const pet_geometry *g, const int32_t *h_counts,
+                                const float *h_gamma, const pet_params *params,
+                                float *h_img_inout, double *h_objective, void *stream);
+
+/* ------------------------------------------------------------------------------------------
+ * Single steps of the hot path, for parity checks (same kernels as pet_subiter).
+ * pet_rdp_gradient: d_grad = grad R(d_img) (Eq. gradRD, 8-neighbourhood in-plane), float.
+ * pet_smoothness_nu: d_nu = P_{nu1}^{nu2}(mean(mu) / mu), mu = max(0.01, grad(f)/mean(f))
+ *   (Sec. III, Eq. nuki), grad = Matlab-style numerical gradient magnitude; float.
+ * pet_objective: Phi(d_img) for given data (Eqs. FidelityTerm, ObjectiveFunction, RDP), FP64
+ *   sums; h_parts as for pet_state_objective.  Synchronises.
+ * Images float [P][N][N].
+ * ---------------------------------------------------------------------------------------- */
+pet_status pet_rdp_gradient(const pet_geometry *g, const float *d_img, double gamma_r, double eps,
+                            float *d_grad, void *stream);
+pet_status pet_smoothness_nu(const pet_geometry *g, const float *d_img, double nu1, double nu2,
+                             float *d_nu, void *stream);
+pet_status pet_objective(const pet_geometry *g, const int32_t *d_counts, const float *d_gamma,
+                         const float *d_img, double beta, double gamma_r, double eps,
+                         double *h_phi, double *h_parts, void *stream);
+
+/* ------------------------------------------------------------------------------------------
+ * Launch accounting (no counterpart in the paper; instrumentation of this library).
+ * pet_launch_count: kernels launched by this library since load (all threads).
+ * pet_profile_enable(1): from now on, every launch is bracketed by CUDA events on its stream;
+ *   pet_profile_read(kind, ...) waits for the recorded events and returns the accumulated
+ *   device time (ms) and launch count of one kernel kind; pet_profile_reset clears them.
+ * ---------------------------------------------------------------------------------------- */
+typedef enum {
+    PET_K_FORWARD_RATIO = 0,  /* subset forward projection + Poisson ratio (a2, a3) */
+    PET_K_UPDATE = 1,         /* gather backprojection + RDP + nu + update + clamp (a4, a6, a7) */
+    PET_K_MU_SUM = 2,         /* smoothness reduction sum(mu) (a5) */
+    PET_K_OBJ_FORWARD = 3,    /* full forward projection with objective sums (a8) */
+    PET_K_RDP_VALUE = 4,      /* RDP value (a8) */
+    PET_K_LAYOUT = 5,         /* layout conversions and input checks */
+    PET_K_OTHER = 6,          /* stand-alone projectors, sums, maps */
+    PET_K_COUNT = 7
+} pet_kernel_kind;
+
+long long pet_launch_count(void);
+void pet_profile_enable(int on);
+pet_status pet_profile_read(int kind, double *total_ms, long long *launches);
+void pet_profile_reset(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PET_H_ */

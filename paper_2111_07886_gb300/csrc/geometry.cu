@@ -1,0 +1,280 @@
+// Geometry: per-view / per-ray tables of the ray-driven projector and the pixel-driven
+// backprojector (built in FP64 on the host), the subset ordering of Sec. II-B, and the
+// sensitivity p_j of Eq. pj.  Also the error plumbing of the C ABI.
+#include <math.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <cstring>
+#include <string>
+
+#include "pet_common.cuh"
+#include "profile.cuh"
+
+namespace pet {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+pet_status fail(pet_status st, const std::string &msg)
+{
+    g_last_error = msg;
+    return st;
+}
+
+pet_status cuda_fail(cudaError_t e, const char *what)
+{
+    g_last_error = std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? PET_ERR_OOM : PET_ERR_CUDA;
+}
+
+static inline long long to_q32(double x) { return llround(ldexp(x, 32)); }
+
+size_t reducer_bytes(int capacity, int nvals)
+{
+    return (size_t)capacity * nvals * sizeof(double) + 256;
+}
+
+void reducer_bind(Reducer &r, void *mem, int capacity, int nvals)
+{
+    r.partials = reinterpret_cast<double *>(mem);
+    r.ticket = reinterpret_cast<unsigned int *>(reinterpret_cast<char *>(mem) +
+                                                (size_t)capacity * nvals * sizeof(double));
+    r.capacity = capacity;
+}
+
+pet_status geometry_scratch(const pet_geometry *gc, size_t bytes, void **out)
+{
+    pet_geometry *g = const_cast<pet_geometry *>(gc);
+    if (g->scratch_bytes < bytes) {
+        if (g->d_scratch) PET_CUDA(cudaFree(g->d_scratch));
+        g->d_scratch = nullptr;
+        g->scratch_bytes = 0;
+        PET_CUDA(cudaMalloc(&g->d_scratch, bytes));
+        g->scratch_bytes = bytes;
+    }
+    *out = g->d_scratch;
+    return PET_OK;
+}
+
+// p_j = (A^T 1)_j / M, or 1/M where (A^T 1)_j == 0 (Eq. pj); also 1/p_j in FP32 and FP64.
+__global__ void finish_sensitivity(const double *bp, int npix, int M, float *p, float *invp,
+                                   double *invp64)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= npix) return;
+    double v = bp[j];
+    double pj = v > 0.0 ? v / M : 1.0 / M;
+    p[j] = (float)pj;
+    invp[j] = (float)(1.0 / pj);
+    invp64[j] = 1.0 / pj;
+}
+
+}  // namespace pet
+
+using namespace pet;
+
+extern "C" const char *pet_last_error(void) { return pet::g_last_error.c_str(); }
+
+static pet_status build_tables(pet_geometry *g, std::vector<ViewGeo> &views,
+                               std::vector<RayGeo> &rays)
+{
+    const pet_geometry_desc &d = g->desc;
+    const int N = d.n, V = d.nviews, NB = d.nbins, M = d.nsubsets;
+    const double rho = d.bin_mm / d.pixel_mm;
+    const double half = 0.5 * N;
+    g->voff.assign(M + 1, 0);
+    g->view_of_slot.clear();
+    for (int i = 0; i < M; ++i) {
+        g->voff[i] = (int)g->view_of_slot.size();
+        for (int v = i; v < V; v += M) g->view_of_slot.push_back(v);
+    }
+    g->voff[M] = V;
+    views.resize(V);
+    rays.resize((size_t)V * NB);
+    int K = 1;
+    for (int u = 0; u < V; ++u) {
+        const int v = g->view_of_slot[u];
+        const double th = (double)v * 3.14159265358979323846 / (double)V;
+        double c = cos(th), s = sin(th);
+        if (fabs(c) < 1e-12) { c = 0.0; s = s > 0 ? 1.0 : -1.0; }
+        if (fabs(s) < 1e-12) { s = 0.0; c = c > 0 ? 1.0 : -1.0; }
+        const double ac = fabs(c), as = fabs(s);
+        const double major = std::max(ac, as), minor = std::min(ac, as);
+        ViewGeo vg;
+        std::memset(&vg, 0, sizeof(vg));
+        vg.xdrive = as >= ac ? 1 : 0;
+        const double B = vg.xdrive ? -c / s : -s / c;
+        vg.step = B;
+        vg.stepq = to_q32(B);
+        vg.absstepq = vg.stepq < 0 ? -vg.stepq : vg.stepq;
+        vg.L = 1.0 / major;
+        vg.inv_minor = minor > 0.0 ? 1.0 / minor : 0.0;
+        vg.Lf = (float)vg.L;
+        vg.inv_minorf = (float)vg.inv_minor;
+        // backprojection: bin coordinate of the centre of pixel (ix, iy)
+        vg.t0 = ((0.5 - half) * c + (0.5 - half) * s) / rho + 0.5 * (NB - 1);
+        vg.cx = c / rho;
+        vg.cy = s / rho;
+        vg.h = (ac + as) / (2.0 * rho);
+        vg.t0q = to_q32(vg.t0);
+        vg.cxq = to_q32(vg.cx);
+        vg.cyq = to_q32(vg.cy);
+        vg.hq = to_q32(vg.h);
+        vg.axis = minor == 0.0 ? 1 : 0;
+        vg.wslope = minor > 0.0 ? rho / (major * minor) : 0.0;
+        vg.wslopef = (float)vg.wslope;
+        K = std::max(K, (int)floor(2.0 * vg.h) + 1);
+        views[u] = vg;
+        // forward walk: cross coordinate (grid units) at the start of driving step 0
+        const double a = vg.xdrive ? s : c;        // divisor
+        const double o = vg.xdrive ? c : s;        // other component
+        for (int b = 0; b < NB; ++b) {
+            const double r = ((double)b - 0.5 * (NB - 1)) * rho;
+            const double A0 = (r + half * o) / a + half;
+            const double LO0 = A0 + std::min(0.0, B);
+            const double aB = fabs(B);
+            double lower, upper;
+            if (B > 0) { lower = (-LO0 - aB) / B; upper = (N - LO0) / B; }
+            else if (B < 0) { lower = (LO0 - N) / aB; upper = (LO0 + aB) / aB; }
+            else {
+                lower = (LO0 >= -1.0 && LO0 < N + 1.0) ? 0.0 : 1e30;
+                upper = (LO0 >= -1.0 && LO0 < N + 1.0) ? N : -1e30;
+            }
+            long long dlo = (long long)floor(std::max(-1e9, lower)) - 1;
+            long long dhi = (long long)ceil(std::min(1e9, upper)) + 1;
+            dlo = std::max(0LL, dlo);
+            dhi = std::min((long long)N - 1, dhi);
+            RayGeo rg;
+            std::memset(&rg, 0, sizeof(rg));
+            if (dlo > dhi) { rg.d0 = 0; rg.nd = 0; }
+            else { rg.d0 = (int)dlo; rg.nd = (int)(dhi - dlo + 1); }
+            rg.lo = LO0 + rg.d0 * B;
+            rg.loq = to_q32(rg.lo);
+            rays[(size_t)u * NB + b] = rg;
+        }
+    }
+    g->dev.K = K;
+    return PET_OK;
+}
+
+static pet_status geometry_init(pet_geometry *g, cudaStream_t st)
+{
+    const pet_geometry_desc &d = g->desc;
+    std::vector<ViewGeo> views;
+    std::vector<RayGeo> rays;
+    PET_TRY(build_tables(g, views, rays));
+    GeoDev &gd = g->dev;
+    gd.N = d.n;
+    gd.P = d.nplanes;
+    gd.G = d.nplanes == 1 ? 1 : 8;
+    gd.Pp = (d.nplanes + gd.G - 1) / gd.G * gd.G;
+    gd.NG = gd.Pp / gd.G;
+    gd.V = d.nviews;
+    gd.NB = d.nbins;
+    gd.M = d.nsubsets;
+    gd.scale = d.sens * d.pixel_mm;
+    PET_CUDA(cudaMalloc(&g->d_views, sizeof(ViewGeo) * views.size()));
+    PET_CUDA(cudaMalloc(&g->d_rays, sizeof(RayGeo) * rays.size()));
+    PET_CUDA(cudaMalloc(&g->d_view_of_slot, sizeof(int) * g->view_of_slot.size()));
+    PET_CUDA(cudaMemcpyAsync(g->d_views, views.data(), sizeof(ViewGeo) * views.size(),
+                             cudaMemcpyHostToDevice, st));
+    PET_CUDA(cudaMemcpyAsync(g->d_rays, rays.data(), sizeof(RayGeo) * rays.size(),
+                             cudaMemcpyHostToDevice, st));
+    PET_CUDA(cudaMemcpyAsync(g->d_view_of_slot, g->view_of_slot.data(),
+                             sizeof(int) * g->view_of_slot.size(), cudaMemcpyHostToDevice, st));
+    gd.views = g->d_views;
+    gd.rays = g->d_rays;
+    const size_t npix = (size_t)d.n * d.n;
+    PET_CUDA(cudaMalloc(&g->d_p, sizeof(float) * npix));
+    PET_CUDA(cudaMalloc(&g->d_invp, sizeof(float) * npix));
+    PET_CUDA(cudaMalloc(&g->d_invp64, sizeof(double) * npix));
+    const int cap = 4096;
+    void *redmem = nullptr;
+    PET_CUDA(cudaMalloc(&redmem, reducer_bytes(cap, 4)));
+    PET_CUDA(cudaMemsetAsync(redmem, 0, reducer_bytes(cap, 4), st));
+    reducer_bind(g->red, redmem, cap, 4);
+    PET_CUDA(cudaMalloc(&g->d_sums, 16 * sizeof(double)));
+    // sensitivity: one FP64 backprojection of ones over all views, single plane
+    double *bp = nullptr;
+    PET_CUDA(cudaMalloc(&bp, sizeof(double) * npix));
+    BackArgs ba;
+    ba.g = gd;
+    ba.g.P = 1; ba.g.Pp = 1; ba.g.G = 1; ba.g.NG = 1;
+    ba.slot0 = 0;
+    ba.nviews = d.nviews;
+    ba.proj = nullptr;
+    ba.img = bp;
+    pet_status s = launch_back(ba, AR_FP64, st);
+    if (s == PET_OK) {
+        LaunchScope ls(PET_K_OTHER, st);
+        finish_sensitivity<<<(unsigned)((npix + 255) / 256), 256, 0, st>>>(
+            bp, (int)npix, d.nsubsets, g->d_p, g->d_invp, g->d_invp64);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) s = cuda_fail(e, "finish_sensitivity");
+    }
+    cudaError_t e = cudaStreamSynchronize(st);
+    cudaFree(bp);
+    if (s != PET_OK) return s;
+    if (e != cudaSuccess) return cuda_fail(e, "pet_geometry_create");
+    return PET_OK;
+}
+
+extern "C" pet_status pet_geometry_create(const pet_geometry_desc *desc, void *stream,
+                                          pet_geometry **out)
+{
+    if (!desc || !out) return fail(PET_ERR_INVALID, "pet_geometry_create: NULL argument");
+    *out = nullptr;
+    const pet_geometry_desc &d = *desc;
+    if (d.n < 1 || d.n > 8192 || d.nplanes < 1 || d.nviews < 1 || d.nbins < 1 ||
+        d.nsubsets < 1 || d.nsubsets > d.nviews || !(d.pixel_mm > 0) || !(d.bin_mm > 0) ||
+        !(d.sens > 0) || !std::isfinite(d.pixel_mm) || !std::isfinite(d.bin_mm) ||
+        !std::isfinite(d.sens))
+        return fail(PET_ERR_INVALID, "pet_geometry_create: invalid geometry description "
+                                     "(need n in [1,8192], nplanes, nviews, nbins >= 1, "
+                                     "1 <= nsubsets <= nviews, pixel_mm, bin_mm, sens > 0)");
+    if ((double)d.n * d.n * ((d.nplanes + 7) / 8 * 8) > 4.0e9 ||
+        (double)d.nviews * d.nbins * ((d.nplanes + 7) / 8 * 8) > 4.0e9)
+        return fail(PET_ERR_INVALID, "pet_geometry_create: problem too large (> 4e9 elements)");
+    pet_geometry *g = new pet_geometry();
+    g->desc = d;
+    pet_status s = geometry_init(g, as_stream(stream));
+    if (s != PET_OK) {
+        std::string msg = pet_last_error();
+        pet_geometry_destroy(g);
+        return fail(s, msg);
+    }
+    *out = g;
+    return PET_OK;
+}
+
+extern "C" void pet_geometry_destroy(pet_geometry *g)
+{
+    if (!g) return;
+    pet::workspace_free(g->workspace);
+    cudaFree(g->d_views);
+    cudaFree(g->d_rays);
+    cudaFree(g->d_view_of_slot);
+    cudaFree(g->d_p);
+    cudaFree(g->d_invp);
+    cudaFree(g->d_invp64);
+    cudaFree(g->d_scratch);
+    cudaFree(g->red.partials);
+    cudaFree(g->d_sums);
+    delete g;
+}
+
+extern "C" int pet_subset_size(const pet_geometry *g, int subset)
+{
+    if (!g || subset < 0 || subset >= g->desc.nsubsets) return -1;
+    return g->voff[subset + 1] - g->voff[subset];
+}
+
+extern "C" pet_status pet_sensitivity(const pet_geometry *g, float *d_p, void *stream)
+{
+    if (!g || !d_p) return fail(PET_ERR_INVALID, "pet_sensitivity: NULL argument");
+    PET_CUDA(cudaMemcpyAsync(d_p, g->d_p, sizeof(float) * g->desc.n * g->desc.n,
+                             cudaMemcpyDeviceToDevice, as_stream(stream)));
+    return PET_OK;
+}

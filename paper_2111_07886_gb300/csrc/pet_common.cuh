@@ -1,0 +1,181 @@
+// Internal definitions shared by the libpet CUDA sources (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/pet.h"
+
+namespace pet {
+
+// ------------------------------------------------------------------------------------------
+// Error handling: thread-local message, status codes, no exceptions across the ABI.
+// ------------------------------------------------------------------------------------------
+void set_error(const std::string &msg);
+pet_status fail(pet_status st, const std::string &msg);
+pet_status cuda_fail(cudaError_t e, const char *what);
+
+#define PET_CUDA(call)                                                       \
+    do {                                                                     \
+        cudaError_t e_ = (call);                                             \
+        if (e_ != cudaSuccess) return ::pet::cuda_fail(e_, #call);           \
+    } while (0)
+#define PET_TRY(call)                                                        \
+    do {                                                                     \
+        pet_status s_ = (call);                                              \
+        if (s_ != PET_OK) return s_;                                         \
+    } while (0)
+
+inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// ------------------------------------------------------------------------------------------
+// Geometry tables.  Positions are fixed point Q32.32 (int64) for the FP32 kernels, so that the
+// fractional position of a ray inside a pixel keeps 32 bits whatever the image size; the FP64
+// kernels use the double fields.  All values are computed in FP64 on the host.
+// ------------------------------------------------------------------------------------------
+struct ViewGeo {
+    // forward walk along the driving axis (x if |sin| >= |cos|, else y)
+    long long stepq;      // cross-coordinate change per driving step, Q32.32
+    long long absstepq;   // |stepq|
+    double step;          // same, double
+    double L;             // length per driving step = 1 / major, pixel units
+    double inv_minor;     // 1 / minor (0 when minor == 0)
+    float Lf, inv_minorf;
+    int xdrive;           // 1: driving index is ix (columns), cross index is iy
+    // backprojection footprint (bin units, measured from bin 0)
+    long long t0q, cxq, cyq, hq;   // t(ix,iy) = t0 + ix cx + iy cy; half-width h; Q32.32
+    double t0, cx, cy, h;
+    double wslope;        // length per bin unit of (h - |delta|): rho / (major * minor)
+    float wslopef;
+    int axis;             // minor == 0: half-open rule, length L for delta in [-h, h)
+};
+
+struct RayGeo {
+    long long loq;        // low cross coordinate of the first driving step, Q32.32 (grid units)
+    double lo;            // same, double
+    int d0, nd;           // driving range [d0, d0 + nd)
+};
+
+// Kernel-side view of a geometry.
+struct GeoDev {
+    int N, P, Pp, G, NG;      // image side, planes, padded planes, group size, groups
+    int V, NB, M, K;          // views, bins, subsets, max candidate bins per view in the gather
+    double scale;             // sens * pixel_mm
+    const ViewGeo *views;     // [V] in subset order
+    const RayGeo *rays;       // [V * NB] in subset order
+};
+
+struct Reducer {              // deterministic last-block reduction scratch
+    double *partials;         // [capacity * nvals]
+    unsigned int *ticket;     // one counter, returns to 0 after each launch
+    int capacity;
+};
+
+}  // namespace pet
+
+struct pet_geometry {
+    pet_geometry_desc desc;
+    pet::GeoDev dev;
+    std::vector<int> voff;          // subset view offsets (M + 1), views sorted by subset
+    std::vector<int> view_of_slot;  // original view index of each sorted slot
+    pet::ViewGeo *d_views = nullptr;
+    pet::RayGeo *d_rays = nullptr;
+    float *d_p = nullptr;           // p_j, FP32, [N*N]
+    float *d_invp = nullptr;        // 1 / p_j, FP32
+    double *d_invp64 = nullptr;     // 1 / p_j, FP64
+    int *d_view_of_slot = nullptr;
+    // scratch for the standalone projector / step calls (not thread-safe across streams)
+    void *d_scratch = nullptr;
+    size_t scratch_bytes = 0;
+    pet::Reducer red{};
+    double *d_sums = nullptr;       // small FP64 scalar area
+    void *workspace = nullptr;      // reconstruction workspace reused by pet_reconstruct*
+};
+
+namespace pet {
+
+// kernels implemented in project.cu / update.cu, launched from the host files
+struct FwdArgs {
+    GeoDev g;
+    int slot0;                 // first sorted view slot of the subset
+    int nviews;                // views in the subset
+    const void *img;           // [N*N][Pp] (float or double)
+    void *out;                 // [nviews*NB][Pp]: y, or w = 1 - counts/(y + gamma)
+    const int *counts;         // [nviews*NB][Pp] (ratio / objective modes)
+    const float *gamma;        // [nviews*NB][Pp]
+    Reducer red;               // objective mode
+    double *result;            // objective mode: 2 doubles (sum y, sum g ln(y + gamma))
+};
+
+enum FwdMode { FWD_PLAIN = 0, FWD_RATIO = 1, FWD_OBJECTIVE = 2 };
+enum Arith { AR_FP32 = 0, AR_KAHAN = 1, AR_FP64 = 2 };
+
+pet_status launch_forward(const FwdArgs &a, int mode, int arith, cudaStream_t st);
+
+struct BackArgs {
+    GeoDev g;
+    int slot0, nviews;
+    const void *proj;          // [nviews*NB][Pp]; NULL = ones (sensitivity)
+    void *img;                 // [N*N][Pp] out
+};
+pet_status launch_back(const BackArgs &a, int arith, cudaStream_t st);
+
+struct UpdateArgs {
+    GeoDev g;
+    int slot0, nviews;
+    const void *w;             // subset ratio term [nviews*NB][Pp]
+    const void *f;             // f^{k,i-1} [N*N][Pp]
+    void *fout;                // f^{k,i}
+    const void *invp;          // [N*N] (float or double)
+    void *nu_frozen;           // [N*N][Pp]
+    int nu_mode;               // 0: nu = 1, 1: from f, 2: from f and stored, 3: frozen
+    double lam_alpha;          // lambda_k alpha_{k,i}
+    double beta_over_M, gamma_r, eps, t, U, nu1, nu2;
+    const double *sum_f;       // sum of f^{k,i-1} (FP64, device)
+    const double *sum_mu;      // sum of mu (FP64, device)
+    double *sum_fout;          // sum of f^{k,i} (FP64, device, written)
+    Reducer red;
+};
+pet_status launch_update(const UpdateArgs &a, int arith, cudaStream_t st);
+
+struct ImageArgs {
+    GeoDev g;
+    const void *f;             // [N*N][Pp]
+    void *out;                 // per-kernel output
+    double gamma_r, eps, nu1, nu2;
+    const double *sum_f;       // mu pass / nu map: sum of f
+    const double *sum_mu;      // nu map: sum of mu
+    double *result;            // reductions
+    Reducer red;
+};
+pet_status launch_sum(const ImageArgs &a, int arith, cudaStream_t st);        // result[0] = sum f
+pet_status launch_mu_sum(const ImageArgs &a, int arith, cudaStream_t st);     // result[0] = sum mu
+pet_status launch_nu_map(const ImageArgs &a, int arith, cudaStream_t st);     // out = nu
+pet_status launch_rdp_grad(const ImageArgs &a, int arith, cudaStream_t st);   // out = grad R
+pet_status launch_rdp_value(const ImageArgs &a, int arith, cudaStream_t st);  // result[0] = R
+
+// layout conversions (layout.cu)
+pet_status to_internal_image(const GeoDev &g, const void *src, void *dst, int src_is_double,
+                             int dst_is_double, cudaStream_t st);
+pet_status from_internal_image(const GeoDev &g, const void *src, void *dst, int src_is_double,
+                               int dst_is_double, cudaStream_t st);
+pet_status to_internal_sino(const GeoDev &g, const int *d_view_of_slot, int slot0, int nviews,
+                            const void *src, void *dst, int elem, int src_is_subset,
+                            cudaStream_t st);
+pet_status from_internal_sino(const GeoDev &g, const int *d_view_of_slot, int nviews,
+                              const void *src, void *dst, int is_double, cudaStream_t st);
+pet_status validate_data(const GeoDev &g, const int *counts, const float *gamma, size_t n,
+                         int *d_flag, cudaStream_t st);
+
+void workspace_free(void *w);     // state.cu
+
+// geometry helpers (geometry.cu)
+pet_status geometry_scratch(const pet_geometry *g, size_t bytes, void **out);
+size_t reducer_bytes(int capacity, int nvals);
+void reducer_bind(Reducer &r, void *mem, int capacity, int nvals);
+
+}  // namespace pet

@@ -1,0 +1,24 @@
+// Launch accounting shared by the launch wrappers (see profile.cu).
+#pragma once
+
+#include "pet_common.cuh"
+
+namespace pet {
+
+// RAII scope around one kernel launch: counts it and, when profiling is on, brackets it with
+// CUDA events on its stream.
+class LaunchScope {
+public:
+    LaunchScope(int kind, cudaStream_t st);
+    ~LaunchScope();
+    LaunchScope(const LaunchScope &) = delete;
+    LaunchScope &operator=(const LaunchScope &) = delete;
+
+private:
+    int kind_;
+    cudaStream_t st_;
+    bool active_;
+    cudaEvent_t a_{}, b_{};
+};
+
+}  // namespace pet

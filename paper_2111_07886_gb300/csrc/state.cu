@@ -1,0 +1,620 @@
+// Reconstruction state and the SDP-BSREM subiteration (Table I), the whole-reconstruction
+// entry points, and the stand-alone projector / step calls of the C ABI.
+//
+// Per subiteration (k, i), J = kM + i, subset I_i:
+//   host FP64: lambda_k = lambda0 / (a k + 1) (Theorem 2); alpha_{k,i} (Eq.
+//     preconditioner:Nesterov or preconditioner:KM); the nu mode of Eq. nuki;
+//   [J0 < J <= J1] mu pass: sum of mu = max(0.01, grad(f)/mean(f)) in FP64 (Sec. III);
+//   forward + ratio: w = 1 - g_i / (A_i f + gamma_i) (App. A);
+//   fused update: f <- P_t(f - lambda_k alpha_{k,i} nu S(f) (A_i^T w + (beta/M) grad R(f)))
+//     with the FP64 sum of the new f (feeds mean(f) of the next mu pass).
+// Everything stays on the device; the scalars travel as kernel arguments.
+#include <math.h>
+
+#include <cstring>
+
+#include "pet_common.cuh"
+
+using namespace pet;
+
+struct pet_state {
+    const pet_geometry *g = nullptr;
+    pet_params prm{};
+    int arith = AR_KAHAN;
+    size_t esz = 4;                 // bytes per image / ratio element
+    void *f[2] = {nullptr, nullptr};
+    int cur = 0;
+    void *w = nullptr;              // ratio term of the largest subset
+    int *counts = nullptr;          // [V][NB][Pp], views sorted by subset
+    float *gamma = nullptr;
+    void *nu_frozen = nullptr;
+    bool have_frozen = false;
+    double *sums = nullptr;         // [0..1] sum f (ping-pong), [2] sum mu, [3..5] objective
+    double *objhist = nullptr;      // [(T+1) * 3] objective parts per outer iteration
+    int objcap = 0;
+    Reducer red{};
+    void *redmem = nullptr;
+    int *flag = nullptr;
+    int k = 0, i = 0, J = 0;        // next subiteration is (k, i+1) of the paper; J done
+    double tn = 1.0;                // Nesterov t_{k,i}
+    size_t q_bytes = 0, sino_elems = 0, w_bytes = 0;
+};
+
+static const int kRedCap = 4096;
+
+static pet_status check_params(const pet_params *p)
+{
+    if (!p) return fail(PET_ERR_INVALID, "pet_params is NULL");
+    if (p->iterations < 0 || !(p->beta >= 0) || !(p->gamma_r >= 0) || !(p->eps > 0) ||
+        !(p->U > 0) || !(p->t > 0) || !(p->t < p->U) || !(p->lambda0 > 0) || !(p->a >= 0) ||
+        !(p->nu1 > 0) || !(p->nu2 >= p->nu1) || p->precond < 0 || p->precond > 4 ||
+        p->precision < 0 || p->precision > 2 || !(p->delta1 > 0) || !(p->rho > 0) ||
+        !(p->delta2 > 0) || p->J0 < 0 || p->J1 < p->J0)
+        return fail(PET_ERR_INVALID,
+                    "invalid pet_params (need iterations >= 0, beta, gamma_r, a >= 0, eps, "
+                    "lambda0, rho, delta1, delta2 > 0, 0 < t < U, 0 < nu1 <= nu2, "
+                    "0 <= J0 <= J1, precond in 0..4, precision in 0..2)");
+    return PET_OK;
+}
+
+static void state_free(pet_state *s)
+{
+    if (!s) return;
+    cudaFree(s->f[0]);
+    cudaFree(s->f[1]);
+    cudaFree(s->w);
+    cudaFree(s->counts);
+    cudaFree(s->gamma);
+    cudaFree(s->nu_frozen);
+    cudaFree(s->sums);
+    cudaFree(s->objhist);
+    cudaFree(s->redmem);
+    cudaFree(s->flag);
+    s->f[0] = s->f[1] = s->w = s->nu_frozen = s->redmem = nullptr;
+    s->counts = nullptr;
+    s->gamma = nullptr;
+    s->sums = s->objhist = nullptr;
+    s->flag = nullptr;
+}
+
+// (Re)allocate the state's buffers for geometry g and arithmetic `arith` (no-op when they fit).
+static pet_status state_alloc(pet_state *s, const pet_geometry *g, int arith, int iterations)
+{
+    const GeoDev &gd = g->dev;
+    const size_t esz = arith == AR_FP64 ? 8 : 4;
+    const size_t q_bytes = (size_t)gd.N * gd.N * gd.Pp * esz;
+    int maxv = 0;
+    for (int i = 0; i < gd.M; ++i) maxv = std::max(maxv, g->voff[i + 1] - g->voff[i]);
+    const size_t w_bytes = (size_t)maxv * gd.NB * gd.Pp * esz;
+    const size_t sino = (size_t)gd.V * gd.NB * gd.Pp;
+    if (s->g == g && s->esz == esz && s->f[0] && s->objcap >= iterations + 1) {
+        s->arith = arith;
+        return PET_OK;
+    }
+    state_free(s);
+    s->g = g;
+    s->esz = esz;
+    s->arith = arith;
+    s->q_bytes = q_bytes;
+    s->w_bytes = w_bytes;
+    s->sino_elems = sino;
+    PET_CUDA(cudaMalloc(&s->f[0], q_bytes));
+    PET_CUDA(cudaMalloc(&s->f[1], q_bytes));
+    PET_CUDA(cudaMalloc(&s->w, w_bytes));
+    PET_CUDA(cudaMalloc(&s->counts, sino * sizeof(int)));
+    PET_CUDA(cudaMalloc(&s->gamma, sino * sizeof(float)));
+    PET_CUDA(cudaMalloc(&s->nu_frozen, q_bytes));
+    PET_CUDA(cudaMalloc(&s->sums, 16 * sizeof(double)));
+    s->objcap = std::max(iterations + 1, 1);
+    PET_CUDA(cudaMalloc(&s->objhist, (size_t)s->objcap * 3 * sizeof(double)));
+    PET_CUDA(cudaMalloc(&s->redmem, reducer_bytes(kRedCap, 2)));
+    PET_CUDA(cudaMemset(s->redmem, 0, reducer_bytes(kRedCap, 2)));
+    reducer_bind(s->red, s->redmem, kRedCap, 2);
+    PET_CUDA(cudaMalloc(&s->flag, sizeof(int)));
+    return PET_OK;
+}
+
+static pet_status state_sum_f(pet_state *s, cudaStream_t st)
+{
+    ImageArgs a{};
+    a.g = s->g->dev;
+    a.f = s->f[s->cur];
+    a.result = s->sums + s->cur;
+    a.red = s->red;
+    return launch_sum(a, s->arith, st);
+}
+
+// Load data (counts, gamma: [P][V][NB], device) and f^0 ([P][N][N] float, device) into an
+// allocated state and reset the schedule to (k, i) = (0, 1).  Validates the data (synchronises).
+static pet_status state_load(pet_state *s, const int32_t *d_counts, const float *d_gamma,
+                             const pet_params *p, const float *d_img, cudaStream_t st,
+                             bool validate)
+{
+    const pet_geometry *g = s->g;
+    const GeoDev &gd = g->dev;
+    s->prm = *p;
+    if (validate) {
+        const size_t n = (size_t)gd.P * gd.V * gd.NB;
+        PET_TRY(validate_data(gd, d_counts, d_gamma, n, s->flag, st));
+        int h = 0;
+        PET_CUDA(cudaMemcpyAsync(&h, s->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+        PET_CUDA(cudaStreamSynchronize(st));
+        if (h) return fail(PET_ERR_INVALID, "data check failed: need counts >= 0 and 0 < gamma < inf");
+    }
+    PET_TRY(to_internal_sino(gd, g->d_view_of_slot, 0, gd.V, d_counts, s->counts, 0, 0, st));
+    PET_TRY(to_internal_sino(gd, g->d_view_of_slot, 0, gd.V, d_gamma, s->gamma, 1, 0, st));
+    s->cur = 0;
+    PET_TRY(to_internal_image(gd, d_img, s->f[0], 0, s->arith == AR_FP64, st));
+    s->k = s->i = s->J = 0;
+    s->tn = 1.0;
+    s->have_frozen = false;
+    return state_sum_f(s, st);
+}
+
+static pet_status state_subiter(pet_state *s, cudaStream_t st)
+{
+    const pet_geometry *g = s->g;
+    const GeoDev &gd = g->dev;
+    const pet_params &p = s->prm;
+    const int M = gd.M;
+    const int J = s->k * M + s->i + 1;                 // J_{k,i} = kM + i (1-based i)
+    const double lam = p.lambda0 / (p.a * s->k + 1.0);
+    double alpha = 1.0;
+    if (p.precond == PET_PRECOND_M1 || p.precond == PET_PRECOND_P1) {
+        const double tn1 = 0.5 * (1.0 + sqrt(1.0 + 4.0 * s->tn * s->tn));
+        alpha = 1.0 + (s->tn - 1.0) / tn1;
+        s->tn = tn1;
+    } else if (p.precond == PET_PRECOND_M2 || p.precond == PET_PRECOND_P2) {
+        alpha = (p.rho * (J - 1) + p.delta2) / ((double)(J - 1) + p.delta1);
+    }
+    const bool use_nu = p.precond == PET_PRECOND_P1 || p.precond == PET_PRECOND_P2;
+    int nu_mode = 0;
+    if (use_nu && J > p.J0) {
+        if (J <= p.J1) nu_mode = (J == p.J1) ? 2 : 1;
+        else nu_mode = s->have_frozen ? 3 : 0;
+    }
+    const int slot0 = g->voff[s->i], nv = g->voff[s->i + 1] - g->voff[s->i];
+    if (nu_mode == 1 || nu_mode == 2) {
+        ImageArgs a{};
+        a.g = gd;
+        a.f = s->f[s->cur];
+        a.sum_f = s->sums + s->cur;
+        a.result = s->sums + 2;
+        a.red = s->red;
+        PET_TRY(launch_mu_sum(a, s->arith, st));
+    }
+    FwdArgs fa{};
+    fa.g = gd;
+    fa.slot0 = slot0;
+    fa.nviews = nv;
+    fa.img = s->f[s->cur];
+    fa.out = s->w;
+    fa.counts = s->counts + (size_t)slot0 * gd.NB * gd.Pp;
+    fa.gamma = s->gamma + (size_t)slot0 * gd.NB * gd.Pp;
+    PET_TRY(launch_forward(fa, FWD_RATIO, s->arith, st));
+    UpdateArgs ua{};
+    ua.g = gd;
+    ua.slot0 = slot0;
+    ua.nviews = nv;
+    ua.w = s->w;
+    ua.f = s->f[s->cur];
+    ua.fout = s->f[1 - s->cur];
+    ua.invp = s->arith == AR_FP64 ? (const void *)g->d_invp64 : (const void *)g->d_invp;
+    ua.nu_frozen = s->nu_frozen;
+    ua.nu_mode = nu_mode;
+    ua.lam_alpha = lam * alpha;
+    ua.beta_over_M = p.beta / M;
+    ua.gamma_r = p.gamma_r;
+    ua.eps = p.eps;
+    ua.t = p.t;
+    ua.U = p.U;
+    ua.nu1 = p.nu1;
+    ua.nu2 = p.nu2;
+    ua.sum_f = s->sums + s->cur;
+    ua.sum_mu = s->sums + 2;
+    ua.sum_fout = s->sums + (1 - s->cur);
+    ua.red = s->red;
+    PET_TRY(launch_update(ua, s->arith, st));
+    if (nu_mode == 2) s->have_frozen = true;
+    s->cur ^= 1;
+    s->J = J;
+    if (++s->i == M) { s->i = 0; ++s->k; }
+    return PET_OK;
+}
+
+// Objective parts of the current f into out3 (device): sum(Af), sum(g ln(Af+gamma)), R(f).
+static pet_status state_objective_async(pet_state *s, double *out3, cudaStream_t st)
+{
+    const GeoDev &gd = s->g->dev;
+    FwdArgs fa{};
+    fa.g = gd;
+    fa.slot0 = 0;
+    fa.nviews = gd.V;
+    fa.img = s->f[s->cur];
+    fa.counts = s->counts;
+    fa.gamma = s->gamma;
+    fa.red = s->red;
+    fa.result = out3;
+    PET_TRY(launch_forward(fa, FWD_OBJECTIVE, s->arith, st));
+    ImageArgs a{};
+    a.g = gd;
+    a.f = s->f[s->cur];
+    a.gamma_r = s->prm.gamma_r;
+    a.eps = s->prm.eps;
+    a.result = out3 + 2;
+    a.red = s->red;
+    return launch_rdp_value(a, s->arith, st);
+}
+
+static int arith_of(int precision)
+{
+    return precision == PET_PREC_FP64 ? AR_FP64 : (precision == PET_PREC_FP32 ? AR_FP32 : AR_KAHAN);
+}
+
+extern "C" pet_status pet_state_create(const pet_geometry *g, const int32_t *d_counts,
+                                       const float *d_gamma, const pet_params *params,
+                                       const float *d_img_init, void *stream, pet_state **out)
+{
+    if (!g || !d_counts || !d_gamma || !d_img_init || !out)
+        return fail(PET_ERR_INVALID, "pet_state_create: NULL argument");
+    *out = nullptr;
+    PET_TRY(check_params(params));
+    cudaStream_t st = as_stream(stream);
+    pet_state *s = new pet_state();
+    pet_status r = state_alloc(s, g, arith_of(params->precision), params->iterations);
+    if (r == PET_OK) r = state_load(s, d_counts, d_gamma, params, d_img_init, st, true);
+    if (r == PET_OK) {
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) r = cuda_fail(e, "pet_state_create");
+    }
+    if (r != PET_OK) {
+        std::string msg = pet_last_error();
+        state_free(s);
+        delete s;
+        return fail(r, msg);
+    }
+    *out = s;
+    return PET_OK;
+}
+
+extern "C" pet_status pet_subiter(pet_state *s, void *stream)
+{
+    if (!s) return fail(PET_ERR_INVALID, "pet_subiter: NULL state");
+    return state_subiter(s, as_stream(stream));
+}
+
+extern "C" pet_status pet_state_read_image(const pet_state *s, float *d_img, void *stream)
+{
+    if (!s || !d_img) return fail(PET_ERR_INVALID, "pet_state_read_image: NULL argument");
+    return from_internal_image(s->g->dev, s->f[s->cur], d_img, s->arith == AR_FP64, 0,
+                               as_stream(stream));
+}
+
+extern "C" pet_status pet_state_objective(pet_state *s, double *h_phi, double *h_parts,
+                                         void *stream)
+{
+    if (!s || !h_phi) return fail(PET_ERR_INVALID, "pet_state_objective: NULL argument");
+    cudaStream_t st = as_stream(stream);
+    PET_TRY(state_objective_async(s, s->sums + 3, st));
+    double h[3];
+    PET_CUDA(cudaMemcpyAsync(h, s->sums + 3, sizeof(h), cudaMemcpyDeviceToHost, st));
+    PET_CUDA(cudaStreamSynchronize(st));
+    *h_phi = h[0] - h[1] + s->prm.beta * h[2];
+    if (h_parts) { h_parts[0] = h[0]; h_parts[1] = h[1]; h_parts[2] = h[2]; }
+    return PET_OK;
+}
+
+extern "C" int pet_state_subiters(const pet_state *s) { return s ? s->J : -1; }
+
+extern "C" void pet_state_destroy(pet_state *s)
+{
+    if (!s) return;
+    state_free(s);
+    delete s;
+}
+
+// Whole reconstruction on an allocated state: T outer iterations, objective history on device.
+static pet_status run_reconstruct(pet_state *s, double *h_objective, cudaStream_t st)
+{
+    const int T = s->prm.iterations, M = s->g->dev.M;
+    if (h_objective) PET_TRY(state_objective_async(s, s->objhist, st));
+    for (int k = 0; k < T; ++k) {
+        for (int i = 0; i < M; ++i) PET_TRY(state_subiter(s, st));
+        if (h_objective) PET_TRY(state_objective_async(s, s->objhist + 3 * (k + 1), st));
+    }
+    return PET_OK;
+}
+
+static pet_status finish_objective(pet_state *s, double *h_objective, cudaStream_t st)
+{
+    if (!h_objective) return PET_OK;
+    const int T = s->prm.iterations;
+    std::vector<double> h((size_t)(T + 1) * 3);
+    PET_CUDA(cudaMemcpyAsync(h.data(), s->objhist, h.size() * sizeof(double),
+                             cudaMemcpyDeviceToHost, st));
+    PET_CUDA(cudaStreamSynchronize(st));
+    for (int k = 0; k <= T; ++k)
+        h_objective[k] = h[3 * k] - h[3 * k + 1] + s->prm.beta * h[3 * k + 2];
+    return PET_OK;
+}
+
+// The reconstruction entry points keep one workspace per geometry (allocated on first use and
+// reused), so repeated calls do not allocate.  Calls on one geometry must not overlap.
+struct GeoWorkspace {
+    pet_state st;
+    int32_t *counts = nullptr;      // host-entry staging
+    float *gamma = nullptr;
+    float *img = nullptr;
+    size_t cap_counts = 0, cap_img = 0;
+};
+
+static GeoWorkspace *workspace_of(const pet_geometry *g)
+{
+    pet_geometry *gm = const_cast<pet_geometry *>(g);
+    if (!gm->workspace) gm->workspace = new GeoWorkspace();
+    return reinterpret_cast<GeoWorkspace *>(gm->workspace);
+}
+
+namespace pet {
+void workspace_free(void *w)
+{
+    GeoWorkspace *ws = reinterpret_cast<GeoWorkspace *>(w);
+    if (!ws) return;
+    state_free(&ws->st);
+    cudaFree(ws->counts);
+    cudaFree(ws->gamma);
+    cudaFree(ws->img);
+    delete ws;
+}
+}  // namespace pet
+
+extern "C" pet_status pet_reconstruct(const pet_geometry *g, const int32_t *d_counts,
+                                      const float *d_gamma, const pet_params *params,
+                                      float *d_img_inout, double *h_objective, void *stream)
+{
+    if (!g || !d_counts || !d_gamma || !d_img_inout)
+        return fail(PET_ERR_INVALID, "pet_reconstruct: NULL argument");
+    PET_TRY(check_params(params));
+    cudaStream_t st = as_stream(stream);
+    GeoWorkspace *ws = workspace_of(g);
+    pet_state *s = &ws->st;
+    PET_TRY(state_alloc(s, g, arith_of(params->precision), params->iterations));
+    PET_TRY(state_load(s, d_counts, d_gamma, params, d_img_inout, st, true));
+    PET_TRY(run_reconstruct(s, h_objective, st));
+    PET_TRY(from_internal_image(g->dev, s->f[s->cur], d_img_inout, s->arith == AR_FP64, 0, st));
+    PET_TRY(finish_objective(s, h_objective, st));
+    PET_CUDA(cudaStreamSynchronize(st));
+    return PET_OK;
+}
+
+extern "C" pet_status pet_reconstruct_host(const pet_geometry *g, const int32_t *h_counts,
+                                           const float *h_gamma, const pet_params *params,
+                                           float *h_img_inout, double *h_objective, void *stream)
+{
+    if (!g || !h_counts || !h_gamma || !h_img_inout)
+        return fail(PET_ERR_INVALID, "pet_reconstruct_host: NULL argument");
+    PET_TRY(check_params(params));
+    cudaStream_t st = as_stream(stream);
+    GeoWorkspace *ws = workspace_of(g);
+    const GeoDev &gd = g->dev;
+    const size_t nsino = (size_t)gd.P * gd.V * gd.NB, nimg = (size_t)gd.P * gd.N * gd.N;
+    if (ws->cap_counts < nsino) {
+        cudaFree(ws->counts);
+        cudaFree(ws->gamma);
+        ws->counts = nullptr;
+        ws->gamma = nullptr;
+        ws->cap_counts = 0;
+        PET_CUDA(cudaMalloc(&ws->counts, nsino * sizeof(int32_t)));
+        PET_CUDA(cudaMalloc(&ws->gamma, nsino * sizeof(float)));
+        ws->cap_counts = nsino;
+    }
+    if (ws->cap_img < nimg) {
+        cudaFree(ws->img);
+        ws->img = nullptr;
+        ws->cap_img = 0;
+        PET_CUDA(cudaMalloc(&ws->img, nimg * sizeof(float)));
+        ws->cap_img = nimg;
+    }
+    PET_CUDA(cudaMemcpyAsync(ws->counts, h_counts, nsino * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    PET_CUDA(cudaMemcpyAsync(ws->gamma, h_gamma, nsino * sizeof(float), cudaMemcpyHostToDevice, st));
+    PET_CUDA(cudaMemcpyAsync(ws->img, h_img_inout, nimg * sizeof(float), cudaMemcpyHostToDevice, st));
+    pet_state *s = &ws->st;
+    PET_TRY(state_alloc(s, g, arith_of(params->precision), params->iterations));
+    PET_TRY(state_load(s, ws->counts, ws->gamma, params, ws->img, st, true));
+    PET_TRY(run_reconstruct(s, h_objective, st));
+    PET_TRY(from_internal_image(gd, s->f[s->cur], ws->img, s->arith == AR_FP64, 0, st));
+    PET_CUDA(cudaMemcpyAsync(h_img_inout, ws->img, nimg * sizeof(float), cudaMemcpyDeviceToHost, st));
+    PET_TRY(finish_objective(s, h_objective, st));
+    PET_CUDA(cudaStreamSynchronize(st));
+    return PET_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Stand-alone projectors and steps (geometry scratch: calls on one geometry must not overlap)
+// ------------------------------------------------------------------------------------------
+static pet_status subset_range(const pet_geometry *g, int subset, int *slot0, int *nv)
+{
+    if (subset == -1) { *slot0 = 0; *nv = g->desc.nviews; return PET_OK; }
+    if (subset < 0 || subset >= g->desc.nsubsets)
+        return fail(PET_ERR_INVALID, "subset index out of range (need -1 or 0 <= subset < M)");
+    *slot0 = g->voff[subset];
+    *nv = g->voff[subset + 1] - g->voff[subset];
+    return PET_OK;
+}
+
+static pet_status forward_any(const pet_geometry *g, int subset, const void *d_img, void *d_proj,
+                              int is_double, void *stream)
+{
+    if (!g || !d_img || !d_proj) return fail(PET_ERR_INVALID, "forward projection: NULL argument");
+    int slot0, nv;
+    PET_TRY(subset_range(g, subset, &slot0, &nv));
+    cudaStream_t st = as_stream(stream);
+    const GeoDev &gd = g->dev;
+    const size_t esz = is_double ? 8 : 4;
+    const size_t qb = (size_t)gd.N * gd.N * gd.Pp * esz, pb = (size_t)nv * gd.NB * gd.Pp * esz;
+    void *scr = nullptr;
+    PET_TRY(geometry_scratch(g, qb + pb + 256, &scr));
+    void *img_i = scr, *proj_i = reinterpret_cast<char *>(scr) + ((qb + 255) / 256) * 256;
+    PET_TRY(to_internal_image(gd, d_img, img_i, is_double, is_double, st));
+    FwdArgs fa{};
+    fa.g = gd;
+    fa.slot0 = slot0;
+    fa.nviews = nv;
+    fa.img = img_i;
+    fa.out = proj_i;
+    PET_TRY(launch_forward(fa, FWD_PLAIN, is_double ? AR_FP64 : AR_KAHAN, st));
+    return from_internal_sino(gd, subset == -1 ? g->d_view_of_slot : nullptr, nv, proj_i, d_proj,
+                              is_double, st);
+}
+
+static pet_status back_any(const pet_geometry *g, int subset, const void *d_proj, void *d_img,
+                           int is_double, void *stream)
+{
+    if (!g || !d_img || !d_proj) return fail(PET_ERR_INVALID, "backprojection: NULL argument");
+    int slot0, nv;
+    PET_TRY(subset_range(g, subset, &slot0, &nv));
+    cudaStream_t st = as_stream(stream);
+    const GeoDev &gd = g->dev;
+    const size_t esz = is_double ? 8 : 4;
+    const size_t qb = (size_t)gd.N * gd.N * gd.Pp * esz, pb = (size_t)nv * gd.NB * gd.Pp * esz;
+    void *scr = nullptr;
+    PET_TRY(geometry_scratch(g, qb + pb + 256, &scr));
+    void *img_i = scr, *proj_i = reinterpret_cast<char *>(scr) + ((qb + 255) / 256) * 256;
+    PET_TRY(to_internal_sino(gd, g->d_view_of_slot, slot0, nv, d_proj, proj_i, is_double ? 3 : 2,
+                             subset == -1 ? 0 : 1, st));
+    BackArgs ba{};
+    ba.g = gd;
+    ba.slot0 = slot0;
+    ba.nviews = nv;
+    ba.proj = proj_i;
+    ba.img = img_i;
+    PET_TRY(launch_back(ba, is_double ? AR_FP64 : AR_KAHAN, st));
+    return from_internal_image(gd, img_i, d_img, is_double, is_double, st);
+}
+
+extern "C" pet_status pet_forward_subset(const pet_geometry *g, int subset, const float *d_img,
+                                         float *d_proj, void *stream)
+{
+    return forward_any(g, subset, d_img, d_proj, 0, stream);
+}
+
+extern "C" pet_status pet_back_subset(const pet_geometry *g, int subset, const float *d_proj,
+                                      float *d_img, void *stream)
+{
+    return back_any(g, subset, d_proj, d_img, 0, stream);
+}
+
+extern "C" pet_status pet_forward_subset_f64(const pet_geometry *g, int subset,
+                                             const double *d_img, double *d_proj, void *stream)
+{
+    return forward_any(g, subset, d_img, d_proj, 1, stream);
+}
+
+extern "C" pet_status pet_back_subset_f64(const pet_geometry *g, int subset, const double *d_proj,
+                                          double *d_img, void *stream)
+{
+    return back_any(g, subset, d_proj, d_img, 1, stream);
+}
+
+// image -> internal image in geometry scratch (two internal images of room)
+static pet_status stage_image(const pet_geometry *g, const float *d_img, void **img_i,
+                              void **out_i, cudaStream_t st)
+{
+    const GeoDev &gd = g->dev;
+    const size_t qb = ((size_t)gd.N * gd.N * gd.Pp * 4 + 255) / 256 * 256;
+    void *scr = nullptr;
+    PET_TRY(geometry_scratch(g, 2 * qb, &scr));
+    *img_i = scr;
+    *out_i = reinterpret_cast<char *>(scr) + qb;
+    return to_internal_image(gd, d_img, *img_i, 0, 0, st);
+}
+
+extern "C" pet_status pet_rdp_gradient(const pet_geometry *g, const float *d_img, double gamma_r,
+                                       double eps, float *d_grad, void *stream)
+{
+    if (!g || !d_img || !d_grad) return fail(PET_ERR_INVALID, "pet_rdp_gradient: NULL argument");
+    cudaStream_t st = as_stream(stream);
+    void *img_i, *out_i;
+    PET_TRY(stage_image(g, d_img, &img_i, &out_i, st));
+    ImageArgs a{};
+    a.g = g->dev;
+    a.f = img_i;
+    a.out = out_i;
+    a.gamma_r = gamma_r;
+    a.eps = eps;
+    a.red = g->red;
+    PET_TRY(launch_rdp_grad(a, AR_FP32, st));
+    return from_internal_image(g->dev, out_i, d_grad, 0, 0, st);
+}
+
+extern "C" pet_status pet_smoothness_nu(const pet_geometry *g, const float *d_img, double nu1,
+                                        double nu2, float *d_nu, void *stream)
+{
+    if (!g || !d_img || !d_nu) return fail(PET_ERR_INVALID, "pet_smoothness_nu: NULL argument");
+    if (!(nu1 > 0) || !(nu2 >= nu1)) return fail(PET_ERR_INVALID, "pet_smoothness_nu: need 0 < nu1 <= nu2");
+    cudaStream_t st = as_stream(stream);
+    void *img_i, *out_i;
+    PET_TRY(stage_image(g, d_img, &img_i, &out_i, st));
+    ImageArgs a{};
+    a.g = g->dev;
+    a.f = img_i;
+    a.out = out_i;
+    a.nu1 = nu1;
+    a.nu2 = nu2;
+    a.red = g->red;
+    a.result = g->d_sums;
+    PET_TRY(launch_sum(a, AR_FP32, st));                  // d_sums[0] = sum f
+    a.sum_f = g->d_sums;
+    a.result = g->d_sums + 1;
+    PET_TRY(launch_mu_sum(a, AR_FP32, st));               // d_sums[1] = sum mu
+    a.sum_mu = g->d_sums + 1;
+    PET_TRY(launch_nu_map(a, AR_FP32, st));
+    return from_internal_image(g->dev, out_i, d_nu, 0, 0, st);
+}
+
+extern "C" pet_status pet_objective(const pet_geometry *g, const int32_t *d_counts,
+                                    const float *d_gamma, const float *d_img, double beta,
+                                    double gamma_r, double eps, double *h_phi, double *h_parts,
+                                    void *stream)
+{
+    if (!g || !d_counts || !d_gamma || !d_img || !h_phi)
+        return fail(PET_ERR_INVALID, "pet_objective: NULL argument");
+    cudaStream_t st = as_stream(stream);
+    const GeoDev &gd = g->dev;
+    const size_t qb = ((size_t)gd.N * gd.N * gd.Pp * 4 + 255) / 256 * 256;
+    const size_t sino = (size_t)gd.V * gd.NB * gd.Pp;
+    const size_t sb = (sino * 4 + 255) / 256 * 256;
+    void *scr = nullptr;
+    PET_TRY(geometry_scratch(g, qb + 2 * sb, &scr));
+    char *base = reinterpret_cast<char *>(scr);
+    void *img_i = base;
+    int *cnt_i = reinterpret_cast<int *>(base + qb);
+    float *gam_i = reinterpret_cast<float *>(base + qb + sb);
+    PET_TRY(to_internal_image(gd, d_img, img_i, 0, 0, st));
+    PET_TRY(to_internal_sino(gd, g->d_view_of_slot, 0, gd.V, d_counts, cnt_i, 0, 0, st));
+    PET_TRY(to_internal_sino(gd, g->d_view_of_slot, 0, gd.V, d_gamma, gam_i, 1, 0, st));
+    FwdArgs fa{};
+    fa.g = gd;
+    fa.slot0 = 0;
+    fa.nviews = gd.V;
+    fa.img = img_i;
+    fa.counts = cnt_i;
+    fa.gamma = gam_i;
+    fa.red = g->red;
+    fa.result = g->d_sums + 4;
+    PET_TRY(launch_forward(fa, FWD_OBJECTIVE, AR_KAHAN, st));
+    ImageArgs a{};
+    a.g = gd;
+    a.f = img_i;
+    a.gamma_r = gamma_r;
+    a.eps = eps;
+    a.red = g->red;
+    a.result = g->d_sums + 6;
+    PET_TRY(launch_rdp_value(a, AR_FP32, st));
+    double h[3];
+    PET_CUDA(cudaMemcpyAsync(h, g->d_sums + 4, sizeof(h), cudaMemcpyDeviceToHost, st));
+    PET_CUDA(cudaStreamSynchronize(st));
+    *h_phi = h[0] - h[1] + beta * h[2];
+    if (h_parts) { h_parts[0] = h[0]; h_parts[1] = h[1]; h_parts[2] = h[2]; }
+    return PET_OK;
+}

@@ -1,0 +1,265 @@
+"""Thin ctypes binding of libpet (declared in include/pet.h).
+
+Argument marshalling only: every function forwards torch tensors' device pointers (or numpy
+host buffers) to the C ABI of the same name, and raises ``PetError`` on a non-OK status.  All
+computation happens in the CUDA library; there is no fallback: if ``libpet.so`` is missing
+or cannot be loaded, importing a function raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpet.so")
+_lock = threading.Lock()
+_lib = None
+
+OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, PENDING, ERR_NOT_FOUND = range(7)
+PRECOND = dict(BSREM=0, M1=1, M2=2, P1=3, P2=4)
+PREC_FP32, PREC_FP32_KAHAN, PREC_FP64 = 0, 1, 2
+
+
+class PetError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"libpet status {status}: {msg}")
+        self.status = status
+
+
+class GeometryDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("nplanes", ctypes.c_int), ("pixel_mm", ctypes.c_double),
+                ("nviews", ctypes.c_int), ("nbins", ctypes.c_int), ("bin_mm", ctypes.c_double),
+                ("nsubsets", ctypes.c_int), ("sens", ctypes.c_double)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int)] + [
+        (k, ctypes.c_double) for k in ("beta", "gamma_r", "eps", "t", "U", "lambda0", "a",
+                                       "rho", "delta1", "delta2", "nu1", "nu2")] + [
+        ("J0", ctypes.c_int), ("J1", ctypes.c_int), ("precond", ctypes.c_int),
+        ("precision", ctypes.c_int)]
+
+
+_VP = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_DP = ctypes.POINTER(ctypes.c_double)
+
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "pet_last_error": (ctypes.c_char_p, []),
+    "pet_geometry_create": (_I, [ctypes.POINTER(GeometryDesc), _VP, ctypes.POINTER(_VP)]),
+    "pet_geometry_destroy": (None, [_VP]),
+    "pet_subset_size": (_I, [_VP, _I]),
+    "pet_sensitivity": (_I, [_VP, _VP, _VP]),
+    "pet_forward_subset": (_I, [_VP, _I, _VP, _VP, _VP]),
+    "pet_back_subset": (_I, [_VP, _I, _VP, _VP, _VP]),
+    "pet_forward_subset_f64": (_I, [_VP, _I, _VP, _VP, _VP]),
+    "pet_back_subset_f64": (_I, [_VP, _I, _VP, _VP, _VP]),
+    "pet_state_create": (_I, [_VP, _VP, _VP, ctypes.POINTER(Params), _VP, _VP, ctypes.POINTER(_VP)]),
+    "pet_subiter": (_I, [_VP, _VP]),
+    "pet_state_read_image": (_I, [_VP, _VP, _VP]),
+    "pet_state_objective": (_I, [_VP, _DP, _DP, _VP]),
+    "pet_state_subiters": (_I, [_VP]),
+    "pet_state_destroy": (None, [_VP]),
+    "pet_reconstruct": (_I, [_VP, _VP, _VP, ctypes.POINTER(Params), _VP, _DP, _VP]),
+    "pet_reconstruct_host": (_I, [_VP, _VP, _VP, ctypes.POINTER(Params), _VP, _DP, _VP]),
+    "pet_rdp_gradient": (_I, [_VP, _VP, _D, _D, _VP, _VP]),
+    "pet_smoothness_nu": (_I, [_VP, _VP, _D, _D, _VP, _VP]),
+    "pet_objective": (_I, [_VP, _VP, _VP, _VP, _D, _D, _D, _DP, _DP, _VP]),
+    "pet_launch_count": (ctypes.c_longlong, []),
+    "pet_profile_enable": (None, [_I]),
+    "pet_profile_read": (_I, [_I, _DP, ctypes.POINTER(ctypes.c_longlong)]),
+    "pet_profile_reset": (None, []),
+}
+
+KERNEL_KINDS = ["forward_ratio", "update", "mu_sum", "obj_forward", "rdp_value", "layout", "other"]
+
+
+def lib():
+    """Load libpet.so (built by ``__graft_entry__.build()``); raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise PetError(ERR_CUDA, f"{LIB_PATH} is not built; run __graft_entry__.build()")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != OK:
+        raise PetError(status, lib().pet_last_error().decode())
+
+
+def _ptr(t) -> int | None:
+    """Device pointer of a torch tensor (contiguous), host pointer of a numpy array."""
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        assert t.is_contiguous(), "tensors passed to libpet must be contiguous"
+        return t.data_ptr()
+    assert t.flags["C_CONTIGUOUS"], "arrays passed to libpet must be C-contiguous"
+    return t.ctypes.data
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def make_params(p, precision: int | None = None) -> Params:
+    """Params from an object with AlgoParams attribute names."""
+    return Params(p.iterations, p.beta, p.gamma_r, p.eps, p.t, p.U, p.lambda0, p.a, p.rho,
+                  p.delta1, p.delta2, p.nu1, p.nu2, p.J0, p.J1, p.precond,
+                  p.precision if precision is None else precision)
+
+
+class Geometry:
+    """pet_geometry handle (Sec. II-A/B geometry, subsets, sensitivity)."""
+
+    def __init__(self, n, nplanes, pixel_mm, nviews, nbins, bin_mm, nsubsets, sens, stream=None):
+        self.desc = GeometryDesc(n, nplanes, pixel_mm, nviews, nbins, bin_mm, nsubsets, sens)
+        h = _VP()
+        _check(lib().pet_geometry_create(ctypes.byref(self.desc), _stream(stream), ctypes.byref(h)))
+        self.handle = h
+        self.n, self.nplanes, self.nviews, self.nbins, self.nsubsets = n, nplanes, nviews, nbins, nsubsets
+
+    @classmethod
+    def from_dict(cls, geometry: dict, sens: float, stream=None):
+        g = geometry
+        return cls(g["n"], g["nplanes"], g["pixel_mm"], g["nviews"], g["nbins"], g["bin_mm"],
+                   g["nsubsets"], sens, stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().pet_geometry_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def subset_size(self, subset: int) -> int:
+        return lib().pet_subset_size(self.handle, subset)
+
+
+def sensitivity(g: Geometry, d_p, stream=None):
+    _check(lib().pet_sensitivity(g.handle, _ptr(d_p), _stream(stream)))
+
+
+def forward_subset(g: Geometry, subset: int, d_img, d_proj, stream=None):
+    fn = lib().pet_forward_subset_f64 if str(d_img.dtype) == "torch.float64" else lib().pet_forward_subset
+    _check(fn(g.handle, subset, _ptr(d_img), _ptr(d_proj), _stream(stream)))
+
+
+def back_subset(g: Geometry, subset: int, d_proj, d_img, stream=None):
+    fn = lib().pet_back_subset_f64 if str(d_proj.dtype) == "torch.float64" else lib().pet_back_subset
+    _check(fn(g.handle, subset, _ptr(d_proj), _ptr(d_img), _stream(stream)))
+
+
+class State:
+    """pet_state handle: resident reconstruction state (Table I)."""
+
+    def __init__(self, g: Geometry, d_counts, d_gamma, params: Params, d_img_init, stream=None):
+        h = _VP()
+        self.params = params
+        _check(lib().pet_state_create(g.handle, _ptr(d_counts), _ptr(d_gamma), ctypes.byref(params),
+                                      _ptr(d_img_init), _stream(stream), ctypes.byref(h)))
+        self.handle = h
+
+    def subiter(self, stream=None):
+        _check(lib().pet_subiter(self.handle, _stream(stream)))
+
+    def read_image(self, d_img, stream=None):
+        _check(lib().pet_state_read_image(self.handle, _ptr(d_img), _stream(stream)))
+
+    def objective(self, stream=None):
+        phi = ctypes.c_double()
+        parts = (ctypes.c_double * 3)()
+        _check(lib().pet_state_objective(self.handle, ctypes.byref(phi), parts, _stream(stream)))
+        return phi.value, list(parts)
+
+    @property
+    def subiters(self) -> int:
+        return lib().pet_state_subiters(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().pet_state_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def reconstruct(g: Geometry, d_counts, d_gamma, params: Params, d_img_inout, objective=False,
+                stream=None):
+    """f^0 -> f^T in place; returns the objective history (T+1 values) if requested."""
+    obj = (ctypes.c_double * (params.iterations + 1))() if objective else None
+    _check(lib().pet_reconstruct(g.handle, _ptr(d_counts), _ptr(d_gamma), ctypes.byref(params),
+                                 _ptr(d_img_inout), obj, _stream(stream)))
+    return list(obj) if objective else None
+
+
+def reconstruct_host(g: Geometry, h_counts, h_gamma, params: Params, h_img_inout, objective=False,
+                     stream=None):
+    """Host-buffer variant (numpy or pinned CPU tensors); copies happen inside the call."""
+    obj = (ctypes.c_double * (params.iterations + 1))() if objective else None
+    _check(lib().pet_reconstruct_host(g.handle, _ptr(h_counts), _ptr(h_gamma), ctypes.byref(params),
+                                      _ptr(h_img_inout), obj, _stream(stream)))
+    return list(obj) if objective else None
+
+
+def rdp_gradient(g: Geometry, d_img, gamma_r, eps, d_grad, stream=None):
+    _check(lib().pet_rdp_gradient(g.handle, _ptr(d_img), gamma_r, eps, _ptr(d_grad), _stream(stream)))
+
+
+def smoothness_nu(g: Geometry, d_img, nu1, nu2, d_nu, stream=None):
+    _check(lib().pet_smoothness_nu(g.handle, _ptr(d_img), nu1, nu2, _ptr(d_nu), _stream(stream)))
+
+
+def objective(g: Geometry, d_counts, d_gamma, d_img, beta, gamma_r, eps, stream=None):
+    phi = ctypes.c_double()
+    parts = (ctypes.c_double * 3)()
+    _check(lib().pet_objective(g.handle, _ptr(d_counts), _ptr(d_gamma), _ptr(d_img), beta, gamma_r,
+                               eps, ctypes.byref(phi), parts, _stream(stream)))
+    return phi.value, list(parts)
+
+
+def launch_count() -> int:
+    return lib().pet_launch_count()
+
+
+def profile_enable(on: bool = True):
+    lib().pet_profile_enable(1 if on else 0)
+
+
+def profile_reset():
+    lib().pet_profile_reset()
+
+
+def profile_read() -> dict:
+    """{kind: (total device ms, launches)} for every kernel kind (synchronises)."""
+    out = {}
+    for k, name in enumerate(KERNEL_KINDS):
+        ms = ctypes.c_double()
+        n = ctypes.c_longlong()
+        _check(lib().pet_profile_read(k, ctypes.byref(ms), ctypes.byref(n)))
+        out[name] = (ms.value, n.value)
+    return out
