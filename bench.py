@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--workload", default="stacked", choices=["stacked", "2d"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
+    ap.add_argument("--no-kernel-times", action="store_true",
+                    help="skip the per-kernel event pass (roofline)")
     return ap.parse_args()
 
 
@@ -216,7 +219,28 @@ def run_ours(args, rank, world, local):
     ms_per_step = ms_max / args.steps
     value = world * subiters / (ms_per_step / 1e3)
 
-    # per-kernel device time: a second pass with every launch bracketed by events
+    line = {
+        "metric": "OS subiters/s", "value": round(value, 2), "unit": "subiters/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (Kahan sums) + f64 scalars/objective",
+        "data": "synthetic (seeded random-ellipsoid phantom, analytic projections, Poisson counts)",
+        "config": workload_config(w), "clocks": clk, "gpu_launches": int(launches),
+        "wall_s_timed": round(wall, 3), "objective_final": obj[-1] if obj else None,
+    }
+    if not args.no_kernel_times:
+        line.update(kernel_times(args, w, pet, step, flush))
+    if not args.no_e2e:
+        line["e2e"] = end_to_end(args, w, scan, g, prm, pet, flush, dev, world, subiters)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, scan, args.cpu_seconds)
+    return line
+
+
+def kernel_times(args, w, pet, step, flush) -> dict:
+    """Per-kernel device time: a second pass with every launch bracketed by CUDA events on
+    its stream; the dominant kernel's roofline from its algorithmic bytes per launch."""
+    import torch
     pet.profile_reset()
     pet.profile_enable(True)
     for k in range(args.steps):
@@ -237,8 +261,12 @@ def run_ours(args, rank, world, local):
             "peak_source": peaks["source"] + " (burst copy)", "unit": "GB/s",
             "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": ncu_traffic(dom),
             "algorithmic_bytes_per_launch": byts[dom], "avg_launch_ms": round(avg_ms, 5)}
+    return {"roofline": roof, "kernels": shares}
 
-    # end to end through the host-buffer entry point (pinned host memory)
+
+def end_to_end(args, w, scan, g, prm, pet, flush, dev, world, subiters) -> dict:
+    """Same metric through pet_reconstruct_host from pinned host buffers."""
+    import torch
     h_counts = torch.from_numpy(scan["counts"]).pin_memory()
     h_gamma = torch.from_numpy(scan["gamma"]).pin_memory()
     h_img = torch.ones((w.nplanes, w.n, w.n), dtype=torch.float32).pin_memory()
@@ -261,20 +289,7 @@ def run_ours(args, rank, world, local):
            "h2d_bytes_per_step": int(h_counts.numel() * 4 + h_gamma.numel() * 4 + h_img.numel() * 4),
            "d2h_bytes_per_step": int(h_img.numel() * 4 + 8 * (w.params.iterations + 1)),
            "api": "pet_reconstruct_host", "ms_per_step": round(float(te.item()), 3)}
-
-    line = {
-        "metric": "OS subiters/s", "value": round(value, 2), "unit": "subiters/s",
-        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (Kahan sums) + f64 scalars/objective",
-        "data": "synthetic (seeded random-ellipsoid phantom, analytic projections, Poisson counts)",
-        "config": workload_config(w), "clocks": clk, "gpu_launches": int(launches),
-        "wall_s_timed": round(wall, 3), "roofline": roof, "kernels": shares, "e2e": e2e,
-        "objective_final": obj[-1] if obj else None,
-    }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(w, scan, args.cpu_seconds)
-    return line
+    return e2e
 
 
 def cpu_baseline(w, scan, seconds: float) -> dict:

@@ -146,6 +146,7 @@ pet_status pet_back_subset_f64(const pet_geometry *g, int subset, const double *
  * pet_subiter: one subiteration f^{k,i} = P_t(f^{k,i-1} - lambda_k S^{k,i}(f^{k,i-1})
  *   grad Phi_i(f^{k,i-1})), then advances (k, i).  Asynchronous.
  * pet_state_read_image: d_img = current f as float [P][N][N].
+ * pet_state_read_image_f64: the same as double [P][N][N] (exact for PET_PREC_FP64 states).
  * pet_state_objective: *h_phi = Phi(current f) (Eqs. FidelityTerm, ObjectiveFunction), FP64;
  *   h_parts (optional, 3 doubles) = sum(Af), sum(g ln(Af + gamma)), R(f).  Synchronises.
  * pet_state_subiters: completed subiterations J.
@@ -155,6 +156,7 @@ pet_status pet_state_create(const pet_geometry *g, const int32_t *d_counts, cons
                             pet_state **out);
 pet_status pet_subiter(pet_state *s, void *stream);
 pet_status pet_state_read_image(const pet_state *s, float *d_img, void *stream);
+pet_status pet_state_read_image_f64(const pet_state *s, double *d_img, void *stream);
 pet_status pet_state_objective(pet_state *s, double *h_phi, double *h_parts, void *stream);
 int pet_state_subiters(const pet_state *s);
 void pet_state_destroy(pet_state *s);

@@ -187,9 +187,9 @@ template <int G, int AR> struct GroupSum {
 //   acc_p += sum_{u < nviews} sum_b len(view u, bin b, pixel) * proj[u][b][plane p]
 // len is the exact length of the line of bin b inside the pixel square: the trapezoid
 // min(L, (h - |delta|) rho / (major minor)) of the pixel's footprint, or, for views along an
-// axis, L on delta in [-h, h) (the half-open pixel rule).  delta = b - t(ix, iy), in bins.
-// proj == nullptr backprojects ones.  Views are taken in order and each view's (<= K)-term
-// partial is added with one compensated step: the sum order is fixed (deterministic).
+// axis, L for the rays inside the pixel's half-open column.  delta = b - t(ix, iy), in bins.
+// proj == nullptr backprojects ones.  Views are taken in order and each view's candidate bins
+// are added in pairs with one compensated step: the sum order is fixed (deterministic).
 // ------------------------------------------------------------------------------------------
 template <int G, int AR>
 __device__ __forceinline__ void gather_bp(const GeoDev &g, int slot0, int nviews,
@@ -198,98 +198,71 @@ __device__ __forceinline__ void gather_bp(const GeoDev &g, int slot0, int nviews
 {
     using T = typename ArithT<AR>::T;
     const int NB = g.NB, Pp = g.Pp, K = g.K;
+    T zero[G];
+#pragma unroll
+    for (int p = 0; p < G; ++p) zero[p] = T(0);
     for (int u = 0; u < nviews; ++u) {
         const ViewGeo &vw = g.views[slot0 + u];
-        T w[2];
-        int bc[2];
-        if constexpr (AR == AR_FP64) {
-            const double t = vw.t0 + (double)ix * vw.cx + (double)iy * vw.cy;
-            const double h = vw.h;
-            const int b0 = (int)ceil(t - h);
-            // K is 2 for bin spacing >= pixel / sqrt(2) (all workloads here); larger K adds
-            // further candidates below.
+        const T *base = proj ? proj + (size_t)u * NB * Pp + (size_t)grp * G : nullptr;
+        if (vw.axis) {
+            // Views along an axis: every ray runs along one pixel column (row).  Ray b belongs
+            // to the pixel whose half-open column contains it, decided from the very start
+            // coordinate the forward walk uses, so ties on pixel edges match it exactly.
+            const int cross = vw.xdrive ? iy : ix;
+            const RayGeo *rr = g.rays + (size_t)(slot0 + u) * NB;
+            int bs;
+            if constexpr (AR == AR_FP64)
+                bs = (int)floor(vw.t0 + (double)ix * vw.cx + (double)iy * vw.cy - vw.h);
+            else
+                bs = (int)((vw.t0q + (long long)ix * vw.cxq + (long long)iy * vw.cyq - vw.hq) >> 32);
+            for (int k = 0; k <= K; ++k) {
+                const int b = bs + k;
+                if ((unsigned)b >= (unsigned)NB) continue;
+                int c;
+                if constexpr (AR == AR_FP64) c = (int)floor(rr[b].lo);
+                else c = (int)(rr[b].loq >> 32);
+                if (c != cross) continue;
+                if (base == nullptr) {
+                    acc.add_scalar((T)vw.L);
+                } else {
+                    T x[G];
+                    load_group<G, T>(base + (size_t)b * Pp, x);
+                    acc.add2terms((T)vw.L, x, T(0), zero);
+                }
+            }
+            continue;
+        }
+        // Oblique views: trapezoid footprint; the candidate bins are ceil(t - h) + k, k < K.
+        for (int k0 = 0; k0 < K; k0 += 2) {
+            T w[2];
+            int bc[2];
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
-                const int b = b0 + k;
-                const double dl = (double)b - t;
-                double ww;
-                if (vw.axis) ww = (dl >= -h && dl < h) ? vw.L : 0.0;
-                else {
-                    const double dd = h - fabs(dl);
+                T ww;
+                int b;
+                if constexpr (AR == AR_FP64) {
+                    const double t = vw.t0 + (double)ix * vw.cx + (double)iy * vw.cy;
+                    b = (int)ceil(t - vw.h) + k0 + k;
+                    const double dd = vw.h - fabs((double)b - t);
                     ww = dd > 0.0 ? fmin(vw.L, dd * vw.wslope) : 0.0;
-                }
-                const bool ok = (unsigned)b < (unsigned)NB;
-                w[k] = ok ? ww : 0.0;
-                bc[k] = ok ? b : 0;
-            }
-        } else {
-            const long long tq = vw.t0q + (long long)ix * vw.cxq + (long long)iy * vw.cyq;
-            const long long hq = vw.hq;
-            const int b0 = (int)((tq - hq + 0xFFFFFFFFLL) >> 32);   // ceil(t - h)
-#pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                const int b = b0 + k;
-                const long long dq = ((long long)b << 32) - tq;
-                float ww;
-                if (vw.axis) ww = (dq >= -hq && dq < hq) ? vw.Lf : 0.f;
-                else {
-                    const long long adq = dq < 0 ? -dq : dq;
-                    const long long dd = hq - adq;
-                    ww = dd > 0 ? fminf(vw.Lf, __ll2float_rn(dd) * kQ32 * vw.wslopef) : 0.f;
-                }
-                const bool ok = (unsigned)b < (unsigned)NB;
-                w[k] = ok ? ww : 0.f;
-                bc[k] = ok ? b : 0;
-            }
-        }
-        if (proj == nullptr) {
-            acc.add_scalar(w[0] + w[1]);
-        } else {
-            T x0[G], x1[G];
-            const T *base = proj + (size_t)u * NB * Pp + (size_t)grp * G;
-            load_group<G, T>(base + (size_t)bc[0] * Pp, x0);
-            load_group<G, T>(base + (size_t)bc[1] * Pp, x1);
-            acc.add2terms(w[0], x0, w[1], x1);
-        }
-        // further candidate bins when the footprint spans more than two bins
-        for (int k = 2; k < K; ++k) {
-            T wk;
-            int bk;
-            if constexpr (AR == AR_FP64) {
-                const double t = vw.t0 + (double)ix * vw.cx + (double)iy * vw.cy;
-                const int b = (int)ceil(t - vw.h) + k;
-                const double dl = (double)b - t;
-                double ww;
-                if (vw.axis) ww = (dl >= -vw.h && dl < vw.h) ? vw.L : 0.0;
-                else {
-                    const double dd = vw.h - fabs(dl);
-                    ww = dd > 0.0 ? fmin(vw.L, dd * vw.wslope) : 0.0;
-                }
-                const bool ok = (unsigned)b < (unsigned)NB;
-                wk = ok ? ww : 0.0;
-                bk = ok ? b : 0;
-            } else {
-                const long long tq = vw.t0q + (long long)ix * vw.cxq + (long long)iy * vw.cyq;
-                const int b = (int)((tq - vw.hq + 0xFFFFFFFFLL) >> 32) + k;
-                const long long dq = ((long long)b << 32) - tq;
-                float ww;
-                if (vw.axis) ww = (dq >= -vw.hq && dq < vw.hq) ? vw.Lf : 0.f;
-                else {
+                } else {
+                    const long long tq = vw.t0q + (long long)ix * vw.cxq + (long long)iy * vw.cyq;
+                    b = (int)((tq - vw.hq + 0xFFFFFFFFLL) >> 32) + k0 + k;   // ceil(t - h) + k
+                    const long long dq = ((long long)b << 32) - tq;
                     const long long dd = vw.hq - (dq < 0 ? -dq : dq);
                     ww = dd > 0 ? fminf(vw.Lf, __ll2float_rn(dd) * kQ32 * vw.wslopef) : 0.f;
                 }
-                const bool ok = (unsigned)b < (unsigned)NB;
-                wk = ok ? ww : 0.f;
-                bk = ok ? b : 0;
+                const bool ok = (unsigned)b < (unsigned)NB && k0 + k < K;
+                w[k] = ok ? ww : T(0);
+                bc[k] = ok ? b : 0;
             }
-            if (proj == nullptr) {
-                acc.add_scalar(wk);
+            if (base == nullptr) {
+                acc.add_scalar(w[0] + w[1]);
             } else {
-                T xk[G], zero[G];
-#pragma unroll
-                for (int p = 0; p < G; ++p) zero[p] = T(0);
-                load_group<G, T>(proj + ((size_t)u * NB + bk) * Pp + (size_t)grp * G, xk);
-                acc.add2terms(wk, xk, T(0), zero);
+                T x0[G], x1[G];
+                load_group<G, T>(base + (size_t)bc[0] * Pp, x0);
+                load_group<G, T>(base + (size_t)bc[1] * Pp, x1);
+                acc.add2terms(w[0], x0, w[1], x1);
             }
         }
     }

@@ -290,6 +290,13 @@ extern "C" pet_status pet_state_read_image(const pet_state *s, float *d_img, voi
                                as_stream(stream));
 }
 
+extern "C" pet_status pet_state_read_image_f64(const pet_state *s, double *d_img, void *stream)
+{
+    if (!s || !d_img) return fail(PET_ERR_INVALID, "pet_state_read_image_f64: NULL argument");
+    return from_internal_image(s->g->dev, s->f[s->cur], d_img, s->arith == AR_FP64, 1,
+                               as_stream(stream));
+}
+
 extern "C" pet_status pet_state_objective(pet_state *s, double *h_phi, double *h_parts,
                                          void *stream)
 {

@@ -60,6 +60,7 @@ SIGNATURES = {
     "pet_state_create": (_I, [_VP, _VP, _VP, ctypes.POINTER(Params), _VP, _VP, ctypes.POINTER(_VP)]),
     "pet_subiter": (_I, [_VP, _VP]),
     "pet_state_read_image": (_I, [_VP, _VP, _VP]),
+    "pet_state_read_image_f64": (_I, [_VP, _VP, _VP]),
     "pet_state_objective": (_I, [_VP, _DP, _DP, _VP]),
     "pet_state_subiters": (_I, [_VP]),
     "pet_state_destroy": (None, [_VP]),
@@ -184,7 +185,8 @@ class State:
         _check(lib().pet_subiter(self.handle, _stream(stream)))
 
     def read_image(self, d_img, stream=None):
-        _check(lib().pet_state_read_image(self.handle, _ptr(d_img), _stream(stream)))
+        fn = lib().pet_state_read_image_f64 if str(d_img.dtype) == "torch.float64" else lib().pet_state_read_image
+        _check(fn(self.handle, _ptr(d_img), _stream(stream)))
 
     def objective(self, stream=None):
         phi = ctypes.c_double()
