@@ -153,12 +153,26 @@ def load_peaks() -> dict:
         return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
+def kernel_source_hash() -> str:
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    base = os.path.join(ROOT, "paper_2111_07886_gb300", "csrc")
+    for f in sorted(glob.glob(os.path.join(base, "*.cu")) + glob.glob(os.path.join(base, "*.cuh"))):
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def ncu_traffic(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary of the same kernel, if current."""
+    """DRAM bytes per launch from the committed ncu summary of the same kernel; None when the
+    kernel sources changed since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as fh:
             d = json.load(fh)
+        if d.get("source_hash") != kernel_source_hash():
+            return None
         return d.get(kernel)
     except Exception:
         return None

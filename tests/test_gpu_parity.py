@@ -48,11 +48,17 @@ def to_dev(a, dtype=torch.float32):
     return torch.from_numpy(np.ascontiguousarray(a)).to(DEV, dtype)
 
 
+def f32(a):
+    """The float32 rounding of `a`, in float64: the exact input an FP32 kernel sees, so that
+    both sides of a parity check get identical values."""
+    return np.asarray(a, np.float32).astype(np.float64)
+
+
 @pytest.mark.parametrize("geom", GEOMS)
 def test_forward_parity(geom):
     g, og = _geoms(*geom)
     N, P, V, NB, M, _ = geom
-    x = synth.random_image((P, N, N), seed=N + P)
+    x = f32(synth.random_image((P, N, N), seed=N + P))
     xd = to_dev(x)
     for i in list(range(M)) + [-1]:
         nv = V if i < 0 else og and oracle.subset_size(og, i)
@@ -73,7 +79,7 @@ def test_back_parity(geom):
     N, P, V, NB, M, _ = geom
     for i in list(range(M)) + [-1]:
         nv = V if i < 0 else oracle.subset_size(og, i)
-        y = synth.random_image((P, nv, NB), seed=7 * i + 100 + N)
+        y = f32(synth.random_image((P, nv, NB), seed=7 * i + 100 + N))
         ref = oracle.back(og, i, y)
         out = torch.empty((P, N, N), dtype=torch.float32, device=DEV)
         pet.back_subset(g, i, to_dev(y), out)
@@ -89,10 +95,10 @@ def test_back_parity(geom):
 
 def test_adjointness_gpu():
     g, og = _geoms(64, 11, 40, 91, 6, 1.0)
-    x = synth.random_image((11, 64, 64), seed=1)
+    x = f32(synth.random_image((11, 64, 64), seed=1))
     for i in range(6):
         nv = oracle.subset_size(og, i)
-        y = synth.random_image((11, nv, 91), seed=2 + i)
+        y = f32(synth.random_image((11, nv, 91), seed=2 + i))
         ax = torch.empty((11, nv, 91), device=DEV)
         aty = torch.empty((11, 64, 64), device=DEV)
         pet.forward_subset(g, i, to_dev(x), ax)
@@ -131,7 +137,7 @@ def test_sensitivity_parity():
 
 def test_rdp_gradient_and_nu_parity():
     g, og = _geoms(48, 11, 30, 69, 7, 1.0)
-    x = synth.random_image((11, 48, 48), seed=5, lo=0.2, hi=3.0)
+    x = f32(synth.random_image((11, 48, 48), seed=5, lo=0.2, hi=3.0))
     out = torch.empty((11, 48, 48), device=DEV)
     pet.rdp_gradient(g, to_dev(x), 2.0, 1e-12, out)
     torch.cuda.synchronize()
@@ -141,7 +147,7 @@ def test_rdp_gradient_and_nu_parity():
     # smooth image with an edge so that the clamp of nu is partly active
     img = np.ones((11, 48, 48))
     img[:, :, 20:] = 2.5
-    img += 0.05 * synth.random_image((11, 48, 48), seed=6, lo=0.0, hi=1.0)
+    img = f32(img + 0.05 * synth.random_image((11, 48, 48), seed=6, lo=0.0, hi=1.0))
     pet.smoothness_nu(g, to_dev(img), 0.8, 2.2, out)
     torch.cuda.synchronize()
     ref = oracle.nu_from_image(img, 0.8, 2.2)
@@ -155,7 +161,7 @@ def test_objective_parity():
     scan = synth.make_scan(w)
     g = pet.Geometry.from_dict(w.geometry(), scan["sens"])
     og = oracle.geom_from(w.geometry(), scan["sens"])
-    x = synth.random_image((1, w.n, w.n), seed=9, lo=0.5, hi=2.0)
+    x = f32(synth.random_image((1, w.n, w.n), seed=9, lo=0.5, hi=2.0))
     phi, parts = pet.objective(g, to_dev(scan["counts"], torch.int32), to_dev(scan["gamma"]),
                                to_dev(x), w.params.beta, 2.0, 1e-12)
     ref = oracle.objective(og, scan["counts"], scan["gamma"], x, w.params.beta)
@@ -263,14 +269,15 @@ def test_stacked_full_size_single_steps():
     scan = synth.make_scan(w)
     og = oracle.geom_from(w.geometry(), scan["sens"])
     g = pet.Geometry.from_dict(w.geometry(), scan["sens"])
-    x = synth.random_image((89, 256, 256), seed=3)
+    x = f32(synth.random_image((89, 256, 256), seed=3))
     ref = oracle.forward(og, 5, x)
     out = torch.empty(ref.shape, device=DEV)
     pet.forward_subset(g, 5, to_dev(x), out)
     torch.cuda.synchronize()
     assert per_projection_rel(out.cpu().numpy(), ref) <= 1e-5
-    bref = oracle.back(og, 5, ref)
     bout = torch.empty((89, 256, 256), device=DEV)
+    ref = f32(ref)
+    bref = oracle.back(og, 5, ref)
     pet.back_subset(g, 5, to_dev(ref), bout)
     torch.cuda.synchronize()
     got = bout.cpu().numpy()
