@@ -69,6 +69,7 @@ SIGNATURES = {
     "pet_rdp_gradient": (_I, [_VP, _VP, _D, _D, _VP, _VP]),
     "pet_smoothness_nu": (_I, [_VP, _VP, _D, _D, _VP, _VP]),
     "pet_objective": (_I, [_VP, _VP, _VP, _VP, _D, _D, _D, _DP, _DP, _VP]),
+    "pet_objective_static": (_I, [_VP, _VP, _VP, _VP, _D, _D, _D, _DP, _DP, _VP]),
     "pet_launch_count": (ctypes.c_longlong, []),
     "pet_profile_enable": (None, [_I]),
     "pet_profile_read": (_I, [_I, _DP, ctypes.POINTER(ctypes.c_longlong)]),
@@ -241,6 +242,15 @@ def objective(g: Geometry, d_counts, d_gamma, d_img, beta, gamma_r, eps, stream=
     parts = (ctypes.c_double * 3)()
     _check(lib().pet_objective(g.handle, _ptr(d_counts), _ptr(d_gamma), _ptr(d_img), beta, gamma_r,
                                eps, ctypes.byref(phi), parts, _stream(stream)))
+    return phi.value, list(parts)
+
+
+def objective_static(g: Geometry, d_counts, d_gamma, d_img, beta, gamma_r, eps, stream=None):
+    """Phi(d_img) like ``objective``, through the entry point that allocates no memory."""
+    phi = ctypes.c_double()
+    parts = (ctypes.c_double * 3)()
+    _check(lib().pet_objective_static(g.handle, _ptr(d_counts), _ptr(d_gamma), _ptr(d_img), beta,
+                                      gamma_r, eps, ctypes.byref(phi), parts, _stream(stream)))
     return phi.value, list(parts)
 
 
