@@ -183,87 +183,127 @@ template <int G, int AR> struct GroupSum {
 };
 
 // ------------------------------------------------------------------------------------------
-// Pixel-driven gather backprojection for pixel (ix, iy) and one plane group:
-//   acc_p += sum_{u < nviews} sum_b len(view u, bin b, pixel) * proj[u][b][plane p]
-// len is the exact length of the line of bin b inside the pixel square: the trapezoid
-// min(L, (h - |delta|) rho / (major minor)) of the pixel's footprint, or, for views along an
-// axis, L for the rays inside the pixel's half-open column.  delta = b - t(ix, iy), in bins.
-// proj == nullptr backprojects ones.  Views are taken in order and each view's candidate bins
-// are added in pairs with one compensated step: the sum order is fixed (deterministic).
+// Pixel-driven gather backprojection, in two phases per block.
+//
+// Phase 1 (bp_weights): for every (pixel, view) pair of the block, the first candidate bin b0
+// and the exact lengths w[k] of the lines of bins b0 + k (k < KC) inside the pixel square go to a
+// shared-memory table.  Oblique views: the trapezoid min(L, (h - |delta|) rho / (major minor))
+// of the pixel's footprint, delta = b - t(ix, iy) in bins, from Q32.32 integers so that the
+// feet of the trapezoid keep relative precision.  Views along an axis: length L for each ray
+// inside the pixel's half-open column, membership decided from the very start coordinate the
+// forward walk uses, so ties on pixel edges match the forward projector exactly.
+// Phase 2 (bp_accumulate): every plane group of the pixel adds, view by view in order, the
+// <= KC-term partial with one compensated step (fixed order: deterministic, no atomics).
 // ------------------------------------------------------------------------------------------
-template <int G, int AR>
-__device__ __forceinline__ void gather_bp(const GeoDev &g, int slot0, int nviews,
-                                          const typename ArithT<AR>::T *__restrict__ proj,
-                                          int grp, int ix, int iy, GroupSum<G, AR> &acc)
+template <int KC, int AR> struct BpTable {
+    using T = typename ArithT<AR>::T;
+    static constexpr int CAP = AR == AR_FP64 ? 1024 : 2048;   // (pixel, view) entries
+    int b0[CAP];
+    T w[KC][CAP];
+};
+
+template <int KC, int AR>
+__device__ __forceinline__ void bp_weights(const GeoDev &g, const ViewGeo &vw, int slot, int ix,
+                                           int iy, int &b0, typename ArithT<AR>::T (&w)[KC])
 {
     using T = typename ArithT<AR>::T;
-    const int NB = g.NB, Pp = g.Pp, K = g.K;
-    T zero[G];
+    const int NB = g.NB;
+    if (vw.axis) {
+        const int cross = vw.xdrive ? iy : ix;
+        const RayGeo *rr = g.rays + (size_t)slot * NB;
+        int bs;
+        if constexpr (AR == AR_FP64)
+            bs = (int)floor(vw.t0 + (double)ix * vw.cx + (double)iy * vw.cy - vw.h);
+        else
+            bs = (int)((vw.t0q + (long long)ix * vw.cxq + (long long)iy * vw.cyq - vw.hq) >> 32);
+        auto member = [&](int b) -> bool {
+            if ((unsigned)b >= (unsigned)NB) return false;
+            if constexpr (AR == AR_FP64) return (int)floor(rr[b].lo) == cross;
+            else return (int)(rr[b].loq >> 32) == cross;
+        };
+        b0 = member(bs) ? bs : bs + 1;
 #pragma unroll
-    for (int p = 0; p < G; ++p) zero[p] = T(0);
-    for (int u = 0; u < nviews; ++u) {
-        const ViewGeo &vw = g.views[slot0 + u];
-        const T *base = proj ? proj + (size_t)u * NB * Pp + (size_t)grp * G : nullptr;
-        if (vw.axis) {
-            // Views along an axis: every ray runs along one pixel column (row).  Ray b belongs
-            // to the pixel whose half-open column contains it, decided from the very start
-            // coordinate the forward walk uses, so ties on pixel edges match it exactly.
-            const int cross = vw.xdrive ? iy : ix;
-            const RayGeo *rr = g.rays + (size_t)(slot0 + u) * NB;
-            int bs;
-            if constexpr (AR == AR_FP64)
-                bs = (int)floor(vw.t0 + (double)ix * vw.cx + (double)iy * vw.cy - vw.h);
-            else
-                bs = (int)((vw.t0q + (long long)ix * vw.cxq + (long long)iy * vw.cyq - vw.hq) >> 32);
-            for (int k = 0; k <= K; ++k) {
-                const int b = bs + k;
-                if ((unsigned)b >= (unsigned)NB) continue;
-                int c;
-                if constexpr (AR == AR_FP64) c = (int)floor(rr[b].lo);
-                else c = (int)(rr[b].loq >> 32);
-                if (c != cross) continue;
-                if (base == nullptr) {
-                    acc.add_scalar((T)vw.L);
-                } else {
-                    T x[G];
-                    load_group<G, T>(base + (size_t)b * Pp, x);
-                    acc.add2terms((T)vw.L, x, T(0), zero);
-                }
-            }
+        for (int k = 0; k < KC; ++k) w[k] = member(b0 + k) ? (T)vw.L : T(0);
+        return;
+    }
+    if constexpr (AR == AR_FP64) {
+        const double t = vw.t0 + (double)ix * vw.cx + (double)iy * vw.cy;
+        b0 = (int)ceil(t - vw.h);
+#pragma unroll
+        for (int k = 0; k < KC; ++k) {
+            const int b = b0 + k;
+            const double dd = vw.h - fabs((double)b - t);
+            const double ww = dd > 0.0 ? fmin(vw.L, dd * vw.wslope) : 0.0;
+            w[k] = (unsigned)b < (unsigned)NB ? ww : 0.0;
+        }
+    } else {
+        const long long tq = vw.t0q + (long long)ix * vw.cxq + (long long)iy * vw.cyq;
+        b0 = (int)((tq - vw.hq + 0xFFFFFFFFLL) >> 32);          // ceil(t - h)
+        const float ws = vw.wslopef * kQ32;
+#pragma unroll
+        for (int k = 0; k < KC; ++k) {
+            const int b = b0 + k;
+            const long long dq = ((long long)b << 32) - tq;
+            const long long dd = vw.hq - (dq < 0 ? -dq : dq);
+            const float ww = dd > 0 ? fminf(vw.Lf, __ll2float_rn(dd) * ws) : 0.f;
+            w[k] = (unsigned)b < (unsigned)NB ? ww : 0.f;
+        }
+    }
+}
+
+// Fill the table for pixels [j0, j0 + np) x views [u0, u0 + nvc) (entry e = pixel * nvc + view).
+template <int KC, int AR>
+__device__ __forceinline__ void bp_fill(const GeoDev &g, int slot0, int u0, int nvc, int j0,
+                                        int np, BpTable<KC, AR> &tb)
+{
+    using T = typename ArithT<AR>::T;
+    const int nthr = blockDim.x;
+    for (int e = threadIdx.x; e < np * nvc; e += nthr) {
+        const int pl = e / nvc, u = u0 + e % nvc;
+        const int j = j0 + pl;
+        int b0 = 0;
+        T w[KC];
+        if (j < g.N * g.N) {
+            bp_weights<KC, AR>(g, g.views[slot0 + u], slot0 + u, j % g.N, j / g.N, b0, w);
+        } else {
+#pragma unroll
+            for (int k = 0; k < KC; ++k) w[k] = T(0);
+        }
+        tb.b0[e] = b0;
+#pragma unroll
+        for (int k = 0; k < KC; ++k) tb.w[k][e] = w[k];
+    }
+}
+
+// Accumulate views [u0, u0 + nvc) of the table into acc for local pixel pl and plane group grp.
+// proj (subset rows [u][NB][Pp]) == nullptr backprojects ones.
+template <int G, int KC, int AR>
+__device__ __forceinline__ void bp_accumulate(const GeoDev &g, const BpTable<KC, AR> &tb,
+                                              const typename ArithT<AR>::T *__restrict__ proj,
+                                              int u0, int nvc, int pl, int grp,
+                                              GroupSum<G, AR> &acc)
+{
+    using T = typename ArithT<AR>::T;
+    const int NB = g.NB, Pp = g.Pp;
+    for (int uu = 0; uu < nvc; ++uu) {
+        const int e = pl * nvc + uu;
+        const int b0 = tb.b0[e];
+        if (proj == nullptr) {
+            T s = T(0);
+#pragma unroll
+            for (int k = 0; k < KC; ++k) s += tb.w[k][e];
+            acc.add_scalar(s);
             continue;
         }
-        // Oblique views: trapezoid footprint; the candidate bins are ceil(t - h) + k, k < K.
-        for (int k0 = 0; k0 < K; k0 += 2) {
-            T w[2];
-            int bc[2];
+        const T *base = proj + (size_t)(u0 + uu) * NB * Pp + (size_t)grp * G;
 #pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                T ww;
-                int b;
-                if constexpr (AR == AR_FP64) {
-                    const double t = vw.t0 + (double)ix * vw.cx + (double)iy * vw.cy;
-                    b = (int)ceil(t - vw.h) + k0 + k;
-                    const double dd = vw.h - fabs((double)b - t);
-                    ww = dd > 0.0 ? fmin(vw.L, dd * vw.wslope) : 0.0;
-                } else {
-                    const long long tq = vw.t0q + (long long)ix * vw.cxq + (long long)iy * vw.cyq;
-                    b = (int)((tq - vw.hq + 0xFFFFFFFFLL) >> 32) + k0 + k;   // ceil(t - h) + k
-                    const long long dq = ((long long)b << 32) - tq;
-                    const long long dd = vw.hq - (dq < 0 ? -dq : dq);
-                    ww = dd > 0 ? fminf(vw.Lf, __ll2float_rn(dd) * kQ32 * vw.wslopef) : 0.f;
-                }
-                const bool ok = (unsigned)b < (unsigned)NB && k0 + k < K;
-                w[k] = ok ? ww : T(0);
-                bc[k] = ok ? b : 0;
-            }
-            if (base == nullptr) {
-                acc.add_scalar(w[0] + w[1]);
-            } else {
-                T x0[G], x1[G];
-                load_group<G, T>(base + (size_t)bc[0] * Pp, x0);
-                load_group<G, T>(base + (size_t)bc[1] * Pp, x1);
-                acc.add2terms(w[0], x0, w[1], x1);
-            }
+        for (int k = 0; k < KC; k += 2) {
+            const T w0 = tb.w[k][e], w1 = tb.w[k + 1][e];
+            const int ba = b0 + k, bb = b0 + k + 1;
+            T x0[G], x1[G];
+            load_group<G, T>(base + (size_t)((unsigned)ba < (unsigned)NB ? ba : 0) * Pp, x0);
+            load_group<G, T>(base + (size_t)((unsigned)bb < (unsigned)NB ? bb : 0) * Pp, x1);
+            acc.add2terms(w0, x0, w1, x1);
         }
     }
 }

@@ -5,39 +5,49 @@
 //     iterate in the epilogue;
 //   - the mu reduction that feeds mean(mu), the plain sum behind mean(f), and the stand-alone
 //     RDP value / gradient and nu maps.
-// One thread handles one pixel and one group of G planes; neighbours come through L1.
+// Pixel-driven: one thread handles one pixel and one group of G planes; neighbours come
+// through L1; the gather's (pixel, view) weights are shared by all groups through shared memory.
 #include "kernels.cuh"
 #include "profile.cuh"
 
 namespace pet {
 
-// Loads the 3x3 in-plane neighbourhood of pixel (ix, iy) for one plane group and returns
-// the RDP gradient sum, the RDP value and the Matlab-style gradient magnitude as requested.
+// Loads the 3x3 in-plane neighbourhood of pixel (ix, iy) for one plane group.
 //   RG: gr_p = 2 sum_k (f_j - f_k)(gamma_R |f_j - f_k| + f_j + 3 f_k + 2 eps) / den^2
-//   RV: rv  += sum_k (f_j - f_k)^2 / den             (den = f_j + f_k + gamma_R|f_j-f_k| + eps)
-//   MU: gm_p = sqrt(gx^2 + gy^2), central differences inside, one-sided at the edges
-template <int G, int AR, bool RG, bool RV, bool MU>
+//       (den = f_j + f_k + gamma_R |f_j - f_k| + eps; FP32 kernels use the fast reciprocal)
+//   MU: gx_p, gy_p of the Matlab-style gradient: central differences inside, one-sided at
+//       the edges (the missing side counts as the centre value)
+//   RV: rv_p = sum_k (f_j - f_k)^2 / den
+template <int G, int AR, bool RG, bool MU, bool RV>
 __device__ __forceinline__ void stencil(const GeoDev &g, const typename ArithT<AR>::T *f, int grp,
                                         int ix, int iy, typename ArithT<AR>::T gamma_r,
                                         typename ArithT<AR>::T eps,
                                         typename ArithT<AR>::T (&fc)[G],
                                         typename ArithT<AR>::T (&gr)[G],
-                                        typename ArithT<AR>::T (&gm)[G], double &rv)
+                                        typename ArithT<AR>::T (&gx)[G],
+                                        typename ArithT<AR>::T (&gy)[G],
+                                        typename ArithT<AR>::T (&rv)[G])
 {
     using T = typename ArithT<AR>::T;
     const int N = g.N, Pp = g.Pp;
     const T *base = f + (size_t)grp * G;
     load_group<G, T>(base + ((size_t)iy * N + ix) * Pp, fc);
-    T xl[G], xr[G], yd[G], yu[G];
+    const T hx = (ix > 0 && ix < N - 1) ? T(0.5) : T(1);
+    const T hy = (iy > 0 && iy < N - 1) ? T(0.5) : T(1);
 #pragma unroll
-    for (int p = 0; p < G; ++p) {
-        gr[p] = T(0);
-        xl[p] = xr[p] = yd[p] = yu[p] = fc[p];
+    for (int p = 0; p < G; ++p) { gr[p] = T(0); gx[p] = T(0); gy[p] = T(0); rv[p] = T(0); }
+    if constexpr (MU) {
+        // a missing neighbour on one side is replaced by the centre value
+        const T sx = (ix == 0 ? -hx : T(0)) + (ix == N - 1 ? hx : T(0));
+        const T sy = (iy == 0 ? -hy : T(0)) + (iy == N - 1 ? hy : T(0));
+#pragma unroll
+        for (int p = 0; p < G; ++p) { gx[p] = sx * fc[p]; gy[p] = sy * fc[p]; }
     }
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
-        if (q == 4) continue;
         const int dx = q % 3 - 1, dy = q / 3 - 1;
+        if (q == 4) continue;
+        if (!RG && !RV && dx != 0 && dy != 0) continue;    // gradient only: axial neighbours
         const int x = ix + dx, y = iy + dy;
         if (x < 0 || y < 0 || x >= N || y >= N) continue;
         T fk[G];
@@ -48,92 +58,109 @@ __device__ __forceinline__ void stencil(const GeoDev &g, const typename ArithT<A
                 const T d = fc[p] - fk[p];
                 const T ad = d < T(0) ? -d : d;
                 const T den = fc[p] + fk[p] + gamma_r * ad + eps;
-                if constexpr (RG) gr[p] += d * (gamma_r * ad + fc[p] + T(3) * fk[p] + T(2) * eps) / (den * den);
+                if constexpr (RG) {
+                    const T num = d * (gamma_r * ad + fc[p] + T(3) * fk[p] + T(2) * eps);
+                    if constexpr (AR == AR_FP64) gr[p] += num / (den * den);
+                    else gr[p] += __fdividef(num, den * den);
+                }
                 if constexpr (RV) {
-                    if (grp * G + p < g.P) rv += (double)(d * d / den);
+                    if constexpr (AR == AR_FP64) rv[p] += d * d / den;
+                    else rv[p] += __fdividef(d * d, den);
                 }
             }
         }
         if constexpr (MU) {
-            if (dy == 0 && dx == -1) {
+            if (dy == 0) {
+                const T sgn = dx < 0 ? -hx : hx;
 #pragma unroll
-                for (int p = 0; p < G; ++p) xl[p] = fk[p];
-            } else if (dy == 0 && dx == 1) {
+                for (int p = 0; p < G; ++p) gx[p] += sgn * fk[p];
+            } else if (dx == 0) {
+                const T sgn = dy < 0 ? -hy : hy;
 #pragma unroll
-                for (int p = 0; p < G; ++p) xr[p] = fk[p];
-            } else if (dx == 0 && dy == -1) {
-#pragma unroll
-                for (int p = 0; p < G; ++p) yd[p] = fk[p];
-            } else if (dx == 0 && dy == 1) {
-#pragma unroll
-                for (int p = 0; p < G; ++p) yu[p] = fk[p];
+                for (int p = 0; p < G; ++p) gy[p] += sgn * fk[p];
             }
         }
     }
+    if constexpr (RG) {
 #pragma unroll
-    for (int p = 0; p < G; ++p) {
-        if constexpr (RG) gr[p] *= T(2);
-        if constexpr (MU) {
-            // interior: (f[+1] - f[-1]) / 2; edges: one-sided (the missing side equals fc)
-            const T hx = (ix > 0 && ix < N - 1) ? T(0.5) : T(1);
-            const T hy = (iy > 0 && iy < N - 1) ? T(0.5) : T(1);
-            const T gx = (xr[p] - xl[p]) * hx, gy = (yu[p] - yd[p]) * hy;
-            gm[p] = sqrt(gx * gx + gy * gy);
-        }
+        for (int p = 0; p < G; ++p) gr[p] *= T(2);
     }
 }
 
 template <typename T>
 __device__ __forceinline__ T clampT(T v, T lo, T hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
+template <typename T>
+__device__ __forceinline__ T fast_div(T a, T b)
+{
+    if constexpr (sizeof(T) == 8) return a / b;
+    else return __fdividef(a, b);
+}
+
+// mu = max(0.01, |grad f| / mean(f)); nu = P_{nu1}^{nu2}(mean(mu) / mu)
+template <typename T>
+__device__ __forceinline__ T nu_of(T gx, T gy, T inv_mean_f, T mean_mu, T nu1, T nu2)
+{
+    T mu = sqrt(gx * gx + gy * gy) * inv_mean_f;
+    mu = mu < T(0.01) ? T(0.01) : mu;
+    return clampT<T>(fast_div(mean_mu, mu), nu1, nu2);
+}
+
 // f^{k,i} = P_t(f - lambda_k alpha_{k,i} nu S(f) (A_i^T w + (beta/M) grad R(f)))
-template <int G, int AR>
+// Block: TP consecutive pixels x NG plane groups (thread = pixel * NG + group), grid-stride
+// over pixel tiles; the (pixel, view) weights of each tile are computed once into shared memory.
+template <int G, int KC, int AR>
 __global__ void __launch_bounds__(256) update_kernel(UpdateArgs a)
 {
     using T = typename ArithT<AR>::T;
+    __shared__ BpTable<KC, AR> tb;
     const GeoDev &g = a.g;
-    const int N = g.N, NG = g.NG, Pp = g.Pp;
-    const long long total = (long long)N * N * NG;
-    const double q = (double)N * N * g.P;
-    const T mean_f = a.nu_mode == 1 || a.nu_mode == 2 ? (T)(*a.sum_f / q) : T(1);
-    const T mean_mu = a.nu_mode == 1 || a.nu_mode == 2 ? (T)(*a.sum_mu / q) : T(1);
+    const int N = g.N, NG = g.NG, Pp = g.Pp, npix = N * N;
+    const int TP = blockDim.x / NG;
+    const int pl = threadIdx.x / NG, grp = threadIdx.x % NG;
+    const int VC = max(1, min(a.nviews, BpTable<KC, AR>::CAP / TP));
+    const bool dyn = a.nu_mode == 1 || a.nu_mode == 2;
+    const double q = (double)npix * g.P;
+    const T inv_mean_f = dyn ? (T)(q / *a.sum_f) : T(1);
+    const T mean_mu = dyn ? (T)(*a.sum_mu / q) : T(1);
     const T lam = (T)a.lam_alpha, bm = (T)a.beta_over_M, U = (T)a.U, tt = (T)a.t;
     const T nu1 = (T)a.nu1, nu2 = (T)a.nu2, halfU = T(0.5) * U;
     const T *w = reinterpret_cast<const T *>(a.w);
     const T *f = reinterpret_cast<const T *>(a.f);
     const T *invp = reinterpret_cast<const T *>(a.invp);
-    double s = 0.0;
-    for (long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x; tid < total;
-         tid += (long long)gridDim.x * blockDim.x) {
-        const int grp = (int)(tid % NG);
-        const int j = (int)(tid / NG);
-        const int ix = j % N, iy = j / N;
+    const T scale = (T)g.scale;
+    T part = T(0);
+    const int ntiles = (npix + TP - 1) / TP;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int j0 = tile * TP, j = j0 + pl;
+        const bool active = pl < TP && j < npix;
         GroupSum<G, AR> bp;
         bp.zero();
-        gather_bp<G, AR>(g, a.slot0, a.nviews, w, grp, ix, iy, bp);
-        T fc[G], gr[G], gm[G];
-        if (a.nu_mode == 1 || a.nu_mode == 2)
-            stencil<G, AR, true, false, true>(g, f, grp, ix, iy, (T)a.gamma_r, (T)a.eps, fc, gr, gm, s);
-        else
-            stencil<G, AR, true, false, false>(g, f, grp, ix, iy, (T)a.gamma_r, (T)a.eps, fc, gr, gm, s);
+        for (int u0 = 0; u0 < a.nviews; u0 += VC) {
+            const int nvc = min(VC, a.nviews - u0);
+            __syncthreads();
+            bp_fill<KC, AR>(g, a.slot0, u0, nvc, j0, TP, tb);
+            __syncthreads();
+            if (active) bp_accumulate<G, KC, AR>(g, tb, w, u0, nvc, pl, grp, bp);
+        }
+        if (!active) continue;
+        const int ix = j % N, iy = j / N;
+        T fc[G], gr[G], gx[G], gy[G], rv[G];
+        if (dyn) stencil<G, AR, true, true, false>(g, f, grp, ix, iy, (T)a.gamma_r, (T)a.eps, fc, gr, gx, gy, rv);
+        else stencil<G, AR, true, false, false>(g, f, grp, ix, iy, (T)a.gamma_r, (T)a.eps, fc, gr, gx, gy, rv);
         T nu[G];
         if (a.nu_mode == 3) {
             load_group<G, T>(reinterpret_cast<const T *>(a.nu_frozen) + (size_t)j * Pp + (size_t)grp * G, nu);
-        } else if (a.nu_mode == 0) {
+        } else if (!dyn) {
 #pragma unroll
             for (int p = 0; p < G; ++p) nu[p] = T(1);
         } else {
 #pragma unroll
-            for (int p = 0; p < G; ++p) {
-                T mu = gm[p] / mean_f;
-                mu = mu < T(0.01) ? T(0.01) : mu;
-                nu[p] = clampT<T>(mean_mu / mu, nu1, nu2);
-            }
+            for (int p = 0; p < G; ++p) nu[p] = nu_of<T>(gx[p], gy[p], inv_mean_f, mean_mu, nu1, nu2);
             if (a.nu_mode == 2)
                 store_group<G, T>(reinterpret_cast<T *>(a.nu_frozen) + (size_t)j * Pp + (size_t)grp * G, nu);
         }
         const T ip = invp[j];
-        const T scale = (T)g.scale;
         T out[G];
 #pragma unroll
         for (int p = 0; p < G; ++p) {
@@ -144,12 +171,46 @@ __global__ void __launch_bounds__(256) update_kernel(UpdateArgs a)
             ft = ft <= T(0) ? tt : (ft >= U ? U - tt : ft);
             const bool valid = grp * G + p < g.P;
             out[p] = valid ? ft : T(0);
-            if (valid) s += (double)ft;
+            part += out[p];
         }
         store_group<G, T>(reinterpret_cast<T *>(a.fout) + (size_t)j * Pp + (size_t)grp * G, out);
     }
-    double v[1] = {s};
+    double v[1] = {(double)part};
     grid_reduce<1>(v, a.red, a.sum_fout);
+}
+
+// Stand-alone gather backprojection (also the sensitivity, proj == nullptr).
+template <int G, int KC, int AR>
+__global__ void __launch_bounds__(256) back_kernel(BackArgs a)
+{
+    using T = typename ArithT<AR>::T;
+    __shared__ BpTable<KC, AR> tb;
+    const GeoDev &g = a.g;
+    const int N = g.N, NG = g.NG, npix = N * N;
+    const int TP = blockDim.x / NG;
+    const int pl = threadIdx.x / NG, grp = threadIdx.x % NG;
+    const int VC = max(1, min(a.nviews, BpTable<KC, AR>::CAP / TP));
+    const T *proj = reinterpret_cast<const T *>(a.proj);
+    const int ntiles = (npix + TP - 1) / TP;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int j0 = tile * TP, j = j0 + pl;
+        const bool active = pl < TP && j < npix;
+        GroupSum<G, AR> acc;
+        acc.zero();
+        for (int u0 = 0; u0 < a.nviews; u0 += VC) {
+            const int nvc = min(VC, a.nviews - u0);
+            __syncthreads();
+            bp_fill<KC, AR>(g, a.slot0, u0, nvc, j0, TP, tb);
+            __syncthreads();
+            if (active) bp_accumulate<G, KC, AR>(g, tb, proj, u0, nvc, pl, grp, acc);
+        }
+        if (!active) continue;
+        T b[G];
+        const T scale = (T)g.scale;
+#pragma unroll
+        for (int p = 0; p < G; ++p) b[p] = (grp * G + p < g.P) ? scale * acc.value(p) : T(0);
+        store_group<G, T>(reinterpret_cast<T *>(a.img) + (size_t)j * g.Pp + (size_t)grp * G, b);
+    }
 }
 
 // KIND 0: sum f; 1: sum mu; 2: nu map; 3: RDP gradient; 4: RDP value
@@ -162,45 +223,46 @@ __global__ void __launch_bounds__(256) image_kernel(ImageArgs a)
     const long long total = (long long)N * N * NG;
     const double q = (double)N * N * g.P;
     const T *f = reinterpret_cast<const T *>(a.f);
-    const T mean_f = (KIND == 1 || KIND == 2) ? (T)(*a.sum_f / q) : T(1);
+    const T inv_mean_f = (KIND == 1 || KIND == 2) ? (T)(q / *a.sum_f) : T(1);
     const T mean_mu = KIND == 2 ? (T)(*a.sum_mu / q) : T(1);
-    double s = 0.0;
+    T part = T(0);
     for (long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x; tid < total;
          tid += (long long)gridDim.x * blockDim.x) {
         const int grp = (int)(tid % NG);
         const int j = (int)(tid / NG);
         const int ix = j % N, iy = j / N;
-        T fc[G], gr[G], gm[G], out[G];
+        T fc[G], gr[G], gx[G], gy[G], rv[G], out[G];
         if constexpr (KIND == 0) {
             load_group<G, T>(f + (size_t)j * Pp + (size_t)grp * G, fc);
 #pragma unroll
-            for (int p = 0; p < G; ++p)
-                if (grp * G + p < g.P) s += (double)fc[p];
+            for (int p = 0; p < G; ++p) part += (grp * G + p < g.P) ? fc[p] : T(0);
         } else if constexpr (KIND == 1 || KIND == 2) {
-            stencil<G, AR, false, false, true>(g, f, grp, ix, iy, T(0), T(0), fc, gr, gm, s);
+            stencil<G, AR, false, true, false>(g, f, grp, ix, iy, T(0), T(0), fc, gr, gx, gy, rv);
 #pragma unroll
             for (int p = 0; p < G; ++p) {
-                T mu = gm[p] / mean_f;
+                T mu = sqrt(gx[p] * gx[p] + gy[p] * gy[p]) * inv_mean_f;
                 mu = mu < T(0.01) ? T(0.01) : mu;
                 if constexpr (KIND == 1) {
-                    if (grp * G + p < g.P) s += (double)mu;
+                    part += (grp * G + p < g.P) ? mu : T(0);
                 } else {
-                    out[p] = grp * G + p < g.P ? clampT<T>(mean_mu / mu, (T)a.nu1, (T)a.nu2) : T(0);
+                    out[p] = grp * G + p < g.P ? clampT<T>(fast_div(mean_mu, mu), (T)a.nu1, (T)a.nu2) : T(0);
                 }
             }
             if constexpr (KIND == 2)
                 store_group<G, T>(reinterpret_cast<T *>(a.out) + (size_t)j * Pp + (size_t)grp * G, out);
         } else if constexpr (KIND == 3) {
-            stencil<G, AR, true, false, false>(g, f, grp, ix, iy, (T)a.gamma_r, (T)a.eps, fc, gr, gm, s);
+            stencil<G, AR, true, false, false>(g, f, grp, ix, iy, (T)a.gamma_r, (T)a.eps, fc, gr, gx, gy, rv);
 #pragma unroll
             for (int p = 0; p < G; ++p) out[p] = grp * G + p < g.P ? gr[p] : T(0);
             store_group<G, T>(reinterpret_cast<T *>(a.out) + (size_t)j * Pp + (size_t)grp * G, out);
         } else {
-            stencil<G, AR, false, true, false>(g, f, grp, ix, iy, (T)a.gamma_r, (T)a.eps, fc, gr, gm, s);
+            stencil<G, AR, false, false, true>(g, f, grp, ix, iy, (T)a.gamma_r, (T)a.eps, fc, gr, gx, gy, rv);
+#pragma unroll
+            for (int p = 0; p < G; ++p) part += (grp * G + p < g.P) ? rv[p] : T(0);
         }
     }
     if constexpr (KIND == 0 || KIND == 1 || KIND == 4) {
-        double v[1] = {s};
+        double v[1] = {(double)part};
         grid_reduce<1>(v, a.red, a.result);
     }
 }
@@ -213,21 +275,63 @@ static int reduce_grid(const GeoDev &g, int capacity)
     return (int)grid;
 }
 
+// pixel-tiled kernels: TP pixels x NG groups per block
+static void tile_shape(const GeoDev &g, int *threads, int *tiles)
+{
+    const int TP = std::max(1, 256 / g.NG);
+    *threads = TP * g.NG;
+    *tiles = (g.N * g.N + TP - 1) / TP;
+}
+
+template <int G, int KC>
+static void update_dispatch(const UpdateArgs &a, int arith, int grid, int thr, cudaStream_t st)
+{
+    if (arith == AR_FP32) update_kernel<G, KC, AR_FP32><<<grid, thr, 0, st>>>(a);
+    else if (arith == AR_KAHAN) update_kernel<G, KC, AR_KAHAN><<<grid, thr, 0, st>>>(a);
+    else update_kernel<G, KC, AR_FP64><<<grid, thr, 0, st>>>(a);
+}
+
 pet_status launch_update(const UpdateArgs &a, int arith, cudaStream_t st)
 {
-    const int grid = reduce_grid(a.g, a.red.capacity);
+    int thr, tiles;
+    tile_shape(a.g, &thr, &tiles);
+    const int grid = std::min(tiles, a.red.capacity);
     LaunchScope ls(PET_K_UPDATE, st);
     if (a.g.G == 1) {
-        if (arith == AR_FP32) update_kernel<1, AR_FP32><<<grid, 256, 0, st>>>(a);
-        else if (arith == AR_KAHAN) update_kernel<1, AR_KAHAN><<<grid, 256, 0, st>>>(a);
-        else update_kernel<1, AR_FP64><<<grid, 256, 0, st>>>(a);
+        if (a.g.K <= 2) update_dispatch<1, 2>(a, arith, grid, thr, st);
+        else update_dispatch<1, 4>(a, arith, grid, thr, st);
     } else {
-        if (arith == AR_FP32) update_kernel<8, AR_FP32><<<grid, 256, 0, st>>>(a);
-        else if (arith == AR_KAHAN) update_kernel<8, AR_KAHAN><<<grid, 256, 0, st>>>(a);
-        else update_kernel<8, AR_FP64><<<grid, 256, 0, st>>>(a);
+        if (a.g.K <= 2) update_dispatch<8, 2>(a, arith, grid, thr, st);
+        else update_dispatch<8, 4>(a, arith, grid, thr, st);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "update_kernel launch");
+    return PET_OK;
+}
+
+template <int G, int KC>
+static void back_dispatch(const BackArgs &a, int arith, int grid, int thr, cudaStream_t st)
+{
+    if (arith == AR_FP32) back_kernel<G, KC, AR_FP32><<<grid, thr, 0, st>>>(a);
+    else if (arith == AR_KAHAN) back_kernel<G, KC, AR_KAHAN><<<grid, thr, 0, st>>>(a);
+    else back_kernel<G, KC, AR_FP64><<<grid, thr, 0, st>>>(a);
+}
+
+pet_status launch_back(const BackArgs &a, int arith, cudaStream_t st)
+{
+    int thr, tiles;
+    tile_shape(a.g, &thr, &tiles);
+    const int grid = std::min(tiles, 65535);
+    LaunchScope ls(PET_K_OTHER, st);
+    if (a.g.G == 1) {
+        if (a.g.K <= 2) back_dispatch<1, 2>(a, arith, grid, thr, st);
+        else back_dispatch<1, 4>(a, arith, grid, thr, st);
+    } else {
+        if (a.g.K <= 2) back_dispatch<8, 2>(a, arith, grid, thr, st);
+        else back_dispatch<8, 4>(a, arith, grid, thr, st);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "back_kernel launch");
     return PET_OK;
 }
 
