@@ -192,6 +192,77 @@ pet_status pet_objective(const pet_geometry *g, const int32_t *d_counts, const f
                          double *h_phi, double *h_parts, void *stream);
 
 /* ------------------------------------------------------------------------------------------
+ * Batches (Table I for many independent scans at once; no counterpart in the paper).
+ * A batch holds up to `capacity` reconstruction states of any geometries.  pet_batch_step
+ * advances every running state of the batch by one subiteration: scans sharing one kernel
+ * instantiation (plane-group size, precision) are processed by one persistent kernel per step
+ * kind (mu pass, forward + ratio, fused update, objective projection, RDP value); with
+ * use_graph != 0 and a non-default stream, each class's step is captured once as a CUDA graph
+ * and replayed.  A state runs until it has done params.iterations x M subiterations; with
+ * with_objective, Phi(f^k) is recorded for k = 0..T (read it with pet_state_objective_history).
+ * Results of a scan are bitwise the same alone (pet_subiter) and in any batch.
+ * pet_batch_add: the state joins at its current subiteration (Phi(f^0) is enqueued on `stream`
+ *   when requested and J = 0); PET_ERR_OOM if the batch is full.
+ * pet_batch_step: *running_after (optional) = states still running after this step.  The step is
+ *   asynchronous; the host waits only to reuse its double-buffered descriptor memory.
+ * pet_batch_remove: detach a state (waits for in-flight steps that read its descriptors).
+ * pet_batch_size: running states.  The batch does not own the states.
+ * pet_state_objective_history: h_obj[k] = Phi(f^k) for k = 0..T recorded so far (synchronises);
+ *   entries not computed yet are NaN.
+ * ---------------------------------------------------------------------------------------- */
+typedef struct pet_batch pet_batch;
+pet_status pet_batch_create(int capacity, int use_graph, pet_batch **out);
+pet_status pet_batch_add(pet_batch *b, pet_state *s, int with_objective, void *stream);
+pet_status pet_batch_remove(pet_batch *b, pet_state *s);
+pet_status pet_batch_step(pet_batch *b, void *stream, int *running_after);
+int pet_batch_size(const pet_batch *b);
+void pet_batch_destroy(pet_batch *b);
+pet_status pet_state_objective_history(pet_state *s, double *h_obj, void *stream);
+
+/* ------------------------------------------------------------------------------------------
+ * Serving (continuous batching of reconstruction requests; no counterpart in the paper).
+ * pet_serve_create: a server on CUDA device `device` with a device-memory budget (bytes, for
+ *   scan states, geometry tables and upload staging) and at most `max_slots` scans resident at
+ *   once.  It runs two host threads: a preparer that admits queued requests in arrival order
+ *   while slots and the budget allow (geometry tables cached by description; upload; resident
+ *   state), and a runner that keeps one pet_batch of all resident scans stepping: requests that
+ *   arrive while others are on the GPU join at the next step; finished scans are read back and
+ *   their memory and slot freed.
+ * pet_serve_submit: copies the request's host data (validated: counts >= 0, 0 < gamma < inf)
+ *   and returns a ticket; the caller may free its buffers on return.  A request larger than the
+ *   whole budget fails with PET_ERR_OOM (reported by poll).
+ * pet_serve_poll: PET_PENDING while queued or running; otherwise the request's final status,
+ *   with f^T copied to h_img_out (float [P][N][N], may be NULL), Phi(f^k) k = 0..T to h_obj_out
+ *   (T+1 doubles, NaN without with_objective; may be NULL) and *latency_s = seconds from submit
+ *   to result available; the ticket is then forgotten (PET_ERR_NOT_FOUND afterwards).
+ * pet_serve_stats_get: counters, p50/p99/mean latency of completed requests, scans/s from first
+ *   submit to last completion, device bytes in use.
+ * pet_serve_destroy: drops queued requests, finishes resident ones, joins the threads.
+ * Thread-safe: submit/poll/stats may be called from any host thread.
+ * ---------------------------------------------------------------------------------------- */
+typedef struct {
+    pet_geometry_desc geom;
+    const int32_t *h_counts;     /* [P][V][n_b] */
+    const float *h_gamma;        /* [P][V][n_b] */
+    const float *h_img_init;     /* [P][N][N], or NULL for f^0 = 1 */
+    pet_params params;
+    int with_objective;
+} pet_request;
+
+typedef struct {
+    long long submitted, completed, failed, running, queued;
+    double p50_s, p99_s, mean_s, scans_per_s;
+    size_t hbm_in_use;
+} pet_serve_stats;
+
+pet_status pet_serve_create(size_t hbm_budget_bytes, int max_slots, int device, pet_server **out);
+pet_status pet_serve_submit(pet_server *sv, const pet_request *req, uint64_t *ticket);
+pet_status pet_serve_poll(pet_server *sv, uint64_t ticket, float *h_img_out, double *h_obj_out,
+                          double *latency_s);
+pet_status pet_serve_stats_get(pet_server *sv, pet_serve_stats *out);
+void pet_serve_destroy(pet_server *sv);
+
+/* ------------------------------------------------------------------------------------------
  * pet_objective_static: the same values as pet_objective, from a call that allocates nothing.
  * The paper has no counterpart; this serves callers that may not allocate device memory at the
  * moment they need the objective: a pipeline whose device memory is handed to a fixed pool at

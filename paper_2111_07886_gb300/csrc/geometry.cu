@@ -198,7 +198,7 @@ static pet_status geometry_init(pet_geometry *g, cudaStream_t st)
     PET_CUDA(cudaMalloc(&g->d_sums, 16 * sizeof(double)));
     // sensitivity: one FP64 backprojection of ones over all views, single plane
     double *bp = nullptr;
-    PET_CUDA(cudaMalloc(&bp, sizeof(double) * npix));
+    PET_CUDA(cudaMallocAsync((void **)&bp, sizeof(double) * npix, st));
     BackArgs ba;
     ba.g = gd;
     ba.g.P = 1; ba.g.Pp = 1; ba.g.G = 1; ba.g.NG = 1;
@@ -214,8 +214,8 @@ static pet_status geometry_init(pet_geometry *g, cudaStream_t st)
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) s = cuda_fail(e, "finish_sensitivity");
     }
+    cudaFreeAsync(bp, st);
     cudaError_t e = cudaStreamSynchronize(st);
-    cudaFree(bp);
     if (s != PET_OK) return s;
     if (e != cudaSuccess) return cuda_fail(e, "pet_geometry_create");
     return PET_OK;
@@ -234,6 +234,11 @@ extern "C" pet_status pet_geometry_create(const pet_geometry_desc *desc, void *s
         return fail(PET_ERR_INVALID, "pet_geometry_create: invalid geometry description "
                                      "(need n in [1,8192], nplanes, nviews, nbins >= 1, "
                                      "1 <= nsubsets <= nviews, pixel_mm, bin_mm, sens > 0)");
+    if (d.nplanes > 2048)
+        return fail(PET_ERR_INVALID, "pet_geometry_create: at most 2048 planes");
+    if (d.bin_mm < 0.36 * d.pixel_mm)
+        return fail(PET_ERR_INVALID, "pet_geometry_create: bin_mm must be >= 0.36 pixel_mm "
+                                     "(at most 4 rays of one view cross a pixel)");
     if ((double)d.n * d.n * ((d.nplanes + 7) / 8 * 8) > 4.0e9 ||
         (double)d.nviews * d.nbins * ((d.nplanes + 7) / 8 * 8) > 4.0e9)
         return fail(PET_ERR_INVALID, "pet_geometry_create: problem too large (> 4e9 elements)");

@@ -339,14 +339,14 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double (*sh)[32])
     }
 }
 
+// Reduction over the nblocks virtual blocks of one scan; bid is this virtual block's index.
 template <int NV>
-__device__ void grid_reduce(double (&v)[NV], const Reducer &red, double *result)
+__device__ void grid_reduce(double (&v)[NV], const Reducer &red, double *result, int bid,
+                            int nblocks)
 {
     __shared__ double sh[NV][32];
     __shared__ bool last;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    const int nblocks = gridDim.x * gridDim.y * gridDim.z;
-    const int bid = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     block_sum<NV>(v, sh);
     if (tid == 0) {
 #pragma unroll
@@ -371,6 +371,39 @@ __device__ void grid_reduce(double (&v)[NV], const Reducer &red, double *result)
         for (int k = 0; k < NV; ++k) result[k] = acc[k];
         *red.ticket = 0u;
     }
+    __syncthreads();
+}
+
+template <int NV>
+__device__ void grid_reduce(double (&v)[NV], const Reducer &red, double *result)
+{
+    grid_reduce<NV>(v, red, result,
+                    (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x,
+                    gridDim.x * gridDim.y * gridDim.z);
+}
+
+// Virtual-block dispatch: returns the arguments of the scan owning virtual block vb and its
+// index / count within that scan.
+template <class A>
+__device__ __forceinline__ const A *scan_of(const A &one, const Batch &b, int vb, int &local,
+                                            int &count)
+{
+    if (b.nscans == 0) { local = vb; count = one.nvb; return &one; }
+    int lo = 0, hi = b.nscans;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(&b.prefix[mid]) <= vb) lo = mid;
+        else hi = mid;
+    }
+    local = vb - __ldg(&b.prefix[lo]);
+    count = __ldg(&b.prefix[lo + 1]) - __ldg(&b.prefix[lo]);
+    return reinterpret_cast<const A *>(b.args) + lo;
+}
+
+template <class A>
+__device__ __forceinline__ int total_vblocks(const A &one, const Batch &b)
+{
+    return b.nscans == 0 ? one.nvb : __ldg(&b.prefix[b.nscans]);
 }
 
 }  // namespace pet

@@ -63,6 +63,15 @@ __global__ void sino_from_internal(const E *src, E *dst, const int *view_of_slot
     dst[((size_t)p * nviews + v) * NB + b] = src[(size_t)rb * Pp + p];
 }
 
+// ones in the valid planes, zero in the pad planes
+template <typename D>
+__global__ void img_ones_internal(D *dst, long long n, int P, int Pp)
+{
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= n) return;
+    dst[tid] = (int)(tid % Pp) < P ? (D)1 : (D)0;
+}
+
 __global__ void check_data(const int *counts, const float *gamma, size_t n, int *flag)
 {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -131,6 +140,16 @@ pet_status from_internal_sino(const GeoDev &g, const int *d_view_of_slot, int nv
     else sino_from_internal<float><<<blocks(n), 256, 0, st>>>((const float *)src, (float *)dst, d_view_of_slot, nviews, g.NB, g.P, g.Pp);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? PET_OK : cuda_fail(e, "sino_from_internal");
+}
+
+pet_status fill_internal_ones(const GeoDev &g, void *dst, int is_double, cudaStream_t st)
+{
+    const long long n = (long long)g.N * g.N * g.Pp;
+    LaunchScope ls(PET_K_LAYOUT, st);
+    if (is_double) img_ones_internal<double><<<blocks(n), 256, 0, st>>>((double *)dst, n, g.P, g.Pp);
+    else img_ones_internal<float><<<blocks(n), 256, 0, st>>>((float *)dst, n, g.P, g.Pp);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? PET_OK : cuda_fail(e, "img_ones_internal");
 }
 
 pet_status validate_data(const GeoDev &g, const int *counts, const float *gamma, size_t n,

@@ -99,6 +99,14 @@ struct pet_geometry {
 namespace pet {
 
 // kernels implemented in project.cu / update.cu, launched from the host files
+// A launch over several scans: the virtual blocks of scan s are [prefix[s], prefix[s+1]);
+// a persistent grid strides over all of them.  nscans == 0 means a single scan passed by value.
+struct Batch {
+    const void *args;          // device array of per-scan argument structs
+    const int *prefix;         // device, nscans + 1 entries
+    int nscans;
+    int grid;                  // CTAs of the persistent grid
+};
 struct FwdArgs {
     GeoDev g;
     int slot0;                 // first sorted view slot of the subset
@@ -109,19 +117,27 @@ struct FwdArgs {
     const float *gamma;        // [nviews*NB][Pp]
     Reducer red;               // objective mode
     double *result;            // objective mode: 2 doubles (sum y, sum g ln(y + gamma))
+    int S, R;                  // launch shape: chunks per ray, rays per ray tile
+    int tpv;                   // ray tiles per virtual block
+    int nvb;                   // virtual blocks of this scan
 };
 
 enum FwdMode { FWD_PLAIN = 0, FWD_RATIO = 1, FWD_OBJECTIVE = 2 };
 enum Arith { AR_FP32 = 0, AR_KAHAN = 1, AR_FP64 = 2 };
 
 pet_status launch_forward(const FwdArgs &a, int mode, int arith, cudaStream_t st);
+void forward_shape(FwdArgs &a, int mode);                 // fills S, R, nvb
+pet_status launch_forward_batch(const FwdArgs &shape, const Batch &b, int mode, int arith,
+                                cudaStream_t st);
 
 struct BackArgs {
     GeoDev g;
     int slot0, nviews;
     const void *proj;          // [nviews*NB][Pp]; NULL = ones (sensitivity)
     void *img;                 // [N*N][Pp] out
+    int nvb;
 };
+
 pet_status launch_back(const BackArgs &a, int arith, cudaStream_t st);
 
 struct UpdateArgs {
@@ -131,6 +147,7 @@ struct UpdateArgs {
     const void *f;             // f^{k,i-1} [N*N][Pp]
     void *fout;                // f^{k,i}
     const void *invp;          // [N*N] (float or double)
+    double invp_scale;         // multiplies invp (a scan whose sens differs from the geometry's)
     void *nu_frozen;           // [N*N][Pp]
     int nu_mode;               // 0: nu = 1, 1: from f, 2: from f and stored, 3: frozen
     double lam_alpha;          // lambda_k alpha_{k,i}
@@ -139,8 +156,13 @@ struct UpdateArgs {
     const double *sum_mu;      // sum of mu (FP64, device)
     double *sum_fout;          // sum of f^{k,i} (FP64, device, written)
     Reducer red;
+    int tpv;                   // pixel tiles per virtual block
+    int nvb;                   // virtual blocks of this scan
 };
 pet_status launch_update(const UpdateArgs &a, int arith, cudaStream_t st);
+void update_shape(UpdateArgs &a);                          // fills nvb
+pet_status launch_update_batch(const UpdateArgs &shape, const Batch &b, int arith,
+                               cudaStream_t st);
 
 struct ImageArgs {
     GeoDev g;
@@ -151,12 +173,66 @@ struct ImageArgs {
     const double *sum_mu;      // nu map: sum of mu
     double *result;            // reductions
     Reducer red;
+    int ipt, nvb;              // items per thread, virtual blocks of this scan
 };
 pet_status launch_sum(const ImageArgs &a, int arith, cudaStream_t st);        // result[0] = sum f
 pet_status launch_mu_sum(const ImageArgs &a, int arith, cudaStream_t st);     // result[0] = sum mu
 pet_status launch_nu_map(const ImageArgs &a, int arith, cudaStream_t st);     // out = nu
 pet_status launch_rdp_grad(const ImageArgs &a, int arith, cudaStream_t st);   // out = grad R
 pet_status launch_rdp_value(const ImageArgs &a, int arith, cudaStream_t st);  // result[0] = R
+void image_shape(ImageArgs &a);                            // fills ipt, nvb
+pet_status launch_mu_sum_batch(const ImageArgs &shape, const Batch &b, int arith, cudaStream_t st);
+pet_status launch_rdp_value_batch(const ImageArgs &shape, const Batch &b, int arith,
+                                  cudaStream_t st);
+
+// per-scan reconstruction state (state.cu)
+}  // namespace pet
+struct pet_state {
+    const pet_geometry *g = nullptr;
+    pet_params prm{};
+    int arith = pet::AR_KAHAN;
+    size_t esz = 4;                 // bytes per image / ratio element
+    void *f[2] = {nullptr, nullptr};
+    int cur = 0;
+    void *w = nullptr;              // ratio term of the largest subset
+    int *counts = nullptr;          // [V][NB][Pp], views sorted by subset
+    float *gamma = nullptr;
+    void *nu_frozen = nullptr;
+    bool have_frozen = false;
+    double *sums = nullptr;         // [0..1] sum f (ping-pong), [2] sum mu, [3..5] objective
+    double *objhist = nullptr;      // [(T+1) * 3] objective parts per outer iteration
+    int objcap = 0;
+    pet::Reducer red{};
+    void *redmem = nullptr;
+    int *flag = nullptr;
+    int k = 0, i = 0, J = 0;        // next subiteration is (k, i+1) of the paper; J done
+    double tn = 1.0;                // Nesterov t_{k,i}
+    double sens_ratio = 1.0;        // this scan's sens / the geometry's sens (A and p scale with it)
+    cudaStream_t alloc_stream = nullptr;   // non-null: buffers are stream-ordered allocations
+    size_t q_bytes = 0, sino_elems = 0, w_bytes = 0;
+};
+
+namespace pet {
+
+struct SubiterPlan {
+    int arith;
+    bool mu;                   // mu pass needed (dynamic nu)
+    ImageArgs mu_args;
+    FwdArgs fwd;               // subset forward projection + ratio
+    UpdateArgs upd;            // fused update
+    bool objective;            // Phi(f^{k+1}) after this subiteration
+    FwdArgs obj_fwd;
+    ImageArgs obj_rdp;
+};
+void plan_subiter(pet_state *s, SubiterPlan *pl, bool with_objective);
+pet_status state_create_loaded(const pet_geometry *g, double sens, const int32_t *d_counts,
+                               const float *d_gamma, const float *d_img, const pet_params *p,
+                               cudaStream_t st, pet_state **out);
+size_t state_bytes(const pet_geometry *g, int precision, int iterations);
+void state_release(pet_state *s, cudaStream_t st);
+pet_status check_params(const pet_params *p);
+pet_status fill_internal_ones(const GeoDev &g, void *dst, int is_double, cudaStream_t st);
+void objective_args(pet_state *s, double *out3, FwdArgs *fa, ImageArgs *ra);
 
 // layout conversions (layout.cu)
 pet_status to_internal_image(const GeoDev &g, const void *src, void *dst, int src_is_double,

@@ -14,29 +14,36 @@
 
 namespace pet {
 
-// Thread layout: block = R rays x S chunks x NG plane groups (thread = (ray * S + chunk) * NG +
-// group).  Chunk c walks driving steps [c Lc, (c + 1) Lc) of its ray, Lc = ceil(nd / S), so that
-// short subsets still fill the GPU; the S partial sums of a (ray, group) are combined in chunk
-// order through shared memory (deterministic).  Rays are taken in tiles of R, grid-stride.
+// Thread layout: a virtual block is R rays x S chunks x NG plane groups (thread = (ray * S +
+// chunk) * NG + group; threads beyond R S NG idle).  Chunk c walks driving steps
+// [c Lc, (c + 1) Lc) of its ray, Lc = ceil(nd / S), so that short subsets still fill the GPU; the
+// S partial sums of a (ray, group) are combined in chunk order through shared memory
+// (deterministic).  A persistent grid strides over the virtual blocks of one scan or a batch.
 template <int G, int AR, int MODE>
-__global__ void __launch_bounds__(256) fwd_kernel(FwdArgs a, int S, int R)
+__global__ void __launch_bounds__(256) fwd_kernel(const __grid_constant__ FwdArgs one, const Batch bt)
 {
     using T = typename ArithT<AR>::T;
     __shared__ T comb_s[256 * G];
     __shared__ T comb_e[256 * G];
-    const GeoDev &g = a.g;
-    const int NG = g.NG, NB = g.NB, N = g.N, Pp = g.Pp;
-    const int nrays = a.nviews * NB;
-    const int grp = threadIdx.x % NG;
-    const int c = (threadIdx.x / NG) % S;
-    const int rl = threadIdx.x / (NG * S);
-    double obj[2] = {0.0, 0.0};
-    const int ntiles = (nrays + R - 1) / R;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int total = total_vblocks(one, bt);
+    for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
+        int vloc, nv;
+        const FwdArgs &a = *scan_of(one, bt, vb, vloc, nv);
+        const GeoDev &g = a.g;
+        const int NG = g.NG, NB = g.NB, N = g.N, Pp = g.Pp, S = a.S, R = a.R;
+        const int nrays = a.nviews * NB;
+        const int ntiles = (nrays + R - 1) / R;
+        const bool lane_ok = (int)threadIdx.x < R * S * NG;
+        double obj[2] = {0.0, 0.0};
+        for (int tile = vloc * a.tpv; tile < min(ntiles, (vloc + 1) * a.tpv); ++tile) {
+        const int grp = threadIdx.x % NG;
+        const int c = (threadIdx.x / NG) % S;
+        const int rl = threadIdx.x / (NG * S);
         const int ray = tile * R + rl;               // subset-local ray index u * NB + b
+        const bool live = lane_ok && ray < nrays;
         GroupSum<G, AR> acc;
         acc.zero();
-        if (ray < nrays) {
+        if (live) {
             const int slot = a.slot0 + ray / NB;
             const ViewGeo &vw = g.views[slot];
             const RayGeo &rg = g.rays[(size_t)a.slot0 * NB + ray];
@@ -90,16 +97,16 @@ __global__ void __launch_bounds__(256) fwd_kernel(FwdArgs a, int S, int R)
             __syncthreads();
 #pragma unroll
             for (int p = 0; p < G; ++p) {
-                comb_s[threadIdx.x * G + p] = acc.s[p];
-                comb_e[threadIdx.x * G + p] = acc.e[p];
+                comb_s[p * 256 + threadIdx.x] = acc.s[p];
+                comb_e[p * 256 + threadIdx.x] = acc.e[p];
             }
             __syncthreads();
-            if (c == 0) {
 #pragma unroll
-                for (int p = 0; p < G; ++p) {
-                    T s0 = acc.s[p], e0 = acc.e[p];
+            for (int p = 0; p < G; ++p) {
+                T s0 = acc.s[p], e0 = acc.e[p];
+                if (c == 0 && lane_ok) {            // idle lanes (>= R S NG) have no chunks
                     for (int cc = 1; cc < S; ++cc) {
-                        const int o = ((rl * S + cc) * NG + grp) * G + p;
+                        const int o = p * 256 + (rl * S + cc) * NG + grp;
                         if constexpr (AR == AR_KAHAN) {
                             const T y = comb_s[o] + (comb_e[o] + e0);
                             const T t = s0 + y;
@@ -109,71 +116,72 @@ __global__ void __launch_bounds__(256) fwd_kernel(FwdArgs a, int S, int R)
                             s0 += comb_s[o];
                         }
                     }
-                    tot[p] = s0 + e0;
                 }
+                tot[p] = s0 + e0;
             }
         } else {
 #pragma unroll
             for (int p = 0; p < G; ++p) tot[p] = acc.value(p);
         }
-        if (c != 0 || ray >= nrays) continue;
-        const size_t o = (size_t)ray * Pp + (size_t)grp * G;
-        const T scale = (T)g.scale;
-        if constexpr (MODE == FWD_PLAIN) {
-            T y[G];
+        if (live && c == 0) {
+            const size_t o = (size_t)ray * Pp + (size_t)grp * G;
+            const T scale = (T)g.scale;
+            if constexpr (MODE == FWD_PLAIN) {
+                T y[G];
 #pragma unroll
-            for (int p = 0; p < G; ++p) y[p] = scale * tot[p];
-            store_group<G, T>(reinterpret_cast<T *>(a.out) + o, y);
-        } else {
-            int cnt[G];
-            float gam[G];
-            load_group_i<G>(a.counts + o, cnt);
-            load_group<G, float>(a.gamma + o, gam);
-            if constexpr (MODE == FWD_RATIO) {
-                T w[G];
-#pragma unroll
-                for (int p = 0; p < G; ++p) {
-                    const T y = scale * tot[p] + (T)gam[p];
-                    w[p] = (grp * G + p < g.P) ? T(1) - (T)cnt[p] / y : T(0);
-                }
-                store_group<G, T>(reinterpret_cast<T *>(a.out) + o, w);
+                for (int p = 0; p < G; ++p) y[p] = scale * tot[p];
+                store_group<G, T>(reinterpret_cast<T *>(a.out) + o, y);
             } else {
-                T s_af = T(0), s_gl = T(0);
+                int cnt[G];
+                float gam[G];
+                load_group_i<G>(a.counts + o, cnt);
+                load_group<G, float>(a.gamma + o, gam);
+                if constexpr (MODE == FWD_RATIO) {
+                    T w[G];
 #pragma unroll
-                for (int p = 0; p < G; ++p) {
-                    if (grp * G + p < g.P) {
-                        const T af = scale * tot[p];
-                        s_af += af;
-                        if (cnt[p] != 0) s_gl += (T)cnt[p] * log(af + (T)gam[p]);
+                    for (int p = 0; p < G; ++p) {
+                        const T y = scale * tot[p] + (T)gam[p];
+                        w[p] = (grp * G + p < g.P) ? T(1) - (T)cnt[p] / y : T(0);
                     }
+                    store_group<G, T>(reinterpret_cast<T *>(a.out) + o, w);
+                } else {
+                    T s_af = T(0), s_gl = T(0);
+#pragma unroll
+                    for (int p = 0; p < G; ++p) {
+                        if (grp * G + p < g.P) {
+                            const T af = scale * tot[p];
+                            s_af += af;
+                            if (cnt[p] != 0) s_gl += (T)cnt[p] * log(af + (T)gam[p]);
+                        }
+                    }
+                    obj[0] += (double)s_af;
+                    obj[1] += (double)s_gl;
                 }
-                obj[0] += (double)s_af;
-                obj[1] += (double)s_gl;
             }
         }
+        }  // tiles of this virtual block
+        if constexpr (MODE == FWD_OBJECTIVE) grid_reduce<2>(obj, a.red, a.result, vloc, nv);
     }
-    if constexpr (MODE == FWD_OBJECTIVE) grid_reduce<2>(obj, a.red, a.result);
 }
 
 template <int G, int AR>
-static void fwd_dispatch_mode(const FwdArgs &a, int mode, int grid, int thr, int S, int R,
-                              cudaStream_t st)
+static void fwd_dispatch_mode(const FwdArgs &a, const Batch &b, int mode, int grid, cudaStream_t st)
 {
-    if (mode == FWD_PLAIN) fwd_kernel<G, AR, FWD_PLAIN><<<grid, thr, 0, st>>>(a, S, R);
-    else if (mode == FWD_RATIO) fwd_kernel<G, AR, FWD_RATIO><<<grid, thr, 0, st>>>(a, S, R);
-    else fwd_kernel<G, AR, FWD_OBJECTIVE><<<grid, thr, 0, st>>>(a, S, R);
+    if (mode == FWD_PLAIN) fwd_kernel<G, AR, FWD_PLAIN><<<grid, 256, 0, st>>>(a, b);
+    else if (mode == FWD_RATIO) fwd_kernel<G, AR, FWD_RATIO><<<grid, 256, 0, st>>>(a, b);
+    else fwd_kernel<G, AR, FWD_OBJECTIVE><<<grid, 256, 0, st>>>(a, b);
 }
 
 template <int G>
-static void fwd_dispatch(const FwdArgs &a, int mode, int arith, int grid, int thr, int S, int R,
+static void fwd_dispatch(const FwdArgs &a, const Batch &b, int mode, int arith, int grid,
                          cudaStream_t st)
 {
-    if (arith == AR_FP32) fwd_dispatch_mode<G, AR_FP32>(a, mode, grid, thr, S, R, st);
-    else if (arith == AR_KAHAN) fwd_dispatch_mode<G, AR_KAHAN>(a, mode, grid, thr, S, R, st);
-    else fwd_dispatch_mode<G, AR_FP64>(a, mode, grid, thr, S, R, st);
+    if (arith == AR_FP32) fwd_dispatch_mode<G, AR_FP32>(a, b, mode, grid, st);
+    else if (arith == AR_KAHAN) fwd_dispatch_mode<G, AR_KAHAN>(a, b, mode, grid, st);
+    else fwd_dispatch_mode<G, AR_FP64>(a, b, mode, grid, st);
 }
 
-static int sm_count()
+int sm_count()
 {
     static int n = 0;
     if (n == 0) {
@@ -185,26 +193,54 @@ static int sm_count()
     return n;
 }
 
-pet_status launch_forward(const FwdArgs &a, int mode, int arith, cudaStream_t st)
+// Chunks per ray (S) so that one subset projection has about one full-occupancy wave of
+// threads, with >= 16 driving steps per chunk; R rays per 256-thread virtual block.  The
+// objective mode uses virtual blocks of several ray tiles so that it never needs more partial
+// sums than its reducer holds.
+void forward_shape(FwdArgs &a, int mode)
 {
     const long long nrays = (long long)a.nviews * a.g.NB;
-    if (nrays == 0) return PET_OK;
-    // chunks per ray: enough threads for ~one full-occupancy wave, >= 16 steps per chunk
     const long long want = (long long)sm_count() * 2048;
-    const long long have = nrays * a.g.NG;
+    const long long have = std::max<long long>(1, nrays * a.g.NG);
     int S = (int)std::min<long long>(8, std::max<long long>(1, (want + have - 1) / have));
     S = std::max(1, std::min(S, a.g.N / 16));
-    const int R = std::max(1, 256 / (S * a.g.NG));
-    const int thr = R * S * a.g.NG;
-    long long grid = (nrays + R - 1) / R;
-    if (mode == FWD_OBJECTIVE && grid > a.red.capacity) grid = a.red.capacity;
-    if (grid > 1 << 30) grid = 1 << 30;
+    while (S > 1 && (256 / a.g.NG) % S) --S;          // S divides the rays-per-block budget
+    a.S = S;
+    a.R = std::max(1, 256 / (S * a.g.NG));
+    const long long ntiles = (nrays + a.R - 1) / a.R;
+    a.tpv = 1;
+    if (mode == FWD_OBJECTIVE && a.red.capacity > 0 && ntiles > a.red.capacity)
+        a.tpv = (int)((ntiles + a.red.capacity - 1) / a.red.capacity);
+    a.nvb = (int)((ntiles + a.tpv - 1) / a.tpv);
+}
+
+pet_status launch_forward(const FwdArgs &a0, int mode, int arith, cudaStream_t st)
+{
+    FwdArgs a = a0;
+    const long long nrays = (long long)a.nviews * a.g.NB;
+    if (nrays == 0) return PET_OK;
+    forward_shape(a, mode);
+    const int grid = std::max(1, std::min(a.nvb, sm_count() * 8));
+    Batch b{nullptr, nullptr, 0, grid};
     LaunchScope ls(mode == FWD_RATIO ? PET_K_FORWARD_RATIO
                    : (mode == FWD_OBJECTIVE ? PET_K_OBJ_FORWARD : PET_K_OTHER), st);
-    if (a.g.G == 1) fwd_dispatch<1>(a, mode, arith, (int)grid, thr, S, R, st);
-    else fwd_dispatch<8>(a, mode, arith, (int)grid, thr, S, R, st);
+    if (a.g.G == 1) fwd_dispatch<1>(a, b, mode, arith, grid, st);
+    else fwd_dispatch<8>(a, b, mode, arith, grid, st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "fwd_kernel launch");
+    return PET_OK;
+}
+
+// Batched launch: all scans share the plane-group size of `shape` (G and the kernel template).
+pet_status launch_forward_batch(const FwdArgs &shape, const Batch &b, int mode, int arith,
+                                cudaStream_t st)
+{
+    LaunchScope ls(mode == FWD_RATIO ? PET_K_FORWARD_RATIO
+                   : (mode == FWD_OBJECTIVE ? PET_K_OBJ_FORWARD : PET_K_OTHER), st);
+    if (shape.g.G == 1) fwd_dispatch<1>(shape, b, mode, arith, b.grid, st);
+    else fwd_dispatch<8>(shape, b, mode, arith, b.grid, st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "fwd_kernel batch launch");
     return PET_OK;
 }
 

@@ -17,32 +17,9 @@
 
 using namespace pet;
 
-struct pet_state {
-    const pet_geometry *g = nullptr;
-    pet_params prm{};
-    int arith = AR_KAHAN;
-    size_t esz = 4;                 // bytes per image / ratio element
-    void *f[2] = {nullptr, nullptr};
-    int cur = 0;
-    void *w = nullptr;              // ratio term of the largest subset
-    int *counts = nullptr;          // [V][NB][Pp], views sorted by subset
-    float *gamma = nullptr;
-    void *nu_frozen = nullptr;
-    bool have_frozen = false;
-    double *sums = nullptr;         // [0..1] sum f (ping-pong), [2] sum mu, [3..5] objective
-    double *objhist = nullptr;      // [(T+1) * 3] objective parts per outer iteration
-    int objcap = 0;
-    Reducer red{};
-    void *redmem = nullptr;
-    int *flag = nullptr;
-    int k = 0, i = 0, J = 0;        // next subiteration is (k, i+1) of the paper; J done
-    double tn = 1.0;                // Nesterov t_{k,i}
-    size_t q_bytes = 0, sino_elems = 0, w_bytes = 0;
-};
+static const int kRedCap = 4096;   // reduction partials per scan
 
-static const int kRedCap = 4096;
-
-static pet_status check_params(const pet_params *p)
+pet_status pet::check_params(const pet_params *p)
 {
     if (!p) return fail(PET_ERR_INVALID, "pet_params is NULL");
     if (p->iterations < 0 || !(p->beta >= 0) || !(p->gamma_r >= 0) || !(p->eps > 0) ||
@@ -60,16 +37,21 @@ static pet_status check_params(const pet_params *p)
 static void state_free(pet_state *s)
 {
     if (!s) return;
-    cudaFree(s->f[0]);
-    cudaFree(s->f[1]);
-    cudaFree(s->w);
-    cudaFree(s->counts);
-    cudaFree(s->gamma);
-    cudaFree(s->nu_frozen);
-    cudaFree(s->sums);
-    cudaFree(s->objhist);
-    cudaFree(s->redmem);
-    cudaFree(s->flag);
+    auto rel = [&](void *p) {
+        if (!p) return;
+        if (s->alloc_stream) cudaFreeAsync(p, s->alloc_stream);
+        else cudaFree(p);
+    };
+    rel(s->f[0]);
+    rel(s->f[1]);
+    rel(s->w);
+    rel(s->counts);
+    rel(s->gamma);
+    rel(s->nu_frozen);
+    rel(s->sums);
+    rel(s->objhist);
+    rel(s->redmem);
+    rel(s->flag);
     s->f[0] = s->f[1] = s->w = s->nu_frozen = s->redmem = nullptr;
     s->counts = nullptr;
     s->gamma = nullptr;
@@ -98,19 +80,24 @@ static pet_status state_alloc(pet_state *s, const pet_geometry *g, int arith, in
     s->q_bytes = q_bytes;
     s->w_bytes = w_bytes;
     s->sino_elems = sino;
-    PET_CUDA(cudaMalloc(&s->f[0], q_bytes));
-    PET_CUDA(cudaMalloc(&s->f[1], q_bytes));
-    PET_CUDA(cudaMalloc(&s->w, w_bytes));
-    PET_CUDA(cudaMalloc(&s->counts, sino * sizeof(int)));
-    PET_CUDA(cudaMalloc(&s->gamma, sino * sizeof(float)));
-    PET_CUDA(cudaMalloc(&s->nu_frozen, q_bytes));
-    PET_CUDA(cudaMalloc(&s->sums, 16 * sizeof(double)));
+    cudaStream_t as = s->alloc_stream;
+    auto get = [&](void **p, size_t n) -> cudaError_t {
+        return as ? cudaMallocAsync(p, n, as) : cudaMalloc(p, n);
+    };
+    PET_CUDA(get(&s->f[0], q_bytes));
+    PET_CUDA(get(&s->f[1], q_bytes));
+    PET_CUDA(get(&s->w, w_bytes));
+    PET_CUDA(get((void **)&s->counts, sino * sizeof(int)));
+    PET_CUDA(get((void **)&s->gamma, sino * sizeof(float)));
+    PET_CUDA(get(&s->nu_frozen, q_bytes));
+    PET_CUDA(get((void **)&s->sums, 16 * sizeof(double)));
     s->objcap = std::max(iterations + 1, 1);
-    PET_CUDA(cudaMalloc(&s->objhist, (size_t)s->objcap * 3 * sizeof(double)));
-    PET_CUDA(cudaMalloc(&s->redmem, reducer_bytes(kRedCap, 2)));
-    PET_CUDA(cudaMemset(s->redmem, 0, reducer_bytes(kRedCap, 2)));
+    PET_CUDA(get((void **)&s->objhist, (size_t)s->objcap * 3 * sizeof(double)));
+    PET_CUDA(get(&s->redmem, reducer_bytes(kRedCap, 2)));
+    PET_CUDA(cudaMemsetAsync(s->redmem, 0, reducer_bytes(kRedCap, 2), as));
     reducer_bind(s->red, s->redmem, kRedCap, 2);
-    PET_CUDA(cudaMalloc(&s->flag, sizeof(int)));
+    PET_CUDA(get((void **)&s->flag, sizeof(int)));
+    if (!as) PET_CUDA(cudaStreamSynchronize(nullptr));
     return PET_OK;
 }
 
@@ -151,12 +138,15 @@ static pet_status state_load(pet_state *s, const int32_t *d_counts, const float 
     return state_sum_f(s, st);
 }
 
-static pet_status state_subiter(pet_state *s, cudaStream_t st)
+// Plan the next subiteration of s (host FP64 scalars, argument structs) and advance its
+// schedule.  Shapes depend on the scan alone, so a scan computes the same bits on its own and
+// inside any batch.  with_objective: also plan Phi(f^{k+1}) when this subiteration ends an
+// outer iteration (written to objhist[3 (k+1) ..]).
+void pet::plan_subiter(pet_state *s, SubiterPlan *pl, bool with_objective)
 {
     const pet_geometry *g = s->g;
-    const GeoDev &gd = g->dev;
     const pet_params &p = s->prm;
-    const int M = gd.M;
+    const int M = g->dev.M;
     const int J = s->k * M + s->i + 1;                 // J_{k,i} = kM + i (1-based i)
     const double lam = p.lambda0 / (p.a * s->k + 1.0);
     double alpha = 1.0;
@@ -174,16 +164,19 @@ static pet_status state_subiter(pet_state *s, cudaStream_t st)
         else nu_mode = s->have_frozen ? 3 : 0;
     }
     const int slot0 = g->voff[s->i], nv = g->voff[s->i + 1] - g->voff[s->i];
-    if (nu_mode == 1 || nu_mode == 2) {
-        ImageArgs a{};
-        a.g = gd;
-        a.f = s->f[s->cur];
-        a.sum_f = s->sums + s->cur;
-        a.result = s->sums + 2;
-        a.red = s->red;
-        PET_TRY(launch_mu_sum(a, s->arith, st));
-    }
-    FwdArgs fa{};
+    *pl = SubiterPlan{};
+    GeoDev gd = g->dev;
+    gd.scale *= s->sens_ratio;
+    pl->arith = s->arith;
+    pl->mu = nu_mode == 1 || nu_mode == 2;
+    ImageArgs &a = pl->mu_args;
+    a.g = gd;
+    a.f = s->f[s->cur];
+    a.sum_f = s->sums + s->cur;
+    a.result = s->sums + 2;
+    a.red = s->red;
+    image_shape(a);
+    FwdArgs &fa = pl->fwd;
     fa.g = gd;
     fa.slot0 = slot0;
     fa.nviews = nv;
@@ -191,8 +184,8 @@ static pet_status state_subiter(pet_state *s, cudaStream_t st)
     fa.out = s->w;
     fa.counts = s->counts + (size_t)slot0 * gd.NB * gd.Pp;
     fa.gamma = s->gamma + (size_t)slot0 * gd.NB * gd.Pp;
-    PET_TRY(launch_forward(fa, FWD_RATIO, s->arith, st));
-    UpdateArgs ua{};
+    forward_shape(fa, FWD_RATIO);
+    UpdateArgs &ua = pl->upd;
     ua.g = gd;
     ua.slot0 = slot0;
     ua.nviews = nv;
@@ -200,6 +193,7 @@ static pet_status state_subiter(pet_state *s, cudaStream_t st)
     ua.f = s->f[s->cur];
     ua.fout = s->f[1 - s->cur];
     ua.invp = s->arith == AR_FP64 ? (const void *)g->d_invp64 : (const void *)g->d_invp;
+    ua.invp_scale = 1.0 / s->sens_ratio;
     ua.nu_frozen = s->nu_frozen;
     ua.nu_mode = nu_mode;
     ua.lam_alpha = lam * alpha;
@@ -214,41 +208,122 @@ static pet_status state_subiter(pet_state *s, cudaStream_t st)
     ua.sum_mu = s->sums + 2;
     ua.sum_fout = s->sums + (1 - s->cur);
     ua.red = s->red;
-    PET_TRY(launch_update(ua, s->arith, st));
+    update_shape(ua);
     if (nu_mode == 2) s->have_frozen = true;
     s->cur ^= 1;
     s->J = J;
+    const bool iter_end = (s->i + 1 == M);
     if (++s->i == M) { s->i = 0; ++s->k; }
-    return PET_OK;
+    pl->objective = with_objective && iter_end && s->k < s->objcap;
+    if (pl->objective) objective_args(s, s->objhist + 3 * s->k, &pl->obj_fwd, &pl->obj_rdp);
 }
 
-// Objective parts of the current f into out3 (device): sum(Af), sum(g ln(Af+gamma)), R(f).
+static pet_status state_subiter(pet_state *s, cudaStream_t st)
+{
+    SubiterPlan pl;
+    plan_subiter(s, &pl, false);
+    if (pl.mu) PET_TRY(launch_mu_sum(pl.mu_args, pl.arith, st));
+    PET_TRY(launch_forward(pl.fwd, FWD_RATIO, pl.arith, st));
+    return launch_update(pl.upd, pl.arith, st);
+}
+
+// Argument structs for Phi(current f): parts sum(Af), sum(g ln(Af+gamma)) -> out3[0..1],
+// R(f) -> out3[2].
+void pet::objective_args(pet_state *s, double *out3, FwdArgs *fa, ImageArgs *ra)
+{
+    GeoDev gd = s->g->dev;
+    gd.scale *= s->sens_ratio;
+    *fa = FwdArgs{};
+    fa->g = gd;
+    fa->slot0 = 0;
+    fa->nviews = gd.V;
+    fa->img = s->f[s->cur];
+    fa->counts = s->counts;
+    fa->gamma = s->gamma;
+    fa->red = s->red;
+    fa->result = out3;
+    forward_shape(*fa, FWD_OBJECTIVE);
+    *ra = ImageArgs{};
+    ra->g = gd;
+    ra->f = s->f[s->cur];
+    ra->gamma_r = s->prm.gamma_r;
+    ra->eps = s->prm.eps;
+    ra->result = out3 + 2;
+    ra->red = s->red;
+    image_shape(*ra);
+}
+
 static pet_status state_objective_async(pet_state *s, double *out3, cudaStream_t st)
 {
-    const GeoDev &gd = s->g->dev;
-    FwdArgs fa{};
-    fa.g = gd;
-    fa.slot0 = 0;
-    fa.nviews = gd.V;
-    fa.img = s->f[s->cur];
-    fa.counts = s->counts;
-    fa.gamma = s->gamma;
-    fa.red = s->red;
-    fa.result = out3;
+    FwdArgs fa;
+    ImageArgs ra;
+    objective_args(s, out3, &fa, &ra);
     PET_TRY(launch_forward(fa, FWD_OBJECTIVE, s->arith, st));
-    ImageArgs a{};
-    a.g = gd;
-    a.f = s->f[s->cur];
-    a.gamma_r = s->prm.gamma_r;
-    a.eps = s->prm.eps;
-    a.result = out3 + 2;
-    a.red = s->red;
-    return launch_rdp_value(a, s->arith, st);
+    return launch_rdp_value(ra, s->arith, st);
 }
 
 static int arith_of(int precision)
 {
     return precision == PET_PREC_FP64 ? AR_FP64 : (precision == PET_PREC_FP32 ? AR_FP32 : AR_KAHAN);
+}
+
+// Internal creation for the serving loop: allocate a state for geometry g and parameters p and
+// load it from device buffers in the C-ABI layouts (d_img may be NULL: f^0 = 1).  The data were
+// validated by the caller.  sens: this scan's sensitivity (may differ from the geometry's).
+pet_status pet::state_create_loaded(const pet_geometry *g, double sens, const int32_t *d_counts,
+                                    const float *d_gamma, const float *d_img,
+                                    const pet_params *p, cudaStream_t st, pet_state **out)
+{
+    *out = nullptr;
+    PET_TRY(check_params(p));
+    pet_state *s = new pet_state();
+    s->alloc_stream = st;                       // stream-ordered memory: no device-wide syncs
+    pet_status r = state_alloc(s, g, arith_of(p->precision), p->iterations);
+    if (r == PET_OK) {
+        s->sens_ratio = sens / g->desc.sens;
+        if (d_img) {
+            r = state_load(s, d_counts, d_gamma, p, d_img, st, false);
+        } else {
+            // f^0 = 1: fill the internal image, then load data
+            s->prm = *p;
+            const GeoDev &gd = g->dev;
+            r = to_internal_sino(gd, g->d_view_of_slot, 0, gd.V, d_counts, s->counts, 0, 0, st);
+            if (r == PET_OK) r = to_internal_sino(gd, g->d_view_of_slot, 0, gd.V, d_gamma, s->gamma, 1, 0, st);
+            if (r == PET_OK) r = fill_internal_ones(gd, s->f[0], s->arith == AR_FP64, st);
+            s->cur = 0;
+            s->k = s->i = s->J = 0;
+            s->tn = 1.0;
+            s->have_frozen = false;
+            if (r == PET_OK) r = state_sum_f(s, st);
+        }
+    }
+    if (r != PET_OK) {
+        std::string msg = pet_last_error();
+        state_free(s);
+        delete s;
+        return fail(r, msg);
+    }
+    *out = s;
+    return PET_OK;
+}
+
+size_t pet::state_bytes(const pet_geometry *g, int precision, int iterations)
+{
+    const GeoDev &gd = g->dev;
+    const size_t esz = precision == PET_PREC_FP64 ? 8 : 4;
+    const size_t q = (size_t)gd.N * gd.N * gd.Pp * esz;
+    int maxv = 0;
+    for (int i = 0; i < gd.M; ++i) maxv = std::max(maxv, g->voff[i + 1] - g->voff[i]);
+    const size_t sino = (size_t)gd.V * gd.NB * gd.Pp;
+    return 3 * q + (size_t)maxv * gd.NB * gd.Pp * esz + sino * 8 + reducer_bytes(kRedCap, 2) +
+           (size_t)(iterations + 1) * 24 + 1024;
+}
+
+void pet::state_release(pet_state *s, cudaStream_t st)
+{
+    if (s->alloc_stream) s->alloc_stream = st;  // free in the order of the last user's stream
+    state_free(s);
+    delete s;
 }
 
 extern "C" pet_status pet_state_create(const pet_geometry *g, const int32_t *d_counts,
@@ -312,6 +387,23 @@ extern "C" pet_status pet_state_objective(pet_state *s, double *h_phi, double *h
 }
 
 extern "C" int pet_state_subiters(const pet_state *s) { return s ? s->J : -1; }
+
+extern "C" pet_status pet_state_objective_history(pet_state *s, double *h_obj, void *stream)
+{
+    if (!s || !h_obj) return fail(PET_ERR_INVALID, "pet_state_objective_history: NULL argument");
+    cudaStream_t st = as_stream(stream);
+    const int T = s->prm.iterations;
+    std::vector<double> h((size_t)(T + 1) * 3);
+    PET_CUDA(cudaMemcpyAsync(h.data(), s->objhist, h.size() * sizeof(double),
+                             cudaMemcpyDeviceToHost, st));
+    PET_CUDA(cudaStreamSynchronize(st));
+    const int M = s->g->dev.M;
+    const int kdone = s->J / M;                       // objectives recorded for k <= kdone
+    for (int k = 0; k <= T; ++k)
+        h_obj[k] = k <= kdone ? h[3 * k] - h[3 * k + 1] + s->prm.beta * h[3 * k + 2]
+                              : __builtin_nan("");
+    return PET_OK;
+}
 
 extern "C" void pet_state_destroy(pet_state *s)
 {

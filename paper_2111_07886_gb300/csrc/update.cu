@@ -107,87 +107,95 @@ __device__ __forceinline__ T nu_of(T gx, T gy, T inv_mean_f, T mean_mu, T nu1, T
 }
 
 // f^{k,i} = P_t(f - lambda_k alpha_{k,i} nu S(f) (A_i^T w + (beta/M) grad R(f)))
-// Block: TP consecutive pixels x NG plane groups (thread = pixel * NG + group), grid-stride
-// over pixel tiles; the (pixel, view) weights of each tile are computed once into shared memory.
+// Virtual block: tpv tiles of TP consecutive pixels x NG plane groups (thread = pixel * NG +
+// group); the (pixel, view) weights of each tile are computed once into shared memory.  A
+// persistent grid strides over the virtual blocks of one scan or of a batch of scans.
 template <int G, int KC, int AR>
-__global__ void __launch_bounds__(256) update_kernel(UpdateArgs a)
+__global__ void __launch_bounds__(256) update_kernel(const __grid_constant__ UpdateArgs one,
+                                                     const Batch bt)
 {
     using T = typename ArithT<AR>::T;
     __shared__ BpTable<KC, AR> tb;
-    const GeoDev &g = a.g;
-    const int N = g.N, NG = g.NG, Pp = g.Pp, npix = N * N;
-    const int TP = blockDim.x / NG;
-    const int pl = threadIdx.x / NG, grp = threadIdx.x % NG;
-    const int VC = max(1, min(a.nviews, BpTable<KC, AR>::CAP / TP));
-    const bool dyn = a.nu_mode == 1 || a.nu_mode == 2;
-    const double q = (double)npix * g.P;
-    const T inv_mean_f = dyn ? (T)(q / *a.sum_f) : T(1);
-    const T mean_mu = dyn ? (T)(*a.sum_mu / q) : T(1);
-    const T lam = (T)a.lam_alpha, bm = (T)a.beta_over_M, U = (T)a.U, tt = (T)a.t;
-    const T nu1 = (T)a.nu1, nu2 = (T)a.nu2, halfU = T(0.5) * U;
-    const T *w = reinterpret_cast<const T *>(a.w);
-    const T *f = reinterpret_cast<const T *>(a.f);
-    const T *invp = reinterpret_cast<const T *>(a.invp);
-    const T scale = (T)g.scale;
-    T part = T(0);
-    const int ntiles = (npix + TP - 1) / TP;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int j0 = tile * TP, j = j0 + pl;
-        const bool active = pl < TP && j < npix;
-        GroupSum<G, AR> bp;
-        bp.zero();
-        for (int u0 = 0; u0 < a.nviews; u0 += VC) {
-            const int nvc = min(VC, a.nviews - u0);
-            __syncthreads();
-            bp_fill<KC, AR>(g, a.slot0, u0, nvc, j0, TP, tb);
-            __syncthreads();
-            if (active) bp_accumulate<G, KC, AR>(g, tb, w, u0, nvc, pl, grp, bp);
-        }
-        if (!active) continue;
-        const int ix = j % N, iy = j / N;
-        T fc[G], gr[G], gx[G], gy[G], rv[G];
-        if (dyn) stencil<G, AR, true, true, false>(g, f, grp, ix, iy, (T)a.gamma_r, (T)a.eps, fc, gr, gx, gy, rv);
-        else stencil<G, AR, true, false, false>(g, f, grp, ix, iy, (T)a.gamma_r, (T)a.eps, fc, gr, gx, gy, rv);
-        T nu[G];
-        if (a.nu_mode == 3) {
-            load_group<G, T>(reinterpret_cast<const T *>(a.nu_frozen) + (size_t)j * Pp + (size_t)grp * G, nu);
-        } else if (!dyn) {
+    const int total = total_vblocks(one, bt);
+    for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
+        int vloc, nv;
+        const UpdateArgs &a = *scan_of(one, bt, vb, vloc, nv);
+        const GeoDev &g = a.g;
+        const int N = g.N, NG = g.NG, Pp = g.Pp, npix = N * N;
+        const int TP = 256 / NG;
+        const int pl = threadIdx.x / NG, grp = threadIdx.x % NG;
+        const int VC = max(1, min(a.nviews, BpTable<KC, AR>::CAP / TP));
+        const bool dyn = a.nu_mode == 1 || a.nu_mode == 2;
+        const double q = (double)npix * g.P;
+        const T inv_mean_f = dyn ? (T)(q / *a.sum_f) : T(1);
+        const T mean_mu = dyn ? (T)(*a.sum_mu / q) : T(1);
+        const T lam = (T)a.lam_alpha, bm = (T)a.beta_over_M, U = (T)a.U, tt = (T)a.t;
+        const T nu1 = (T)a.nu1, nu2 = (T)a.nu2, halfU = T(0.5) * U;
+        const T *w = reinterpret_cast<const T *>(a.w);
+        const T *f = reinterpret_cast<const T *>(a.f);
+        const T *invp = reinterpret_cast<const T *>(a.invp);
+        const T scale = (T)g.scale;
+        const int ntiles = (npix + TP - 1) / TP;
+        T part = T(0);
+        for (int tile = vloc * a.tpv; tile < min(ntiles, (vloc + 1) * a.tpv); ++tile) {
+            const int j0 = tile * TP, j = j0 + pl;
+            const bool active = pl < TP && j < npix;
+            GroupSum<G, AR> bp;
+            bp.zero();
+            for (int u0 = 0; u0 < a.nviews; u0 += VC) {
+                const int nvc = min(VC, a.nviews - u0);
+                __syncthreads();
+                bp_fill<KC, AR>(g, a.slot0, u0, nvc, j0, TP, tb);
+                __syncthreads();
+                if (active) bp_accumulate<G, KC, AR>(g, tb, w, u0, nvc, pl, grp, bp);
+            }
+            if (!active) continue;
+            const int ix = j % N, iy = j / N;
+            T fc[G], gr[G], gx[G], gy[G], rv[G];
+            if (dyn) stencil<G, AR, true, true, false>(g, f, grp, ix, iy, (T)a.gamma_r, (T)a.eps, fc, gr, gx, gy, rv);
+            else stencil<G, AR, true, false, false>(g, f, grp, ix, iy, (T)a.gamma_r, (T)a.eps, fc, gr, gx, gy, rv);
+            T nu[G];
+            if (a.nu_mode == 3) {
+                load_group<G, T>(reinterpret_cast<const T *>(a.nu_frozen) + (size_t)j * Pp + (size_t)grp * G, nu);
+            } else if (!dyn) {
 #pragma unroll
-            for (int p = 0; p < G; ++p) nu[p] = T(1);
-        } else {
+                for (int p = 0; p < G; ++p) nu[p] = T(1);
+            } else {
 #pragma unroll
-            for (int p = 0; p < G; ++p) nu[p] = nu_of<T>(gx[p], gy[p], inv_mean_f, mean_mu, nu1, nu2);
-            if (a.nu_mode == 2)
-                store_group<G, T>(reinterpret_cast<T *>(a.nu_frozen) + (size_t)j * Pp + (size_t)grp * G, nu);
-        }
-        const T ip = invp[j];
-        T out[G];
+                for (int p = 0; p < G; ++p) nu[p] = nu_of<T>(gx[p], gy[p], inv_mean_f, mean_mu, nu1, nu2);
+                if (a.nu_mode == 2)
+                    store_group<G, T>(reinterpret_cast<T *>(a.nu_frozen) + (size_t)j * Pp + (size_t)grp * G, nu);
+            }
+            const T ip = invp[j] * (T)a.invp_scale;
+            T out[G];
 #pragma unroll
-        for (int p = 0; p < G; ++p) {
-            const T fj = fc[p];
-            const T d = scale * bp.value(p) + bm * gr[p];
-            const T S = (fj < halfU ? fj : U - fj) * ip;
-            T ft = fj - lam * nu[p] * S * d;
-            ft = ft <= T(0) ? tt : (ft >= U ? U - tt : ft);
-            const bool valid = grp * G + p < g.P;
-            out[p] = valid ? ft : T(0);
-            part += out[p];
+            for (int p = 0; p < G; ++p) {
+                const T fj = fc[p];
+                const T d = scale * bp.value(p) + bm * gr[p];
+                const T S = (fj < halfU ? fj : U - fj) * ip;
+                T ft = fj - lam * nu[p] * S * d;
+                ft = ft <= T(0) ? tt : (ft >= U ? U - tt : ft);
+                const bool valid = grp * G + p < g.P;
+                out[p] = valid ? ft : T(0);
+                part += out[p];
+            }
+            store_group<G, T>(reinterpret_cast<T *>(a.fout) + (size_t)j * Pp + (size_t)grp * G, out);
         }
-        store_group<G, T>(reinterpret_cast<T *>(a.fout) + (size_t)j * Pp + (size_t)grp * G, out);
+        double v[1] = {(double)part};
+        grid_reduce<1>(v, a.red, a.sum_fout, vloc, nv);
     }
-    double v[1] = {(double)part};
-    grid_reduce<1>(v, a.red, a.sum_fout);
 }
 
-// Stand-alone gather backprojection (also the sensitivity, proj == nullptr).
+// Stand-alone gather backprojection (also the sensitivity, proj == nullptr); one pixel tile
+// per virtual block.
 template <int G, int KC, int AR>
-__global__ void __launch_bounds__(256) back_kernel(BackArgs a)
+__global__ void __launch_bounds__(256) back_kernel(const __grid_constant__ BackArgs a)
 {
     using T = typename ArithT<AR>::T;
     __shared__ BpTable<KC, AR> tb;
     const GeoDev &g = a.g;
     const int N = g.N, NG = g.NG, npix = N * N;
-    const int TP = blockDim.x / NG;
+    const int TP = 256 / NG;
     const int pl = threadIdx.x / NG, grp = threadIdx.x % NG;
     const int VC = max(1, min(a.nviews, BpTable<KC, AR>::CAP / TP));
     const T *proj = reinterpret_cast<const T *>(a.proj);
@@ -213,122 +221,145 @@ __global__ void __launch_bounds__(256) back_kernel(BackArgs a)
     }
 }
 
-// KIND 0: sum f; 1: sum mu; 2: nu map; 3: RDP gradient; 4: RDP value
+// KIND 0: sum f; 1: sum mu; 2: nu map; 3: RDP gradient; 4: RDP value.  Virtual block: 256 x ipt
+// (pixel, plane group) items, item = thread + 256 k.
 template <int G, int AR, int KIND>
-__global__ void __launch_bounds__(256) image_kernel(ImageArgs a)
+__global__ void __launch_bounds__(256) image_kernel(const __grid_constant__ ImageArgs one,
+                                                    const Batch bt)
 {
     using T = typename ArithT<AR>::T;
-    const GeoDev &g = a.g;
-    const int N = g.N, NG = g.NG, Pp = g.Pp;
-    const long long total = (long long)N * N * NG;
-    const double q = (double)N * N * g.P;
-    const T *f = reinterpret_cast<const T *>(a.f);
-    const T inv_mean_f = (KIND == 1 || KIND == 2) ? (T)(q / *a.sum_f) : T(1);
-    const T mean_mu = KIND == 2 ? (T)(*a.sum_mu / q) : T(1);
-    T part = T(0);
-    for (long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x; tid < total;
-         tid += (long long)gridDim.x * blockDim.x) {
-        const int grp = (int)(tid % NG);
-        const int j = (int)(tid / NG);
-        const int ix = j % N, iy = j / N;
-        T fc[G], gr[G], gx[G], gy[G], rv[G], out[G];
-        if constexpr (KIND == 0) {
-            load_group<G, T>(f + (size_t)j * Pp + (size_t)grp * G, fc);
+    const int total = total_vblocks(one, bt);
+    for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
+        int vloc, nv;
+        const ImageArgs &a = *scan_of(one, bt, vb, vloc, nv);
+        const GeoDev &g = a.g;
+        const int N = g.N, NG = g.NG, Pp = g.Pp;
+        const long long items = (long long)N * N * NG;
+        const double q = (double)N * N * g.P;
+        const T *f = reinterpret_cast<const T *>(a.f);
+        const T inv_mean_f = (KIND == 1 || KIND == 2) ? (T)(q / *a.sum_f) : T(1);
+        const T mean_mu = KIND == 2 ? (T)(*a.sum_mu / q) : T(1);
+        T part = T(0);
+        for (int k = 0; k < a.ipt; ++k) {
+            const long long tid = ((long long)vloc * a.ipt + k) * 256 + threadIdx.x;
+            if (tid >= items) break;
+            const int grp = (int)(tid % NG);
+            const int j = (int)(tid / NG);
+            const int ix = j % N, iy = j / N;
+            T fc[G], gr[G], gx[G], gy[G], rv[G], out[G];
+            if constexpr (KIND == 0) {
+                load_group<G, T>(f + (size_t)j * Pp + (size_t)grp * G, fc);
 #pragma unroll
-            for (int p = 0; p < G; ++p) part += (grp * G + p < g.P) ? fc[p] : T(0);
-        } else if constexpr (KIND == 1 || KIND == 2) {
-            stencil<G, AR, false, true, false>(g, f, grp, ix, iy, T(0), T(0), fc, gr, gx, gy, rv);
+                for (int p = 0; p < G; ++p) part += (grp * G + p < g.P) ? fc[p] : T(0);
+            } else if constexpr (KIND == 1 || KIND == 2) {
+                stencil<G, AR, false, true, false>(g, f, grp, ix, iy, T(0), T(0), fc, gr, gx, gy, rv);
 #pragma unroll
-            for (int p = 0; p < G; ++p) {
-                T mu = sqrt(gx[p] * gx[p] + gy[p] * gy[p]) * inv_mean_f;
-                mu = mu < T(0.01) ? T(0.01) : mu;
-                if constexpr (KIND == 1) {
-                    part += (grp * G + p < g.P) ? mu : T(0);
-                } else {
-                    out[p] = grp * G + p < g.P ? clampT<T>(fast_div(mean_mu, mu), (T)a.nu1, (T)a.nu2) : T(0);
+                for (int p = 0; p < G; ++p) {
+                    T mu = sqrt(gx[p] * gx[p] + gy[p] * gy[p]) * inv_mean_f;
+                    mu = mu < T(0.01) ? T(0.01) : mu;
+                    if constexpr (KIND == 1) {
+                        part += (grp * G + p < g.P) ? mu : T(0);
+                    } else {
+                        out[p] = grp * G + p < g.P ? clampT<T>(fast_div(mean_mu, mu), (T)a.nu1, (T)a.nu2) : T(0);
+                    }
                 }
-            }
-            if constexpr (KIND == 2)
+                if constexpr (KIND == 2)
+                    store_group<G, T>(reinterpret_cast<T *>(a.out) + (size_t)j * Pp + (size_t)grp * G, out);
+            } else if constexpr (KIND == 3) {
+                stencil<G, AR, true, false, false>(g, f, grp, ix, iy, (T)a.gamma_r, (T)a.eps, fc, gr, gx, gy, rv);
+#pragma unroll
+                for (int p = 0; p < G; ++p) out[p] = grp * G + p < g.P ? gr[p] : T(0);
                 store_group<G, T>(reinterpret_cast<T *>(a.out) + (size_t)j * Pp + (size_t)grp * G, out);
-        } else if constexpr (KIND == 3) {
-            stencil<G, AR, true, false, false>(g, f, grp, ix, iy, (T)a.gamma_r, (T)a.eps, fc, gr, gx, gy, rv);
+            } else {
+                stencil<G, AR, false, false, true>(g, f, grp, ix, iy, (T)a.gamma_r, (T)a.eps, fc, gr, gx, gy, rv);
 #pragma unroll
-            for (int p = 0; p < G; ++p) out[p] = grp * G + p < g.P ? gr[p] : T(0);
-            store_group<G, T>(reinterpret_cast<T *>(a.out) + (size_t)j * Pp + (size_t)grp * G, out);
-        } else {
-            stencil<G, AR, false, false, true>(g, f, grp, ix, iy, (T)a.gamma_r, (T)a.eps, fc, gr, gx, gy, rv);
-#pragma unroll
-            for (int p = 0; p < G; ++p) part += (grp * G + p < g.P) ? rv[p] : T(0);
+                for (int p = 0; p < G; ++p) part += (grp * G + p < g.P) ? rv[p] : T(0);
+            }
+        }
+        if constexpr (KIND == 0 || KIND == 1 || KIND == 4) {
+            double v[1] = {(double)part};
+            grid_reduce<1>(v, a.red, a.result, vloc, nv);
         }
     }
-    if constexpr (KIND == 0 || KIND == 1 || KIND == 4) {
-        double v[1] = {(double)part};
-        grid_reduce<1>(v, a.red, a.result);
-    }
 }
 
-static int reduce_grid(const GeoDev &g, int capacity)
+extern int sm_count();
+
+// pixel tiles per virtual block so that a scan never needs more partial sums than its reducer
+void update_shape(UpdateArgs &a)
 {
-    const long long total = (long long)g.N * g.N * g.NG;
-    long long grid = (total + 255) / 256;
-    if (grid > capacity) grid = capacity;
-    return (int)grid;
+    const int TP = 256 / a.g.NG;
+    const int ntiles = (a.g.N * a.g.N + TP - 1) / TP;
+    a.tpv = std::max(1, (ntiles + a.red.capacity - 1) / a.red.capacity);
+    a.nvb = (ntiles + a.tpv - 1) / a.tpv;
 }
 
-// pixel-tiled kernels: TP pixels x NG groups per block
-static void tile_shape(const GeoDev &g, int *threads, int *tiles)
+void image_shape(ImageArgs &a)
 {
-    const int TP = std::max(1, 256 / g.NG);
-    *threads = TP * g.NG;
-    *tiles = (g.N * g.N + TP - 1) / TP;
+    const long long items = (long long)a.g.N * a.g.N * a.g.NG;
+    const long long nblk = (items + 255) / 256;
+    const int cap = a.red.capacity > 0 ? a.red.capacity : (1 << 30);
+    a.ipt = (int)std::max<long long>(1, (nblk + cap - 1) / cap);
+    a.nvb = (int)((nblk + a.ipt - 1) / a.ipt);
 }
+
+static int persistent_grid(int nvb) { return std::max(1, std::min(nvb, sm_count() * 8)); }
 
 template <int G, int KC>
-static void update_dispatch(const UpdateArgs &a, int arith, int grid, int thr, cudaStream_t st)
+static void update_dispatch(const UpdateArgs &a, const Batch &b, int arith, int grid, cudaStream_t st)
 {
-    if (arith == AR_FP32) update_kernel<G, KC, AR_FP32><<<grid, thr, 0, st>>>(a);
-    else if (arith == AR_KAHAN) update_kernel<G, KC, AR_KAHAN><<<grid, thr, 0, st>>>(a);
-    else update_kernel<G, KC, AR_FP64><<<grid, thr, 0, st>>>(a);
+    if (arith == AR_FP32) update_kernel<G, KC, AR_FP32><<<grid, 256, 0, st>>>(a, b);
+    else if (arith == AR_KAHAN) update_kernel<G, KC, AR_KAHAN><<<grid, 256, 0, st>>>(a, b);
+    else update_kernel<G, KC, AR_FP64><<<grid, 256, 0, st>>>(a, b);
 }
 
-pet_status launch_update(const UpdateArgs &a, int arith, cudaStream_t st)
+static pet_status update_any(const UpdateArgs &a, const Batch &b, int arith, int grid, cudaStream_t st)
 {
-    int thr, tiles;
-    tile_shape(a.g, &thr, &tiles);
-    const int grid = std::min(tiles, a.red.capacity);
     LaunchScope ls(PET_K_UPDATE, st);
     if (a.g.G == 1) {
-        if (a.g.K <= 2) update_dispatch<1, 2>(a, arith, grid, thr, st);
-        else update_dispatch<1, 4>(a, arith, grid, thr, st);
+        if (a.g.K <= 2) update_dispatch<1, 2>(a, b, arith, grid, st);
+        else update_dispatch<1, 4>(a, b, arith, grid, st);
     } else {
-        if (a.g.K <= 2) update_dispatch<8, 2>(a, arith, grid, thr, st);
-        else update_dispatch<8, 4>(a, arith, grid, thr, st);
+        if (a.g.K <= 2) update_dispatch<8, 2>(a, b, arith, grid, st);
+        else update_dispatch<8, 4>(a, b, arith, grid, st);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "update_kernel launch");
     return PET_OK;
 }
 
-template <int G, int KC>
-static void back_dispatch(const BackArgs &a, int arith, int grid, int thr, cudaStream_t st)
+pet_status launch_update(const UpdateArgs &a0, int arith, cudaStream_t st)
 {
-    if (arith == AR_FP32) back_kernel<G, KC, AR_FP32><<<grid, thr, 0, st>>>(a);
-    else if (arith == AR_KAHAN) back_kernel<G, KC, AR_KAHAN><<<grid, thr, 0, st>>>(a);
-    else back_kernel<G, KC, AR_FP64><<<grid, thr, 0, st>>>(a);
+    UpdateArgs a = a0;
+    update_shape(a);
+    return update_any(a, Batch{nullptr, nullptr, 0, 0}, arith, persistent_grid(a.nvb), st);
+}
+
+pet_status launch_update_batch(const UpdateArgs &shape, const Batch &b, int arith, cudaStream_t st)
+{
+    return update_any(shape, b, arith, b.grid, st);
+}
+
+template <int G, int KC>
+static void back_dispatch(const BackArgs &a, int arith, int grid, cudaStream_t st)
+{
+    if (arith == AR_FP32) back_kernel<G, KC, AR_FP32><<<grid, 256, 0, st>>>(a);
+    else if (arith == AR_KAHAN) back_kernel<G, KC, AR_KAHAN><<<grid, 256, 0, st>>>(a);
+    else back_kernel<G, KC, AR_FP64><<<grid, 256, 0, st>>>(a);
 }
 
 pet_status launch_back(const BackArgs &a, int arith, cudaStream_t st)
 {
-    int thr, tiles;
-    tile_shape(a.g, &thr, &tiles);
-    const int grid = std::min(tiles, 65535);
+    const int TP = 256 / a.g.NG;
+    const int ntiles = (a.g.N * a.g.N + TP - 1) / TP;
+    const int grid = persistent_grid(ntiles);
     LaunchScope ls(PET_K_OTHER, st);
     if (a.g.G == 1) {
-        if (a.g.K <= 2) back_dispatch<1, 2>(a, arith, grid, thr, st);
-        else back_dispatch<1, 4>(a, arith, grid, thr, st);
+        if (a.g.K <= 2) back_dispatch<1, 2>(a, arith, grid, st);
+        else back_dispatch<1, 4>(a, arith, grid, st);
     } else {
-        if (a.g.K <= 2) back_dispatch<8, 2>(a, arith, grid, thr, st);
-        else back_dispatch<8, 4>(a, arith, grid, thr, st);
+        if (a.g.K <= 2) back_dispatch<8, 2>(a, arith, grid, st);
+        else back_dispatch<8, 4>(a, arith, grid, st);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "back_kernel launch");
@@ -336,21 +367,28 @@ pet_status launch_back(const BackArgs &a, int arith, cudaStream_t st)
 }
 
 template <int KIND>
-static pet_status launch_image(const ImageArgs &a, int arith, cudaStream_t st)
+static pet_status image_any(const ImageArgs &a, const Batch &b, int arith, int grid, cudaStream_t st)
 {
-    const int grid = reduce_grid(a.g, a.red.capacity > 0 ? a.red.capacity : (1 << 30));
     LaunchScope ls(KIND == 1 ? PET_K_MU_SUM : (KIND == 4 ? PET_K_RDP_VALUE : PET_K_OTHER), st);
     // FP32 and Kahan modes share the FP32 image arithmetic
     if (a.g.G == 1) {
-        if (arith == AR_FP64) image_kernel<1, AR_FP64, KIND><<<grid, 256, 0, st>>>(a);
-        else image_kernel<1, AR_FP32, KIND><<<grid, 256, 0, st>>>(a);
+        if (arith == AR_FP64) image_kernel<1, AR_FP64, KIND><<<grid, 256, 0, st>>>(a, b);
+        else image_kernel<1, AR_FP32, KIND><<<grid, 256, 0, st>>>(a, b);
     } else {
-        if (arith == AR_FP64) image_kernel<8, AR_FP64, KIND><<<grid, 256, 0, st>>>(a);
-        else image_kernel<8, AR_FP32, KIND><<<grid, 256, 0, st>>>(a);
+        if (arith == AR_FP64) image_kernel<8, AR_FP64, KIND><<<grid, 256, 0, st>>>(a, b);
+        else image_kernel<8, AR_FP32, KIND><<<grid, 256, 0, st>>>(a, b);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "image_kernel launch");
     return PET_OK;
+}
+
+template <int KIND>
+static pet_status launch_image(const ImageArgs &a0, int arith, cudaStream_t st)
+{
+    ImageArgs a = a0;
+    image_shape(a);
+    return image_any<KIND>(a, Batch{nullptr, nullptr, 0, 0}, arith, persistent_grid(a.nvb), st);
 }
 
 pet_status launch_sum(const ImageArgs &a, int arith, cudaStream_t st) { return launch_image<0>(a, arith, st); }
@@ -358,5 +396,13 @@ pet_status launch_mu_sum(const ImageArgs &a, int arith, cudaStream_t st) { retur
 pet_status launch_nu_map(const ImageArgs &a, int arith, cudaStream_t st) { return launch_image<2>(a, arith, st); }
 pet_status launch_rdp_grad(const ImageArgs &a, int arith, cudaStream_t st) { return launch_image<3>(a, arith, st); }
 pet_status launch_rdp_value(const ImageArgs &a, int arith, cudaStream_t st) { return launch_image<4>(a, arith, st); }
+pet_status launch_mu_sum_batch(const ImageArgs &shape, const Batch &b, int arith, cudaStream_t st)
+{
+    return image_any<1>(shape, b, arith, b.grid, st);
+}
+pet_status launch_rdp_value_batch(const ImageArgs &shape, const Batch &b, int arith, cudaStream_t st)
+{
+    return image_any<4>(shape, b, arith, b.grid, st);
+}
 
 }  // namespace pet

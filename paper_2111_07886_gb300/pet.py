@@ -41,6 +41,17 @@ class Params(ctypes.Structure):
         ("precision", ctypes.c_int)]
 
 
+class Request(ctypes.Structure):
+    _fields_ = [("geom", GeometryDesc), ("h_counts", ctypes.c_void_p), ("h_gamma", ctypes.c_void_p),
+                ("h_img_init", ctypes.c_void_p), ("params", Params), ("with_objective", ctypes.c_int)]
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_longlong) for k in ("submitted", "completed", "failed", "running", "queued")] + [
+        (k, ctypes.c_double) for k in ("p50_s", "p99_s", "mean_s", "scans_per_s")] + [
+        ("hbm_in_use", ctypes.c_size_t)]
+
+
 _VP = ctypes.c_void_p
 _I = ctypes.c_int
 _D = ctypes.c_double
@@ -70,6 +81,18 @@ SIGNATURES = {
     "pet_smoothness_nu": (_I, [_VP, _VP, _D, _D, _VP, _VP]),
     "pet_objective": (_I, [_VP, _VP, _VP, _VP, _D, _D, _D, _DP, _DP, _VP]),
     "pet_objective_static": (_I, [_VP, _VP, _VP, _VP, _D, _D, _D, _DP, _DP, _VP]),
+    "pet_batch_create": (_I, [_I, _I, ctypes.POINTER(_VP)]),
+    "pet_batch_add": (_I, [_VP, _VP, _I, _VP]),
+    "pet_batch_remove": (_I, [_VP, _VP]),
+    "pet_batch_step": (_I, [_VP, _VP, ctypes.POINTER(_I)]),
+    "pet_batch_size": (_I, [_VP]),
+    "pet_batch_destroy": (None, [_VP]),
+    "pet_state_objective_history": (_I, [_VP, _DP, _VP]),
+    "pet_serve_create": (_I, [ctypes.c_size_t, _I, _I, ctypes.POINTER(_VP)]),
+    "pet_serve_submit": (_I, [_VP, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
+    "pet_serve_poll": (_I, [_VP, ctypes.c_uint64, _VP, _DP, _DP]),
+    "pet_serve_stats_get": (_I, [_VP, ctypes.POINTER(ServeStats)]),
+    "pet_serve_destroy": (None, [_VP]),
     "pet_launch_count": (ctypes.c_longlong, []),
     "pet_profile_enable": (None, [_I]),
     "pet_profile_read": (_I, [_I, _DP, ctypes.POINTER(ctypes.c_longlong)]),
@@ -199,6 +222,12 @@ class State:
     def subiters(self) -> int:
         return lib().pet_state_subiters(self.handle)
 
+    def objective_history(self, stream=None):
+        """Phi(f^k), k = 0..T, recorded so far (NaN where not computed)."""
+        out = (ctypes.c_double * (self.params.iterations + 1))()
+        _check(lib().pet_state_objective_history(self.handle, out, _stream(stream)))
+        return list(out)
+
     def close(self):
         if getattr(self, "handle", None):
             lib().pet_state_destroy(self.handle)
@@ -275,3 +304,98 @@ def profile_read() -> dict:
         _check(lib().pet_profile_read(k, ctypes.byref(ms), ctypes.byref(n)))
         out[name] = (ms.value, n.value)
     return out
+
+
+class Batch:
+    """pet_batch: many states advanced together by batched, graph-replayed kernels."""
+
+    def __init__(self, capacity: int, use_graph: bool = True):
+        h = _VP()
+        _check(lib().pet_batch_create(capacity, 1 if use_graph else 0, ctypes.byref(h)))
+        self.handle = h
+        self.members = []
+
+    def add(self, state: State, with_objective: bool = False, stream=None):
+        _check(lib().pet_batch_add(self.handle, state.handle, 1 if with_objective else 0, _stream(stream)))
+        self.members.append(state)
+
+    def remove(self, state: State):
+        _check(lib().pet_batch_remove(self.handle, state.handle))
+        self.members.remove(state)
+
+    def step(self, stream=None) -> int:
+        n = ctypes.c_int()
+        _check(lib().pet_batch_step(self.handle, _stream(stream), ctypes.byref(n)))
+        return n.value
+
+    @property
+    def running(self) -> int:
+        return lib().pet_batch_size(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().pet_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """pet_server: continuous batching of reconstruction requests (host buffers in and out)."""
+
+    def __init__(self, hbm_budget_bytes: int, max_slots: int, device: int = 0):
+        h = _VP()
+        _check(lib().pet_serve_create(int(hbm_budget_bytes), max_slots, device, ctypes.byref(h)))
+        self.handle = h
+        self.shapes = {}
+
+    def submit(self, geometry: dict, sens: float, counts, gamma, params: Params, img0=None,
+               with_objective: bool = True) -> int:
+        import numpy as np
+        g = geometry
+        desc = GeometryDesc(g["n"], g["nplanes"], g["pixel_mm"], g["nviews"], g["nbins"], g["bin_mm"],
+                            g["nsubsets"], sens)
+        counts = np.ascontiguousarray(counts, dtype=np.int32)
+        gamma = np.ascontiguousarray(gamma, dtype=np.float32)
+        img0 = None if img0 is None else np.ascontiguousarray(img0, dtype=np.float32)
+        req = Request(desc, counts.ctypes.data, gamma.ctypes.data,
+                      None if img0 is None else img0.ctypes.data, params, 1 if with_objective else 0)
+        t = ctypes.c_uint64()
+        _check(lib().pet_serve_submit(self.handle, ctypes.byref(req), ctypes.byref(t)))
+        self.shapes[t.value] = ((g["nplanes"], g["n"], g["n"]), params.iterations + 1)
+        return t.value
+
+    def poll(self, ticket: int):
+        """None while pending; else (image [P][N][N] float32, objective list, latency_s)."""
+        import numpy as np
+        shape, nobj = self.shapes.get(ticket, ((0,), 1))
+        img = np.empty(shape, np.float32)
+        obj = (ctypes.c_double * nobj)()
+        lat = ctypes.c_double()
+        st = lib().pet_serve_poll(self.handle, ticket, img.ctypes.data if img.size else None,
+                                  obj, ctypes.byref(lat))
+        if st == PENDING:
+            return None
+        self.shapes.pop(ticket, None)
+        _check(st)
+        return img, list(obj), lat.value
+
+    def stats(self) -> dict:
+        s = ServeStats()
+        _check(lib().pet_serve_stats_get(self.handle, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in ServeStats._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().pet_serve_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
