@@ -47,6 +47,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
     ap.add_argument("--no-kernel-times", action="store_true",
                     help="skip the per-kernel event pass (roofline)")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 64-scan batched run")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop run")
+    ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-rates", default="0.5,0.9,1.5",
+                    help="arrival rates as fractions of the sequential plain capacity")
     return ap.parse_args()
 
 
@@ -246,6 +251,10 @@ def run_ours(args, rank, world, local):
         line.update(kernel_times(args, w, pet, step, flush))
     if not args.no_e2e:
         line["e2e"] = end_to_end(args, w, scan, g, prm, pet, flush, dev, world, subiters)
+    if not args.no_batched:
+        line["batched"] = batched_measure(pet, torch)
+    if not args.no_serving:
+        line["serving"] = serving_measure(args, pet, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, scan, args.cpu_seconds)
     return line
@@ -304,6 +313,143 @@ def end_to_end(args, w, scan, g, prm, pet, flush, dev, world, subiters) -> dict:
            "d2h_bytes_per_step": int(h_img.numel() * 4 + 8 * (w.params.iterations + 1)),
            "api": "pet_reconstruct_host", "ms_per_step": round(float(te.item()), 3)}
     return e2e
+
+
+def batched_measure(pet, torch) -> dict:
+    """64 independent 2-D scans of mixed sizes (N in {128, 200, 256, 400}, 120-360 views,
+    12-36 subsets, 10 iterations, objective each iteration): all advanced together by the
+    batched, graph-replayed kernels, against the plain path (pet_reconstruct, one scan at a
+    time).  Same states, same bits (tests check it); both timed with CUDA events."""
+    dev = torch.device("cuda")
+    ws = synth.mixed_2d_scans(64, seed=0, iterations=10)
+    scans = [synth.make_scan(w) for w in ws]
+    stream = torch.cuda.Stream()
+    items = []
+    for w, sc in zip(ws, scans):
+        g = pet.Geometry.from_dict(w.geometry(), sc["sens"])
+        c = torch.from_numpy(sc["counts"]).to(dev)
+        gm = torch.from_numpy(sc["gamma"]).to(dev)
+        f0 = torch.ones((1, w.n, w.n), device=dev)
+        st = pet.State(g, c, gm, pet.make_params(w.params), f0)
+        items.append((w, g, c, gm, f0, st))
+    subiters = sum(w.params.iterations * w.nsubsets for w in ws)
+    batch = pet.Batch(64, use_graph=True)
+
+    def batched_run():
+        for it in items:
+            if it[5] in batch.members:
+                batch.remove(it[5])
+            it[5].reset(stream=stream)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for it in items:
+            batch.add(it[5], with_objective=True, stream=stream)
+        n0 = pet.launch_count()
+        ticks = 0
+        while batch.step(stream=stream) > 0:
+            ticks += 1
+        b.record(stream)
+        stream.synchronize()
+        return a.elapsed_time(b) / 1e3, ticks + 1, pet.launch_count() - n0
+
+    batched_run()                               # warm-up: graph capture, caches
+    tb, ticks, launches = batched_run()
+
+    def plain_run():
+        t = 0.0
+        for w, g, c, gm, f0, st in items:
+            img = f0.clone()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            pet.reconstruct(g, c, gm, pet.make_params(w.params), img, objective=True)
+            b.record()
+            torch.cuda.synchronize()
+            t += a.elapsed_time(b) / 1e3
+        return t
+
+    plain_run()
+    tp = plain_run()
+    return {"workload": "64 mixed 2-D scans (N 128-400, 120-360 views, 12-36 subsets, 10 it.)",
+            "subiters": subiters, "ticks": ticks, "gpu_launches": int(launches),
+            "batched_s": round(tb, 4), "plain_s": round(tp, 4),
+            "batched_subiters_per_s": round(subiters / tb, 1),
+            "plain_subiters_per_s": round(subiters / tp, 1),
+            "batched_scans_per_s": round(len(ws) / tb, 2), "plain_scans_per_s": round(len(ws) / tp, 2),
+            "speedup_vs_plain": round(tp / tb, 2)}
+
+
+def serving_measure(args, pet, torch) -> dict:
+    """Serving loop: a Poisson-arrival stream of requests drawn from the mixed 2-D scans plus 5 %
+    stacked 256 x 256 x 89 jobs, each run to 20 iterations, at rates that are fractions of the
+    sequential plain capacity.  Reports scans/s and p50/p99 latency (submit to result), next to
+    the same arrival stream served by the plain per-scan path one request at a time (FIFO,
+    service times measured on the GPU)."""
+    import math
+    dev = torch.device("cuda")
+    ws = synth.mixed_2d_scans(64, seed=1, iterations=20)[:16]
+    ws.append(synth.config_stacked_256x89(seed=5))
+    scans = [synth.make_scan(w) for w in ws]
+    # plain service time of every pool entry (pet_reconstruct, inputs resident, events)
+    service = []
+    for w, sc in zip(ws, scans):
+        g = pet.Geometry.from_dict(w.geometry(), sc["sens"])
+        c = torch.from_numpy(sc["counts"]).to(dev)
+        gm = torch.from_numpy(sc["gamma"]).to(dev)
+        img = torch.ones((w.nplanes, w.n, w.n), device=dev)
+        pet.reconstruct(g, c, gm, pet.make_params(w.params), img, objective=True)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        img.fill_(1.0)
+        a.record()
+        pet.reconstruct(g, c, gm, pet.make_params(w.params), img, objective=True)
+        b.record()
+        torch.cuda.synchronize()
+        service.append(a.elapsed_time(b) / 1e3)
+        del g, c, gm, img
+    rng = np.random.Generator(np.random.PCG64(42))
+    n = args.serve_requests
+    pick = [len(ws) - 1 if rng.uniform() < 0.05 else int(rng.integers(0, len(ws) - 1)) for _ in range(n)]
+    mean_service = float(np.mean([service[k] for k in pick]))
+    capacity = 1.0 / mean_service
+    out = {"requests": n, "pool": f"{len(ws) - 1} mixed 2-D scans + 1 stacked 256x256x89 (5 %)",
+           "iterations": 20, "plain_capacity_scans_per_s": round(capacity, 2), "rates": []}
+    for rho in [float(x) for x in args.serve_rates.split(",") if x]:
+        gaps = rng.exponential(1.0 / (rho * capacity), size=n)
+        arrivals = np.cumsum(gaps) - gaps[0]
+        server = pet.Server(hbm_budget_bytes=64 << 30, max_slots=64)
+        tickets = {}
+        t0 = time.perf_counter()
+        done = {}
+        k = 0
+        while len(done) < n:
+            now = time.perf_counter() - t0
+            while k < n and arrivals[k] <= now:
+                w, sc = ws[pick[k]], scans[pick[k]]
+                tickets[server.submit(w.geometry(), sc["sens"], sc["counts"], sc["gamma"],
+                                      pet.make_params(w.params), with_objective=True)] = k
+                k += 1
+            for t in list(tickets):
+                r = server.poll(t)
+                if r is not None:
+                    done[tickets.pop(t)] = r[2]
+            time.sleep(0.0005)
+        st = server.stats()
+        server.close()
+        # the same arrivals served one at a time by the plain path (FIFO)
+        finish, lat = 0.0, []
+        for i in range(n):
+            start = max(arrivals[i], finish)
+            finish = start + service[pick[i]]
+            lat.append(finish - arrivals[i])
+        lat = np.sort(np.array(lat))
+        span_plain = finish - arrivals[0]
+        out["rates"].append({
+            "rho": rho, "served_scans_per_s": round(st["scans_per_s"], 2),
+            "p50_s": round(st["p50_s"], 4), "p99_s": round(st["p99_s"], 4),
+            "failed": int(st["failed"]),
+            "plain_scans_per_s": round(n / span_plain, 2),
+            "plain_p50_s": round(float(np.percentile(lat, 50)), 4),
+            "plain_p99_s": round(float(np.percentile(lat, 99)), 4)})
+    return out
 
 
 def cpu_baseline(w, scan, seconds: float) -> dict:

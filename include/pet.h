@@ -150,6 +150,8 @@ pet_status pet_back_subset_f64(const pet_geometry *g, int subset, const double *
  * pet_state_objective: *h_phi = Phi(current f) (Eqs. FidelityTerm, ObjectiveFunction), FP64;
  *   h_parts (optional, 3 doubles) = sum(Af), sum(g ln(Af + gamma)), R(f).  Synchronises.
  * pet_state_subiters: completed subiterations J.
+ * pet_state_reset: restart at (k, i) = (0, 1) from d_img_init (float [P][N][N]; NULL: f^0 = 1),
+ *   keeping the data; asynchronous.
  * ---------------------------------------------------------------------------------------- */
 pet_status pet_state_create(const pet_geometry *g, const int32_t *d_counts, const float *d_gamma,
                             const pet_params *params, const float *d_img_init, void *stream,
@@ -159,6 +161,7 @@ pet_status pet_state_read_image(const pet_state *s, float *d_img, void *stream);
 pet_status pet_state_read_image_f64(const pet_state *s, double *d_img, void *stream);
 pet_status pet_state_objective(pet_state *s, double *h_phi, double *h_parts, void *stream);
 int pet_state_subiters(const pet_state *s);
+pet_status pet_state_reset(pet_state *s, const float *d_img_init, void *stream);
 void pet_state_destroy(pet_state *s);
 
 /* ------------------------------------------------------------------------------------------

@@ -386,6 +386,20 @@ extern "C" pet_status pet_state_objective(pet_state *s, double *h_phi, double *h
     return PET_OK;
 }
 
+extern "C" pet_status pet_state_reset(pet_state *s, const float *d_img_init, void *stream)
+{
+    if (!s) return fail(PET_ERR_INVALID, "pet_state_reset: NULL state");
+    cudaStream_t st = as_stream(stream);
+    const GeoDev &gd = s->g->dev;
+    if (d_img_init) PET_TRY(to_internal_image(gd, d_img_init, s->f[0], 0, s->arith == AR_FP64, st));
+    else PET_TRY(fill_internal_ones(gd, s->f[0], s->arith == AR_FP64, st));
+    s->cur = 0;
+    s->k = s->i = s->J = 0;
+    s->tn = 1.0;
+    s->have_frozen = false;
+    return state_sum_f(s, st);
+}
+
 extern "C" int pet_state_subiters(const pet_state *s) { return s ? s->J : -1; }
 
 extern "C" pet_status pet_state_objective_history(pet_state *s, double *h_obj, void *stream)

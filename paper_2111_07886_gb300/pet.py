@@ -74,6 +74,7 @@ SIGNATURES = {
     "pet_state_read_image_f64": (_I, [_VP, _VP, _VP]),
     "pet_state_objective": (_I, [_VP, _DP, _DP, _VP]),
     "pet_state_subiters": (_I, [_VP]),
+    "pet_state_reset": (_I, [_VP, _VP, _VP]),
     "pet_state_destroy": (None, [_VP]),
     "pet_reconstruct": (_I, [_VP, _VP, _VP, ctypes.POINTER(Params), _VP, _DP, _VP]),
     "pet_reconstruct_host": (_I, [_VP, _VP, _VP, ctypes.POINTER(Params), _VP, _DP, _VP]),
@@ -207,6 +208,9 @@ class State:
 
     def subiter(self, stream=None):
         _check(lib().pet_subiter(self.handle, _stream(stream)))
+
+    def reset(self, d_img_init=None, stream=None):
+        _check(lib().pet_state_reset(self.handle, _ptr(d_img_init), _stream(stream)))
 
     def read_image(self, d_img, stream=None):
         fn = lib().pet_state_read_image_f64 if str(d_img.dtype) == "torch.float64" else lib().pet_state_read_image
