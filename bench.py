@@ -68,6 +68,25 @@ def workload_config(w) -> dict:
             "global_batch": 1, "parallelism": "replicas"}
 
 
+def replica_seed(base_seed: int, rank: int) -> int:
+    """Each replica reconstructs its own scan (weak scaling, no data-path collective)."""
+    return base_seed + 1000 * rank
+
+
+def reduce_max(value: float, world: int, device) -> float:
+    """Max over ranks (the job is as slow as its slowest replica)."""
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: int, world: int, ms_max: float) -> float:
+    """Whole-job units per second: all ranks' units over the slowest rank's time."""
+    return world * units_per_rank / (ms_max / 1e3)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -191,9 +210,10 @@ def run_ours(args, rank, world, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     w = workload(args.workload)
-    w.seed = w.seed + rank                 # each replica reconstructs its own scan
+    w.seed = replica_seed(w.seed, rank)
     scan = synth.make_scan(w)
     g = pet.Geometry.from_dict(w.geometry(), scan["sens"])
+    tuned_S = g.autotune()
     prm = pet.make_params(w.params)
     counts = torch.from_numpy(scan["counts"]).to(dev)
     gamma = torch.from_numpy(scan["gamma"]).to(dev)
@@ -230,13 +250,11 @@ def run_ours(args, rank, world, local):
     launches = (pet.launch_count() - n0) // args.steps
     clk = clocks.stop()
     ms = sum(a.elapsed_time(b) for a, b in evs)
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
     if world > 1:
         torch.distributed.barrier()
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = reduce_max(ms, world, dev)
     ms_per_step = ms_max / args.steps
-    value = world * subiters / (ms_per_step / 1e3)
+    value = job_throughput(subiters, world, ms_per_step)
 
     line = {
         "metric": "OS subiters/s", "value": round(value, 2), "unit": "subiters/s",
@@ -244,7 +262,8 @@ def run_ours(args, rank, world, local):
         "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 (Kahan sums) + f64 scalars/objective",
         "data": "synthetic (seeded random-ellipsoid phantom, analytic projections, Poisson counts)",
-        "config": workload_config(w), "clocks": clk, "gpu_launches": int(launches),
+        "config": {**workload_config(w), "autotuned_ray_chunks": tuned_S},
+        "clocks": clk, "gpu_launches": int(launches),
         "wall_s_timed": round(wall, 3), "objective_final": obj[-1] if obj else None,
     }
     if not args.no_kernel_times:
@@ -305,13 +324,11 @@ def end_to_end(args, w, scan, g, prm, pet, flush, dev, world, subiters) -> dict:
         pet.reconstruct_host(g, h_counts.numpy(), h_gamma.numpy(), prm, h_img.numpy(), objective=True)
         e2e_ms += (time.perf_counter() - t0) * 1e3
     e2e_ms /= e2e_steps
-    te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
-    e2e = {"value": round(world * subiters / (float(te.item()) / 1e3), 2), "unit": "subiters/s",
+    e2e_max = reduce_max(e2e_ms, world, dev)
+    e2e = {"value": round(job_throughput(subiters, world, e2e_max), 2), "unit": "subiters/s",
            "h2d_bytes_per_step": int(h_counts.numel() * 4 + h_gamma.numel() * 4 + h_img.numel() * 4),
            "d2h_bytes_per_step": int(h_img.numel() * 4 + 8 * (w.params.iterations + 1)),
-           "api": "pet_reconstruct_host", "ms_per_step": round(float(te.item()), 3)}
+           "api": "pet_reconstruct_host", "ms_per_step": round(e2e_max, 3)}
     return e2e
 
 
@@ -463,9 +480,9 @@ def cpu_baseline(w, scan, seconds: float) -> dict:
         t0 = time.perf_counter()
         oracle.reconstruct(og, scan["counts"], scan["gamma"], w.params, f0, nsub=n)
         dt = time.perf_counter() - t0
-        if dt >= seconds / 3 or n >= w.params.iterations * w.nsubsets:
+        if dt >= 0.6 * seconds or n >= w.params.iterations * w.nsubsets:
             break
-        n = min(w.params.iterations * w.nsubsets, max(n + 1, int(n * seconds / 3 / max(dt, 1e-3))))
+        n = min(w.params.iterations * w.nsubsets, max(n + 1, int(n * seconds / max(dt, 1e-3))))
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"value": round(n / dt, 4), "unit": "subiters/s", "cores": cores, "kind": "oracle",
             "sample": f"{n} subiterations of {w.name} from f0 = 1 (incl. its sensitivity setup), "

@@ -111,6 +111,12 @@ const char *pet_last_error(void);
 pet_status pet_geometry_create(const pet_geometry_desc *desc, void *stream, pet_geometry **out);
 void pet_geometry_destroy(pet_geometry *g);
 
+/* Autotuner (no counterpart in the paper): times the forward projector of subset 0 for each
+ * admissible number of ray chunks (threads sharing one ray) and keeps the fastest in the
+ * geometry; *best_S (optional) receives it.  Tune before creating states on the geometry (the
+ * chunking changes the order of the ray sums, within rounding).  Synchronises `stream`. */
+pet_status pet_autotune(pet_geometry *g, void *stream, int *best_S);
+
 /* Number of views V_i in subset `subset` (0 <= subset < M), or -1 if out of range. */
 int pet_subset_size(const pet_geometry *g, int subset);
 

@@ -73,6 +73,7 @@ def lib():
             L.ora_alpha_km.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
             L.ora_objective.argtypes = [gp, ip, fp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
             L.ora_reconstruct.argtypes = [gp, ip, fp, ctypes.POINTER(Params), dp, ctypes.c_int, dp]
+            L.ora_reconstruct_snap.argtypes = [gp, ip, fp, ctypes.POINTER(Params), dp, ctypes.c_int, dp, dp]
             _lib = L
     return _lib
 
@@ -207,3 +208,19 @@ def reconstruct(g: Geom, counts, gamma, params, f0, nsub: int = -1, with_objecti
                           f.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), nsub,
                           obj.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if obj is not None else None)
     return f, obj
+
+
+def reconstruct_snapshots(g: Geom, counts, gamma, params, f0):
+    """Full run (T iterations) returning (f after each iteration [T][P][N][N], objective T+1)."""
+    counts = np.ascontiguousarray(counts, dtype=np.int32)
+    gamma = np.ascontiguousarray(gamma, dtype=np.float32)
+    f = np.array(f0, dtype=np.float64, copy=True, order="C")
+    prm = params if isinstance(params, Params) else params_from(params)
+    obj = np.full(prm.iterations + 1, np.nan)
+    snaps = np.zeros((prm.iterations,) + f.shape)
+    lib().ora_reconstruct_snap(ctypes.byref(g), counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                               gamma.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), ctypes.byref(prm),
+                               f.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), -1,
+                               obj.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                               snaps.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return snaps, obj

@@ -377,8 +377,19 @@ void ora_objective(const ora_geom *g, const int *counts, const float *gamma, con
  *   f      = P_t(f~)                                                           (Eq. OperatorPt)
  * nu is computed from f^{k,i-1}, the iterate the preconditioner is applied to.
  * ------------------------------------------------------------------------------------- */
+void ora_reconstruct_snap(const ora_geom *g, const int *counts, const float *gamma,
+                          const ora_params *prm, double *f, int nsub, double *obj, double *snaps);
+
 void ora_reconstruct(const ora_geom *g, const int *counts, const float *gamma,
                      const ora_params *prm, double *f, int nsub, double *obj)
+{
+    ora_reconstruct_snap(g, counts, gamma, prm, f, nsub, obj, NULL);
+}
+
+/* As ora_reconstruct; snaps (optional, T x q doubles) receives f^{k+1} after each completed
+   outer iteration k. */
+void ora_reconstruct_snap(const ora_geom *g, const int *counts, const float *gamma,
+                          const ora_params *prm, double *f, int nsub, double *obj, double *snaps)
 {
     const int N = g->n, P = g->nplanes, M = g->nsubsets, NB = g->nbins;
     const size_t q = (size_t)N * N * P, npix = (size_t)N * N;
@@ -446,6 +457,7 @@ void ora_reconstruct(const ora_geom *g, const int *counts, const float *gamma,
             ora_objective(g, counts, gamma, f, prm->beta, prm->gamma_r, prm->eps, o);
             obj[k + 1] = o[3];
         }
+        if (snaps && i == M) memcpy(snaps + (size_t)k * q, f, sizeof(double) * q);
     }
     free(pj); free(alpha); free(nu); free(nu_frozen); free(grad); free(rgrad);
     free(views); free(ysub);

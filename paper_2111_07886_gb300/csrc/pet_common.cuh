@@ -64,6 +64,7 @@ struct RayGeo {
 struct GeoDev {
     int N, P, Pp, G, NG;      // image side, planes, padded planes, group size, groups
     int V, NB, M, K;          // views, bins, subsets, max candidate bins per view in the gather
+    int tuneS;                // forward projector chunks per ray picked by pet_autotune (0: heuristic)
     double scale;             // sens * pixel_mm
     const ViewGeo *views;     // [V] in subset order
     const RayGeo *rays;       // [V * NB] in subset order

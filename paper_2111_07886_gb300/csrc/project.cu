@@ -204,6 +204,7 @@ void forward_shape(FwdArgs &a, int mode)
     const long long have = std::max<long long>(1, nrays * a.g.NG);
     int S = (int)std::min<long long>(8, std::max<long long>(1, (want + have - 1) / have));
     S = std::max(1, std::min(S, a.g.N / 16));
+    if (a.g.tuneS > 0 && mode != FWD_OBJECTIVE) S = a.g.tuneS;
     while (S > 1 && (256 / a.g.NG) % S) --S;          // S divides the rays-per-block budget
     a.S = S;
     a.R = std::max(1, 256 / (S * a.g.NG));
@@ -245,3 +246,55 @@ pet_status launch_forward_batch(const FwdArgs &shape, const Batch &b, int mode, 
 }
 
 }  // namespace pet
+
+using namespace pet;
+
+// Autotuner: times the subset-0 forward projection for every admissible chunk count S (1..8,
+// dividing the 256-thread block budget) and keeps the fastest in the geometry.  The choice is
+// per geometry, so every scan using it (alone or batched) runs the same shapes.
+extern "C" pet_status pet_autotune(pet_geometry *g, void *stream, int *best_S)
+{
+    if (!g) return fail(PET_ERR_INVALID, "pet_autotune: NULL geometry");
+    cudaStream_t st = as_stream(stream);
+    GeoDev &gd = g->dev;
+    const int nv = g->voff[1] - g->voff[0];
+    const size_t qb = (size_t)gd.N * gd.N * gd.Pp * 4, pb = (size_t)nv * gd.NB * gd.Pp * 4;
+    void *scr = nullptr;
+    PET_TRY(geometry_scratch(g, ((qb + 255) / 256) * 256 + pb, &scr));
+    char *img = reinterpret_cast<char *>(scr);
+    PET_CUDA(cudaMemsetAsync(img, 0, qb, st));
+    cudaEvent_t a, b;
+    PET_CUDA(cudaEventCreate(&a));
+    PET_CUDA(cudaEventCreate(&b));
+    float best = 1e30f;
+    int bestS = 0;
+    const int save = gd.tuneS;
+    for (int S = 1; S <= 8; ++S) {
+        if ((256 / gd.NG) % S) continue;
+        gd.tuneS = S;
+        FwdArgs fa{};
+        fa.g = gd;
+        fa.slot0 = g->voff[0];
+        fa.nviews = nv;
+        fa.img = img;
+        fa.out = img + ((qb + 255) / 256) * 256;
+        pet_status r = launch_forward(fa, FWD_PLAIN, AR_KAHAN, st);         // warm-up
+        float tot = 0.f;
+        for (int rep = 0; rep < 3 && r == PET_OK; ++rep) {
+            cudaEventRecord(a, st);
+            r = launch_forward(fa, FWD_PLAIN, AR_KAHAN, st);
+            cudaEventRecord(b, st);
+            cudaEventSynchronize(b);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, a, b);
+            tot += ms;
+        }
+        if (r != PET_OK) { gd.tuneS = save; cudaEventDestroy(a); cudaEventDestroy(b); return r; }
+        if (tot < best) { best = tot; bestS = S; }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    gd.tuneS = bestS;
+    if (best_S) *best_S = bestS;
+    return PET_OK;
+}

@@ -97,21 +97,32 @@ __device__ __forceinline__ T fast_div(T a, T b)
     else return __fdividef(a, b);
 }
 
+// |(gx, gy)|: FP32 kernels use x rsqrt(x) (two instructions, a few ulp)
+template <typename T>
+__device__ __forceinline__ T grad_norm(T gx, T gy)
+{
+    const T x = gx * gx + gy * gy;
+    if constexpr (sizeof(T) == 8) return sqrt(x);
+    else return x > 0.f ? x * rsqrtf(x) : 0.f;
+}
+
 // mu = max(0.01, |grad f| / mean(f)); nu = P_{nu1}^{nu2}(mean(mu) / mu)
 template <typename T>
 __device__ __forceinline__ T nu_of(T gx, T gy, T inv_mean_f, T mean_mu, T nu1, T nu2)
 {
-    T mu = sqrt(gx * gx + gy * gy) * inv_mean_f;
+    T mu = grad_norm(gx, gy) * inv_mean_f;
     mu = mu < T(0.01) ? T(0.01) : mu;
     return clampT<T>(fast_div(mean_mu, mu), nu1, nu2);
 }
+
+int sm_count();
 
 // f^{k,i} = P_t(f - lambda_k alpha_{k,i} nu S(f) (A_i^T w + (beta/M) grad R(f)))
 // Virtual block: tpv tiles of TP consecutive pixels x NG plane groups (thread = pixel * NG +
 // group); the (pixel, view) weights of each tile are computed once into shared memory.  A
 // persistent grid strides over the virtual blocks of one scan or of a batch of scans.
 template <int G, int KC, int AR>
-__global__ void __launch_bounds__(256) update_kernel(const __grid_constant__ UpdateArgs one,
+__global__ void __launch_bounds__(256, 3) update_kernel(const __grid_constant__ UpdateArgs one,
                                                      const Batch bt)
 {
     using T = typename ArithT<AR>::T;
@@ -255,7 +266,7 @@ __global__ void __launch_bounds__(256) image_kernel(const __grid_constant__ Imag
                 stencil<G, AR, false, true, false>(g, f, grp, ix, iy, T(0), T(0), fc, gr, gx, gy, rv);
 #pragma unroll
                 for (int p = 0; p < G; ++p) {
-                    T mu = sqrt(gx[p] * gx[p] + gy[p] * gy[p]) * inv_mean_f;
+                    T mu = grad_norm(gx[p], gy[p]) * inv_mean_f;
                     mu = mu < T(0.01) ? T(0.01) : mu;
                     if constexpr (KIND == 1) {
                         part += (grp * G + p < g.P) ? mu : T(0);
@@ -283,8 +294,6 @@ __global__ void __launch_bounds__(256) image_kernel(const __grid_constant__ Imag
     }
 }
 
-extern int sm_count();
-
 // pixel tiles per virtual block so that a scan never needs more partial sums than its reducer
 void update_shape(UpdateArgs &a)
 {
@@ -294,12 +303,15 @@ void update_shape(UpdateArgs &a)
     a.nvb = (ntiles + a.tpv - 1) / a.tpv;
 }
 
+// items per thread: at most ~4 virtual blocks per SM (each ends in a block reduction) and never
+// more virtual blocks than reduction slots
 void image_shape(ImageArgs &a)
 {
     const long long items = (long long)a.g.N * a.g.N * a.g.NG;
     const long long nblk = (items + 255) / 256;
     const int cap = a.red.capacity > 0 ? a.red.capacity : (1 << 30);
-    a.ipt = (int)std::max<long long>(1, (nblk + cap - 1) / cap);
+    const long long target = (long long)sm_count() * 4;
+    a.ipt = (int)std::max<long long>({1, (nblk + cap - 1) / cap, (nblk + target - 1) / target});
     a.nvb = (int)((nblk + a.ipt - 1) / a.ipt);
 }
 

@@ -63,6 +63,7 @@ SIGNATURES = {
     "pet_geometry_create": (_I, [ctypes.POINTER(GeometryDesc), _VP, ctypes.POINTER(_VP)]),
     "pet_geometry_destroy": (None, [_VP]),
     "pet_subset_size": (_I, [_VP, _I]),
+    "pet_autotune": (_I, [_VP, _VP, ctypes.POINTER(_I)]),
     "pet_sensitivity": (_I, [_VP, _VP, _VP]),
     "pet_forward_subset": (_I, [_VP, _I, _VP, _VP, _VP]),
     "pet_back_subset": (_I, [_VP, _I, _VP, _VP, _VP]),
@@ -180,6 +181,12 @@ class Geometry:
 
     def subset_size(self, subset: int) -> int:
         return lib().pet_subset_size(self.handle, subset)
+
+    def autotune(self, stream=None) -> int:
+        """Pick the forward projector's ray chunking by timing it; returns the chosen value."""
+        s = ctypes.c_int()
+        _check(lib().pet_autotune(self.handle, _stream(stream), ctypes.byref(s)))
+        return s.value
 
 
 def sensitivity(g: Geometry, d_p, stream=None):

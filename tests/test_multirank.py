@@ -1,0 +1,56 @@
+"""The multi-GPU path of bench.py is replicas only: each rank reconstructs its own scan, and
+the job's throughput is all ranks' subiterations over the slowest rank's time.  This runs that
+host logic as two gloo ranks on the CPU."""
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, world, port, q):
+    import torch
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    ms_local = [120.0, 150.0][rank]
+    ms_max = bench.reduce_max(ms_local, world, torch.device("cpu"))
+    value = bench.job_throughput(480, world, ms_max)
+    q.put((rank, ms_max, value, bench.replica_seed(0, rank)))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_aggregate_max_time_and_total_units():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert [r[1] for r in res] == [150.0, 150.0]
+    assert all(abs(r[2] - 2 * 480 / 0.150) < 1e-9 for r in res)
+    assert res[0][3] != res[1][3]                 # each replica gets its own scan
+
+
+def test_reference_arm_prints_only_on_rank0(monkeypatch, capsys):
+    import bench
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setattr("sys.argv", ["bench.py", "--impl", "reference"])
+    bench.main()
+    assert capsys.readouterr().out == ""
