@@ -3,6 +3,8 @@
 // backprojection gather, and the deterministic last-block FP64 reduction.
 #pragma once
 
+#include <type_traits>
+
 #include "pet_common.cuh"
 
 namespace pet {
@@ -92,6 +94,17 @@ __device__ __forceinline__ float2 add2(float2 a, float2 b)
     return r;
 }
 
+__device__ __forceinline__ float2 mul2(float2 a, float2 b)
+{
+    float2 r;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+
 __device__ __forceinline__ float2 sub2(float2 a, float2 b)
 {
     float2 r;
@@ -113,51 +126,64 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b)
 // ------------------------------------------------------------------------------------------
 template <int G, int AR> struct GroupSum {
     using T = typename ArithT<AR>::T;
-    T s[G], e[G];
+    static constexpr bool PACK = (AR != AR_FP64) && (G % 2 == 0);
+    static constexpr int NS = PACK ? G / 2 : G;
+    // packed: s2[q] holds planes (2q, 2q+1), so every f32x2 operand is an aligned register pair
+    typename std::conditional<PACK, float2, T>::type s2[NS], e2[NS];
 
     __device__ __forceinline__ void zero()
     {
 #pragma unroll
-        for (int p = 0; p < G; ++p) { s[p] = T(0); e[p] = T(0); }
+        for (int q = 0; q < NS; ++q) {
+            if constexpr (PACK) { s2[q] = make_float2(0.f, 0.f); e2[q] = make_float2(0.f, 0.f); }
+            else { s2[q] = T(0); e2[q] = T(0); }
+        }
+    }
+
+    __device__ __forceinline__ T s_at(int p) const
+    {
+        if constexpr (PACK) return (p & 1) ? s2[p >> 1].y : s2[p >> 1].x;
+        else return s2[p];
+    }
+    __device__ __forceinline__ T e_at(int p) const
+    {
+        if constexpr (PACK) return (p & 1) ? e2[p >> 1].y : e2[p >> 1].x;
+        else return e2[p];
     }
 
     // y_p = w0 x0_p + w1 x1_p (+ e_p for Kahan), then accumulate
     __device__ __forceinline__ void add2terms(T w0, const T (&x0)[G], T w1, const T (&x1)[G])
     {
-        if constexpr (AR == AR_KAHAN && G % 2 == 0) {
+        if constexpr (PACK) {
             const float2 W0 = make_float2(w0, w0), W1 = make_float2(w1, w1);
 #pragma unroll
-            for (int p = 0; p < G; p += 2) {
-                float2 S = make_float2(s[p], s[p + 1]), E = make_float2(e[p], e[p + 1]);
-                float2 y = fma2(W0, make_float2(x0[p], x0[p + 1]), E);
-                y = fma2(W1, make_float2(x1[p], x1[p + 1]), y);
-                float2 t = add2(S, y);
-                E = sub2(y, sub2(t, S));
-                s[p] = t.x; s[p + 1] = t.y; e[p] = E.x; e[p + 1] = E.y;
+            for (int q = 0; q < NS; ++q) {
+                const float2 X0 = make_float2(x0[2 * q], x0[2 * q + 1]);
+                const float2 X1 = make_float2(x1[2 * q], x1[2 * q + 1]);
+                if constexpr (AR == AR_KAHAN) {
+                    float2 y = fma2(W0, X0, e2[q]);
+                    y = fma2(W1, X1, y);
+                    const float2 t = add2(s2[q], y);
+                    e2[q] = sub2(y, sub2(t, s2[q]));
+                    s2[q] = t;
+                } else {
+                    s2[q] = fma2(W1, X1, fma2(W0, X0, s2[q]));
+                }
             }
         } else if constexpr (AR == AR_KAHAN) {
 #pragma unroll
             for (int p = 0; p < G; ++p) {
-                float y = fmaf(w0, x0[p], e[p]);
+                float y = fmaf(w0, x0[p], e2[p]);
                 y = fmaf(w1, x1[p], y);
-                float t = s[p] + y;
-                e[p] = y - (t - s[p]);
-                s[p] = t;
-            }
-        } else if constexpr (AR == AR_FP32 && G % 2 == 0) {
-            const float2 W0 = make_float2(w0, w0), W1 = make_float2(w1, w1);
-#pragma unroll
-            for (int p = 0; p < G; p += 2) {
-                float2 S = make_float2(s[p], s[p + 1]);
-                S = fma2(W0, make_float2(x0[p], x0[p + 1]), S);
-                S = fma2(W1, make_float2(x1[p], x1[p + 1]), S);
-                s[p] = S.x; s[p + 1] = S.y;
+                const float t = s2[p] + y;
+                e2[p] = y - (t - s2[p]);
+                s2[p] = t;
             }
         } else {
 #pragma unroll
             for (int p = 0; p < G; ++p) {
-                s[p] = fma(w0, x0[p], s[p]);
-                s[p] = fma(w1, x1[p], s[p]);
+                s2[p] = fma(w0, x0[p], s2[p]);
+                s2[p] = fma(w1, x1[p], s2[p]);
             }
         }
     }
@@ -165,21 +191,13 @@ template <int G, int AR> struct GroupSum {
     // scalar-weight-only form (sensitivity: x == 1)
     __device__ __forceinline__ void add_scalar(T y0)
     {
-        if constexpr (AR == AR_KAHAN) {
+        T x0[G], x1[G];
 #pragma unroll
-            for (int p = 0; p < G; ++p) {
-                float y = y0 + e[p];
-                float t = s[p] + y;
-                e[p] = y - (t - s[p]);
-                s[p] = t;
-            }
-        } else {
-#pragma unroll
-            for (int p = 0; p < G; ++p) s[p] += y0;
-        }
+        for (int p = 0; p < G; ++p) { x0[p] = T(1); x1[p] = T(0); }
+        add2terms(y0, x0, T(0), x1);
     }
 
-    __device__ __forceinline__ T value(int p) const { return s[p] + e[p]; }
+    __device__ __forceinline__ T value(int p) const { return s_at(p) + e_at(p); }
 };
 
 // ------------------------------------------------------------------------------------------
@@ -195,11 +213,17 @@ template <int G, int AR> struct GroupSum {
 // Phase 2 (bp_accumulate): every plane group of the pixel adds, view by view in order, the
 // <= KC-term partial with one compensated step (fixed order: deterministic, no atomics).
 // ------------------------------------------------------------------------------------------
-template <int KC, int AR> struct BpTable {
+template <int KC, int AR> struct BpEntry {
     using T = typename ArithT<AR>::T;
-    static constexpr int CAP = AR == AR_FP64 ? 1024 : 2048;   // (pixel, view) entries
-    int b0[CAP];
-    T w[KC][CAP];
+    int b0;
+    T w[KC];
+};
+
+template <int KC, int AR> struct BpTable {
+    static constexpr int CAP = (AR == AR_FP64 ? 1024 : 2048) / (KC > 2 ? 2 : 1);   // entries
+    // one entry per (pixel, view): read with one or two wide shared-memory loads
+    struct __align__(16) E : BpEntry<KC, AR> {};
+    E e[CAP];
 };
 
 template <int KC, int AR>
@@ -269,9 +293,11 @@ __device__ __forceinline__ void bp_fill(const GeoDev &g, int slot0, int u0, int 
 #pragma unroll
             for (int k = 0; k < KC; ++k) w[k] = T(0);
         }
-        tb.b0[e] = b0;
+        typename BpTable<KC, AR>::E ent;
+        ent.b0 = b0;
 #pragma unroll
-        for (int k = 0; k < KC; ++k) tb.w[k][e] = w[k];
+        for (int k = 0; k < KC; ++k) ent.w[k] = w[k];
+        tb.e[e] = ent;
     }
 }
 
@@ -286,19 +312,19 @@ __device__ __forceinline__ void bp_accumulate(const GeoDev &g, const BpTable<KC,
     using T = typename ArithT<AR>::T;
     const int NB = g.NB, Pp = g.Pp;
     for (int uu = 0; uu < nvc; ++uu) {
-        const int e = pl * nvc + uu;
-        const int b0 = tb.b0[e];
+        const typename BpTable<KC, AR>::E ent = tb.e[pl * nvc + uu];
+        const int b0 = ent.b0;
         if (proj == nullptr) {
             T s = T(0);
 #pragma unroll
-            for (int k = 0; k < KC; ++k) s += tb.w[k][e];
+            for (int k = 0; k < KC; ++k) s += ent.w[k];
             acc.add_scalar(s);
             continue;
         }
         const T *base = proj + (size_t)(u0 + uu) * NB * Pp + (size_t)grp * G;
 #pragma unroll
         for (int k = 0; k < KC; k += 2) {
-            const T w0 = tb.w[k][e], w1 = tb.w[k + 1][e];
+            const T w0 = ent.w[k], w1 = ent.w[k + 1];
             const int ba = b0 + k, bb = b0 + k + 1;
             T x0[G], x1[G];
             load_group<G, T>(base + (size_t)((unsigned)ba < (unsigned)NB ? ba : 0) * Pp, x0);

@@ -162,6 +162,7 @@ struct UpdateArgs {
 };
 pet_status launch_update(const UpdateArgs &a, int arith, cudaStream_t st);
 void update_shape(UpdateArgs &a);                          // fills nvb
+GeoDev update_geo(const GeoDev &g);                        // plane grouping of the update kernel
 pet_status launch_update_batch(const UpdateArgs &shape, const Batch &b, int arith,
                                cudaStream_t st);
 

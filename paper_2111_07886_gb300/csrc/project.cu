@@ -97,13 +97,13 @@ __global__ void __launch_bounds__(256) fwd_kernel(const __grid_constant__ FwdArg
             __syncthreads();
 #pragma unroll
             for (int p = 0; p < G; ++p) {
-                comb_s[p * 256 + threadIdx.x] = acc.s[p];
-                comb_e[p * 256 + threadIdx.x] = acc.e[p];
+                comb_s[p * 256 + threadIdx.x] = acc.s_at(p);
+                comb_e[p * 256 + threadIdx.x] = acc.e_at(p);
             }
             __syncthreads();
 #pragma unroll
             for (int p = 0; p < G; ++p) {
-                T s0 = acc.s[p], e0 = acc.e[p];
+                T s0 = acc.s_at(p), e0 = acc.e_at(p);
                 if (c == 0 && lane_ok) {            // idle lanes (>= R S NG) have no chunks
                     for (int cc = 1; cc < S; ++cc) {
                         const int o = p * 256 + (rl * S + cc) * NG + grp;

@@ -186,7 +186,7 @@ void pet::plan_subiter(pet_state *s, SubiterPlan *pl, bool with_objective)
     fa.gamma = s->gamma + (size_t)slot0 * gd.NB * gd.Pp;
     forward_shape(fa, FWD_RATIO);
     UpdateArgs &ua = pl->upd;
-    ua.g = gd;
+    ua.g = update_geo(gd);
     ua.slot0 = slot0;
     ua.nviews = nv;
     ua.w = s->w;

@@ -52,7 +52,23 @@ __device__ __forceinline__ void stencil(const GeoDev &g, const typename ArithT<A
         if (x < 0 || y < 0 || x >= N || y >= N) continue;
         T fk[G];
         load_group<G, T>(base + ((size_t)y * N + x) * Pp, fk);
-        if constexpr (RG || RV) {
+        if constexpr (RG && AR != AR_FP64 && G % 2 == 0) {
+            // packed FP32x2: two planes per instruction; 1/den^2 from the fast reciprocal
+            const float2 GR = make_float2(gamma_r, gamma_r), THREE = make_float2(3.f, 3.f);
+#pragma unroll
+            for (int p = 0; p < G; p += 2) {
+                const float2 c2 = make_float2(fc[p], fc[p + 1]), k2 = make_float2(fk[p], fk[p + 1]);
+                const float2 d = sub2(c2, k2);
+                const float2 ad = make_float2(fabsf(d.x), fabsf(d.y));
+                const float2 den = fma2(GR, ad, add2(add2(c2, k2), make_float2(eps, eps)));
+                const float2 t = fma2(GR, ad, fma2(THREE, k2, add2(c2, make_float2(2.f * eps, 2.f * eps))));
+                const float2 num = mul2(d, t);
+                const float2 den2 = mul2(den, den);
+                const float2 q = make_float2(__fdividef(num.x, den2.x), __fdividef(num.y, den2.y));
+                gr[p] += q.x;
+                gr[p + 1] += q.y;
+            }
+        } else if constexpr (RG || RV) {
 #pragma unroll
             for (int p = 0; p < G; ++p) {
                 const T d = fc[p] - fk[p];
@@ -294,6 +310,18 @@ __global__ void __launch_bounds__(256) image_kernel(const __grid_constant__ Imag
     }
 }
 
+// The update kernel works on half plane groups (4 planes, one 16-byte load per pixel): its
+// per-thread state then fits the register budget of three blocks per SM.
+GeoDev update_geo(const GeoDev &g)
+{
+    GeoDev u = g;
+    if (g.G == 8) {
+        u.G = 4;
+        u.NG = g.Pp / 4;
+    }
+    return u;
+}
+
 // pixel tiles per virtual block so that a scan never needs more partial sums than its reducer
 void update_shape(UpdateArgs &a)
 {
@@ -332,8 +360,8 @@ static pet_status update_any(const UpdateArgs &a, const Batch &b, int arith, int
         if (a.g.K <= 2) update_dispatch<1, 2>(a, b, arith, grid, st);
         else update_dispatch<1, 4>(a, b, arith, grid, st);
     } else {
-        if (a.g.K <= 2) update_dispatch<8, 2>(a, b, arith, grid, st);
-        else update_dispatch<8, 4>(a, b, arith, grid, st);
+        if (a.g.K <= 2) update_dispatch<4, 2>(a, b, arith, grid, st);
+        else update_dispatch<4, 4>(a, b, arith, grid, st);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "update_kernel launch");
