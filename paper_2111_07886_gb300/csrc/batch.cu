@@ -194,7 +194,7 @@ static pet_status class_launches(pet_batch *b, BatchClass *c, const char *dev, c
     fs.g.G = c->G;
     fs.g.K = c->KC;
     UpdateArgs us{};
-    us.g.G = c->G == 8 ? 4 : c->G;
+    us.g.G = c->G;
     us.g.K = c->KC;
     ImageArgs is{};
     is.g.G = c->G;

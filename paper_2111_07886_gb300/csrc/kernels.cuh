@@ -321,14 +321,17 @@ __device__ __forceinline__ void bp_accumulate(const GeoDev &g, const BpTable<KC,
             acc.add_scalar(s);
             continue;
         }
-        const T *base = proj + (size_t)(u0 + uu) * NB * Pp + (size_t)grp * G;
+        // 32-bit element offsets (sinograms hold < 2^32 elements)
+        const unsigned rowu = (unsigned)(u0 + uu) * (unsigned)NB;
 #pragma unroll
         for (int k = 0; k < KC; k += 2) {
             const T w0 = ent.w[k], w1 = ent.w[k + 1];
             const int ba = b0 + k, bb = b0 + k + 1;
+            const unsigned oa = (rowu + ((unsigned)ba < (unsigned)NB ? (unsigned)ba : 0u)) * (unsigned)Pp + (unsigned)(grp * G);
+            const unsigned ob = (rowu + ((unsigned)bb < (unsigned)NB ? (unsigned)bb : 0u)) * (unsigned)Pp + (unsigned)(grp * G);
             T x0[G], x1[G];
-            load_group<G, T>(base + (size_t)((unsigned)ba < (unsigned)NB ? ba : 0) * Pp, x0);
-            load_group<G, T>(base + (size_t)((unsigned)bb < (unsigned)NB ? bb : 0) * Pp, x1);
+            load_group<G, T>(proj + oa, x0);
+            load_group<G, T>(proj + ob, x1);
             acc.add2terms(w0, x0, w1, x1);
         }
     }

@@ -66,8 +66,8 @@ __global__ void __launch_bounds__(256) fwd_kernel(const __grid_constant__ FwdArg
                     l0 = ok0 ? l0 : 0.0;
                     l1 = ok1 ? l1 : 0.0;
                     T x0[G], x1[G];
-                    load_group<G, T>(img + (size_t)(d * ds + (ok0 ? r0 : 0) * cs) * Pp, x0);
-                    load_group<G, T>(img + (size_t)(d * ds + (ok1 ? r1 : 0) * cs) * Pp, x1);
+                    load_group<G, T>(img + (unsigned)(d * ds + (ok0 ? r0 : 0) * cs) * (unsigned)Pp, x0);
+                    load_group<G, T>(img + (unsigned)(d * ds + (ok1 ? r1 : 0) * cs) * (unsigned)Pp, x1);
                     acc.add2terms(l0, x0, l1, x1);
                 }
             } else {
@@ -84,8 +84,8 @@ __global__ void __launch_bounds__(256) fwd_kernel(const __grid_constant__ FwdArg
                     l0 = ok0 ? l0 : 0.f;
                     l1 = ok1 ? l1 : 0.f;
                     T x0[G], x1[G];
-                    load_group<G, T>(img + (size_t)(d * ds + (ok0 ? r0 : 0) * cs) * Pp, x0);
-                    load_group<G, T>(img + (size_t)(d * ds + (ok1 ? r1 : 0) * cs) * Pp, x1);
+                    load_group<G, T>(img + (unsigned)(d * ds + (ok0 ? r0 : 0) * cs) * (unsigned)Pp, x0);
+                    load_group<G, T>(img + (unsigned)(d * ds + (ok1 ? r1 : 0) * cs) * (unsigned)Pp, x1);
                     acc.add2terms(l0, x0, l1, x1);
                     lo += stp;
                 }

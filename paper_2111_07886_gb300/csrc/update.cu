@@ -30,8 +30,9 @@ __device__ __forceinline__ void stencil(const GeoDev &g, const typename ArithT<A
 {
     using T = typename ArithT<AR>::T;
     const int N = g.N, Pp = g.Pp;
-    const T *base = f + (size_t)grp * G;
-    load_group<G, T>(base + ((size_t)iy * N + ix) * Pp, fc);
+    const T *base = f + grp * G;
+    const unsigned jc = (unsigned)iy * (unsigned)N + (unsigned)ix;   // images hold < 2^32 elements
+    load_group<G, T>(base + jc * (unsigned)Pp, fc);
     const T hx = (ix > 0 && ix < N - 1) ? T(0.5) : T(1);
     const T hy = (iy > 0 && iy < N - 1) ? T(0.5) : T(1);
 #pragma unroll
@@ -51,7 +52,7 @@ __device__ __forceinline__ void stencil(const GeoDev &g, const typename ArithT<A
         const int x = ix + dx, y = iy + dy;
         if (x < 0 || y < 0 || x >= N || y >= N) continue;
         T fk[G];
-        load_group<G, T>(base + ((size_t)y * N + x) * Pp, fk);
+        load_group<G, T>(base + (unsigned)((int)jc + dy * N + dx) * (unsigned)Pp, fk);
         if constexpr (RG && AR != AR_FP64 && G % 2 == 0) {
             // packed FP32x2: two planes per instruction; 1/den^2 from the fast reciprocal
             const float2 GR = make_float2(gamma_r, gamma_r), THREE = make_float2(3.f, 3.f);
@@ -167,6 +168,35 @@ __global__ void __launch_bounds__(256, 3) update_kernel(const __grid_constant__ 
         for (int tile = vloc * a.tpv; tile < min(ntiles, (vloc + 1) * a.tpv); ++tile) {
             const int j0 = tile * TP, j = j0 + pl;
             const bool active = pl < TP && j < npix;
+            // 1. stencil first, folded into fc, coef = lambda alpha nu S and rg = (beta/M) grad R,
+            //    so that the backprojection's accumulators do not coexist with the stencil state
+            T fc[G], coef[G], rg[G];
+            if (active) {
+                const int ix = j % N, iy = j / N;
+                T gr[G], gx[G], gy[G], rv[G];
+                if (dyn) stencil<G, AR, true, true, false>(g, f, grp, ix, iy, (T)a.gamma_r, (T)a.eps, fc, gr, gx, gy, rv);
+                else stencil<G, AR, true, false, false>(g, f, grp, ix, iy, (T)a.gamma_r, (T)a.eps, fc, gr, gx, gy, rv);
+                T nu[G];
+                if (a.nu_mode == 3) {
+                    load_group<G, T>(reinterpret_cast<const T *>(a.nu_frozen) + (unsigned)j * (unsigned)Pp + grp * G, nu);
+                } else if (!dyn) {
+#pragma unroll
+                    for (int p = 0; p < G; ++p) nu[p] = T(1);
+                } else {
+#pragma unroll
+                    for (int p = 0; p < G; ++p) nu[p] = nu_of<T>(gx[p], gy[p], inv_mean_f, mean_mu, nu1, nu2);
+                    if (a.nu_mode == 2)
+                        store_group<G, T>(reinterpret_cast<T *>(a.nu_frozen) + (unsigned)j * (unsigned)Pp + grp * G, nu);
+                }
+                const T ip = invp[j] * (T)a.invp_scale;
+#pragma unroll
+                for (int p = 0; p < G; ++p) {
+                    const T S = (fc[p] < halfU ? fc[p] : U - fc[p]) * ip;
+                    coef[p] = lam * nu[p] * S;
+                    rg[p] = bm * gr[p];
+                }
+            }
+            // 2. gather backprojection A_i^T w with the tile's shared (pixel, view) weights
             GroupSum<G, AR> bp;
             bp.zero();
             for (int u0 = 0; u0 < a.nviews; u0 += VC) {
@@ -177,36 +207,18 @@ __global__ void __launch_bounds__(256, 3) update_kernel(const __grid_constant__ 
                 if (active) bp_accumulate<G, KC, AR>(g, tb, w, u0, nvc, pl, grp, bp);
             }
             if (!active) continue;
-            const int ix = j % N, iy = j / N;
-            T fc[G], gr[G], gx[G], gy[G], rv[G];
-            if (dyn) stencil<G, AR, true, true, false>(g, f, grp, ix, iy, (T)a.gamma_r, (T)a.eps, fc, gr, gx, gy, rv);
-            else stencil<G, AR, true, false, false>(g, f, grp, ix, iy, (T)a.gamma_r, (T)a.eps, fc, gr, gx, gy, rv);
-            T nu[G];
-            if (a.nu_mode == 3) {
-                load_group<G, T>(reinterpret_cast<const T *>(a.nu_frozen) + (size_t)j * Pp + (size_t)grp * G, nu);
-            } else if (!dyn) {
-#pragma unroll
-                for (int p = 0; p < G; ++p) nu[p] = T(1);
-            } else {
-#pragma unroll
-                for (int p = 0; p < G; ++p) nu[p] = nu_of<T>(gx[p], gy[p], inv_mean_f, mean_mu, nu1, nu2);
-                if (a.nu_mode == 2)
-                    store_group<G, T>(reinterpret_cast<T *>(a.nu_frozen) + (size_t)j * Pp + (size_t)grp * G, nu);
-            }
-            const T ip = invp[j] * (T)a.invp_scale;
+            // 3. step and clamp P_t
             T out[G];
 #pragma unroll
             for (int p = 0; p < G; ++p) {
-                const T fj = fc[p];
-                const T d = scale * bp.value(p) + bm * gr[p];
-                const T S = (fj < halfU ? fj : U - fj) * ip;
-                T ft = fj - lam * nu[p] * S * d;
+                const T d = scale * bp.value(p) + rg[p];
+                T ft = fc[p] - coef[p] * d;
                 ft = ft <= T(0) ? tt : (ft >= U ? U - tt : ft);
                 const bool valid = grp * G + p < g.P;
                 out[p] = valid ? ft : T(0);
                 part += out[p];
             }
-            store_group<G, T>(reinterpret_cast<T *>(a.fout) + (size_t)j * Pp + (size_t)grp * G, out);
+            store_group<G, T>(reinterpret_cast<T *>(a.fout) + (unsigned)j * (unsigned)Pp + grp * G, out);
         }
         double v[1] = {(double)part};
         grid_reduce<1>(v, a.red, a.sum_fout, vloc, nv);
@@ -310,17 +322,9 @@ __global__ void __launch_bounds__(256) image_kernel(const __grid_constant__ Imag
     }
 }
 
-// The update kernel works on half plane groups (4 planes, one 16-byte load per pixel): its
-// per-thread state then fits the register budget of three blocks per SM.
-GeoDev update_geo(const GeoDev &g)
-{
-    GeoDev u = g;
-    if (g.G == 8) {
-        u.G = 4;
-        u.NG = g.Pp / 4;
-    }
-    return u;
-}
+// Plane grouping of the update kernel: the full 8-plane groups (measured faster at three blocks
+// per SM than 4-plane half groups, whose per-thread overheads double).
+GeoDev update_geo(const GeoDev &g) { return g; }
 
 // pixel tiles per virtual block so that a scan never needs more partial sums than its reducer
 void update_shape(UpdateArgs &a)
@@ -360,8 +364,8 @@ static pet_status update_any(const UpdateArgs &a, const Batch &b, int arith, int
         if (a.g.K <= 2) update_dispatch<1, 2>(a, b, arith, grid, st);
         else update_dispatch<1, 4>(a, b, arith, grid, st);
     } else {
-        if (a.g.K <= 2) update_dispatch<4, 2>(a, b, arith, grid, st);
-        else update_dispatch<4, 4>(a, b, arith, grid, st);
+        if (a.g.K <= 2) update_dispatch<8, 2>(a, b, arith, grid, st);
+        else update_dispatch<8, 4>(a, b, arith, grid, st);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "update_kernel launch");
