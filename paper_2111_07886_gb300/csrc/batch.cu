@@ -63,6 +63,8 @@ struct pet_batch {
     int use_graph = 1;
     std::vector<pet::BatchClass *> classes;
     int grid = 0;
+    cudaStream_t side = nullptr;            // mu passes run beside the forward projections
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 using namespace pet;
@@ -86,6 +88,13 @@ extern "C" pet_status pet_batch_create(int capacity, int use_graph, pet_batch **
     b->capacity = capacity;
     b->use_graph = use_graph ? 1 : 0;
     b->grid = sm_count() * 4;
+    cudaError_t e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        delete b;
+        return cuda_fail(e, "pet_batch_create: side stream");
+    }
     *out = b;
     return PET_OK;
 }
@@ -97,6 +106,12 @@ extern "C" void pet_batch_destroy(pet_batch *b)
         for (int k = 0; k < 2; ++k)
             if (c->done[k] && c->used[k]) cudaEventSynchronize(c->done[k]);
         class_free(c);
+    }
+    if (b->side) {
+        cudaStreamSynchronize(b->side);
+        cudaStreamDestroy(b->side);
+        cudaEventDestroy(b->ev_fork);
+        cudaEventDestroy(b->ev_join);
     }
     delete b;
 }
@@ -204,8 +219,13 @@ static pet_status class_launches(pet_batch *b, BatchClass *c, const char *dev, c
     Batch bu{dev + c->off_upd, pre + 2 * (cap + 1), cap, b->grid};
     Batch bo{dev + c->off_objf, pre + 3 * (cap + 1), cap, b->grid};
     Batch br{dev + c->off_objr, pre + 4 * (cap + 1), cap, b->grid};
-    PET_TRY(launch_mu_sum_batch(is, bm, c->arith, st));
+    // mu passes on the side stream, joined before the update (a parallel branch in the graph)
+    PET_CUDA(cudaEventRecord(b->ev_fork, st));
+    PET_CUDA(cudaStreamWaitEvent(b->side, b->ev_fork, 0));
+    PET_TRY(launch_mu_sum_batch(is, bm, c->arith, b->side));
+    PET_CUDA(cudaEventRecord(b->ev_join, b->side));
     PET_TRY(launch_forward_batch(fs, bf, FWD_RATIO, c->arith, st));
+    PET_CUDA(cudaStreamWaitEvent(st, b->ev_join, 0));
     PET_TRY(launch_update_batch(us, bu, c->arith, st));
     PET_TRY(launch_forward_batch(fs, bo, FWD_OBJECTIVE, c->arith, st));
     PET_TRY(launch_rdp_value_batch(is, br, c->arith, st));

@@ -23,6 +23,17 @@ __device__ __forceinline__ void load_group(const T *__restrict__ p, T (&v)[G])
 {
     if constexpr (G == 1) {
         v[0] = __ldg(p);
+    } else if constexpr (G == 8 && sizeof(T) == 4) {
+        // one 256-bit load per plane group (sm_100+; the group is 32-byte aligned)
+        asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                     : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]),
+                       "=f"(v[6]), "=f"(v[7])
+                     : "l"(p));
+    } else if constexpr (G == 8 && sizeof(T) == 8) {
+        asm("ld.global.nc.v4.f64 {%0, %1, %2, %3}, [%4];"
+                     : "=d"(v[0]), "=d"(v[1]), "=d"(v[2]), "=d"(v[3]) : "l"(p));
+        asm("ld.global.nc.v4.f64 {%0, %1, %2, %3}, [%4];"
+                     : "=d"(v[4]), "=d"(v[5]), "=d"(v[6]), "=d"(v[7]) : "l"(p + 4));
     } else if constexpr (sizeof(T) == 4) {
 #pragma unroll
         for (int q = 0; q < G / 4; ++q) {
@@ -43,6 +54,11 @@ __device__ __forceinline__ void load_group_i(const int *__restrict__ p, int (&v)
 {
     if constexpr (G == 1) {
         v[0] = __ldg(p);
+    } else if constexpr (G == 8) {
+        asm("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                     : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                       "=r"(v[6]), "=r"(v[7])
+                     : "l"(p));
     } else {
 #pragma unroll
         for (int q = 0; q < G / 4; ++q) {
@@ -57,6 +73,11 @@ __device__ __forceinline__ void store_group(T *__restrict__ p, const T (&v)[G])
 {
     if constexpr (G == 1) {
         p[0] = v[0];
+    } else if constexpr (G == 8 && sizeof(T) == 4) {
+        asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
+                     :: "l"(p), "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]),
+                        "f"(v[6]), "f"(v[7])
+                     : "memory");
     } else if constexpr (sizeof(T) == 4) {
 #pragma unroll
         for (int q = 0; q < G / 4; ++q)

@@ -211,6 +211,8 @@ struct pet_state {
     double tn = 1.0;                // Nesterov t_{k,i}
     double sens_ratio = 1.0;        // this scan's sens / the geometry's sens (A and p scale with it)
     cudaStream_t alloc_stream = nullptr;   // non-null: buffers are stream-ordered allocations
+    cudaStream_t side = nullptr;           // the mu pass runs here, beside the forward projection
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     size_t q_bytes = 0, sino_elems = 0, w_bytes = 0;
 };
 

@@ -37,6 +37,14 @@ pet_status pet::check_params(const pet_params *p)
 static void state_free(pet_state *s)
 {
     if (!s) return;
+    if (s->side) {
+        cudaStreamSynchronize(s->side);
+        cudaStreamDestroy(s->side);
+        cudaEventDestroy(s->ev_fork);
+        cudaEventDestroy(s->ev_join);
+        s->side = nullptr;
+        s->ev_fork = s->ev_join = nullptr;
+    }
     auto rel = [&](void *p) {
         if (!p) return;
         if (s->alloc_stream) cudaFreeAsync(p, s->alloc_stream);
@@ -218,12 +226,25 @@ void pet::plan_subiter(pet_state *s, SubiterPlan *pl, bool with_objective)
     if (pl->objective) objective_args(s, s->objhist + 3 * s->k, &pl->obj_fwd, &pl->obj_rdp);
 }
 
+// The mu pass and the forward projection only read f^{k,i-1}: the mu pass runs on a side stream
+// forked from `st` and joined before the update.
 static pet_status state_subiter(pet_state *s, cudaStream_t st)
 {
     SubiterPlan pl;
     plan_subiter(s, &pl, false);
-    if (pl.mu) PET_TRY(launch_mu_sum(pl.mu_args, pl.arith, st));
+    if (pl.mu) {
+        if (!s->side) {
+            PET_CUDA(cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking));
+            PET_CUDA(cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming));
+            PET_CUDA(cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming));
+        }
+        PET_CUDA(cudaEventRecord(s->ev_fork, st));
+        PET_CUDA(cudaStreamWaitEvent(s->side, s->ev_fork, 0));
+        PET_TRY(launch_mu_sum(pl.mu_args, pl.arith, s->side));
+        PET_CUDA(cudaEventRecord(s->ev_join, s->side));
+    }
     PET_TRY(launch_forward(pl.fwd, FWD_RATIO, pl.arith, st));
+    if (pl.mu) PET_CUDA(cudaStreamWaitEvent(st, s->ev_join, 0));
     return launch_update(pl.upd, pl.arith, st);
 }
 
