@@ -106,7 +106,9 @@ const char *pet_last_error(void);
 /* ------------------------------------------------------------------------------------------
  * Geometry (Sec. II-A/II-B).  Builds the per-view / per-ray walk tables in FP64 on the host,
  * uploads them, and computes the sensitivity p_j of Eq. pj (one backprojection of ones over all
- * views) on the device.  Synchronises `stream` before returning.  PET_ERR_INVALID for a bad desc.
+ * views) on the device.  Synchronises `stream` before returning.  PET_ERR_INVALID for a bad desc
+ * (limits: 1 <= n <= 8192, 1 <= nplanes <= 2048, nbins >= 4, 1 <= nsubsets <= nviews,
+ * bin_mm >= 0.36 pixel_mm, fewer than 4e9 image or sinogram elements).
  * ---------------------------------------------------------------------------------------- */
 pet_status pet_geometry_create(const pet_geometry_desc *desc, void *stream, pet_geometry **out);
 void pet_geometry_destroy(pet_geometry *g);

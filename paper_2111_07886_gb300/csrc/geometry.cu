@@ -227,12 +227,12 @@ extern "C" pet_status pet_geometry_create(const pet_geometry_desc *desc, void *s
     if (!desc || !out) return fail(PET_ERR_INVALID, "pet_geometry_create: NULL argument");
     *out = nullptr;
     const pet_geometry_desc &d = *desc;
-    if (d.n < 1 || d.n > 8192 || d.nplanes < 1 || d.nviews < 1 || d.nbins < 1 ||
+    if (d.n < 1 || d.n > 8192 || d.nplanes < 1 || d.nviews < 1 || d.nbins < 4 ||
         d.nsubsets < 1 || d.nsubsets > d.nviews || !(d.pixel_mm > 0) || !(d.bin_mm > 0) ||
         !(d.sens > 0) || !std::isfinite(d.pixel_mm) || !std::isfinite(d.bin_mm) ||
         !std::isfinite(d.sens))
         return fail(PET_ERR_INVALID, "pet_geometry_create: invalid geometry description "
-                                     "(need n in [1,8192], nplanes, nviews, nbins >= 1, "
+                                     "(need n in [1,8192], nplanes, nviews >= 1, nbins >= 4, "
                                      "1 <= nsubsets <= nviews, pixel_mm, bin_mm, sens > 0)");
     if (d.nplanes > 2048)
         return fail(PET_ERR_INVALID, "pet_geometry_create: at most 2048 planes");

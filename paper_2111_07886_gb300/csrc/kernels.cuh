@@ -138,6 +138,82 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b)
 }
 
 // ------------------------------------------------------------------------------------------
+// Two FP32 planes in one 64-bit register pair (low word = even plane): the operands of the
+// f32x2 instructions stay paired, with no repacking between instructions.
+// ------------------------------------------------------------------------------------------
+typedef unsigned long long f2x;
+
+__device__ __forceinline__ f2x vpk(float lo, float hi)
+{
+    f2x r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ f2x vsplat(float v) { return vpk(v, v); }
+__device__ __forceinline__ void vunpk(f2x v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2x vfma(f2x a, f2x b, f2x c)
+{
+    f2x r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ f2x vadd(f2x a, f2x b)
+{
+    f2x r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2x vsub(f2x a, f2x b)
+{
+    f2x r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2x vmul(f2x a, f2x b)
+{
+    f2x r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2x vabs(f2x a)       // clears both sign bits
+{
+    f2x r;
+    asm("and.b64 %0, %1, 0x7FFFFFFF7FFFFFFF;" : "=l"(r) : "l"(a));
+    return r;
+}
+__device__ __forceinline__ f2x vrcp(f2x a)       // hardware approximate reciprocal per lane
+{
+    float x, y;
+    vunpk(a, x, y);
+    asm("rcp.approx.ftz.f32 %0, %0;" : "+f"(x));
+    asm("rcp.approx.ftz.f32 %0, %0;" : "+f"(y));
+    return vpk(x, y);
+}
+__device__ __forceinline__ f2x vrsqrt(f2x a)     // hardware approximate 1/sqrt per lane
+{
+    float x, y;
+    vunpk(a, x, y);
+    asm("rsqrt.approx.ftz.f32 %0, %0;" : "+f"(x));
+    asm("rsqrt.approx.ftz.f32 %0, %0;" : "+f"(y));
+    return vpk(x, y);
+}
+
+// one 8-plane FP32 group (32-byte aligned) as four pairs, through the read-only path
+__device__ __forceinline__ void load8x(const float *__restrict__ p, f2x (&v)[4])
+{
+    asm("ld.global.nc.v4.b64 {%0, %1, %2, %3}, [%4];"
+        : "=l"(v[0]), "=l"(v[1]), "=l"(v[2]), "=l"(v[3]) : "l"(p));
+}
+__device__ __forceinline__ void store8x(float *__restrict__ p, const f2x (&v)[4])
+{
+    asm volatile("st.global.v4.b64 [%0], {%1, %2, %3, %4};"
+                 :: "l"(p), "l"(v[0]), "l"(v[1]), "l"(v[2]), "l"(v[3]) : "memory");
+}
+
+// ------------------------------------------------------------------------------------------
 // Sums of G planes.  Each step adds the two-term contribution w0 x0 + w1 x1 of one driving
 // step (forward) or one view (backward).
 //   AR_FP32 : s += w0 x0 + w1 x1 with FMAs
@@ -236,8 +312,8 @@ template <int G, int AR> struct GroupSum {
 // ------------------------------------------------------------------------------------------
 template <int KC, int AR> struct BpEntry {
     using T = typename ArithT<AR>::T;
-    int b0;
-    T w[KC];
+    unsigned off;      // element offset of the group row (u NB + b0) Pp, b0 clamped to [0, NB - KC]
+    T w[KC];           // lengths for bins b0 .. b0 + KC - 1 (zero outside the footprint)
 };
 
 template <int KC, int AR> struct BpTable {
@@ -304,7 +380,7 @@ __device__ __forceinline__ void bp_fill(const GeoDev &g, int slot0, int u0, int 
     using T = typename ArithT<AR>::T;
     const int nthr = blockDim.x;
     for (int e = threadIdx.x; e < np * nvc; e += nthr) {
-        const int pl = e / nvc, u = u0 + e % nvc;
+        const int pl = e / nvc, u = u0 + e % nvc;   // u: view within the subset
         const int j = j0 + pl;
         int b0 = 0;
         T w[KC];
@@ -314,10 +390,19 @@ __device__ __forceinline__ void bp_fill(const GeoDev &g, int slot0, int u0, int 
 #pragma unroll
             for (int k = 0; k < KC; ++k) w[k] = T(0);
         }
+        // Clamp the first bin into [0, NB - KC] and shift the lengths with it, so that all KC
+        // rows of the entry exist (bins outside [0, NB) already carry zero length).
+        const int bc = min(max(b0, 0), g.NB - KC);
         typename BpTable<KC, AR>::E ent;
-        ent.b0 = b0;
+        ent.off = ((unsigned)u * (unsigned)g.NB + (unsigned)bc) * (unsigned)g.Pp;
 #pragma unroll
-        for (int k = 0; k < KC; ++k) ent.w[k] = w[k];
+        for (int k = 0; k < KC; ++k) {
+            const int src = k + bc - b0;
+            T v = T(0);
+#pragma unroll
+            for (int m = 0; m < KC; ++m) v = (m == src) ? w[m] : v;
+            ent.w[k] = v;
+        }
         tb.e[e] = ent;
     }
 }
@@ -331,10 +416,10 @@ __device__ __forceinline__ void bp_accumulate(const GeoDev &g, const BpTable<KC,
                                               GroupSum<G, AR> &acc)
 {
     using T = typename ArithT<AR>::T;
-    const int NB = g.NB, Pp = g.Pp;
+    const unsigned Pp = (unsigned)g.Pp;
+    const T *base = proj + grp * G;
     for (int uu = 0; uu < nvc; ++uu) {
         const typename BpTable<KC, AR>::E ent = tb.e[pl * nvc + uu];
-        const int b0 = ent.b0;
         if (proj == nullptr) {
             T s = T(0);
 #pragma unroll
@@ -343,17 +428,13 @@ __device__ __forceinline__ void bp_accumulate(const GeoDev &g, const BpTable<KC,
             continue;
         }
         // 32-bit element offsets (sinograms hold < 2^32 elements)
-        const unsigned rowu = (unsigned)(u0 + uu) * (unsigned)NB;
+        const T *row = base + ent.off;
 #pragma unroll
         for (int k = 0; k < KC; k += 2) {
-            const T w0 = ent.w[k], w1 = ent.w[k + 1];
-            const int ba = b0 + k, bb = b0 + k + 1;
-            const unsigned oa = (rowu + ((unsigned)ba < (unsigned)NB ? (unsigned)ba : 0u)) * (unsigned)Pp + (unsigned)(grp * G);
-            const unsigned ob = (rowu + ((unsigned)bb < (unsigned)NB ? (unsigned)bb : 0u)) * (unsigned)Pp + (unsigned)(grp * G);
             T x0[G], x1[G];
-            load_group<G, T>(proj + oa, x0);
-            load_group<G, T>(proj + ob, x1);
-            acc.add2terms(w0, x0, w1, x1);
+            load_group<G, T>(row + k * Pp, x0);
+            load_group<G, T>(row + (k + 1) * Pp, x1);
+            acc.add2terms(ent.w[k], x0, ent.w[k + 1], x1);
         }
     }
 }

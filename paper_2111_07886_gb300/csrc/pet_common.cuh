@@ -127,7 +127,7 @@ enum FwdMode { FWD_PLAIN = 0, FWD_RATIO = 1, FWD_OBJECTIVE = 2 };
 enum Arith { AR_FP32 = 0, AR_KAHAN = 1, AR_FP64 = 2 };
 
 pet_status launch_forward(const FwdArgs &a, int mode, int arith, cudaStream_t st);
-void forward_shape(FwdArgs &a, int mode);                 // fills S, R, nvb
+void forward_shape(FwdArgs &a, int mode, int arith);      // fills S, R, tpv, nvb
 pet_status launch_forward_batch(const FwdArgs &shape, const Batch &b, int mode, int arith,
                                 cudaStream_t st);
 
@@ -161,7 +161,7 @@ struct UpdateArgs {
     int nvb;                   // virtual blocks of this scan
 };
 pet_status launch_update(const UpdateArgs &a, int arith, cudaStream_t st);
-void update_shape(UpdateArgs &a);                          // fills nvb
+void update_shape(UpdateArgs &a, int arith);               // fills tpv, nvb
 GeoDev update_geo(const GeoDev &g);                        // plane grouping of the update kernel
 pet_status launch_update_batch(const UpdateArgs &shape, const Batch &b, int arith,
                                cudaStream_t st);

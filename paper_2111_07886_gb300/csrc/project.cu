@@ -9,6 +9,9 @@
 // lengths are l1 = frac(hi) / minor and l0 = L - l1, which is Siddon's length set computed in
 // a fixed-trip loop without a merge.  The cross coordinate is stepped exactly in Q32.32 fixed
 // point (FP32 kernels) so positions keep 32 fractional bits at any image size.
+#include <mutex>
+#include <vector>
+
 #include "kernels.cuh"
 #include "profile.cuh"
 
@@ -181,6 +184,39 @@ static void fwd_dispatch(const FwdArgs &a, const Batch &b, int mode, int arith, 
     else fwd_dispatch_mode<G, AR_FP64>(a, b, mode, grid, st);
 }
 
+template <int G, int AR>
+static const void *fwd_fn_mode(int mode)
+{
+    if (mode == FWD_PLAIN) return (const void *)fwd_kernel<G, AR, FWD_PLAIN>;
+    if (mode == FWD_RATIO) return (const void *)fwd_kernel<G, AR, FWD_RATIO>;
+    return (const void *)fwd_kernel<G, AR, FWD_OBJECTIVE>;
+}
+
+template <int G>
+static const void *fwd_fn_g(int mode, int arith)
+{
+    if (arith == AR_FP32) return fwd_fn_mode<G, AR_FP32>(mode);
+    if (arith == AR_KAHAN) return fwd_fn_mode<G, AR_KAHAN>(mode);
+    return fwd_fn_mode<G, AR_FP64>(mode);
+}
+
+// Resident 256-thread blocks per SM of one kernel instantiation (cached per function).
+int resident_blocks(const void *fn)
+{
+    static std::mutex mu;
+    static std::vector<std::pair<const void *, int>> cache;
+    std::lock_guard<std::mutex> lk(mu);
+    for (const auto &c : cache)
+        if (c.first == fn) return c.second;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, 256, 0) != cudaSuccess || n < 1) {
+        cudaGetLastError();
+        n = 1;
+    }
+    cache.emplace_back(fn, n);
+    return n;
+}
+
 int sm_count()
 {
     static int n = 0;
@@ -195,9 +231,9 @@ int sm_count()
 
 // Chunks per ray (S) so that one subset projection has about one full-occupancy wave of
 // threads, with >= 16 driving steps per chunk; R rays per 256-thread virtual block.  The
-// objective mode uses virtual blocks of several ray tiles so that it never needs more partial
-// sums than its reducer holds.
-void forward_shape(FwdArgs &a, int mode)
+// objective mode groups its ray tiles into one wave of virtual blocks (each ends in a reduction
+// step), never more than its reducer holds partial sums for.
+void forward_shape(FwdArgs &a, int mode, int arith)
 {
     const long long nrays = (long long)a.nviews * a.g.NB;
     const long long want = (long long)sm_count() * 2048;
@@ -210,8 +246,14 @@ void forward_shape(FwdArgs &a, int mode)
     a.R = std::max(1, 256 / (S * a.g.NG));
     const long long ntiles = (nrays + a.R - 1) / a.R;
     a.tpv = 1;
-    if (mode == FWD_OBJECTIVE && a.red.capacity > 0 && ntiles > a.red.capacity)
-        a.tpv = (int)((ntiles + a.red.capacity - 1) / a.red.capacity);
+    if (mode == FWD_OBJECTIVE) {
+        // each virtual block ends in a block reduction and a grid-wide ticket: one wave of them
+        const void *fn = a.g.G == 1 ? fwd_fn_g<1>(mode, arith) : fwd_fn_g<8>(mode, arith);
+        const long long slots = (long long)sm_count() * resident_blocks(fn);
+        long long tpv = (ntiles + slots - 1) / slots;
+        if (a.red.capacity > 0) tpv = std::max(tpv, (ntiles + a.red.capacity - 1) / a.red.capacity);
+        a.tpv = (int)std::max(1LL, tpv);
+    }
     a.nvb = (int)((ntiles + a.tpv - 1) / a.tpv);
 }
 
@@ -220,7 +262,7 @@ pet_status launch_forward(const FwdArgs &a0, int mode, int arith, cudaStream_t s
     FwdArgs a = a0;
     const long long nrays = (long long)a.nviews * a.g.NB;
     if (nrays == 0) return PET_OK;
-    forward_shape(a, mode);
+    forward_shape(a, mode, arith);
     const int grid = std::max(1, std::min(a.nvb, sm_count() * 8));
     Batch b{nullptr, nullptr, 0, grid};
     LaunchScope ls(mode == FWD_RATIO ? PET_K_FORWARD_RATIO

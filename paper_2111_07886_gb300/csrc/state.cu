@@ -192,7 +192,7 @@ void pet::plan_subiter(pet_state *s, SubiterPlan *pl, bool with_objective)
     fa.out = s->w;
     fa.counts = s->counts + (size_t)slot0 * gd.NB * gd.Pp;
     fa.gamma = s->gamma + (size_t)slot0 * gd.NB * gd.Pp;
-    forward_shape(fa, FWD_RATIO);
+    forward_shape(fa, FWD_RATIO, s->arith);
     UpdateArgs &ua = pl->upd;
     ua.g = update_geo(gd);
     ua.slot0 = slot0;
@@ -216,7 +216,7 @@ void pet::plan_subiter(pet_state *s, SubiterPlan *pl, bool with_objective)
     ua.sum_mu = s->sums + 2;
     ua.sum_fout = s->sums + (1 - s->cur);
     ua.red = s->red;
-    update_shape(ua);
+    update_shape(ua, s->arith);
     if (nu_mode == 2) s->have_frozen = true;
     s->cur ^= 1;
     s->J = J;
@@ -263,7 +263,7 @@ void pet::objective_args(pet_state *s, double *out3, FwdArgs *fa, ImageArgs *ra)
     fa->gamma = s->gamma;
     fa->red = s->red;
     fa->result = out3;
-    forward_shape(*fa, FWD_OBJECTIVE);
+    forward_shape(*fa, FWD_OBJECTIVE, s->arith);
     *ra = ImageArgs{};
     ra->g = gd;
     ra->f = s->f[s->cur];

@@ -10,6 +10,10 @@
 #include "kernels.cuh"
 #include "profile.cuh"
 
+#ifndef UPDATE_X8_BLOCKS
+#define UPDATE_X8_BLOCKS 3      // resident blocks per SM the packed update kernel is built for
+#endif
+
 namespace pet {
 
 // Loads the 3x3 in-plane neighbourhood of pixel (ix, iy) for one plane group.
@@ -225,6 +229,187 @@ __global__ void __launch_bounds__(256, 3) update_kernel(const __grid_constant__ 
     }
 }
 
+// FP32 update for 8-plane groups held as four f32x2 pairs.  Same step as update_kernel, with:
+//   - the 3x3 stencil loading every neighbour with missing ones (image border) replaced by the
+//     centre value: their RDP term is exactly zero (d = 0) and the Matlab-style gradient becomes
+//     the one-sided difference, as in the generic stencil;
+//   - the RDP pair term written as d (den + 2 f_k + eps) / den^2 (the numerator
+//     gamma_R |d| + f_j + 3 f_k + 2 eps equals den + 2 f_k + eps), from one reciprocal of den;
+//   - nu = P_{nu1}^{nu2}(mean(mu) / mu) from 1 / mu = min(100, mean(f) / |grad f|);
+//   - the step folded into two per-plane constants before the gather,
+//     f^{k,i} = P_t(A + B b) with A = f - c (beta/M) grad R, B = -c scale, c = lambda alpha nu S,
+//     so that only A, B and the sums of b = A_i^T w stay live across the gather.
+template <int KC, int AR>
+__global__ void __launch_bounds__(256, UPDATE_X8_BLOCKS) update_kernel_x8(
+    const __grid_constant__ UpdateArgs one, const Batch bt)
+{
+    static_assert(AR != AR_FP64, "FP32 arithmetic only");
+    __shared__ BpTable<KC, AR> tb;
+    const int total = total_vblocks(one, bt);
+    for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
+        int vloc, nv;
+        const UpdateArgs &a = *scan_of(one, bt, vb, vloc, nv);
+        const GeoDev &g = a.g;
+        const int N = g.N, NG = g.NG, npix = N * N;
+        const unsigned Pp = (unsigned)g.Pp;
+        const int TP = 256 / NG;
+        const int pl = threadIdx.x / NG, grp = threadIdx.x % NG;
+        const int VC = max(1, min(a.nviews, BpTable<KC, AR>::CAP / TP));
+        const bool dyn = a.nu_mode == 1 || a.nu_mode == 2;
+        const double q = (double)npix * g.P;
+        const float mean_f = dyn ? (float)(*a.sum_f / q) : 1.f;
+        const float mean_mu = dyn ? (float)(*a.sum_mu / q) : 1.f;
+        const float U = (float)a.U, tt = (float)a.t;
+        // eps >= 1e-30 keeps 1/den finite, so that a zero-difference term stays exactly zero
+        const float eps = fmaxf((float)a.eps, 1e-30f);
+        const float *f = reinterpret_cast<const float *>(a.f) + grp * 8;
+        const float *w = reinterpret_cast<const float *>(a.w) + grp * 8;
+        const float *invp = reinterpret_cast<const float *>(a.invp);
+        const int ntiles = (npix + TP - 1) / TP;
+        float part = 0.f;
+        for (int tile = vloc * a.tpv; tile < min(ntiles, (vloc + 1) * a.tpv); ++tile) {
+            const int j0 = tile * TP, j = j0 + pl;
+            const bool active = pl < TP && j < npix;
+            f2x A[4], B[4];
+            if (active) {
+                const int ix = j % N, iy = j / N;
+                const unsigned jc = (unsigned)j;
+                const unsigned xm = ix > 0 ? jc - 1 : jc, xp = ix < N - 1 ? jc + 1 : jc;
+                const unsigned ym = iy > 0 ? jc - N : jc, yp = iy < N - 1 ? jc + N : jc;
+                const f2x GR = vsplat((float)a.gamma_r), EP = vsplat(eps), TWO = vsplat(2.f);
+                f2x c[4], ce[4], gr[4], g2[4], nb0[4], nb1[4];
+                load8x(f + jc * Pp, c);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) { ce[k] = vadd(c[k], EP); gr[k] = 0ull; }
+                auto rdp = [&](const f2x(&x)[4]) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const f2x d = vsub(c[k], x[k]);
+                        const f2x den = vfma(GR, vabs(d), vadd(ce[k], x[k]));
+                        const f2x num = vadd(den, vfma(TWO, x[k], EP));
+                        const f2x r = vrcp(den);
+                        gr[k] = vfma(vmul(d, vmul(num, r)), r, gr[k]);
+                    }
+                };
+                // axial neighbours: RDP terms and the Matlab-style gradient
+                load8x(f + xm * Pp, nb0);
+                load8x(f + xp * Pp, nb1);
+                rdp(nb0);
+                rdp(nb1);
+                if (dyn) {
+                    const f2x HX = vsplat((ix > 0 && ix < N - 1) ? 0.5f : 1.f);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const f2x t = vmul(HX, vsub(nb1[k], nb0[k]));
+                        g2[k] = vmul(t, t);
+                    }
+                }
+                load8x(f + ym * Pp, nb0);
+                load8x(f + yp * Pp, nb1);
+                rdp(nb0);
+                rdp(nb1);
+                f2x nu[4];
+                if (dyn) {
+                    const f2x HY = vsplat((iy > 0 && iy < N - 1) ? 0.5f : 1.f);
+                    const float nu1 = (float)a.nu1, nu2 = (float)a.nu2;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const f2x t = vmul(HY, vsub(nb1[k], nb0[k]));
+                        float r0, r1;
+                        vunpk(vrsqrt(vfma(t, t, g2[k])), r0, r1);
+                        // 1 / mu = 1 / max(0.01, |grad f| / mean f) = min(100, mean f / |grad f|)
+                        r0 = fminf(100.f, r0 * mean_f);
+                        r1 = fminf(100.f, r1 * mean_f);
+                        nu[k] = vpk(fminf(fmaxf(mean_mu * r0, nu1), nu2),
+                                    fminf(fmaxf(mean_mu * r1, nu1), nu2));
+                    }
+                    if (a.nu_mode == 2)
+                        store8x(reinterpret_cast<float *>(a.nu_frozen) + jc * Pp + grp * 8, nu);
+                } else if (a.nu_mode == 3) {
+                    load8x(reinterpret_cast<const float *>(a.nu_frozen) + jc * Pp + grp * 8, nu);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) nu[k] = vsplat(1.f);
+                }
+                // diagonal neighbours
+                const unsigned dm = iy > 0 ? jc - N : jc, dp = iy < N - 1 ? jc + N : jc;
+                load8x(f + (ix > 0 && iy > 0 ? dm - 1 : jc) * Pp, nb0);
+                load8x(f + (ix < N - 1 && iy > 0 ? dm + 1 : jc) * Pp, nb1);
+                rdp(nb0);
+                rdp(nb1);
+                load8x(f + (ix > 0 && iy < N - 1 ? dp - 1 : jc) * Pp, nb0);
+                load8x(f + (ix < N - 1 && iy < N - 1 ? dp + 1 : jc) * Pp, nb1);
+                rdp(nb0);
+                rdp(nb1);
+                // c = lambda alpha nu S, S = min(f, U - f) / p;  A = f - c (beta/M) 2 gr;  B = -c scale
+                const f2x NK = vsplat(-(float)a.lam_alpha * invp[j] * (float)a.invp_scale);
+                const f2x BM = vsplat(2.f * (float)a.beta_over_M), SC = vsplat((float)g.scale);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    float c0, c1;
+                    vunpk(c[k], c0, c1);
+                    const f2x S = vpk(fminf(c0, U - c0), fminf(c1, U - c1));
+                    const f2x cn = vmul(vmul(nu[k], S), NK);
+                    A[k] = vfma(cn, vmul(BM, gr[k]), c[k]);
+                    B[k] = vmul(cn, SC);
+                }
+            }
+            // gather backprojection b = A_i^T w with the tile's shared (pixel, view) weights
+            f2x sm[4], er[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) { sm[k] = 0ull; er[k] = 0ull; }
+            for (int u0 = 0; u0 < a.nviews; u0 += VC) {
+                const int nvc = min(VC, a.nviews - u0);
+                __syncthreads();
+                bp_fill<KC, AR>(g, a.slot0, u0, nvc, j0, TP, tb);
+                __syncthreads();
+                if (!active) continue;
+                for (int uu = 0; uu < nvc; ++uu) {
+                    const typename BpTable<KC, AR>::E ent = tb.e[pl * nvc + uu];
+                    const float *row = w + ent.off;
+#pragma unroll
+                    for (int kb = 0; kb < KC; kb += 2) {
+                        f2x x0[4], x1[4];
+                        load8x(row + kb * Pp, x0);
+                        load8x(row + (kb + 1) * Pp, x1);
+                        const f2x W0 = vsplat(ent.w[kb]), W1 = vsplat(ent.w[kb + 1]);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            if constexpr (AR == AR_KAHAN) {
+                                const f2x y = vfma(W1, x1[k], vfma(W0, x0[k], er[k]));
+                                const f2x t = vadd(sm[k], y);
+                                er[k] = vsub(y, vsub(t, sm[k]));
+                                sm[k] = t;
+                            } else {
+                                sm[k] = vfma(W1, x1[k], vfma(W0, x0[k], sm[k]));
+                            }
+                        }
+                    }
+                }
+            }
+            if (!active) continue;
+            // step and clamp P_t
+            f2x out[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const f2x b = AR == AR_KAHAN ? vadd(sm[k], er[k]) : sm[k];
+                float f0, f1;
+                vunpk(vfma(B[k], b, A[k]), f0, f1);
+                f0 = f0 <= 0.f ? tt : (f0 >= U ? U - tt : f0);
+                f1 = f1 <= 0.f ? tt : (f1 >= U ? U - tt : f1);
+                const int p0 = grp * 8 + 2 * k;
+                f0 = p0 < g.P ? f0 : 0.f;
+                f1 = p0 + 1 < g.P ? f1 : 0.f;
+                part += f0 + f1;
+                out[k] = vpk(f0, f1);
+            }
+            store8x(reinterpret_cast<float *>(a.fout) + (unsigned)j * Pp + grp * 8, out);
+        }
+        double v[1] = {(double)part};
+        grid_reduce<1>(v, a.red, a.sum_fout, vloc, nv);
+    }
+}
+
 // Stand-alone gather backprojection (also the sensitivity, proj == nullptr); one pixel tile
 // per virtual block.
 template <int G, int KC, int AR>
@@ -327,11 +512,32 @@ __global__ void __launch_bounds__(256) image_kernel(const __grid_constant__ Imag
 GeoDev update_geo(const GeoDev &g) { return g; }
 
 // pixel tiles per virtual block so that a scan never needs more partial sums than its reducer
-void update_shape(UpdateArgs &a)
+int resident_blocks(const void *fn);
+
+template <int G, int KC>
+static const void *update_fn(int arith)
+{
+    if constexpr (G == 8) {
+        if (arith == AR_FP32) return (const void *)update_kernel_x8<KC, AR_FP32>;
+        if (arith == AR_KAHAN) return (const void *)update_kernel_x8<KC, AR_KAHAN>;
+    } else {
+        if (arith == AR_FP32) return (const void *)update_kernel<G, KC, AR_FP32>;
+        if (arith == AR_KAHAN) return (const void *)update_kernel<G, KC, AR_KAHAN>;
+    }
+    return (const void *)update_kernel<G, KC, AR_FP64>;
+}
+
+// Pixel tiles per virtual block: each virtual block ends in a block reduction and a grid-wide
+// ticket, so the tiles are grouped into one wave of virtual blocks over the resident block
+// slots (and never more virtual blocks than the reducer has partial sums for).
+void update_shape(UpdateArgs &a, int arith)
 {
     const int TP = 256 / a.g.NG;
     const int ntiles = (a.g.N * a.g.N + TP - 1) / TP;
-    a.tpv = std::max(1, (ntiles + a.red.capacity - 1) / a.red.capacity);
+    const void *fn = a.g.G == 1 ? (a.g.K <= 2 ? update_fn<1, 2>(arith) : update_fn<1, 4>(arith))
+                                : (a.g.K <= 2 ? update_fn<8, 2>(arith) : update_fn<8, 4>(arith));
+    const int slots = sm_count() * resident_blocks(fn);
+    a.tpv = std::max({1, (ntiles + a.red.capacity - 1) / a.red.capacity, (ntiles + slots - 1) / slots});
     a.nvb = (ntiles + a.tpv - 1) / a.tpv;
 }
 
@@ -352,9 +558,15 @@ static int persistent_grid(int nvb) { return std::max(1, std::min(nvb, sm_count(
 template <int G, int KC>
 static void update_dispatch(const UpdateArgs &a, const Batch &b, int arith, int grid, cudaStream_t st)
 {
-    if (arith == AR_FP32) update_kernel<G, KC, AR_FP32><<<grid, 256, 0, st>>>(a, b);
-    else if (arith == AR_KAHAN) update_kernel<G, KC, AR_KAHAN><<<grid, 256, 0, st>>>(a, b);
-    else update_kernel<G, KC, AR_FP64><<<grid, 256, 0, st>>>(a, b);
+    if constexpr (G == 8) {
+        if (arith == AR_FP32) update_kernel_x8<KC, AR_FP32><<<grid, 256, 0, st>>>(a, b);
+        else if (arith == AR_KAHAN) update_kernel_x8<KC, AR_KAHAN><<<grid, 256, 0, st>>>(a, b);
+        else update_kernel<G, KC, AR_FP64><<<grid, 256, 0, st>>>(a, b);
+    } else {
+        if (arith == AR_FP32) update_kernel<G, KC, AR_FP32><<<grid, 256, 0, st>>>(a, b);
+        else if (arith == AR_KAHAN) update_kernel<G, KC, AR_KAHAN><<<grid, 256, 0, st>>>(a, b);
+        else update_kernel<G, KC, AR_FP64><<<grid, 256, 0, st>>>(a, b);
+    }
 }
 
 static pet_status update_any(const UpdateArgs &a, const Batch &b, int arith, int grid, cudaStream_t st)
@@ -375,7 +587,7 @@ static pet_status update_any(const UpdateArgs &a, const Batch &b, int arith, int
 pet_status launch_update(const UpdateArgs &a0, int arith, cudaStream_t st)
 {
     UpdateArgs a = a0;
-    update_shape(a);
+    update_shape(a, arith);
     return update_any(a, Batch{nullptr, nullptr, 0, 0}, arith, persistent_grid(a.nvb), st);
 }
 
