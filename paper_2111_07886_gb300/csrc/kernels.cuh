@@ -207,6 +207,14 @@ __device__ __forceinline__ void load8x(const float *__restrict__ p, f2x (&v)[4])
     asm("ld.global.nc.v4.b64 {%0, %1, %2, %3}, [%4];"
         : "=l"(v[0]), "=l"(v[1]), "=l"(v[2]), "=l"(v[3]) : "l"(p));
 }
+// as load8x when `on`, else four zero pairs (no memory access)
+__device__ __forceinline__ void load8x_if(const float *__restrict__ p, bool on, f2x (&v)[4])
+{
+    asm("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %5, 0;\n\t"
+        "mov.b64 %0, 0;\n\tmov.b64 %1, 0;\n\tmov.b64 %2, 0;\n\tmov.b64 %3, 0;\n\t"
+        "@q ld.global.nc.v4.b64 {%0, %1, %2, %3}, [%4];\n\t}"
+        : "=l"(v[0]), "=l"(v[1]), "=l"(v[2]), "=l"(v[3]) : "l"(p), "r"((unsigned)on));
+}
 __device__ __forceinline__ void store8x(float *__restrict__ p, const f2x (&v)[4])
 {
     asm volatile("st.global.v4.b64 [%0], {%1, %2, %3, %4};"
@@ -295,6 +303,18 @@ template <int G, int AR> struct GroupSum {
     }
 
     __device__ __forceinline__ T value(int p) const { return s_at(p) + e_at(p); }
+
+    // overwrite plane p's sum and compensation
+    __device__ __forceinline__ void set(int p, T s, T e)
+    {
+        if constexpr (PACK) {
+            if (p & 1) { s2[p >> 1].y = s; e2[p >> 1].y = e; }
+            else { s2[p >> 1].x = s; e2[p >> 1].x = e; }
+        } else {
+            s2[p] = s;
+            e2[p] = e;
+        }
+    }
 };
 
 // ------------------------------------------------------------------------------------------

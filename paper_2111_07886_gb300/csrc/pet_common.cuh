@@ -183,6 +183,7 @@ pet_status launch_nu_map(const ImageArgs &a, int arith, cudaStream_t st);     //
 pet_status launch_rdp_grad(const ImageArgs &a, int arith, cudaStream_t st);   // out = grad R
 pet_status launch_rdp_value(const ImageArgs &a, int arith, cudaStream_t st);  // result[0] = R
 void image_shape(ImageArgs &a);                            // fills ipt, nvb
+void mu_shape(ImageArgs &a, int arith);                    // shape of the mu pass
 pet_status launch_mu_sum_batch(const ImageArgs &shape, const Batch &b, int arith, cudaStream_t st);
 pet_status launch_rdp_value_batch(const ImageArgs &shape, const Batch &b, int arith,
                                   cudaStream_t st);

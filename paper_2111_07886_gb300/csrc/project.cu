@@ -23,7 +23,7 @@ namespace pet {
 // S partial sums of a (ray, group) are combined in chunk order through shared memory
 // (deterministic).  A persistent grid strides over the virtual blocks of one scan or a batch.
 template <int G, int AR, int MODE>
-__global__ void __launch_bounds__(256) fwd_kernel(const __grid_constant__ FwdArgs one, const Batch bt)
+__global__ void __launch_bounds__(256, 3) fwd_kernel(const __grid_constant__ FwdArgs one, const Batch bt)
 {
     using T = typename ArithT<AR>::T;
     __shared__ T comb_s[256 * G];
@@ -72,6 +72,49 @@ __global__ void __launch_bounds__(256) fwd_kernel(const __grid_constant__ FwdArg
                     load_group<G, T>(img + (unsigned)(d * ds + (ok0 ? r0 : 0) * cs) * (unsigned)Pp, x0);
                     load_group<G, T>(img + (unsigned)(d * ds + (ok1 ? r1 : 0) * cs) * (unsigned)Pp, x1);
                     acc.add2terms(l0, x0, l1, x1);
+                }
+            } else if constexpr (G == 8) {
+                // FP32 pairs; the second pixel of a step is read only when the line crosses
+                // into it (l1 > 0), on about |slope| of the steps
+                const long long stp = vw.stepq, ast = vw.absstepq;
+                const float L = vw.Lf, im = vw.inv_minorf * kQ32;
+                const float *imf = reinterpret_cast<const float *>(img);
+                long long lo = rg.loq + (long long)k0 * stp;
+                f2x sm[4], er[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) { sm[q] = 0ull; er[q] = 0ull; }
+                for (int k = k0; k < k1; ++k) {
+                    const int d = rg.d0 + k;
+                    const long long hi = lo + ast;
+                    const int r0 = (int)(lo >> 32), r1 = (int)(hi >> 32);
+                    const bool ok0 = (unsigned)r0 < (unsigned)N;
+                    const bool ok1 = r1 != r0 && (unsigned)r1 < (unsigned)N;
+                    const float l1 = ok1 ? __uint2float_rn((unsigned)(hi & 0xFFFFFFFFLL)) * im : 0.f;
+                    const float l0 = ok0 ? L - (r1 != r0 ? __uint2float_rn((unsigned)(hi & 0xFFFFFFFFLL)) * im : 0.f) : 0.f;
+                    f2x x0[4], x1[4];
+                    load8x(imf + (unsigned)(d * ds + (ok0 ? r0 : 0) * cs) * (unsigned)Pp, x0);
+                    load8x_if(imf + (unsigned)(d * ds + (ok1 ? r1 : 0) * cs) * (unsigned)Pp, ok1, x1);
+                    const f2x W0 = vsplat(l0), W1 = vsplat(l1);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        if constexpr (AR == AR_KAHAN) {
+                            const f2x y = vfma(W1, x1[q], vfma(W0, x0[q], er[q]));
+                            const f2x t = vadd(sm[q], y);
+                            er[q] = vsub(y, vsub(t, sm[q]));
+                            sm[q] = t;
+                        } else {
+                            sm[q] = vfma(W1, x1[q], vfma(W0, x0[q], sm[q]));
+                        }
+                    }
+                    lo += stp;
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float a0, a1, b0, b1;
+                    vunpk(sm[q], a0, a1);
+                    vunpk(er[q], b0, b1);
+                    acc.set(2 * q, a0, b0);
+                    acc.set(2 * q + 1, a1, b1);
                 }
             } else {
                 const long long stp = vw.stepq, ast = vw.absstepq;

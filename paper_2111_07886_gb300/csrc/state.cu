@@ -183,7 +183,7 @@ void pet::plan_subiter(pet_state *s, SubiterPlan *pl, bool with_objective)
     a.sum_f = s->sums + s->cur;
     a.result = s->sums + 2;
     a.red = s->red;
-    image_shape(a);
+    mu_shape(a, s->arith);
     FwdArgs &fa = pl->fwd;
     fa.g = gd;
     fa.slot0 = slot0;

@@ -507,6 +507,55 @@ __global__ void __launch_bounds__(256) image_kernel(const __grid_constant__ Imag
     }
 }
 
+// FP32 mu pass for 8-plane groups: sum over voxels of mu = max(0.01, |grad f| / mean(f))
+// (Matlab-style gradient: central differences inside, one-sided at the border, where the
+// missing neighbour is the centre value).  Thread layout of the update kernel (pixel x plane
+// group, TP = 256 / NG pixels per tile); a virtual block takes a.ipt tiles.
+__global__ void __launch_bounds__(256) mu_kernel_x8(const __grid_constant__ ImageArgs one, const Batch bt)
+{
+    const int total = total_vblocks(one, bt);
+    for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
+        int vloc, nv;
+        const ImageArgs &a = *scan_of(one, bt, vb, vloc, nv);
+        const GeoDev &g = a.g;
+        const int N = g.N, NG = g.NG, npix = N * N;
+        const unsigned Pp = (unsigned)g.Pp;
+        const int TP = 256 / NG;
+        const int pl = threadIdx.x / NG, grp = threadIdx.x % NG;
+        const int ntiles = (npix + TP - 1) / TP;
+        const float inv_mean_f = (float)((double)npix * g.P / *a.sum_f);
+        const float *f = reinterpret_cast<const float *>(a.f) + grp * 8;
+        const int nvalid = min(8, g.P - grp * 8);             // real planes of this group
+        float part = 0.f;
+        for (int tile = vloc * a.ipt; tile < min(ntiles, (vloc + 1) * a.ipt); ++tile) {
+            const int j = tile * TP + pl;
+            if (pl >= TP || j >= npix) continue;
+            const int ix = j % N, iy = j / N;
+            const unsigned jc = (unsigned)j;
+            f2x w_[4], e_[4], n_[4], s_[4];
+            load8x(f + (ix > 0 ? jc - 1 : jc) * Pp, w_);
+            load8x(f + (ix < N - 1 ? jc + 1 : jc) * Pp, e_);
+            load8x(f + (iy > 0 ? jc - N : jc) * Pp, n_);
+            load8x(f + (iy < N - 1 ? jc + N : jc) * Pp, s_);
+            const f2x HX = vsplat((ix > 0 && ix < N - 1) ? 0.5f : 1.f);
+            const f2x HY = vsplat((iy > 0 && iy < N - 1) ? 0.5f : 1.f);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const f2x gx = vmul(HX, vsub(e_[k], w_[k])), gy = vmul(HY, vsub(s_[k], n_[k]));
+                const f2x x2 = vfma(gx, gx, vmul(gy, gy));
+                float x0, x1, r0, r1;
+                vunpk(x2, x0, x1);
+                vunpk(vrsqrt(x2), r0, r1);
+                const float m0 = fmaxf(0.01f, x0 > 0.f ? x0 * r0 * inv_mean_f : 0.f);
+                const float m1 = fmaxf(0.01f, x1 > 0.f ? x1 * r1 * inv_mean_f : 0.f);
+                part += (2 * k < nvalid ? m0 : 0.f) + (2 * k + 1 < nvalid ? m1 : 0.f);
+            }
+        }
+        double v[1] = {(double)part};
+        grid_reduce<1>(v, a.red, a.result, vloc, nv);
+    }
+}
+
 // Plane grouping of the update kernel: the full 8-plane groups (measured faster at three blocks
 // per SM than 4-plane half groups, whose per-thread overheads double).
 GeoDev update_geo(const GeoDev &g) { return g; }
@@ -648,13 +697,45 @@ static pet_status launch_image(const ImageArgs &a0, int arith, cudaStream_t st)
 }
 
 pet_status launch_sum(const ImageArgs &a, int arith, cudaStream_t st) { return launch_image<0>(a, arith, st); }
-pet_status launch_mu_sum(const ImageArgs &a, int arith, cudaStream_t st) { return launch_image<1>(a, arith, st); }
+// Shape of the mu pass: the packed kernel (8-plane groups, FP32) takes a.ipt pixel tiles per
+// virtual block, one wave of virtual blocks over the resident block slots; otherwise the
+// items-per-thread shape of image_kernel.
+void mu_shape(ImageArgs &a, int arith)
+{
+    if (a.g.G != 8 || arith == AR_FP64) {
+        image_shape(a);
+        return;
+    }
+    const int TP = 256 / a.g.NG;
+    const int ntiles = (a.g.N * a.g.N + TP - 1) / TP;
+    const int slots = sm_count() * resident_blocks((const void *)mu_kernel_x8);
+    const int cap = a.red.capacity > 0 ? a.red.capacity : (1 << 30);
+    a.ipt = std::max({1, (ntiles + cap - 1) / cap, (ntiles + slots - 1) / slots});
+    a.nvb = (ntiles + a.ipt - 1) / a.ipt;
+}
+
+static pet_status mu_any(const ImageArgs &a, const Batch &b, int arith, int grid, cudaStream_t st)
+{
+    if (a.g.G != 8 || arith == AR_FP64) return image_any<1>(a, b, arith, grid, st);
+    LaunchScope ls(PET_K_MU_SUM, st);
+    mu_kernel_x8<<<grid, 256, 0, st>>>(a, b);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "mu_kernel_x8 launch");
+    return PET_OK;
+}
+
+pet_status launch_mu_sum(const ImageArgs &a0, int arith, cudaStream_t st)
+{
+    ImageArgs a = a0;
+    mu_shape(a, arith);
+    return mu_any(a, Batch{nullptr, nullptr, 0, 0}, arith, persistent_grid(a.nvb), st);
+}
 pet_status launch_nu_map(const ImageArgs &a, int arith, cudaStream_t st) { return launch_image<2>(a, arith, st); }
 pet_status launch_rdp_grad(const ImageArgs &a, int arith, cudaStream_t st) { return launch_image<3>(a, arith, st); }
 pet_status launch_rdp_value(const ImageArgs &a, int arith, cudaStream_t st) { return launch_image<4>(a, arith, st); }
 pet_status launch_mu_sum_batch(const ImageArgs &shape, const Batch &b, int arith, cudaStream_t st)
 {
-    return image_any<1>(shape, b, arith, b.grid, st);
+    return mu_any(shape, b, arith, b.grid, st);
 }
 pet_status launch_rdp_value_batch(const ImageArgs &shape, const Batch &b, int arith, cudaStream_t st)
 {
