@@ -292,10 +292,21 @@ def kernel_times(args, w, pet, step, flush) -> dict:
     prof = pet.profile_read()
     pet.profile_enable(False)
     byts = algorithmic_bytes(w)
-    tot = sum(v[0] for v in prof.values())
-    shares = {k: {"ms": round(v[0] / max(1, args.steps), 4), "launches_per_step": v[1] // max(1, args.steps),
-                  "share": round(v[0] / tot, 4) if tot else 0.0} for k, v in prof.items() if v[1]}
-    dom = max((k for k in prof if k in byts and prof[k][1]), key=lambda k: prof[k][0])
+    # the mu pass runs on a side stream beside the forward projection: its event time includes
+    # waiting for SMs, so it is reported as concurrent and left out of the shares of the step
+    concurrent = {"mu_sum"}
+    tot = sum(v[0] for k, v in prof.items() if k not in concurrent)
+    shares = {}
+    for k, v in prof.items():
+        if not v[1]:
+            continue
+        e = {"ms": round(v[0] / max(1, args.steps), 4), "launches_per_step": v[1] // max(1, args.steps)}
+        if k in concurrent:
+            e["concurrent_with"] = "forward_ratio"
+        else:
+            e["share"] = round(v[0] / tot, 4) if tot else 0.0
+        shares[k] = e
+    dom = max((k for k in prof if k in byts and prof[k][1] and k not in concurrent), key=lambda k: prof[k][0])
     avg_ms = prof[dom][0] / prof[dom][1]
     peaks = load_peaks()
     achieved = byts[dom] / (avg_ms / 1e3) / 1e9

@@ -336,8 +336,8 @@ template <int KC, int AR> struct BpEntry {
     T w[KC];           // lengths for bins b0 .. b0 + KC - 1 (zero outside the footprint)
 };
 
-template <int KC, int AR> struct BpTable {
-    static constexpr int CAP = (AR == AR_FP64 ? 1024 : 2048) / (KC > 2 ? 2 : 1);   // entries
+template <int KC, int AR, int CAPX = 0> struct BpTable {
+    static constexpr int CAP = CAPX > 0 ? CAPX : (AR == AR_FP64 ? 1024 : 2048) / (KC > 2 ? 2 : 1);
     // one entry per (pixel, view): read with one or two wide shared-memory loads
     struct __align__(16) E : BpEntry<KC, AR> {};
     E e[CAP];
@@ -393,9 +393,9 @@ __device__ __forceinline__ void bp_weights(const GeoDev &g, const ViewGeo &vw, i
 }
 
 // Fill the table for pixels [j0, j0 + np) x views [u0, u0 + nvc) (entry e = pixel * nvc + view).
-template <int KC, int AR>
+template <int KC, int AR, int CAPX>
 __device__ __forceinline__ void bp_fill(const GeoDev &g, int slot0, int u0, int nvc, int j0,
-                                        int np, BpTable<KC, AR> &tb)
+                                        int np, BpTable<KC, AR, CAPX> &tb)
 {
     using T = typename ArithT<AR>::T;
     const int nthr = blockDim.x;
@@ -413,7 +413,7 @@ __device__ __forceinline__ void bp_fill(const GeoDev &g, int slot0, int u0, int 
         // Clamp the first bin into [0, NB - KC] and shift the lengths with it, so that all KC
         // rows of the entry exist (bins outside [0, NB) already carry zero length).
         const int bc = min(max(b0, 0), g.NB - KC);
-        typename BpTable<KC, AR>::E ent;
+        typename BpTable<KC, AR, CAPX>::E ent;
         ent.off = ((unsigned)u * (unsigned)g.NB + (unsigned)bc) * (unsigned)g.Pp;
 #pragma unroll
         for (int k = 0; k < KC; ++k) {
@@ -429,8 +429,8 @@ __device__ __forceinline__ void bp_fill(const GeoDev &g, int slot0, int u0, int 
 
 // Accumulate views [u0, u0 + nvc) of the table into acc for local pixel pl and plane group grp.
 // proj (subset rows [u][NB][Pp]) == nullptr backprojects ones.
-template <int G, int KC, int AR>
-__device__ __forceinline__ void bp_accumulate(const GeoDev &g, const BpTable<KC, AR> &tb,
+template <int G, int KC, int AR, int CAPX>
+__device__ __forceinline__ void bp_accumulate(const GeoDev &g, const BpTable<KC, AR, CAPX> &tb,
                                               const typename ArithT<AR>::T *__restrict__ proj,
                                               int u0, int nvc, int pl, int grp,
                                               GroupSum<G, AR> &acc)
@@ -439,7 +439,7 @@ __device__ __forceinline__ void bp_accumulate(const GeoDev &g, const BpTable<KC,
     const unsigned Pp = (unsigned)g.Pp;
     const T *base = proj + grp * G;
     for (int uu = 0; uu < nvc; ++uu) {
-        const typename BpTable<KC, AR>::E ent = tb.e[pl * nvc + uu];
+        const typename BpTable<KC, AR, CAPX>::E ent = tb.e[pl * nvc + uu];
         if (proj == nullptr) {
             T s = T(0);
 #pragma unroll

@@ -244,7 +244,9 @@ __global__ void __launch_bounds__(256, UPDATE_X8_BLOCKS) update_kernel_x8(
     const __grid_constant__ UpdateArgs one, const Batch bt)
 {
     static_assert(AR != AR_FP64, "FP32 arithmetic only");
-    __shared__ BpTable<KC, AR> tb;
+    // 16 KB of (pixel, view) entries: the rest of the SM's shared memory stays L1 for the gather
+    using Table = BpTable<KC, AR, 1024 / (KC > 2 ? 2 : 1)>;
+    __shared__ Table tb;
     const int total = total_vblocks(one, bt);
     for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
         int vloc, nv;
@@ -254,7 +256,7 @@ __global__ void __launch_bounds__(256, UPDATE_X8_BLOCKS) update_kernel_x8(
         const unsigned Pp = (unsigned)g.Pp;
         const int TP = 256 / NG;
         const int pl = threadIdx.x / NG, grp = threadIdx.x % NG;
-        const int VC = max(1, min(a.nviews, BpTable<KC, AR>::CAP / TP));
+        const int VC = max(1, min(a.nviews, Table::CAP / TP));
         const bool dyn = a.nu_mode == 1 || a.nu_mode == 2;
         const double q = (double)npix * g.P;
         const float mean_f = dyn ? (float)(*a.sum_f / q) : 1.f;
@@ -365,7 +367,7 @@ __global__ void __launch_bounds__(256, UPDATE_X8_BLOCKS) update_kernel_x8(
                 __syncthreads();
                 if (!active) continue;
                 for (int uu = 0; uu < nvc; ++uu) {
-                    const typename BpTable<KC, AR>::E ent = tb.e[pl * nvc + uu];
+                    const typename Table::E ent = tb.e[pl * nvc + uu];
                     const float *row = w + ent.off;
 #pragma unroll
                     for (int kb = 0; kb < KC; kb += 2) {
