@@ -156,6 +156,26 @@ def test_rdp_gradient_and_nu_parity():
                                out.cpu().numpy().ravel()[err.argmax()], ref.ravel()[err.argmax()])
 
 
+def test_nu_map_with_subnormal_gradients():
+    """A background of ~1e-21 (what the iterates decay to outside the object after a few
+    iterations) has squared gradients below the smallest normal float.  mu must stay
+    max(0.01, |grad f| / mean f) = 0.01 there: a reciprocal square root that flushes them to zero
+    turned |grad f| into inf, the sum of mu into inf and nu into nu2 everywhere."""
+    g = pet.Geometry(48, 11, 2.0, 30, 69, 2.0, 5, 0.9)
+    bg = 3e-21 * (1.0 + 0.5 * synth.random_image((11, 48, 48), seed=8, lo=0.0, hi=1.0))
+    img = bg.copy()
+    img[:, 12:36, 12:36] = 1.0 + synth.random_image((11, 24, 24), seed=9, lo=0.0, hi=1.5)
+    img = f32(img)
+    out = torch.empty((11, 48, 48), device=DEV)
+    pet.smoothness_nu(g, to_dev(img), 0.8, 2.2, out)
+    torch.cuda.synchronize()
+    ref = oracle.nu_from_image(img, 0.8, 2.2)
+    got = out.cpu().numpy()
+    assert np.all(np.isfinite(got))
+    err = np.abs(got - ref)
+    assert err.max() <= 1e-5, (err.max(), np.unravel_index(err.argmax(), err.shape))
+
+
 def test_objective_parity():
     w = synth.config_2d_128(seed=4)
     scan = synth.make_scan(w)
