@@ -184,22 +184,22 @@ __device__ __forceinline__ f2x vabs(f2x a)       // clears both sign bits
     asm("and.b64 %0, %1, 0x7FFFFFFF7FFFFFFF;" : "=l"(r) : "l"(a));
     return r;
 }
-// Hardware approximate reciprocal and 1/sqrt per lane, subnormal inputs kept (no .ftz): a
-// flushed subnormal x would give 1/sqrt(x) = inf and x * rsqrt(x) = inf instead of a tiny |grad|.
+// Hardware approximate reciprocal and 1/sqrt per lane; subnormal inputs are flushed to zero
+// (1/0 = inf), so callers keep their arguments normal or test for it.
 __device__ __forceinline__ f2x vrcp(f2x a)
 {
     float x, y;
     vunpk(a, x, y);
-    asm("rcp.approx.f32 %0, %0;" : "+f"(x));
-    asm("rcp.approx.f32 %0, %0;" : "+f"(y));
+    asm("rcp.approx.ftz.f32 %0, %0;" : "+f"(x));
+    asm("rcp.approx.ftz.f32 %0, %0;" : "+f"(y));
     return vpk(x, y);
 }
 __device__ __forceinline__ f2x vrsqrt(f2x a)
 {
     float x, y;
     vunpk(a, x, y);
-    asm("rsqrt.approx.f32 %0, %0;" : "+f"(x));
-    asm("rsqrt.approx.f32 %0, %0;" : "+f"(y));
+    asm("rsqrt.approx.ftz.f32 %0, %0;" : "+f"(x));
+    asm("rsqrt.approx.ftz.f32 %0, %0;" : "+f"(y));
     return vpk(x, y);
 }
 

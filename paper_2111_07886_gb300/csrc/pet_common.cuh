@@ -214,6 +214,13 @@ struct pet_state {
     cudaStream_t alloc_stream = nullptr;   // non-null: buffers are stream-ordered allocations
     cudaStream_t side = nullptr;           // the mu pass runs here, beside the forward projection
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // objective history of a whole reconstruction, evaluated beside the next subiterations
+    void *fobj = nullptr;                  // snapshot of f^k
+    void *redobj_mem = nullptr;
+    pet::Reducer red_obj{};
+    cudaStream_t ostream = nullptr;
+    cudaEvent_t ev_ofork = nullptr, ev_odone = nullptr;
+    bool obj_pending = false;
     size_t q_bytes = 0, sino_elems = 0, w_bytes = 0;
 };
 

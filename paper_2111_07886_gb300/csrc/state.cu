@@ -45,6 +45,18 @@ static void state_free(pet_state *s)
         s->side = nullptr;
         s->ev_fork = s->ev_join = nullptr;
     }
+    if (s->ostream) {
+        cudaStreamSynchronize(s->ostream);
+        cudaStreamDestroy(s->ostream);
+        cudaEventDestroy(s->ev_ofork);
+        cudaEventDestroy(s->ev_odone);
+        cudaFree(s->fobj);
+        cudaFree(s->redobj_mem);
+        s->ostream = nullptr;
+        s->ev_ofork = s->ev_odone = nullptr;
+        s->fobj = s->redobj_mem = nullptr;
+        s->obj_pending = false;
+    }
     auto rel = [&](void *p) {
         if (!p) return;
         if (s->alloc_stream) cudaFreeAsync(p, s->alloc_stream);
@@ -447,14 +459,49 @@ extern "C" void pet_state_destroy(pet_state *s)
     delete s;
 }
 
+// Phi(f^k) beside the following subiterations: f^k is copied to a snapshot on `st`, and the
+// objective projection and RDP value run on their own stream (own reduction scratch) from the
+// snapshot while `st` goes on with iteration k + 1.  `st` waits for the previous evaluation
+// before overwriting the snapshot, and for the last one before the reconstruction returns.
+static pet_status state_objective_beside(pet_state *s, double *out3, cudaStream_t st)
+{
+    if (!s->ostream) {
+        PET_CUDA(cudaStreamCreateWithFlags(&s->ostream, cudaStreamNonBlocking));
+        PET_CUDA(cudaEventCreateWithFlags(&s->ev_ofork, cudaEventDisableTiming));
+        PET_CUDA(cudaEventCreateWithFlags(&s->ev_odone, cudaEventDisableTiming));
+        PET_CUDA(cudaMalloc(&s->fobj, s->q_bytes));
+        PET_CUDA(cudaMalloc(&s->redobj_mem, reducer_bytes(kRedCap, 2)));
+        PET_CUDA(cudaMemset(s->redobj_mem, 0, reducer_bytes(kRedCap, 2)));
+        reducer_bind(s->red_obj, s->redobj_mem, kRedCap, 2);
+    }
+    if (s->obj_pending) PET_CUDA(cudaStreamWaitEvent(st, s->ev_odone, 0));
+    PET_CUDA(cudaMemcpyAsync(s->fobj, s->f[s->cur], s->q_bytes, cudaMemcpyDeviceToDevice, st));
+    PET_CUDA(cudaEventRecord(s->ev_ofork, st));
+    PET_CUDA(cudaStreamWaitEvent(s->ostream, s->ev_ofork, 0));
+    FwdArgs fa;
+    ImageArgs ra;
+    objective_args(s, out3, &fa, &ra);
+    fa.img = ra.f = s->fobj;
+    fa.red = ra.red = s->red_obj;
+    PET_TRY(launch_forward(fa, FWD_OBJECTIVE, s->arith, s->ostream));
+    PET_TRY(launch_rdp_value(ra, s->arith, s->ostream));
+    PET_CUDA(cudaEventRecord(s->ev_odone, s->ostream));
+    s->obj_pending = true;
+    return PET_OK;
+}
+
 // Whole reconstruction on an allocated state: T outer iterations, objective history on device.
 static pet_status run_reconstruct(pet_state *s, double *h_objective, cudaStream_t st)
 {
     const int T = s->prm.iterations, M = s->g->dev.M;
-    if (h_objective) PET_TRY(state_objective_async(s, s->objhist, st));
+    if (h_objective) PET_TRY(state_objective_beside(s, s->objhist, st));
     for (int k = 0; k < T; ++k) {
         for (int i = 0; i < M; ++i) PET_TRY(state_subiter(s, st));
-        if (h_objective) PET_TRY(state_objective_async(s, s->objhist + 3 * (k + 1), st));
+        if (h_objective) PET_TRY(state_objective_beside(s, s->objhist + 3 * (k + 1), st));
+    }
+    if (s->obj_pending) {
+        PET_CUDA(cudaStreamWaitEvent(st, s->ev_odone, 0));
+        s->obj_pending = false;
     }
     return PET_OK;
 }

@@ -548,8 +548,10 @@ __global__ void __launch_bounds__(256) mu_kernel_x8(const __grid_constant__ Imag
                 float x0, x1, r0, r1;
                 vunpk(x2, x0, x1);
                 vunpk(vrsqrt(x2), r0, r1);
-                const float m0 = fmaxf(0.01f, x0 > 0.f ? x0 * r0 * inv_mean_f : 0.f);
-                const float m1 = fmaxf(0.01f, x1 > 0.f ? x1 * r1 * inv_mean_f : 0.f);
+                // |grad f|^2 below the smallest normal float (|grad f| < 1.1e-19, met on decayed
+                // backgrounds) counts as zero: mu = 0.01 there, and the flushed rsqrt would be inf
+                const float m0 = fmaxf(0.01f, x0 >= 1.17549435e-38f ? x0 * r0 * inv_mean_f : 0.f);
+                const float m1 = fmaxf(0.01f, x1 >= 1.17549435e-38f ? x1 * r1 * inv_mean_f : 0.f);
                 part += (2 * k < nvalid ? m0 : 0.f) + (2 * k + 1 < nvalid ? m1 : 0.f);
             }
         }
