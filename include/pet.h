@@ -119,6 +119,13 @@ void pet_geometry_destroy(pet_geometry *g);
  * chunking changes the order of the ray sums, within rounding).  Synchronises `stream`. */
 pet_status pet_autotune(pet_geometry *g, void *stream, int *best_S);
 
+/* Sets the forward projector's ray chunks S directly (no counterpart in the paper): a choice
+ * taken from an earlier pet_autotune, or fixed for a profiling run, where the profiler's own
+ * per-launch cost distorts the autotuner's timings.  S = 0 returns to the built-in heuristic.
+ * PET_ERR_INVALID unless S == 0 or 1 <= S <= 8 with S dividing 256 / ceil(nplanes / 8) (256 for
+ * one plane).  Same rule as pet_autotune: set it before creating states on the geometry. */
+pet_status pet_set_ray_chunks(pet_geometry *g, int S);
+
 /* Number of views V_i in subset `subset` (0 <= subset < M), or -1 if out of range. */
 int pet_subset_size(const pet_geometry *g, int subset);
 

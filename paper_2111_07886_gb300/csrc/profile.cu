@@ -45,6 +45,12 @@ LaunchScope::~LaunchScope()
     g_pending[kind_].push_back(Pair{a_, b_});
 }
 
+bool profile_active()
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    return g_enabled;
+}
+
 void count_launches(long long n)
 {
     std::lock_guard<std::mutex> lk(g_mu);

@@ -21,4 +21,9 @@ private:
     cudaEvent_t a_{}, b_{};
 };
 
+// Per-kernel timing is on (pet_profile_enable): work that normally runs on side streams beside
+// other kernels (mu pass, objective) then runs on the caller's stream, so that each kernel's
+// events bracket that kernel alone.
+bool profile_active();
+
 }  // namespace pet

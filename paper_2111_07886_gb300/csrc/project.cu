@@ -383,3 +383,12 @@ extern "C" pet_status pet_autotune(pet_geometry *g, void *stream, int *best_S)
     if (best_S) *best_S = bestS;
     return PET_OK;
 }
+
+extern "C" pet_status pet_set_ray_chunks(pet_geometry *g, int S)
+{
+    if (!g) return fail(PET_ERR_INVALID, "pet_set_ray_chunks: NULL geometry");
+    if (S < 0 || S > 8 || (S > 0 && (256 / g->dev.NG) % S))
+        return fail(PET_ERR_INVALID, "pet_set_ray_chunks: S must be 0 or in 1..8 and divide 256 / plane groups");
+    g->dev.tuneS = S;
+    return PET_OK;
+}

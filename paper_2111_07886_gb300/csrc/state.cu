@@ -14,6 +14,7 @@
 #include <cstring>
 
 #include "pet_common.cuh"
+#include "profile.cuh"
 
 using namespace pet;
 
@@ -244,6 +245,11 @@ static pet_status state_subiter(pet_state *s, cudaStream_t st)
 {
     SubiterPlan pl;
     plan_subiter(s, &pl, false);
+    if (pl.mu && profile_active()) {
+        PET_TRY(launch_mu_sum(pl.mu_args, pl.arith, st));
+        PET_TRY(launch_forward(pl.fwd, FWD_RATIO, pl.arith, st));
+        return launch_update(pl.upd, pl.arith, st);
+    }
     if (pl.mu) {
         if (!s->side) {
             PET_CUDA(cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking));
@@ -465,6 +471,13 @@ extern "C" void pet_state_destroy(pet_state *s)
 // before overwriting the snapshot, and for the last one before the reconstruction returns.
 static pet_status state_objective_beside(pet_state *s, double *out3, cudaStream_t st)
 {
+    if (profile_active()) {
+        if (s->obj_pending) {
+            PET_CUDA(cudaStreamWaitEvent(st, s->ev_odone, 0));
+            s->obj_pending = false;
+        }
+        return state_objective_async(s, out3, st);
+    }
     if (!s->ostream) {
         PET_CUDA(cudaStreamCreateWithFlags(&s->ostream, cudaStreamNonBlocking));
         PET_CUDA(cudaEventCreateWithFlags(&s->ev_ofork, cudaEventDisableTiming));

@@ -64,6 +64,7 @@ SIGNATURES = {
     "pet_geometry_destroy": (None, [_VP]),
     "pet_subset_size": (_I, [_VP, _I]),
     "pet_autotune": (_I, [_VP, _VP, ctypes.POINTER(_I)]),
+    "pet_set_ray_chunks": (_I, [_VP, _I]),
     "pet_sensitivity": (_I, [_VP, _VP, _VP]),
     "pet_forward_subset": (_I, [_VP, _I, _VP, _VP, _VP]),
     "pet_back_subset": (_I, [_VP, _I, _VP, _VP, _VP]),
@@ -187,6 +188,10 @@ class Geometry:
         s = ctypes.c_int()
         _check(lib().pet_autotune(self.handle, _stream(stream), ctypes.byref(s)))
         return s.value
+
+    def set_ray_chunks(self, S: int):
+        """Fix the forward projector's ray chunks (0: built-in heuristic)."""
+        _check(lib().pet_set_ray_chunks(self.handle, int(S)))
 
 
 def sensitivity(g: Geometry, d_p, stream=None):
