@@ -394,54 +394,74 @@ __device__ __forceinline__ void bp_weights(const GeoDev &g, const ViewGeo &vw, i
     }
 }
 
-// Fill the table for pixels [j0, j0 + np) x views [u0, u0 + nvc) (entry e = pixel * nvc + view).
+// One table entry: pixel (ix, iy) (inside the image when `in`) against view u of the subset.
+template <int KC, int AR, int CAPX>
+__device__ __forceinline__ typename BpTable<KC, AR, CAPX>::E bp_entry(const GeoDev &g, int slot0, int u,
+                                                                    bool in, int ix, int iy)
+{
+    using T = typename ArithT<AR>::T;
+    int b0 = 0;
+    T w[KC];
+    if (in) {
+        bp_weights<KC, AR>(g, g.views[slot0 + u], slot0 + u, ix, iy, b0, w);
+    } else {
+#pragma unroll
+        for (int k = 0; k < KC; ++k) w[k] = T(0);
+    }
+    // Clamp the first bin into [0, NB - KC] and shift the lengths with it, so that all KC
+    // rows of the entry exist (bins outside [0, NB) already carry zero length).
+    const int bc = min(max(b0, 0), g.NB - KC);
+    typename BpTable<KC, AR, CAPX>::E ent;
+    ent.off = ((unsigned)u * (unsigned)g.NB + (unsigned)bc) * (unsigned)g.Pp;
+#pragma unroll
+    for (int k = 0; k < KC; ++k) {
+        const int src = k + bc - b0;
+        T v = T(0);
+#pragma unroll
+        for (int m = 0; m < KC; ++m) v = (m == src) ? w[m] : v;
+        ent.w[k] = v;
+    }
+    return ent;
+}
+
+// Fill the table for pixels [j0, j0 + np) x views [u0, u0 + nvc), view-major: the entry of local
+// pixel pl and view u0 + uu is tb.e[uu * np + pl], so that threads of consecutive pixels touch
+// consecutive entries.  With one pixel per thread (single-plane images) each thread computes its
+// pixel's coordinates once and walks the views.
 template <int KC, int AR, int CAPX>
 __device__ __forceinline__ void bp_fill(const GeoDev &g, int slot0, int u0, int nvc, int j0,
                                         int np, BpTable<KC, AR, CAPX> &tb)
 {
-    using T = typename ArithT<AR>::T;
-    const int nthr = blockDim.x;
+    const int nthr = blockDim.x, npix = g.N * g.N;
+    if (np == nthr) {
+        const int pl = threadIdx.x, j = j0 + pl;
+        const bool in = j < npix;
+        const int ix = in ? j % g.N : 0, iy = in ? j / g.N : 0;
+        for (int uu = 0; uu < nvc; ++uu)
+            tb.e[uu * np + pl] = bp_entry<KC, AR, CAPX>(g, slot0, u0 + uu, in, ix, iy);
+        return;
+    }
     for (int e = threadIdx.x; e < np * nvc; e += nthr) {
-        const int pl = e / nvc, u = u0 + e % nvc;   // u: view within the subset
+        const int uu = e / np, pl = e - uu * np;
         const int j = j0 + pl;
-        int b0 = 0;
-        T w[KC];
-        if (j < g.N * g.N) {
-            bp_weights<KC, AR>(g, g.views[slot0 + u], slot0 + u, j % g.N, j / g.N, b0, w);
-        } else {
-#pragma unroll
-            for (int k = 0; k < KC; ++k) w[k] = T(0);
-        }
-        // Clamp the first bin into [0, NB - KC] and shift the lengths with it, so that all KC
-        // rows of the entry exist (bins outside [0, NB) already carry zero length).
-        const int bc = min(max(b0, 0), g.NB - KC);
-        typename BpTable<KC, AR, CAPX>::E ent;
-        ent.off = ((unsigned)u * (unsigned)g.NB + (unsigned)bc) * (unsigned)g.Pp;
-#pragma unroll
-        for (int k = 0; k < KC; ++k) {
-            const int src = k + bc - b0;
-            T v = T(0);
-#pragma unroll
-            for (int m = 0; m < KC; ++m) v = (m == src) ? w[m] : v;
-            ent.w[k] = v;
-        }
-        tb.e[e] = ent;
+        const bool in = j < npix;
+        tb.e[e] = bp_entry<KC, AR, CAPX>(g, slot0, u0 + uu, in, in ? j % g.N : 0, in ? j / g.N : 0);
     }
 }
 
-// Accumulate views [u0, u0 + nvc) of the table into acc for local pixel pl and plane group grp.
+// Accumulate the nvc views of the table (np pixels) into acc for local pixel pl and plane group grp.
 // proj (subset rows [u][NB][Pp]) == nullptr backprojects ones.
 template <int G, int KC, int AR, int CAPX>
 __device__ __forceinline__ void bp_accumulate(const GeoDev &g, const BpTable<KC, AR, CAPX> &tb,
                                               const typename ArithT<AR>::T *__restrict__ proj,
-                                              int u0, int nvc, int pl, int grp,
+                                              int np, int nvc, int pl, int grp,
                                               GroupSum<G, AR> &acc)
 {
     using T = typename ArithT<AR>::T;
     const unsigned Pp = (unsigned)g.Pp;
     const T *base = proj + grp * G;
     for (int uu = 0; uu < nvc; ++uu) {
-        const typename BpTable<KC, AR, CAPX>::E ent = tb.e[pl * nvc + uu];
+        const typename BpTable<KC, AR, CAPX>::E ent = tb.e[uu * np + pl];
         if (proj == nullptr) {
             T s = T(0);
 #pragma unroll

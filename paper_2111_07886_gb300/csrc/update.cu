@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(256, 3) update_kernel(const __grid_constant__ 
                 __syncthreads();
                 bp_fill<KC, AR>(g, a.slot0, u0, nvc, j0, TP, tb);
                 __syncthreads();
-                if (active) bp_accumulate<G, KC, AR>(g, tb, w, u0, nvc, pl, grp, bp);
+                if (active) bp_accumulate<G, KC, AR>(g, tb, w, TP, nvc, pl, grp, bp);
             }
             if (!active) continue;
             // 3. step and clamp P_t
@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(256, UPDATE_X8_BLOCKS) update_kernel_x8(
                 __syncthreads();
                 if (!active) continue;
                 for (int uu = 0; uu < nvc; ++uu) {
-                    const typename Table::E ent = tb.e[pl * nvc + uu];
+                    const typename Table::E ent = tb.e[uu * TP + pl];
                     const float *row = w + ent.off;
 #pragma unroll
                     for (int kb = 0; kb < KC; kb += 2) {
@@ -436,7 +436,7 @@ __global__ void __launch_bounds__(256) back_kernel(const __grid_constant__ BackA
             __syncthreads();
             bp_fill<KC, AR>(g, a.slot0, u0, nvc, j0, TP, tb);
             __syncthreads();
-            if (active) bp_accumulate<G, KC, AR>(g, tb, proj, u0, nvc, pl, grp, acc);
+            if (active) bp_accumulate<G, KC, AR>(g, tb, proj, TP, nvc, pl, grp, acc);
         }
         if (!active) continue;
         T b[G];
