@@ -159,8 +159,10 @@ __global__ void __launch_bounds__(256, 3) update_kernel(const __grid_constant__ 
         const int VC = max(1, min(a.nviews, BpTable<KC, AR>::CAP / TP));
         const bool dyn = a.nu_mode == 1 || a.nu_mode == 2;
         const double q = (double)npix * g.P;
-        const T inv_mean_f = dyn ? (T)(q / *a.sum_f) : T(1);
-        const T mean_mu = dyn ? (T)(*a.sum_mu / q) : T(1);
+        // per-scan scalars in the kernel's arithmetic: an FP64 division in every thread of every
+        // virtual block is costly at GB300's FP64 rate
+        const T inv_mean_f = dyn ? (T)q / (T)*a.sum_f : T(1);
+        const T mean_mu = dyn ? (T)*a.sum_mu / (T)q : T(1);
         const T lam = (T)a.lam_alpha, bm = (T)a.beta_over_M, U = (T)a.U, tt = (T)a.t;
         const T nu1 = (T)a.nu1, nu2 = (T)a.nu2, halfU = T(0.5) * U;
         const T *w = reinterpret_cast<const T *>(a.w);
@@ -259,8 +261,9 @@ __global__ void __launch_bounds__(256, UPDATE_X8_BLOCKS) update_kernel_x8(
         const int VC = max(1, min(a.nviews, Table::CAP / TP));
         const bool dyn = a.nu_mode == 1 || a.nu_mode == 2;
         const double q = (double)npix * g.P;
-        const float mean_f = dyn ? (float)(*a.sum_f / q) : 1.f;
-        const float mean_mu = dyn ? (float)(*a.sum_mu / q) : 1.f;
+        // per-scan scalars in FP32 (an FP64 division per thread is costly at GB300's FP64 rate)
+        const float mean_f = dyn ? (float)*a.sum_f / (float)q : 1.f;
+        const float mean_mu = dyn ? (float)*a.sum_mu / (float)q : 1.f;
         const float U = (float)a.U, tt = (float)a.t;
         // eps >= 1e-30 keeps 1/den finite, so that a zero-difference term stays exactly zero
         const float eps = fmaxf((float)a.eps, 1e-30f);
@@ -463,8 +466,8 @@ __global__ void __launch_bounds__(256) image_kernel(const __grid_constant__ Imag
         const long long items = (long long)N * N * NG;
         const double q = (double)N * N * g.P;
         const T *f = reinterpret_cast<const T *>(a.f);
-        const T inv_mean_f = (KIND == 1 || KIND == 2) ? (T)(q / *a.sum_f) : T(1);
-        const T mean_mu = KIND == 2 ? (T)(*a.sum_mu / q) : T(1);
+        const T inv_mean_f = (KIND == 1 || KIND == 2) ? (T)q / (T)*a.sum_f : T(1);
+        const T mean_mu = KIND == 2 ? (T)*a.sum_mu / (T)q : T(1);
         T part = T(0);
         for (int k = 0; k < a.ipt; ++k) {
             const long long tid = ((long long)vloc * a.ipt + k) * 256 + threadIdx.x;
@@ -525,7 +528,7 @@ __global__ void __launch_bounds__(256) mu_kernel_x8(const __grid_constant__ Imag
         const int TP = 256 / NG;
         const int pl = threadIdx.x / NG, grp = threadIdx.x % NG;
         const int ntiles = (npix + TP - 1) / TP;
-        const float inv_mean_f = (float)((double)npix * g.P / *a.sum_f);
+        const float inv_mean_f = (float)((double)npix * g.P) / (float)*a.sum_f;
         const float *f = reinterpret_cast<const float *>(a.f) + grp * 8;
         const int nvalid = min(8, g.P - grp * 8);             // real planes of this group
         float part = 0.f;
