@@ -382,13 +382,15 @@ __device__ __forceinline__ void bp_weights(const GeoDev &g, const ViewGeo &vw, i
     } else {
         const long long tq = vw.t0q + (long long)ix * vw.cxq + (long long)iy * vw.cyq;
         b0 = (int)((tq - vw.hq + 0xFFFFFFFFLL) >> 32);          // ceil(t - h)
-        const float ws = vw.wslopef * kQ32;
+        // dd in (0, h 2^32] fits 32 bits after dropping its 8 lowest bits (2^-24 bin): a 32-bit
+        // integer conversion instead of a 64-bit one, which runs on the (narrow) FP64 pipe
+        const float ws = vw.wslopef * (kQ32 * 256.f);
 #pragma unroll
         for (int k = 0; k < KC; ++k) {
             const int b = b0 + k;
             const long long dq = ((long long)b << 32) - tq;
             const long long dd = vw.hq - (dq < 0 ? -dq : dq);
-            const float ww = dd > 0 ? fminf(vw.Lf, __ll2float_rn(dd) * ws) : 0.f;
+            const float ww = dd > 0 ? fminf(vw.Lf, __int2float_rn((int)(dd >> 8)) * ws) : 0.f;
             w[k] = (unsigned)b < (unsigned)NB ? ww : 0.f;
         }
     }

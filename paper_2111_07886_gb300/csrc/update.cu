@@ -463,17 +463,17 @@ __global__ void __launch_bounds__(256) image_kernel(const __grid_constant__ Imag
         const ImageArgs &a = *scan_of(one, bt, vb, vloc, nv);
         const GeoDev &g = a.g;
         const int N = g.N, NG = g.NG, Pp = g.Pp;
-        const long long items = (long long)N * N * NG;
+        const unsigned items = (unsigned)N * (unsigned)N * (unsigned)NG;    // < 2^32 (geometry limits)
         const double q = (double)N * N * g.P;
         const T *f = reinterpret_cast<const T *>(a.f);
         const T inv_mean_f = (KIND == 1 || KIND == 2) ? (T)q / (T)*a.sum_f : T(1);
         const T mean_mu = KIND == 2 ? (T)*a.sum_mu / (T)q : T(1);
         T part = T(0);
         for (int k = 0; k < a.ipt; ++k) {
-            const long long tid = ((long long)vloc * a.ipt + k) * 256 + threadIdx.x;
+            const unsigned tid = ((unsigned)vloc * (unsigned)a.ipt + (unsigned)k) * 256u + threadIdx.x;
             if (tid >= items) break;
-            const int grp = (int)(tid % NG);
-            const int j = (int)(tid / NG);
+            const int grp = NG == 1 ? 0 : (int)(tid % (unsigned)NG);
+            const int j = NG == 1 ? (int)tid : (int)(tid / (unsigned)NG);
             const int ix = j % N, iy = j / N;
             T fc[G], gr[G], gx[G], gy[G], rv[G], out[G];
             if constexpr (KIND == 0) {
