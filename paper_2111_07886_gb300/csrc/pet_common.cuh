@@ -159,7 +159,12 @@ struct UpdateArgs {
     Reducer red;
     int tpv;                   // pixel tiles per virtual block
     int nvb;                   // virtual blocks of this scan
+    // the scalars above as FP32 for the FP32 kernels (converted once on the host: a conversion
+    // from double on the device runs on the narrow FP64 pipe)
+    float fs_lam, fs_bm, fs_gamma_r, fs_eps, fs_t, fs_U, fs_nu1, fs_nu2, fs_ips, fs_scale;
 };
+// FP32 copies of the update's scalars (call after filling the double fields and g)
+void update_fp32_scalars(UpdateArgs &a);
 pet_status launch_update(const UpdateArgs &a, int arith, cudaStream_t st);
 void update_shape(UpdateArgs &a, int arith);               // fills tpv, nvb
 GeoDev update_geo(const GeoDev &g);                        // plane grouping of the update kernel

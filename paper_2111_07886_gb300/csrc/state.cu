@@ -230,6 +230,7 @@ void pet::plan_subiter(pet_state *s, SubiterPlan *pl, bool with_objective)
     ua.sum_fout = s->sums + (1 - s->cur);
     ua.red = s->red;
     update_shape(ua, s->arith);
+    update_fp32_scalars(ua);
     if (nu_mode == 2) s->have_frozen = true;
     s->cur ^= 1;
     s->J = J;

@@ -138,6 +138,28 @@ __device__ __forceinline__ T nu_of(T gx, T gy, T inv_mean_f, T mean_mu, T nu1, T
 
 int sm_count();
 
+void update_fp32_scalars(UpdateArgs &a)
+{
+    a.fs_lam = (float)a.lam_alpha;
+    a.fs_bm = (float)a.beta_over_M;
+    a.fs_gamma_r = (float)a.gamma_r;
+    a.fs_eps = (float)a.eps;
+    a.fs_t = (float)a.t;
+    a.fs_U = (float)a.U;
+    a.fs_nu1 = (float)a.nu1;
+    a.fs_nu2 = (float)a.nu2;
+    a.fs_ips = (float)a.invp_scale;
+    a.fs_scale = (float)a.g.scale;
+}
+
+// the scalar in the kernel's arithmetic: the host-converted FP32 copy, or the double
+template <typename T>
+__device__ __forceinline__ T scal(double d, float f)
+{
+    if constexpr (sizeof(T) == 4) return f;
+    else return d;
+}
+
 // f^{k,i} = P_t(f - lambda_k alpha_{k,i} nu S(f) (A_i^T w + (beta/M) grad R(f)))
 // Virtual block: tpv tiles of TP consecutive pixels x NG plane groups (thread = pixel * NG +
 // group); the (pixel, view) weights of each tile are computed once into shared memory.  A
@@ -163,12 +185,13 @@ __global__ void __launch_bounds__(256, 3) update_kernel(const __grid_constant__ 
         // virtual block is costly at GB300's FP64 rate
         const T inv_mean_f = dyn ? (T)q / (T)*a.sum_f : T(1);
         const T mean_mu = dyn ? (T)*a.sum_mu / (T)q : T(1);
-        const T lam = (T)a.lam_alpha, bm = (T)a.beta_over_M, U = (T)a.U, tt = (T)a.t;
-        const T nu1 = (T)a.nu1, nu2 = (T)a.nu2, halfU = T(0.5) * U;
+        const T lam = scal<T>(a.lam_alpha, a.fs_lam), bm = scal<T>(a.beta_over_M, a.fs_bm);
+        const T U = scal<T>(a.U, a.fs_U), tt = scal<T>(a.t, a.fs_t);
+        const T nu1 = scal<T>(a.nu1, a.fs_nu1), nu2 = scal<T>(a.nu2, a.fs_nu2), halfU = T(0.5) * U;
         const T *w = reinterpret_cast<const T *>(a.w);
         const T *f = reinterpret_cast<const T *>(a.f);
         const T *invp = reinterpret_cast<const T *>(a.invp);
-        const T scale = (T)g.scale;
+        const T scale = scal<T>(g.scale, a.fs_scale);
         const int ntiles = (npix + TP - 1) / TP;
         T part = T(0);
         for (int tile = vloc * a.tpv; tile < min(ntiles, (vloc + 1) * a.tpv); ++tile) {
@@ -180,8 +203,9 @@ __global__ void __launch_bounds__(256, 3) update_kernel(const __grid_constant__ 
             if (active) {
                 const int ix = j % N, iy = j / N;
                 T gr[G], gx[G], gy[G], rv[G];
-                if (dyn) stencil<G, AR, true, true, false>(g, f, grp, ix, iy, (T)a.gamma_r, (T)a.eps, fc, gr, gx, gy, rv);
-                else stencil<G, AR, true, false, false>(g, f, grp, ix, iy, (T)a.gamma_r, (T)a.eps, fc, gr, gx, gy, rv);
+                const T gam_r = scal<T>(a.gamma_r, a.fs_gamma_r), eps_t = scal<T>(a.eps, a.fs_eps);
+                if (dyn) stencil<G, AR, true, true, false>(g, f, grp, ix, iy, gam_r, eps_t, fc, gr, gx, gy, rv);
+                else stencil<G, AR, true, false, false>(g, f, grp, ix, iy, gam_r, eps_t, fc, gr, gx, gy, rv);
                 T nu[G];
                 if (a.nu_mode == 3) {
                     load_group<G, T>(reinterpret_cast<const T *>(a.nu_frozen) + (unsigned)j * (unsigned)Pp + grp * G, nu);
@@ -194,7 +218,7 @@ __global__ void __launch_bounds__(256, 3) update_kernel(const __grid_constant__ 
                     if (a.nu_mode == 2)
                         store_group<G, T>(reinterpret_cast<T *>(a.nu_frozen) + (unsigned)j * (unsigned)Pp + grp * G, nu);
                 }
-                const T ip = invp[j] * (T)a.invp_scale;
+                const T ip = invp[j] * scal<T>(a.invp_scale, a.fs_ips);
 #pragma unroll
                 for (int p = 0; p < G; ++p) {
                     const T S = (fc[p] < halfU ? fc[p] : U - fc[p]) * ip;
@@ -264,9 +288,9 @@ __global__ void __launch_bounds__(256, UPDATE_X8_BLOCKS) update_kernel_x8(
         // per-scan scalars in FP32 (an FP64 division per thread is costly at GB300's FP64 rate)
         const float mean_f = dyn ? (float)*a.sum_f / (float)q : 1.f;
         const float mean_mu = dyn ? (float)*a.sum_mu / (float)q : 1.f;
-        const float U = (float)a.U, tt = (float)a.t;
+        const float U = a.fs_U, tt = a.fs_t;
         // eps >= 1e-30 keeps 1/den finite, so that a zero-difference term stays exactly zero
-        const float eps = fmaxf((float)a.eps, 1e-30f);
+        const float eps = fmaxf(a.fs_eps, 1e-30f);
         const float *f = reinterpret_cast<const float *>(a.f) + grp * 8;
         const float *w = reinterpret_cast<const float *>(a.w) + grp * 8;
         const float *invp = reinterpret_cast<const float *>(a.invp);
@@ -281,7 +305,7 @@ __global__ void __launch_bounds__(256, UPDATE_X8_BLOCKS) update_kernel_x8(
                 const unsigned jc = (unsigned)j;
                 const unsigned xm = ix > 0 ? jc - 1 : jc, xp = ix < N - 1 ? jc + 1 : jc;
                 const unsigned ym = iy > 0 ? jc - N : jc, yp = iy < N - 1 ? jc + N : jc;
-                const f2x GR = vsplat((float)a.gamma_r), EP = vsplat(eps), TWO = vsplat(2.f);
+                const f2x GR = vsplat(a.fs_gamma_r), EP = vsplat(eps), TWO = vsplat(2.f);
                 f2x c[4], ce[4], gr[4], g2[4], nb0[4], nb1[4];
                 load8x(f + jc * Pp, c);
 #pragma unroll
@@ -316,7 +340,7 @@ __global__ void __launch_bounds__(256, UPDATE_X8_BLOCKS) update_kernel_x8(
                 f2x nu[4];
                 if (dyn) {
                     const f2x HY = vsplat((iy > 0 && iy < N - 1) ? 0.5f : 1.f);
-                    const float nu1 = (float)a.nu1, nu2 = (float)a.nu2;
+                    const float nu1 = a.fs_nu1, nu2 = a.fs_nu2;
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
                         const f2x t = vmul(HY, vsub(nb1[k], nb0[k]));
@@ -347,8 +371,8 @@ __global__ void __launch_bounds__(256, UPDATE_X8_BLOCKS) update_kernel_x8(
                 rdp(nb0);
                 rdp(nb1);
                 // c = lambda alpha nu S, S = min(f, U - f) / p;  A = f - c (beta/M) 2 gr;  B = -c scale
-                const f2x NK = vsplat(-(float)a.lam_alpha * invp[j] * (float)a.invp_scale);
-                const f2x BM = vsplat(2.f * (float)a.beta_over_M), SC = vsplat((float)g.scale);
+                const f2x NK = vsplat(-a.fs_lam * invp[j] * a.fs_ips);
+                const f2x BM = vsplat(2.f * a.fs_bm), SC = vsplat(a.fs_scale);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     float c0, c1;
@@ -644,6 +668,7 @@ pet_status launch_update(const UpdateArgs &a0, int arith, cudaStream_t st)
 {
     UpdateArgs a = a0;
     update_shape(a, arith);
+    update_fp32_scalars(a);
     return update_any(a, Batch{nullptr, nullptr, 0, 0}, arith, persistent_grid(a.nvb), st);
 }
 
