@@ -226,6 +226,8 @@ struct pet_state {
     cudaStream_t ostream = nullptr;
     cudaEvent_t ev_ofork = nullptr, ev_odone = nullptr;
     bool obj_pending = false;
+    cudaStream_t hstream = nullptr;        // whole reconstructions: subiterations at top priority
+    cudaEvent_t ev_h0 = nullptr, ev_h1 = nullptr;
     size_t q_bytes = 0, sino_elems = 0, w_bytes = 0;
 };
 

@@ -46,6 +46,14 @@ static void state_free(pet_state *s)
         s->side = nullptr;
         s->ev_fork = s->ev_join = nullptr;
     }
+    if (s->hstream) {
+        cudaStreamSynchronize(s->hstream);
+        cudaStreamDestroy(s->hstream);
+        cudaEventDestroy(s->ev_h0);
+        cudaEventDestroy(s->ev_h1);
+        s->hstream = nullptr;
+        s->ev_h0 = s->ev_h1 = nullptr;
+    }
     if (s->ostream) {
         cudaStreamSynchronize(s->ostream);
         cudaStreamDestroy(s->ostream);
@@ -253,7 +261,9 @@ static pet_status state_subiter(pet_state *s, cudaStream_t st)
     }
     if (pl.mu) {
         if (!s->side) {
-            PET_CUDA(cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking));
+            int lo = 0, hi = 0;
+            PET_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+            PET_CUDA(cudaStreamCreateWithPriority(&s->side, cudaStreamNonBlocking, hi));
             PET_CUDA(cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming));
             PET_CUDA(cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming));
         }
@@ -505,9 +515,25 @@ static pet_status state_objective_beside(pet_state *s, double *out3, cudaStream_
 }
 
 // Whole reconstruction on an allocated state: T outer iterations, objective history on device.
-static pet_status run_reconstruct(pet_state *s, double *h_objective, cudaStream_t st)
+// The subiterations run on an internal stream of the highest priority forked from `st` (joined
+// back at the end), so that the objective evaluations beside them, at default priority, take
+// only the SM slots the subiterations leave.
+static pet_status run_reconstruct(pet_state *s, double *h_objective, cudaStream_t st0)
 {
     const int T = s->prm.iterations, M = s->g->dev.M;
+    cudaStream_t st = st0;
+    if (h_objective && !profile_active()) {
+        if (!s->hstream) {
+            int lo = 0, hi = 0;
+            PET_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+            PET_CUDA(cudaStreamCreateWithPriority(&s->hstream, cudaStreamNonBlocking, hi));
+            PET_CUDA(cudaEventCreateWithFlags(&s->ev_h0, cudaEventDisableTiming));
+            PET_CUDA(cudaEventCreateWithFlags(&s->ev_h1, cudaEventDisableTiming));
+        }
+        PET_CUDA(cudaEventRecord(s->ev_h0, st0));
+        PET_CUDA(cudaStreamWaitEvent(s->hstream, s->ev_h0, 0));
+        st = s->hstream;
+    }
     if (h_objective) PET_TRY(state_objective_beside(s, s->objhist, st));
     for (int k = 0; k < T; ++k) {
         for (int i = 0; i < M; ++i) PET_TRY(state_subiter(s, st));
@@ -516,6 +542,10 @@ static pet_status run_reconstruct(pet_state *s, double *h_objective, cudaStream_
     if (s->obj_pending) {
         PET_CUDA(cudaStreamWaitEvent(st, s->ev_odone, 0));
         s->obj_pending = false;
+    }
+    if (st != st0) {
+        PET_CUDA(cudaEventRecord(s->ev_h1, st));
+        PET_CUDA(cudaStreamWaitEvent(st0, s->ev_h1, 0));
     }
     return PET_OK;
 }
