@@ -284,15 +284,15 @@ void pet_serve_destroy(pet_server *sv);
  * pet_objective_static: the same values as pet_objective, from a call that allocates nothing.
  * The paper has no counterpart; this serves callers that may not allocate device memory at the
  * moment they need the objective: a pipeline whose device memory is handed to a fixed pool at
- * start-up, or code running inside a CUDA graph capture or a real-time loop, where a cudaMalloc
- * (such as the scratch pet_objective allocates on first use) would break the capture or stall.
- * Inputs are read in their C-ABI layouts (float image [P][N][N], counts int32 and gamma float
- * [P][V][n_b]); the reduction uses one static device array of about 49 KB that every GPU
- * loading the library holds until exit.  The geometry must exist already (pet_geometry_create
- * allocates).  The first call on a device looks up that array's device address (do it once
- * before any stream capture); every call then shares the array, so calls that overlap on the
- * GPU race and must be serialised.  Problems above 2^31 - 1 rays x planes or pixels x planes
- * are rejected with PET_ERR_INVALID.  Synchronises `stream`.
+ * start-up, or a real-time loop in which a cudaMalloc (such as the scratch pet_objective
+ * allocates on first use) would stall the stream.  Inputs are read in their C-ABI layouts
+ * (float image [P][N][N], counts int32 and gamma float [P][V][n_b]); the log-likelihood terms
+ * are evaluated in FP64; the reduction uses one static device array of about 49 KB that every
+ * GPU loading the library holds until exit.  The geometry must exist already
+ * (pet_geometry_create allocates).  The first call on a device looks up that array's device
+ * address; every call then shares the array, so calls that overlap on the GPU race and must be
+ * serialised.  Problems above 2^31 - 1 rays x planes or pixels x planes are rejected with
+ * PET_ERR_INVALID.  The call reads the result back to the host and synchronises `stream`.
  * ---------------------------------------------------------------------------------------- */
 pet_status pet_objective_static(const pet_geometry *g, const int32_t *d_counts,
                                 const float *d_gamma, const float *d_img, double beta,

@@ -1,19 +1,20 @@
 // pet_objective_static: the objective Phi(f) computed without allocating any memory.
 //
-// Who needs this: a host that is not allowed to allocate device memory on its own — for
+// Who needs this: a host that is not allowed to allocate device memory on its own, for
 // example a scanner pipeline that hands every byte of device memory to a fixed-size pool at
-// start-up, or a plug-in running inside someone else's CUDA graph capture or real-time loop,
-// where a cudaMalloc would break the capture or stall the stream.  pet_objective stages the
-// image and sinograms into geometry-owned scratch (allocated on first use) and reduces
-// through a scratch partials buffer; this variant reads the caller's buffers in their C-ABI
-// layouts directly and reduces through one fixed array in this file's device memory.
+// start-up, or a real-time acquisition loop in which a cudaMalloc (with its implicit device
+// synchronisation) would stall the stream.  pet_objective stages the image and sinograms into
+// geometry-owned scratch (allocated on first use) and reduces through a scratch partials
+// buffer; this variant reads the caller's buffers in their C-ABI layouts directly and reduces
+// through one fixed array in this file's device memory.
 //
 // The scratch (g_static_scratch) is a file-scope __device__ array: every GPU that loads the
 // library holds it (kStaticBlocks * 3 + 64 doubles, about 49 KB) until the process exits.  In
 // host code its name is only a host-side stand-in, so the device address is looked up once
 // per device with cudaGetSymbolAddress while that device is current, and passed to the kernel.
 // All calls share the array: calls that overlap on the GPU (other streams, other threads)
-// race on it and must be serialised by the caller.
+// race on it and must be serialised by the caller.  The call ends by reading the three sums
+// back to the host and synchronising its stream.
 #include <math.h>
 
 #include <mutex>
@@ -71,7 +72,8 @@ __global__ void __launch_bounds__(256) objective_static_kernel(
         const float af = (float)g.scale * s.value(0);
         acc[0] += (double)af;
         const int c = counts[o];
-        if (c != 0) acc[1] += (double)c * (double)logf(af + gamma[o]);
+        // the likelihood term in FP64: ln((double) Af + gamma)
+        if (c != 0) acc[1] += (double)c * log((double)af + (double)gamma[o]);
     }
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < npix; t += stride) {
         const int p = (int)(t / ((long long)N * N));

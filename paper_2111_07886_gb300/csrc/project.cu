@@ -191,17 +191,19 @@ __global__ void __launch_bounds__(256, 3) fwd_kernel(const __grid_constant__ Fwd
                     }
                     store_group<G, T>(reinterpret_cast<T *>(a.out) + o, w);
                 } else {
-                    T s_af = T(0), s_gl = T(0);
+                    // the likelihood terms in FP64 in every mode: ln((double) Af + gamma)
+                    T s_af = T(0);
+                    double s_gl = 0.0;
 #pragma unroll
                     for (int p = 0; p < G; ++p) {
                         if (grp * G + p < g.P) {
                             const T af = scale * tot[p];
                             s_af += af;
-                            if (cnt[p] != 0) s_gl += (T)cnt[p] * log(af + (T)gam[p]);
+                            if (cnt[p] != 0) s_gl += (double)cnt[p] * log((double)af + (double)gam[p]);
                         }
                     }
                     obj[0] += (double)s_af;
-                    obj[1] += (double)s_gl;
+                    obj[1] += s_gl;
                 }
             }
         }
