@@ -51,8 +51,10 @@ def parse():
                     help="pin the forward projector's ray chunks instead of autotuning (profiling "
                          "runs: the profiler's per-launch cost distorts the autotuner's timings)")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-scan batched run")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the no-objective and FP32 / FP64 arithmetic measurements")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop run")
-    ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-requests", type=int, default=500)
     ap.add_argument("--serve-rates", default="0.5,0.9,1.5",
                     help="arrival rates as fractions of the sequential plain capacity")
     return ap.parse_args()
@@ -62,10 +64,21 @@ def workload(name: str):
     return synth.config_stacked_256x89(seed=0) if name == "stacked" else synth.config_2d_128(seed=0)
 
 
+def algo_config(p) -> dict:
+    """The SDP-BSREM parameters the run uses (the P2 form of Sec. III with the workload's rho,
+    delta, a and nu bounds, not Table II's SDP-P2 rows)."""
+    names = {0: "BSREM", 1: "SDP-M1", 2: "SDP-M2", 3: "SDP-P1", 4: "SDP-P2"}
+    return {"precond": names[p.precond], "rho": p.rho, "delta1": p.delta1, "delta2": p.delta2,
+            "a": p.a, "lambda0": p.lambda0, "nu1": p.nu1, "nu2": p.nu2, "J0": p.J0, "J1": p.J1,
+            "gamma_r": p.gamma_r, "eps": p.eps, "t": p.t, "U": p.U,
+            "params_source": "P2 form (Sec. III) with workload settings; Table II's P2 rows are "
+                             "chaotic on these phantoms"}
+
+
 def workload_config(w) -> dict:
     return {"workload": w.name, "image": [w.nplanes, w.n, w.n], "pixel_mm": w.pixel_mm,
             "views": w.nviews, "bins": w.nbins, "subsets": w.nsubsets,
-            "iterations": w.params.iterations, "precond": "SDP-P2", "beta": w.params.beta,
+            "iterations": w.params.iterations, **algo_config(w.params), "beta": w.params.beta,
             "counts": w.counts, "subiters_per_step": w.params.iterations * w.nsubsets,
             "objective_per_iteration": True, "l2": "flushed (256 MiB write) before each step",
             "global_batch": 1, "parallelism": "replicas"}
@@ -274,6 +287,8 @@ def run_ours(args, rank, world, local):
         "clocks": clk, "gpu_launches": int(launches),
         "wall_s_timed": round(wall, 3), "objective_final": obj[-1] if obj else None,
     }
+    if not args.no_variants:
+        line["variants"] = variants_measure(args, w, g, counts, gamma, pet, flush, subiters)
     if not args.no_kernel_times:
         line.update(kernel_times(args, w, pet, step, flush))
     if not args.no_e2e:
@@ -285,6 +300,43 @@ def run_ours(args, rank, world, local):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, scan, args.cpu_seconds)
     return line
+
+
+def variants_measure(args, w, g, counts, gamma, pet, flush, subiters) -> dict:
+    """Subiterations per second of the same reconstruction (a) without the per-iteration
+    objective, which the paper evaluates for reporting only, and (b) in the other arithmetics of
+    the precision study: plain FP32 sums and FP64 on the GPU (with the objective, as the main
+    line).  CUDA events, L2 flushed before each step."""
+    import torch
+    stream = torch.cuda.current_stream()
+    f0 = torch.ones((w.nplanes, w.n, w.n), dtype=torch.float32, device=counts.device)
+    img = torch.empty_like(f0)
+
+    def timed(prm, objective, steps, warm):
+        def one():
+            img.copy_(f0)
+            pet.reconstruct(g, counts, gamma, prm, img, objective=objective)
+        for _ in range(warm):
+            one()
+        ms = 0.0
+        for k in range(steps):
+            flush.fill_(float(k))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            one()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms += a.elapsed_time(b)
+        return round(subiters / (ms / steps / 1e3), 2), round(ms / steps, 3)
+
+    out = {"unit": "subiters/s"}
+    v, ms = timed(pet.make_params(w.params), False, max(1, min(args.steps, 3)), 1)
+    out["no_objective"] = {"value": v, "ms_per_step": ms, "precision": "fp32+kahan"}
+    v, ms = timed(pet.make_params(w.params, synth.PREC_FP32), True, max(1, min(args.steps, 3)), 1)
+    out["fp32_plain_sums"] = {"value": v, "ms_per_step": ms, "objective_per_iteration": True}
+    v, ms = timed(pet.make_params(w.params, synth.PREC_FP64), True, 1, 1)
+    out["fp64_on_gpu"] = {"value": v, "ms_per_step": ms, "objective_per_iteration": True}
+    return out
 
 
 def kernel_times(args, w, pet, step, flush) -> dict:
@@ -313,6 +365,20 @@ def kernel_times(args, w, pet, step, flush) -> dict:
             "peak_source": peaks["source"] + " (burst copy)", "unit": "GB/s",
             "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": ncu_traffic(dom),
             "algorithmic_bytes_per_launch": byts[dom], "avg_launch_ms": round(avg_ms, 5)}
+    # every kernel kind against the same peak; the projector's fraction is the one the 50 % HBM
+    # target names (forward_ratio inside the subiteration, obj_forward for the objective)
+    by_kind = {}
+    for k in byts:
+        if k in prof and prof[k][1]:
+            ms_k = prof[k][0] / prof[k][1]
+            ach = byts[k] / (ms_k / 1e3) / 1e9
+            by_kind[k] = {"achieved": round(ach, 1), "frac": round(ach / peaks["hbm_gbs"], 4),
+                          "algorithmic_bytes_per_launch": byts[k], "avg_launch_ms": round(ms_k, 5),
+                          "traffic": ncu_traffic(k)}
+    proj = by_kind.get("forward_ratio", {}).get("frac")
+    roof["by_kernel"] = by_kind
+    roof["projector_target"] = {"kernel": "forward_ratio", "frac": proj, "target_frac": 0.5,
+                                "met": bool(proj is not None and proj >= 0.5)}
     return {"roofline": roof, "kernels": shares}
 
 
@@ -396,24 +462,42 @@ def batched_measure(pet, torch) -> dict:
 
     plain_run()
     tp = plain_run()
+    # the same with every geometry tuned for 64 scans sharing the GPU (pet_autotune_batch)
+    tuned = {}
+    for w, g, c, gm, f0, st in items:
+        tuned[w.name] = g.autotune_batch(len(items), stream=stream)
+    stream.synchronize()
+    batched_run()
+    tbt, ticks_t, launches_t = batched_run()
+    plain_run()
+    tpt = plain_run()
+    for w, g, c, gm, f0, st in items:
+        g.set_ray_chunks(0)
     return {"workload": "64 mixed 2-D scans (N 128-400, 120-360 views, 12-36 subsets, 10 it.)",
             "subiters": subiters, "ticks": ticks, "gpu_launches": int(launches),
             "batched_s": round(tb, 4), "plain_s": round(tp, 4),
             "batched_subiters_per_s": round(subiters / tb, 1),
             "plain_subiters_per_s": round(subiters / tp, 1),
             "batched_scans_per_s": round(len(ws) / tb, 2), "plain_scans_per_s": round(len(ws) / tp, 2),
-            "speedup_vs_plain": round(tp / tb, 2)}
+            "speedup_vs_plain": round(tp / tb, 2),
+            "tuned": {"tuner": "pet_autotune_batch(g, 64): forward ray chunks S per geometry",
+                      "ray_chunks_per_geometry": tuned,
+                      "batched_s": round(tbt, 4), "plain_s": round(tpt, 4),
+                      "batched_subiters_per_s": round(subiters / tbt, 1),
+                      "batched_scans_per_s": round(len(ws) / tbt, 2),
+                      "speedup_vs_untuned_plain": round(tp / tbt, 2),
+                      "speedup_vs_untuned_batched": round(tb / tbt, 3)}}
 
 
 def serving_measure(args, pet, torch) -> dict:
-    """Serving loop: a Poisson-arrival stream of requests drawn from the mixed 2-D scans plus 5 %
-    stacked 256 x 256 x 89 jobs, each run to 20 iterations, at rates that are fractions of the
-    sequential plain capacity.  Reports scans/s and p50/p99 latency (submit to result), next to
-    the same arrival stream served by the plain per-scan path one request at a time (FIFO,
-    service times measured on the GPU)."""
-    import math
+    """Serving loop: a Poisson-arrival stream of requests drawn from the 64 mixed 2-D scans plus
+    5 % stacked 256 x 256 x 89 jobs, each run to 20 iterations, at rates that are fractions of
+    the sequential plain capacity.  Reports scans/s, p50/p99 latency (submit to result) and the
+    mean per-request breakdown (queue, prepare, run, readback), next to the same arrival stream
+    served by the plain per-scan path one request at a time (FIFO over service times measured on
+    the GPU with inputs resident: no host upload, which favours the plain arm)."""
     dev = torch.device("cuda")
-    ws = synth.mixed_2d_scans(64, seed=1, iterations=20)[:16]
+    ws = synth.mixed_2d_scans(64, seed=1, iterations=20)
     ws.append(synth.config_stacked_256x89(seed=5))
     scans = [synth.make_scan(w) for w in ws]
     # plain service time of every pool entry (pet_reconstruct, inputs resident, events)
@@ -437,12 +521,18 @@ def serving_measure(args, pet, torch) -> dict:
     pick = [len(ws) - 1 if rng.uniform() < 0.05 else int(rng.integers(0, len(ws) - 1)) for _ in range(n)]
     mean_service = float(np.mean([service[k] for k in pick]))
     capacity = 1.0 / mean_service
+    slots = 64
     out = {"requests": n, "pool": f"{len(ws) - 1} mixed 2-D scans + 1 stacked 256x256x89 (5 %)",
-           "iterations": 20, "plain_capacity_scans_per_s": round(capacity, 2), "rates": []}
+           "stacked_requests": int(sum(1 for k in pick if k == len(ws) - 1)),
+           "iterations": 20, "slots": slots, "autotune": f"pet_serve_autotune({slots})",
+           "plain_capacity_scans_per_s": round(capacity, 2),
+           "plain_arm": "FIFO over measured GPU service times, inputs resident (no upload)",
+           "rates": []}
     for rho in [float(x) for x in args.serve_rates.split(",") if x]:
         gaps = rng.exponential(1.0 / (rho * capacity), size=n)
         arrivals = np.cumsum(gaps) - gaps[0]
-        server = pet.Server(hbm_budget_bytes=64 << 30, max_slots=64)
+        server = pet.Server(hbm_budget_bytes=64 << 30, max_slots=slots)
+        server.autotune(slots)
         tickets = {}
         t0 = time.perf_counter()
         done = {}
@@ -461,21 +551,30 @@ def serving_measure(args, pet, torch) -> dict:
             time.sleep(0.0005)
         st = server.stats()
         server.close()
+        lat_s = np.array([done[i] for i in range(n)])
+        big = np.array([pick[i] == len(ws) - 1 for i in range(n)])
         # the same arrivals served one at a time by the plain path (FIFO)
         finish, lat = 0.0, []
         for i in range(n):
             start = max(arrivals[i], finish)
             finish = start + service[pick[i]]
             lat.append(finish - arrivals[i])
-        lat = np.sort(np.array(lat))
+        lat = np.array(lat)
         span_plain = finish - arrivals[0]
         out["rates"].append({
             "rho": rho, "served_scans_per_s": round(st["scans_per_s"], 2),
             "p50_s": round(st["p50_s"], 4), "p99_s": round(st["p99_s"], 4),
             "failed": int(st["failed"]),
+            "breakdown_mean_s": {k: round(st["mean_" + k + "_s"], 5)
+                                 for k in ("queue", "prepare", "run", "readback")},
+            "tuned_geometries": int(st["tuned_geometries"]),
+            "p50_2d_s": round(float(np.percentile(lat_s[~big], 50)), 4),
+            "p50_stacked_s": round(float(np.percentile(lat_s[big], 50)), 4) if big.any() else None,
             "plain_scans_per_s": round(n / span_plain, 2),
             "plain_p50_s": round(float(np.percentile(lat, 50)), 4),
-            "plain_p99_s": round(float(np.percentile(lat, 99)), 4)})
+            "plain_p99_s": round(float(np.percentile(lat, 99)), 4),
+            "plain_p50_2d_s": round(float(np.percentile(lat[~big], 50)), 4),
+            "plain_p50_stacked_s": round(float(np.percentile(lat[big], 50)), 4) if big.any() else None})
     return out
 
 
@@ -506,7 +605,8 @@ def run_reference(args, rank, world):
     import oracle
     og = oracle.geom_from(w.geometry(), scan["sens"])
     f0 = np.ones((w.nplanes, w.n, w.n))
-    nsub = 4 if args.workload == "stacked" else 24
+    # past J0, so that most sampled subiterations compute nu (Eq. nuki) as the timed run does
+    nsub = w.params.J0 + 5 if args.workload == "stacked" else 24
     for _ in range(args.warmup):
         oracle.reconstruct(og, scan["counts"], scan["gamma"], w.params, f0, nsub=1)
     t0 = time.perf_counter()
@@ -527,8 +627,22 @@ def run_reference(args, rank, world):
                     "d2h_bytes_per_step": 0}}
 
 
+def spawn_ranks(n: int, argv: list[str]) -> int:
+    """`--gpus N` without a launcher: start N ranks of this script with torch.distributed.run
+    (one process per GPU, rendezvous on 127.0.0.1); rank 0 prints the job's line."""
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n}",
+           "--master-addr", "127.0.0.1", f"--master-port={port}", os.path.abspath(__file__), *argv]
+    return subprocess.call(cmd)
+
+
 def main():
     args = parse()
+    if args.gpus > 1 and "RANK" not in os.environ:
+        sys.exit(spawn_ranks(args.gpus, sys.argv[1:]))
     rank, world, local = dist_env()
     if args.impl == "reference":
         if rank == 0:

@@ -116,8 +116,14 @@ void pet_geometry_destroy(pet_geometry *g);
 /* Autotuner (no counterpart in the paper): times the forward projector of subset 0 for each
  * admissible number of ray chunks (threads sharing one ray) and keeps the fastest in the
  * geometry; *best_S (optional) receives it.  Tune before creating states on the geometry (the
- * chunking changes the order of the ray sums, within rounding).  Synchronises `stream`. */
+ * chunking changes the order of the ray sums, within rounding).  The projection is timed on an
+ * image of ones, best of 5 after a warm-up.  Synchronises `stream`.
+ * pet_autotune_batch: the same, with `concurrent` (1..4096) copies of the projection running as
+ * one batched launch, as they do when that many scans of the geometry step together in a
+ * pet_batch or a server; the choice is kept in the geometry and used alone and in batches alike,
+ * so a scan computes the same bits either way. */
 pet_status pet_autotune(pet_geometry *g, void *stream, int *best_S);
+pet_status pet_autotune_batch(pet_geometry *g, int concurrent, void *stream, int *best_S);
 
 /* Sets the forward projector's ray chunks S directly (no counterpart in the paper): a choice
  * taken from an earlier pet_autotune, or fixed for a profiling run, where the profiler's own
@@ -245,7 +251,10 @@ pet_status pet_state_objective_history(pet_state *s, double *h_obj, void *stream
  *   while slots and the budget allow (geometry tables cached by description; upload; resident
  *   state), and a runner that keeps one pet_batch of all resident scans stepping: requests that
  *   arrive while others are on the GPU join at the next step; finished scans are read back and
- *   their memory and slot freed.
+ *   their memory and slot freed.  Scans are kept in one batch per kernel class (plane-group size,
+ *   arithmetic, gather width), each stepped on its own stream so that the classes advance
+ *   independently and overlap on the device; the stacked (multi-plane) class runs at the higher
+ *   stream priority.
  * pet_serve_submit: copies the request's host data (validated: counts >= 0, 0 < gamma < inf)
  *   and returns a ticket; the caller may free its buffers on return.  A request larger than the
  *   whole budget fails with PET_ERR_OOM (reported by poll).
@@ -254,7 +263,12 @@ pet_status pet_state_objective_history(pet_state *s, double *h_obj, void *stream
  *   (T+1 doubles, NaN without with_objective; may be NULL) and *latency_s = seconds from submit
  *   to result available; the ticket is then forgotten (PET_ERR_NOT_FOUND afterwards).
  * pet_serve_stats_get: counters, p50/p99/mean latency of completed requests, scans/s from first
- *   submit to last completion, device bytes in use.
+ *   submit to last completion, device bytes in use, and the mean per-request breakdown of the
+ *   latency: queue (submit to admission), prepare (geometry, upload, state), run (joining the
+ *   batch to the last subiteration issued) and readback (to the result on the host).
+ * pet_serve_autotune: concurrent > 0 makes the preparer tune every geometry it creates with
+ *   pet_autotune_batch(g, concurrent) before the geometry's first scan runs (0: built-in shapes);
+ *   set it before submitting.
  * pet_serve_destroy: drops queued requests, finishes resident ones, joins the threads.
  * Thread-safe: submit/poll/stats may be called from any host thread.
  * ---------------------------------------------------------------------------------------- */
@@ -271,6 +285,8 @@ typedef struct {
     long long submitted, completed, failed, running, queued;
     double p50_s, p99_s, mean_s, scans_per_s;
     size_t hbm_in_use;
+    double mean_queue_s, mean_prepare_s, mean_run_s, mean_readback_s;
+    long long tuned_geometries;
 } pet_serve_stats;
 
 pet_status pet_serve_create(size_t hbm_budget_bytes, int max_slots, int device, pet_server **out);
@@ -278,6 +294,7 @@ pet_status pet_serve_submit(pet_server *sv, const pet_request *req, uint64_t *ti
 pet_status pet_serve_poll(pet_server *sv, uint64_t ticket, float *h_img_out, double *h_obj_out,
                           double *latency_s);
 pet_status pet_serve_stats_get(pet_server *sv, pet_serve_stats *out);
+pet_status pet_serve_autotune(pet_server *sv, int concurrent);
 void pet_serve_destroy(pet_server *sv);
 
 /* ------------------------------------------------------------------------------------------

@@ -190,6 +190,21 @@ static bool running(const pet_state *s)
     return s && s->J < s->prm.iterations * s->g->dev.M;
 }
 
+namespace pet {
+// True when pet_batch_step would not wait for an earlier tick: every class with running scans
+// has its next descriptor buffer free.
+bool batch_can_step(const pet_batch *b)
+{
+    for (const BatchClass *c : b->classes) {
+        bool any = false;
+        for (const pet_state *s : c->slot) any = any || running(s);
+        if (!any) continue;
+        if (c->used[c->next] && cudaEventQuery(c->done[c->next]) == cudaErrorNotReady) return false;
+    }
+    return true;
+}
+}  // namespace pet
+
 extern "C" int pet_batch_size(const pet_batch *b)
 {
     if (!b) return -1;

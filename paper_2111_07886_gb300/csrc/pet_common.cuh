@@ -18,6 +18,10 @@ namespace pet {
 void set_error(const std::string &msg);
 pet_status fail(pet_status st, const std::string &msg);
 pet_status cuda_fail(cudaError_t e, const char *what);
+inline pet_status cuda_ok(cudaError_t e, const char *what)
+{
+    return e == cudaSuccess ? PET_OK : cuda_fail(e, what);
+}
 
 #define PET_CUDA(call)                                                       \
     do {                                                                     \
@@ -267,6 +271,7 @@ pet_status validate_data(const GeoDev &g, const int *counts, const float *gamma,
                          int *d_flag, cudaStream_t st);
 
 void workspace_free(void *w);     // state.cu
+bool batch_can_step(const pet_batch *b);   // batch.cu: a step would not wait for earlier ticks
 
 // geometry helpers (geometry.cu)
 pet_status geometry_scratch(const pet_geometry *g, size_t bytes, void **out);

@@ -336,27 +336,37 @@ pet_status launch_forward_batch(const FwdArgs &shape, const Batch &b, int mode, 
 
 using namespace pet;
 
-// Autotuner: times the subset-0 forward projection for every admissible chunk count S (1..8,
-// dividing the 256-thread block budget) and keeps the fastest in the geometry.  The choice is
-// per geometry, so every scan using it (alone or batched) runs the same shapes.
-extern "C" pet_status pet_autotune(pet_geometry *g, void *stream, int *best_S)
+// Autotuner: times the subset-0 forward projection of an image of ones for every admissible
+// chunk count S (1..8, dividing the 256-thread block budget) and keeps the fastest in the
+// geometry.  `concurrent` copies of the projection run as one batched launch (the persistent
+// grid of pet_batch), so that a geometry whose scans run in a batch is tuned with the GPU shared
+// the way the batch shares it; concurrent = 1 is a scan alone.  The choice is per geometry, so
+// every scan using it (alone or batched) runs the same shapes and computes the same bits.
+static pet_status autotune_any(pet_geometry *g, int concurrent, cudaStream_t st, int *best_S)
 {
-    if (!g) return fail(PET_ERR_INVALID, "pet_autotune: NULL geometry");
-    cudaStream_t st = as_stream(stream);
     GeoDev &gd = g->dev;
     const int nv = g->voff[1] - g->voff[0];
-    const size_t qb = (size_t)gd.N * gd.N * gd.Pp * 4, pb = (size_t)nv * gd.NB * gd.Pp * 4;
+    const size_t qb = ((size_t)gd.N * gd.N * gd.Pp * 4 + 255) / 256 * 256;
+    const size_t pb = ((size_t)nv * gd.NB * gd.Pp * 4 + 255) / 256 * 256;
+    const size_t ab = ((size_t)concurrent * sizeof(FwdArgs) + 255) / 256 * 256;
+    const size_t prb = ((size_t)(concurrent + 1) * sizeof(int) + 255) / 256 * 256;
     void *scr = nullptr;
-    PET_TRY(geometry_scratch(g, ((qb + 255) / 256) * 256 + pb, &scr));
-    char *img = reinterpret_cast<char *>(scr);
-    PET_CUDA(cudaMemsetAsync(img, 0, qb, st));
+    PET_TRY(geometry_scratch(g, qb + (size_t)concurrent * pb + ab + prb, &scr));
+    char *base = reinterpret_cast<char *>(scr);
+    char *img = base, *outs = base + qb;
+    FwdArgs *d_args = reinterpret_cast<FwdArgs *>(outs + (size_t)concurrent * pb);
+    int *d_pre = reinterpret_cast<int *>(reinterpret_cast<char *>(d_args) + ab);
+    PET_TRY(fill_internal_ones(gd, img, 0, st));
+    std::vector<FwdArgs> h_args(concurrent);
+    std::vector<int> h_pre(concurrent + 1);
     cudaEvent_t a, b;
     PET_CUDA(cudaEventCreate(&a));
     PET_CUDA(cudaEventCreate(&b));
     float best = 1e30f;
     int bestS = 0;
     const int save = gd.tuneS;
-    for (int S = 1; S <= 8; ++S) {
+    pet_status r = PET_OK;
+    for (int S = 1; S <= 8 && r == PET_OK; ++S) {
         if ((256 / gd.NG) % S) continue;
         gd.tuneS = S;
         FwdArgs fa{};
@@ -364,26 +374,56 @@ extern "C" pet_status pet_autotune(pet_geometry *g, void *stream, int *best_S)
         fa.slot0 = g->voff[0];
         fa.nviews = nv;
         fa.img = img;
-        fa.out = img + ((qb + 255) / 256) * 256;
-        pet_status r = launch_forward(fa, FWD_PLAIN, AR_KAHAN, st);         // warm-up
-        float tot = 0.f;
-        for (int rep = 0; rep < 3 && r == PET_OK; ++rep) {
+        forward_shape(fa, FWD_PLAIN, AR_KAHAN);
+        for (int c = 0; c < concurrent; ++c) {
+            h_args[c] = fa;
+            h_args[c].out = outs + (size_t)c * pb;
+            h_pre[c] = c * fa.nvb;
+        }
+        h_pre[concurrent] = concurrent * fa.nvb;
+        r = cuda_ok(cudaMemcpyAsync(d_args, h_args.data(), sizeof(FwdArgs) * concurrent,
+                                    cudaMemcpyHostToDevice, st), "pet_autotune: arguments");
+        if (r == PET_OK)
+            r = cuda_ok(cudaMemcpyAsync(d_pre, h_pre.data(), sizeof(int) * (concurrent + 1),
+                                        cudaMemcpyHostToDevice, st), "pet_autotune: arguments");
+        const Batch bt{d_args, d_pre, concurrent, sm_count() * 4};
+        auto once = [&]() {
+            return concurrent == 1 ? launch_forward(h_args[0], FWD_PLAIN, AR_KAHAN, st)
+                                   : launch_forward_batch(fa, bt, FWD_PLAIN, AR_KAHAN, st);
+        };
+        if (r == PET_OK) r = once();                         // warm-up
+        float tmin = 1e30f;
+        for (int rep = 0; rep < 5 && r == PET_OK; ++rep) {
             cudaEventRecord(a, st);
-            r = launch_forward(fa, FWD_PLAIN, AR_KAHAN, st);
+            r = once();
             cudaEventRecord(b, st);
-            cudaEventSynchronize(b);
+            if (r == PET_OK) r = cuda_ok(cudaEventSynchronize(b), "pet_autotune: timing");
             float ms = 0.f;
             cudaEventElapsedTime(&ms, a, b);
-            tot += ms;
+            tmin = std::min(tmin, ms);
         }
-        if (r != PET_OK) { gd.tuneS = save; cudaEventDestroy(a); cudaEventDestroy(b); return r; }
-        if (tot < best) { best = tot; bestS = S; }
+        if (r == PET_OK && tmin < best) { best = tmin; bestS = S; }
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
+    if (r != PET_OK) { gd.tuneS = save; return r; }
     gd.tuneS = bestS;
     if (best_S) *best_S = bestS;
     return PET_OK;
+}
+
+extern "C" pet_status pet_autotune(pet_geometry *g, void *stream, int *best_S)
+{
+    if (!g) return fail(PET_ERR_INVALID, "pet_autotune: NULL geometry");
+    return autotune_any(g, 1, as_stream(stream), best_S);
+}
+
+extern "C" pet_status pet_autotune_batch(pet_geometry *g, int concurrent, void *stream, int *best_S)
+{
+    if (!g) return fail(PET_ERR_INVALID, "pet_autotune_batch: NULL geometry");
+    if (concurrent < 1 || concurrent > 4096)
+        return fail(PET_ERR_INVALID, "pet_autotune_batch: need 1 <= concurrent <= 4096");
+    return autotune_any(g, concurrent, as_stream(stream), best_S);
 }
 
 extern "C" pet_status pet_set_ray_chunks(pet_geometry *g, int S)

@@ -4,11 +4,16 @@
 // queued requests in arrival order while slots and the device-memory budget allow: it reuses or
 // creates the geometry (cached by description; a scan whose sens differs reuses the tables with a
 // scale factor), uploads counts, gamma and f^0 on its own stream and creates the scan's resident
-// state.  A runner thread moves prepared states into a pet_batch and steps it continuously:
+// state.  A runner thread moves prepared states into batches and steps them continuously:
 // requests that arrive while others are on the GPU join at the next step, and each step advances
-// every running scan by one subiteration (graph-replayed batched kernels).  A scan that has done
-// T x M subiterations is read back (f^T and its objective history) and retired, freeing its
-// memory and slot; poll() returns its result and latency (submit to result available).
+// every running scan of a batch by one subiteration (graph-replayed batched kernels).  Scans are
+// kept in one batch per kernel class (plane-group size, arithmetic, gather width), each on its
+// own stream: the classes step independently and overlap on the device, so a short 2-D scan does
+// not advance in lock-step with a clinical-size stacked one.  The class of the larger scans runs
+// on the stream of higher priority, so a large scan advances at close to its own speed while the
+// small ones fill the SMs it leaves.  A scan that has done T x M subiterations is read back (f^T
+// and its objective history) and retired, freeing its memory and slot; poll() returns its result
+// and latency (submit to result available).
 #include <math.h>
 #include <string.h>
 
@@ -42,7 +47,7 @@ struct Request {
     std::vector<float> img0;                 // empty: f^0 = 1
     pet_params prm{};
     int with_objective = 0;
-    double t_submit = 0, t_admit = 0, t_done = 0;
+    double t_submit = 0, t_prep = 0, t_admit = 0, t_join = 0, t_final = 0, t_done = 0;
     pet_status status = PET_PENDING;
     std::string err;
     std::vector<float> img;                  // result f^T [P][N][N]
@@ -57,6 +62,15 @@ struct Request {
     float *d_img = nullptr;                  // device readback in the C-ABI layout
     cudaEvent_t ready = nullptr;
     bool retiring = false;
+    struct SrvClass *cls = nullptr;          // batch the scan runs in
+};
+
+// One batch per kernel class, stepped on its own stream.
+struct SrvClass {
+    int G = 0, arith = 0, KC = 0;
+    pet_batch *batch = nullptr;
+    cudaStream_t st = nullptr;
+    std::vector<Request *> running;
 };
 
 typedef std::tuple<int, int, double, int, int, double, int> GeoKey;   // desc without sens
@@ -93,7 +107,10 @@ struct pet_server {
     std::condition_variable cv;
     std::deque<Request *> queue;
     std::deque<Request *> ready;
-    std::vector<Request *> running;
+    std::vector<SrvClass *> classes;
+    int nrunning = 0;
+    int autotune = 0;                        // > 0: tune new geometries for that many concurrent scans
+    long long tuned = 0;
     std::map<uint64_t, Request *> all;
     std::map<GeoKey, std::pair<pet_geometry *, size_t>> geoms;
     size_t used = 0;
@@ -102,7 +119,6 @@ struct pet_server {
     uint64_t next_ticket = 1;
     std::thread prep_thread, run_thread;
     cudaStream_t prep_stream = nullptr, run_stream = nullptr;
-    pet_batch *batch = nullptr;
     // staging for uploads (preparer thread only)
     void *d_stage = nullptr;
     size_t stage_bytes = 0;
@@ -111,6 +127,7 @@ struct pet_server {
     std::vector<std::pair<void *, size_t>> pinned_free;
     // statistics
     std::vector<double> latencies;
+    double sum_queue = 0, sum_prep = 0, sum_run = 0, sum_readback = 0;
     long long submitted = 0, completed = 0, failed = 0;
     double t_first = -1, t_last = 0;
     std::string fatal;
@@ -139,11 +156,12 @@ static void *pinned_get(pet_server *sv, size_t bytes)
 // call with sv->mu held
 static void release_request(pet_server *sv, Request *r)
 {
-    if (r->state) { state_release(r->state, sv->run_stream); r->state = nullptr; }
+    cudaStream_t st = r->cls ? r->cls->st : sv->run_stream;
+    if (r->state) { state_release(r->state, st); r->state = nullptr; }
     if (r->ready) { cudaEventDestroy(r->ready); r->ready = nullptr; }
     if (r->h_img) sv->pinned_free.push_back(std::make_pair((void *)r->h_img, r->h_img_bytes));
     if (r->h_obj) sv->pinned_free.push_back(std::make_pair((void *)r->h_obj, r->h_obj_bytes));
-    if (r->d_img) cudaFreeAsync(r->d_img, sv->run_stream);
+    if (r->d_img) cudaFreeAsync(r->d_img, st);
     r->h_img = nullptr;
     r->h_obj = nullptr;
     r->d_img = nullptr;
@@ -167,8 +185,13 @@ static pet_status prepare(pet_server *sv, Request *r)
         pet_geometry_desc gdsc = d;
         pet_geometry *g = nullptr;
         PET_TRY(pet_geometry_create(&gdsc, st, &g));
+        if (sv->autotune > 0) {
+            pet_status ts = pet_autotune_batch(g, sv->autotune, st, nullptr);
+            if (ts != PET_OK) { pet_geometry_destroy(g); return ts; }
+        }
         std::lock_guard<std::mutex> lk(sv->mu);
         sv->geoms[key_of(d)] = std::make_pair(g, geometry_bytes(d));
+        if (sv->autotune > 0) ++sv->tuned;
         r->geom = g;
     }
     const size_t nsino = (size_t)d.nplanes * d.nviews * d.nbins, nimg = (size_t)d.nplanes * d.n * d.n;
@@ -219,7 +242,7 @@ static void prep_loop(pet_server *sv)
         sv->cv.wait(lk, [&] {
             if (sv->stop) return true;
             if (sv->queue.empty()) return false;
-            const int slots = (int)sv->running.size() + (int)sv->ready.size() + sv->preparing;
+            const int slots = sv->nrunning + (int)sv->ready.size() + sv->preparing;
             if (slots >= sv->max_slots) return false;
             Request *h = sv->queue.front();
             const size_t need = request_bytes(h->desc, h->prm) +
@@ -240,6 +263,7 @@ static void prep_loop(pet_server *sv)
         sv->used += need;
         r->bytes = request_bytes(r->desc, r->prm);      // geometry bytes stay with the cache
         ++sv->preparing;
+        r->t_prep = now_s();
         lk.unlock();
         pet_status st = prepare(sv, r);
         std::string msg = st == PET_OK ? "" : pet_last_error();
@@ -261,7 +285,8 @@ static void prep_loop(pet_server *sv)
 // ------------------------------------------------------------------------------------------
 static pet_status start_readback(pet_server *sv, Request *r)
 {
-    cudaStream_t st = sv->run_stream;
+    (void)sv;
+    cudaStream_t st = r->cls->st;
     const GeoDev &gd = r->geom->dev;
     const size_t nimg = (size_t)gd.P * gd.N * gd.N;
     PET_TRY(from_internal_image(gd, r->state->f[r->state->cur], r->d_img, r->state->arith == AR_FP64, 0, st));
@@ -270,7 +295,43 @@ static pet_status start_readback(pet_server *sv, Request *r)
                              (size_t)(r->prm.iterations + 1) * 3 * 8, cudaMemcpyDeviceToHost, st));
     PET_CUDA(cudaEventRecord(r->ready, st));
     r->retiring = true;
+    r->t_final = now_s();
     return PET_OK;
+}
+
+static int kc_class(const pet_state *s) { return s->g->dev.K <= 2 ? 2 : 4; }
+
+// The class batch of a state, created on first use (call with sv->mu held).
+static pet_status class_of(pet_server *sv, const pet_state *s, SrvClass **out)
+{
+    const int G = s->g->dev.G, KC = kc_class(s);
+    for (SrvClass *c : sv->classes)
+        if (c->G == G && c->arith == s->arith && c->KC == KC) { *out = c; return PET_OK; }
+    SrvClass *c = new SrvClass();
+    c->G = G;
+    c->arith = s->arith;
+    c->KC = KC;
+    int lo = 0, hi = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    // stacked (8-plane) scans: highest priority; 2-D scans: lowest
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->st, cudaStreamNonBlocking, G > 1 ? hi : lo);
+    if (e != cudaSuccess) { delete c; return cuda_fail(e, "pet_serve: class stream"); }
+    pet_status r = pet_batch_create(sv->max_slots, 1, &c->batch);
+    if (r != PET_OK) { cudaStreamDestroy(c->st); delete c; return r; }
+    sv->classes.push_back(c);
+    *out = c;
+    return PET_OK;
+}
+
+static void fail_class(pet_server *sv, SrvClass *c, pet_status st, const std::string &msg)
+{
+    for (Request *r : c->running) {
+        pet_batch_remove(c->batch, r->state);
+        release_request(sv, r);
+        finish(sv, r, st, msg);
+    }
+    sv->nrunning -= (int)c->running.size();
+    c->running.clear();
 }
 
 static void run_loop(pet_server *sv)
@@ -282,53 +343,66 @@ static void run_loop(pet_server *sv)
             while (!sv->ready.empty()) {
                 Request *r = sv->ready.front();
                 sv->ready.pop_front();
-                if (pet_batch_add(sv->batch, r->state, r->with_objective, sv->run_stream) != PET_OK) {
+                SrvClass *c = nullptr;
+                pet_status st = class_of(sv, r->state, &c);
+                if (st == PET_OK) {
+                    r->cls = c;
+                    st = pet_batch_add(c->batch, r->state, r->with_objective, c->st);
+                }
+                if (st != PET_OK) {
                     std::string msg = pet_last_error();
                     release_request(sv, r);
                     finish(sv, r, PET_ERR_CUDA, msg);
                     continue;
                 }
-                sv->running.push_back(r);
+                r->t_join = now_s();
+                c->running.push_back(r);
+                ++sv->nrunning;
             }
-            if (sv->running.empty()) {
+            if (sv->nrunning == 0) {
                 if (sv->stop) return;
                 sv->cv.wait_for(lk, std::chrono::milliseconds(2));
                 continue;
             }
         }
-        int nrun = 0;
-        pet_status st = pet_batch_step(sv->batch, sv->run_stream, &nrun);
+        // step every class whose previous ticks leave a descriptor buffer free
+        bool stepped = false;
+        for (SrvClass *c : sv->classes) {
+            if (c->running.empty() || !batch_can_step(c->batch)) continue;
+            int nrun = 0;
+            pet_status st = pet_batch_step(c->batch, c->st, &nrun);
+            stepped = true;
+            if (st != PET_OK) {
+                std::lock_guard<std::mutex> lk(sv->mu);
+                sv->fatal = pet_last_error();
+                fail_class(sv, c, st, sv->fatal);
+                sv->cv.notify_all();
+            }
+        }
         std::vector<Request *> done;
         {
             std::lock_guard<std::mutex> lk(sv->mu);
-            if (st != PET_OK) {
-                sv->fatal = pet_last_error();
-                for (Request *r : sv->running) {
-                    pet_batch_remove(sv->batch, r->state);
-                    release_request(sv, r);
-                    finish(sv, r, st, sv->fatal);
-                }
-                sv->running.clear();
-                sv->cv.notify_all();
-                continue;
-            }
-            for (Request *r : sv->running) {
-                const pet_state *s = r->state;
-                if (!r->retiring && s->J >= s->prm.iterations * s->g->dev.M) {
-                    if (start_readback(sv, r) != PET_OK) {
-                        r->retiring = true;
-                        r->status = PET_ERR_CUDA;       // reported as failed when retired
-                        r->err = pet_last_error();
-                        cudaEventRecord(r->ready, sv->run_stream);
+            for (SrvClass *c : sv->classes)
+                for (Request *r : c->running) {
+                    const pet_state *s = r->state;
+                    if (!r->retiring && s->J >= s->prm.iterations * s->g->dev.M) {
+                        if (start_readback(sv, r) != PET_OK) {
+                            r->retiring = true;
+                            r->status = PET_ERR_CUDA;       // reported as failed when retired
+                            r->err = pet_last_error();
+                            r->t_final = now_s();
+                            cudaEventRecord(r->ready, c->st);
+                        }
                     }
+                    if (r->retiring && cudaEventQuery(r->ready) != cudaErrorNotReady) done.push_back(r);
                 }
-                if (r->retiring && cudaEventQuery(r->ready) != cudaErrorNotReady) done.push_back(r);
-            }
         }
         for (Request *r : done) {
-            pet_batch_remove(sv->batch, r->state);
+            pet_batch_remove(r->cls->batch, r->state);
             std::lock_guard<std::mutex> lk(sv->mu);
-            sv->running.erase(std::find(sv->running.begin(), sv->running.end(), r));
+            std::vector<Request *> &run = r->cls->running;
+            run.erase(std::find(run.begin(), run.end(), r));
+            --sv->nrunning;
             if (r->status == PET_PENDING) {
                 const GeoDev &gd = r->geom->dev;
                 const size_t nimg = (size_t)gd.P * gd.N * gd.N;
@@ -342,6 +416,10 @@ static void run_loop(pet_server *sv)
                 finish(sv, r, PET_OK, "");
                 ++sv->completed;
                 sv->latencies.push_back(r->t_done - r->t_submit);
+                sv->sum_queue += r->t_prep - r->t_submit;
+                sv->sum_prep += r->t_admit - r->t_prep;
+                sv->sum_run += r->t_final - r->t_admit;
+                sv->sum_readback += r->t_done - r->t_final;
                 sv->t_last = r->t_done;
             }
             else {
@@ -350,6 +428,8 @@ static void run_loop(pet_server *sv)
             release_request(sv, r);
             sv->cv.notify_all();
         }
+        // nothing to enqueue: every class waits for its in-flight ticks
+        if (!stepped && done.empty()) std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
 }
 
@@ -370,16 +450,18 @@ extern "C" pet_status pet_serve_create(size_t hbm_budget_bytes, int max_slots, i
         delete sv;
         return cuda_fail(e, "pet_serve_create: streams");
     }
-    pet_status st = pet_batch_create(max_slots, 1, &sv->batch);
-    if (st != PET_OK) {
-        cudaStreamDestroy(sv->prep_stream);
-        cudaStreamDestroy(sv->run_stream);
-        delete sv;
-        return st;
-    }
     sv->prep_thread = std::thread(prep_loop, sv);
     sv->run_thread = std::thread(run_loop, sv);
     *out = sv;
+    return PET_OK;
+}
+
+extern "C" pet_status pet_serve_autotune(pet_server *sv, int concurrent)
+{
+    if (!sv || concurrent < 0 || concurrent > 4096)
+        return fail(PET_ERR_INVALID, "pet_serve_autotune: need a server and 0 <= concurrent <= 4096");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->autotune = concurrent;
     return PET_OK;
 }
 
@@ -446,7 +528,7 @@ extern "C" pet_status pet_serve_stats_get(pet_server *sv, pet_serve_stats *out)
     out->submitted = sv->submitted;
     out->completed = sv->completed;
     out->failed = sv->failed;
-    out->running = (long long)sv->running.size();
+    out->running = sv->nrunning;
     out->queued = (long long)(sv->queue.size() + sv->ready.size() + sv->preparing);
     out->hbm_in_use = sv->used;
     std::vector<double> l = sv->latencies;
@@ -464,7 +546,12 @@ extern "C" pet_status pet_serve_stats_get(pet_server *sv, pet_serve_stats *out)
         out->mean_s = m / l.size();
         const double span = sv->t_last - sv->t_first;
         out->scans_per_s = span > 0 ? sv->completed / span : 0.0;
+        out->mean_queue_s = sv->sum_queue / l.size();
+        out->mean_prepare_s = sv->sum_prep / l.size();
+        out->mean_run_s = sv->sum_run / l.size();
+        out->mean_readback_s = sv->sum_readback / l.size();
     }
+    out->tuned_geometries = sv->tuned;
     return PET_OK;
 }
 
@@ -489,12 +576,22 @@ extern "C" void pet_serve_destroy(pet_server *sv)
     if (sv->run_thread.joinable()) sv->run_thread.join();
     cudaSetDevice(sv->device);
     cudaStreamSynchronize(sv->run_stream);
-    pet_batch_destroy(sv->batch);
+    for (SrvClass *c : sv->classes) {
+        cudaStreamSynchronize(c->st);
+        pet_batch_destroy(c->batch);
+        c->batch = nullptr;
+    }
     for (auto &kv : sv->all) {
         release_request(sv, kv.second);
         delete kv.second;
     }
     cudaStreamSynchronize(sv->run_stream);
+    for (SrvClass *c : sv->classes) {
+        cudaStreamSynchronize(c->st);
+        cudaStreamDestroy(c->st);
+        delete c;
+    }
+    sv->classes.clear();
     for (auto &kv : sv->pinned_free) cudaFreeHost(kv.first);
     for (auto &kv : sv->geoms) pet_geometry_destroy(kv.second.first);
     cudaFree(sv->d_stage);

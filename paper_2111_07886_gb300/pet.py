@@ -49,7 +49,10 @@ class Request(ctypes.Structure):
 class ServeStats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_longlong) for k in ("submitted", "completed", "failed", "running", "queued")] + [
         (k, ctypes.c_double) for k in ("p50_s", "p99_s", "mean_s", "scans_per_s")] + [
-        ("hbm_in_use", ctypes.c_size_t)]
+        ("hbm_in_use", ctypes.c_size_t)] + [
+        (k, ctypes.c_double) for k in ("mean_queue_s", "mean_prepare_s", "mean_run_s",
+                                       "mean_readback_s")] + [
+        ("tuned_geometries", ctypes.c_longlong)]
 
 
 _VP = ctypes.c_void_p
@@ -64,6 +67,7 @@ SIGNATURES = {
     "pet_geometry_destroy": (None, [_VP]),
     "pet_subset_size": (_I, [_VP, _I]),
     "pet_autotune": (_I, [_VP, _VP, ctypes.POINTER(_I)]),
+    "pet_autotune_batch": (_I, [_VP, _I, _VP, ctypes.POINTER(_I)]),
     "pet_set_ray_chunks": (_I, [_VP, _I]),
     "pet_sensitivity": (_I, [_VP, _VP, _VP]),
     "pet_forward_subset": (_I, [_VP, _I, _VP, _VP, _VP]),
@@ -96,6 +100,7 @@ SIGNATURES = {
     "pet_serve_poll": (_I, [_VP, ctypes.c_uint64, _VP, _DP, _DP]),
     "pet_serve_stats_get": (_I, [_VP, ctypes.POINTER(ServeStats)]),
     "pet_serve_destroy": (None, [_VP]),
+    "pet_serve_autotune": (_I, [_VP, _I]),
     "pet_launch_count": (ctypes.c_longlong, []),
     "pet_profile_enable": (None, [_I]),
     "pet_profile_read": (_I, [_I, _DP, ctypes.POINTER(ctypes.c_longlong)]),
@@ -187,6 +192,12 @@ class Geometry:
         """Pick the forward projector's ray chunking by timing it; returns the chosen value."""
         s = ctypes.c_int()
         _check(lib().pet_autotune(self.handle, _stream(stream), ctypes.byref(s)))
+        return s.value
+
+    def autotune_batch(self, concurrent: int, stream=None) -> int:
+        """Pick the ray chunking with `concurrent` projections sharing the GPU (batched scans)."""
+        s = ctypes.c_int()
+        _check(lib().pet_autotune_batch(self.handle, int(concurrent), _stream(stream), ctypes.byref(s)))
         return s.value
 
     def set_ray_chunks(self, S: int):
@@ -399,6 +410,10 @@ class Server:
         self.shapes.pop(ticket, None)
         _check(st)
         return img, list(obj), lat.value
+
+    def autotune(self, concurrent: int):
+        """Tune every new geometry for `concurrent` scans sharing the GPU (0: built-in shapes)."""
+        _check(lib().pet_serve_autotune(self.handle, int(concurrent)))
 
     def stats(self) -> dict:
         s = ServeStats()

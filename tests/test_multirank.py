@@ -54,3 +54,23 @@ def test_reference_arm_prints_only_on_rank0(monkeypatch, capsys):
     monkeypatch.setattr("sys.argv", ["bench.py", "--impl", "reference"])
     bench.main()
     assert capsys.readouterr().out == ""
+
+
+def test_gpus_flag_without_launcher_starts_that_many_ranks():
+    """`bench.py --gpus 2` run directly starts two ranks (torch.distributed.run on 127.0.0.1);
+    the reference arm, which needs no GPU, then prints one line, from rank 0, for the 2-rank
+    job."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = {k: v for k, v in os.environ.items() if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK")}
+    env["OMP_NUM_THREADS"] = "2"
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference",
+                        "--gpus", "2", "--workload", "2d", "--steps", "1", "--warmup", "0"],
+                       capture_output=True, text=True, timeout=600, env=env, cwd=root)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1, r.stdout
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2
