@@ -2,7 +2,7 @@
 //
 // Every tick advances each running scan of the batch by one subiteration.  The scans are grouped
 // into classes that share one kernel instantiation (plane-group size G, arithmetic, candidate
-// bins per view); for each class the per-scan argument structs of the tick are packed, with
+// bins per view, and for 8-plane scans the staged update's groups per tile); for each class the per-scan argument structs of the tick are packed, with
 // per-kernel virtual-block prefix tables, into one pinned buffer and copied to the device, and
 // five persistent kernels (mu pass, forward + ratio, fused update, objective projection, RDP
 // value) stride over the virtual blocks of all scans of the class.  A scan that skips a kernel
@@ -11,6 +11,12 @@
 // replayed.  The descriptor buffers are double-buffered: the host fills one while the previous
 // tick's graph may still read the other.  Each scan keeps its own launch shapes and reduction
 // scratch, so its results are bitwise the same alone or in any mix.
+//
+// Descriptor buffers rotate over kBufs per class (the host may run that many ticks ahead of the
+// GPU).  Before each replay the tick's kernel nodes are fitted to its work: a kernel that no scan
+// needs this tick (the mu pass outside the dynamic-nu range, the objective between iteration ends)
+// is disabled, and every other kernel's grid is cut to its virtual-block count when that is below
+// the persistent grid, so a tick of a few small scans costs what their work costs.
 #include <string.h>
 
 #include <vector>
@@ -23,19 +29,29 @@ namespace pet {
 int sm_count();
 void count_launches(long long n);
 
+constexpr int kBufs = 4;                      // descriptor buffers (ticks in flight) per class
+constexpr int kKinds = 5;                     // mu pass, forward + ratio, update, objective x2
+
 struct BatchClass {
     int G = 0, arith = 0, KC = 0;
+    int GC = 0;                               // plane groups per staged-update tile (8-plane scans)
     int cap = 0;                              // scan slots of this class
     std::vector<pet_state *> slot;            // nullptr = empty
     std::vector<bool> objective;              // per slot: plan objectives
-    // descriptor buffers (pinned host + device), double-buffered
+    // descriptor buffers (pinned host + device), rotating
     size_t bytes = 0;
-    char *host[2] = {nullptr, nullptr};
-    char *dev[2] = {nullptr, nullptr};
-    cudaEvent_t done[2] = {nullptr, nullptr};
-    bool used[2] = {false, false};
-    cudaGraphExec_t exec[2] = {nullptr, nullptr};
-    cudaStream_t exec_stream[2] = {nullptr, nullptr};
+    char *host[kBufs] = {};
+    char *dev[kBufs] = {};
+    cudaEvent_t done[kBufs] = {};
+    bool used[kBufs] = {};
+    cudaGraph_t graph[kBufs] = {};
+    cudaGraphExec_t exec[kBufs] = {};
+    cudaStream_t exec_stream[kBufs] = {};
+    // the captured graph's kernel node of each kind, its captured parameters, and its state in
+    // the instantiated graph (enabled, grid)
+    cudaGraphNode_t knode[kBufs][kKinds] = {};
+    cudaKernelNodeParams kparams[kBufs][kKinds] = {};
+    int kgrid[kBufs][kKinds] = {};
     int next = 0;                             // descriptor buffer of the next tick
 
     // layout of one descriptor buffer
@@ -71,8 +87,9 @@ using namespace pet;
 
 static void class_free(BatchClass *c)
 {
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < kBufs; ++b) {
         if (c->exec[b]) cudaGraphExecDestroy(c->exec[b]);
+        if (c->graph[b]) cudaGraphDestroy(c->graph[b]);
         if (c->done[b]) cudaEventDestroy(c->done[b]);
         cudaFreeHost(c->host[b]);
         cudaFree(c->dev[b]);
@@ -103,7 +120,7 @@ extern "C" void pet_batch_destroy(pet_batch *b)
 {
     if (!b) return;
     for (BatchClass *c : b->classes) {
-        for (int k = 0; k < 2; ++k)
+        for (int k = 0; k < kBufs; ++k)
             if (c->done[k] && c->used[k]) cudaEventSynchronize(c->done[k]);
         class_free(c);
     }
@@ -119,17 +136,19 @@ extern "C" void pet_batch_destroy(pet_batch *b)
 static pet_status class_for(pet_batch *b, pet_state *s, BatchClass **out)
 {
     const int G = s->g->dev.G, arith = s->arith, KC = kc_of(s);
+    const int GC = G == 8 ? std::min(s->g->dev.NG, 4) : 0;
     for (BatchClass *c : b->classes)
-        if (c->G == G && c->arith == arith && c->KC == KC) { *out = c; return PET_OK; }
+        if (c->G == G && c->arith == arith && c->KC == KC && c->GC == GC) { *out = c; return PET_OK; }
     BatchClass *c = new BatchClass();
     c->G = G;
     c->arith = arith;
     c->KC = KC;
+    c->GC = GC;
     c->cap = b->capacity;
     c->slot.assign(c->cap, nullptr);
     c->objective.assign(c->cap, false);
     c->layout();
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < kBufs; ++k) {
         cudaError_t e = cudaMallocHost((void **)&c->host[k], c->bytes);
         if (e == cudaSuccess) e = cudaMalloc((void **)&c->dev[k], c->bytes);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->done[k], cudaEventDisableTiming);
@@ -177,7 +196,7 @@ extern "C" pet_status pet_batch_remove(pet_batch *b, pet_state *s)
         for (int k = 0; k < c->cap; ++k)
             if (c->slot[k] == s) {
                 // the slot's descriptors may still be read by an in-flight tick: wait for it
-                for (int q = 0; q < 2; ++q)
+                for (int q = 0; q < kBufs; ++q)
                     if (c->used[q]) cudaEventSynchronize(c->done[q]);
                 c->slot[k] = nullptr;
                 return PET_OK;
@@ -214,8 +233,12 @@ extern "C" int pet_batch_size(const pet_batch *b)
     return n;
 }
 
-// The five batched launches of one class tick, reading descriptor buffer `dev`.
-static pet_status class_launches(pet_batch *b, BatchClass *c, const char *dev, cudaStream_t st)
+// The five batched launches of one class tick, reading descriptor buffer `dev`.  n: virtual
+// blocks per kind, or nullptr (graph capture: every kernel at the full persistent grid; the
+// replay fits them to each tick).  Without a graph a kernel with no work is skipped and the
+// others get grids of min(virtual blocks, persistent grid).
+static pet_status class_launches(pet_batch *b, BatchClass *c, const char *dev, const int *n,
+                                 cudaStream_t st, int *launched)
 {
     const int cap = c->cap;
     const int *pre = reinterpret_cast<const int *>(dev + c->off_pre);
@@ -226,24 +249,84 @@ static pet_status class_launches(pet_batch *b, BatchClass *c, const char *dev, c
     UpdateArgs us{};
     us.g.G = c->G;
     us.g.K = c->KC;
+    us.g.NG = std::max(1, c->GC);             // selects the staged update's tile (min(NG, 4))
     ImageArgs is{};
     is.g.G = c->G;
     is.g.K = c->KC;
-    Batch bm{dev + c->off_mu, pre + 0 * (cap + 1), cap, b->grid};
-    Batch bf{dev + c->off_fwd, pre + 1 * (cap + 1), cap, b->grid};
-    Batch bu{dev + c->off_upd, pre + 2 * (cap + 1), cap, b->grid};
-    Batch bo{dev + c->off_objf, pre + 3 * (cap + 1), cap, b->grid};
-    Batch br{dev + c->off_objr, pre + 4 * (cap + 1), cap, b->grid};
+    auto grid = [&](int t) { return n ? std::min(n[t], b->grid) : b->grid; };
+    auto on = [&](int t) { return !n || n[t] > 0; };
+    Batch bm{dev + c->off_mu, pre + 0 * (cap + 1), cap, grid(0)};
+    Batch bf{dev + c->off_fwd, pre + 1 * (cap + 1), cap, grid(1)};
+    Batch bu{dev + c->off_upd, pre + 2 * (cap + 1), cap, grid(2)};
+    Batch bo{dev + c->off_objf, pre + 3 * (cap + 1), cap, grid(3)};
+    Batch br{dev + c->off_objr, pre + 4 * (cap + 1), cap, grid(4)};
+    int cnt = 0;
     // mu passes on the side stream, joined before the update (a parallel branch in the graph)
-    PET_CUDA(cudaEventRecord(b->ev_fork, st));
-    PET_CUDA(cudaStreamWaitEvent(b->side, b->ev_fork, 0));
-    PET_TRY(launch_mu_sum_batch(is, bm, c->arith, b->side));
-    PET_CUDA(cudaEventRecord(b->ev_join, b->side));
-    PET_TRY(launch_forward_batch(fs, bf, FWD_RATIO, c->arith, st));
-    PET_CUDA(cudaStreamWaitEvent(st, b->ev_join, 0));
-    PET_TRY(launch_update_batch(us, bu, c->arith, st));
-    PET_TRY(launch_forward_batch(fs, bo, FWD_OBJECTIVE, c->arith, st));
-    PET_TRY(launch_rdp_value_batch(is, br, c->arith, st));
+    if (on(0)) {
+        PET_CUDA(cudaEventRecord(b->ev_fork, st));
+        PET_CUDA(cudaStreamWaitEvent(b->side, b->ev_fork, 0));
+        PET_TRY(launch_mu_sum_batch(is, bm, c->arith, b->side));
+        PET_CUDA(cudaEventRecord(b->ev_join, b->side));
+        ++cnt;
+    }
+    if (on(1)) { PET_TRY(launch_forward_batch(fs, bf, FWD_RATIO, c->arith, st)); ++cnt; }
+    if (on(0)) PET_CUDA(cudaStreamWaitEvent(st, b->ev_join, 0));
+    if (on(2)) { PET_TRY(launch_update_batch(us, bu, c->arith, st)); ++cnt; }
+    if (on(3)) { PET_TRY(launch_forward_batch(fs, bo, FWD_OBJECTIVE, c->arith, st)); ++cnt; }
+    if (on(4)) { PET_TRY(launch_rdp_value_batch(is, br, c->arith, st)); ++cnt; }
+    if (launched) *launched = cnt;
+    return PET_OK;
+}
+
+// Finds the captured graph's kernel node of each kind (by the descriptor array its Batch
+// argument points to) and keeps its parameters for the per-tick updates.
+static pet_status index_kernel_nodes(BatchClass *c, int buf)
+{
+    size_t nn = 0;
+    PET_CUDA(cudaGraphGetNodes(c->graph[buf], nullptr, &nn));
+    std::vector<cudaGraphNode_t> nodes(nn);
+    PET_CUDA(cudaGraphGetNodes(c->graph[buf], nodes.data(), &nn));
+    const size_t off[kKinds] = {c->off_mu, c->off_fwd, c->off_upd, c->off_objf, c->off_objr};
+    int found = 0;
+    for (cudaGraphNode_t nd : nodes) {
+        cudaGraphNodeType ty;
+        PET_CUDA(cudaGraphNodeGetType(nd, &ty));
+        if (ty != cudaGraphNodeTypeKernel) continue;
+        cudaKernelNodeParams kp;
+        PET_CUDA(cudaGraphKernelNodeGetParams(nd, &kp));
+        const Batch *bt = reinterpret_cast<const Batch *>(kp.kernelParams[1]);
+        for (int t = 0; t < kKinds; ++t)
+            if (bt->args == c->dev[buf] + off[t]) {
+                c->knode[buf][t] = nd;
+                c->kparams[buf][t] = kp;
+                c->kgrid[buf][t] = (int)kp.gridDim.x;
+                ++found;
+            }
+    }
+    if (found != kKinds) return fail(PET_ERR_CUDA, "pet_batch: captured graph lacks a kernel node");
+    return PET_OK;
+}
+
+// Fits the instantiated graph of buffer `buf` to this tick: kernels without work disabled,
+// the others' grids cut to their virtual blocks.  Returns the kernels that will run.
+static pet_status fit_graph(pet_batch *b, BatchClass *c, int buf, const int *n, int *launched)
+{
+    int cnt = 0;
+    for (int t = 0; t < kKinds; ++t) {
+        const int want = n[t] > 0 ? std::min(n[t], b->grid) : 0;
+        if (want == c->kgrid[buf][t]) { cnt += want > 0; continue; }
+        if (want == 0) {
+            PET_CUDA(cudaGraphNodeSetEnabled(c->exec[buf], c->knode[buf][t], 0));
+        } else {
+            if (c->kgrid[buf][t] == 0) PET_CUDA(cudaGraphNodeSetEnabled(c->exec[buf], c->knode[buf][t], 1));
+            cudaKernelNodeParams kp = c->kparams[buf][t];
+            kp.gridDim.x = (unsigned)want;
+            PET_CUDA(cudaGraphExecKernelNodeSetParams(c->exec[buf], c->knode[buf][t], &kp));
+            ++cnt;
+        }
+        c->kgrid[buf][t] = want;
+    }
+    *launched = cnt;
     return PET_OK;
 }
 
@@ -251,7 +334,7 @@ static pet_status class_tick(pet_batch *b, BatchClass *c, cudaStream_t st, int *
 {
     const int cap = c->cap;
     const int buf = c->next;
-    c->next ^= 1;
+    c->next = (c->next + 1) % kBufs;
     if (c->used[buf]) PET_CUDA(cudaEventSynchronize(c->done[buf]));   // host may now overwrite it
     char *h = c->host[buf];
     FwdArgs *fwd = reinterpret_cast<FwdArgs *>(h + c->off_fwd);
@@ -260,9 +343,9 @@ static pet_status class_tick(pet_batch *b, BatchClass *c, cudaStream_t st, int *
     FwdArgs *objf = reinterpret_cast<FwdArgs *>(h + c->off_objf);
     ImageArgs *objr = reinterpret_cast<ImageArgs *>(h + c->off_objr);
     int *pre = reinterpret_cast<int *>(h + c->off_pre);
-    int n[5] = {0, 0, 0, 0, 0};
+    int n[kKinds] = {0, 0, 0, 0, 0};
     for (int k = 0; k <= cap; ++k) {
-        for (int t = 0; t < 5; ++t) pre[t * (cap + 1) + k] = n[t];
+        for (int t = 0; t < kKinds; ++t) pre[t * (cap + 1) + k] = n[t];
         if (k == cap) break;
         pet_state *s = c->slot[k];
         if (!running(s)) continue;
@@ -283,29 +366,34 @@ static pet_status class_tick(pet_batch *b, BatchClass *c, cudaStream_t st, int *
         if (running(s)) ++*running_after;
     }
     // prefix tables must close at the totals; the loop above wrote pre[t][cap] = n[t]
+    int launched = 0;
     if (b->use_graph && st != nullptr) {       // the legacy default stream cannot be captured
         if (!c->exec[buf] || c->exec_stream[buf] != st) {
             if (c->exec[buf]) cudaGraphExecDestroy(c->exec[buf]);
+            if (c->graph[buf]) cudaGraphDestroy(c->graph[buf]);
             c->exec[buf] = nullptr;
+            c->graph[buf] = nullptr;
             cudaGraph_t graph = nullptr;
             PET_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
             cudaError_t e = cudaMemcpyAsync(c->dev[buf], c->host[buf], c->bytes,
                                             cudaMemcpyHostToDevice, st);
-            pet_status ls = e == cudaSuccess ? class_launches(b, c, c->dev[buf], st)
+            pet_status ls = e == cudaSuccess ? class_launches(b, c, c->dev[buf], nullptr, st, nullptr)
                                              : cuda_fail(e, "pet_batch: descriptor copy");
             cudaError_t ec = cudaStreamEndCapture(st, &graph);
             if (ls != PET_OK) { if (graph) cudaGraphDestroy(graph); return ls; }
             if (ec != cudaSuccess) return cuda_fail(ec, "pet_batch: end capture");
+            c->graph[buf] = graph;                 // kept: its nodes address the kernel updates
+            PET_TRY(index_kernel_nodes(c, buf));
             e = cudaGraphInstantiate(&c->exec[buf], graph, 0);
-            cudaGraphDestroy(graph);
             if (e != cudaSuccess) return cuda_fail(e, "pet_batch: graph instantiate");
             c->exec_stream[buf] = st;
         }
+        PET_TRY(fit_graph(b, c, buf, n, &launched));
         PET_CUDA(cudaGraphLaunch(c->exec[buf], st));
-        count_launches(5);
+        count_launches(launched);
     } else {
         PET_CUDA(cudaMemcpyAsync(c->dev[buf], c->host[buf], c->bytes, cudaMemcpyHostToDevice, st));
-        PET_TRY(class_launches(b, c, c->dev[buf], st));
+        PET_TRY(class_launches(b, c, c->dev[buf], n, st, &launched));
     }
     PET_CUDA(cudaEventRecord(c->done[buf], st));
     c->used[buf] = true;

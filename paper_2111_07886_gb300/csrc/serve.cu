@@ -428,8 +428,9 @@ static void run_loop(pet_server *sv)
             release_request(sv, r);
             sv->cv.notify_all();
         }
-        // nothing to enqueue: every class waits for its in-flight ticks
-        if (!stepped && done.empty()) std::this_thread::sleep_for(std::chrono::microseconds(20));
+        // nothing to enqueue: every class has its ticks in flight.  Poll again at once (a sleep
+        // would oversleep by the timer slack and let the GPU run dry at light load).
+        if (!stepped && done.empty()) std::this_thread::yield();
     }
 }
 

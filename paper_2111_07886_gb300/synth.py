@@ -28,7 +28,8 @@ import numpy as np
 __all__ = [
     "Workload", "AlgoParams", "config_2d_128", "config_stacked_256x89",
     "mixed_2d_scans", "make_scan", "ellipse_phantom_2d", "ellipsoid_phantom_3d",
-    "rasterize", "random_image",
+    "rasterize", "random_image", "uniform_phantom_2d", "uniform_phantom_rois",
+    "brain_standin_2d",
 ]
 
 # Preconditioner kinds (Sec. III: BSREM, momentum-only M1/M2, SDP P1/P2).
@@ -213,6 +214,53 @@ def ellipsoid_phantom_3d(n: int, nplanes: int, pixel_mm: float, plane_mm: float,
                 sh.append((cx, cy, rr, rr, 0.0, 3.0))
         planes.append(sh)
     return planes
+
+
+def uniform_phantom_2d(n: int = 256, pixel_mm: float = 1.17):
+    """The uniform phantom of Sec. IV-A: a uniform disk background (value 1) holding 4 hot
+    spheres (value 10, contrast 1:10) and 2 cold spheres (value 0) of radii 4, 6, 8 (cold),
+    10 (cold), 12 and 14 pixels.  The paper gives no positions: the six sphere centres sit on a
+    circle of radius 0.25 n pixels, 60 degrees apart, and the background disk has radius
+    0.43 n pixels, leaving the centre free for the background ROI."""
+    rb = 0.43 * n * pixel_mm
+    shapes = [(0.0, 0.0, rb, rb, 0.0, 1.0)]
+    for (cx, cy, r, val) in _uniform_spheres(n, pixel_mm):
+        shapes.append((cx, cy, r, r, 0.0, val - 1.0))
+    return [shapes]
+
+
+def _uniform_spheres(n: int, pixel_mm: float):
+    radii = [(4, 10.0), (6, 10.0), (8, 0.0), (10, 0.0), (12, 10.0), (14, 10.0)]
+    out = []
+    for k, (r_px, val) in enumerate(radii):
+        ang = k * math.pi / 3.0
+        c = 0.25 * n * pixel_mm
+        out.append((c * math.cos(ang), c * math.sin(ang), r_px * pixel_mm, val))
+    return out
+
+
+def uniform_phantom_rois(n: int = 256, pixel_mm: float = 1.17):
+    """The 8 ROIs of the uniform phantom (Fig. 6 of Sec. IV-B): the 4 hot and 2 cold spheres,
+    one background disk of radius 25 pixels at the centre, and all 7 together.  Returns
+    {name: boolean mask [N][N]} over pixel centres."""
+    g = (np.arange(n) + 0.5 - n / 2.0) * pixel_mm
+    X, Y = np.meshgrid(g, g)
+    rois = {}
+    for (cx, cy, r, val) in _uniform_spheres(n, pixel_mm):
+        name = f"{'hot' if val > 1 else 'cold'}_r{int(round(r / pixel_mm))}"
+        rois[name] = (X - cx) ** 2 + (Y - cy) ** 2 <= r * r
+    rois["background_r25"] = X ** 2 + Y ** 2 <= (25 * pixel_mm) ** 2
+    allm = np.zeros((n, n), bool)
+    for m in rois.values():
+        allm |= m
+    rois["all"] = allm
+    return rois
+
+
+def brain_standin_2d(n: int = 256, pixel_mm: float = 1.17, seed: int = 0):
+    """Stand-in for the paper's brain phantom (a clinical image, not available): the random
+    ellipse phantom (disk background 1, ten ellipses of intensity U[0.5, 4])."""
+    return ellipse_phantom_2d(n, pixel_mm, seed)
 
 
 def analytic_sinogram(planes, nviews: int, nbins: int, bin_mm: float) -> np.ndarray:

@@ -241,6 +241,25 @@ def test_subiteration_parity_each_preconditioner(kind):
         assert rel_l2(got64, ref) <= 1e-10, (kind, nsub, rel_l2(got64, ref))
 
 
+@pytest.mark.parametrize("P", [5, 11, 20, 33])
+def test_update_tiles_and_plane_chunks(P):
+    """The 8-plane update kernel at every tile shape it has (1, 2, 3 and 4 plane groups per
+    tile; a ragged last plane chunk for 33 planes) on an image side (37) that no tile divides:
+    subiterations through J0, the dynamic-nu range, the freeze at J1 and beyond, against the
+    oracle."""
+    w = synth.Workload("t", 37, P, 8.0, 30, 53, 8.0, 5, 2e5 * P, "ellipsoid3d",
+                       synth.AlgoParams(iterations=2, J0=2, J1=6, a=0.2), plane_mm=8.0, seed=P)
+    scan = synth.make_scan(w)
+    og = oracle.geom_from(w.geometry(), scan["sens"])
+    for nsub in (3, 9):
+        ref, _ = oracle.reconstruct(og, scan["counts"], scan["gamma"], w.params,
+                                    np.ones((P, 37, 37)), nsub=nsub)
+        got = _run_subiters(w, scan, nsub, synth.PREC_FP32_KAHAN)
+        assert rel_l2(got, ref) <= 1e-5, (P, nsub, rel_l2(got, ref))
+        got32 = _run_subiters(w, scan, nsub, synth.PREC_FP32)
+        assert rel_l2(got32, ref) <= 1e-5, (P, nsub, rel_l2(got32, ref))
+
+
 def test_upper_branch_and_clamp():
     """Small U: the (U - f)/p branch and the U - t clamp are active on both sides."""
     w = synth.Workload("t", 32, 1, 8.0, 24, 45, 8.0, 3, 3e5, "ellipses2d",
