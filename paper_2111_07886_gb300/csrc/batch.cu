@@ -2,7 +2,7 @@
 //
 // Every tick advances each running scan of the batch by one subiteration.  The scans are grouped
 // into classes that share one kernel instantiation (plane-group size G, arithmetic, candidate
-// bins per view, and for 8-plane scans the staged update's groups per tile); for each class the per-scan argument structs of the tick are packed, with
+// bins per view); for each class the per-scan argument structs of the tick are packed, with
 // per-kernel virtual-block prefix tables, into one pinned buffer and copied to the device, and
 // five persistent kernels (mu pass, forward + ratio, fused update, objective projection, RDP
 // value) stride over the virtual blocks of all scans of the class.  A scan that skips a kernel
@@ -34,7 +34,6 @@ constexpr int kKinds = 5;                     // mu pass, forward + ratio, updat
 
 struct BatchClass {
     int G = 0, arith = 0, KC = 0;
-    int GC = 0;                               // plane groups per staged-update tile (8-plane scans)
     int cap = 0;                              // scan slots of this class
     std::vector<pet_state *> slot;            // nullptr = empty
     std::vector<bool> objective;              // per slot: plan objectives
@@ -136,14 +135,12 @@ extern "C" void pet_batch_destroy(pet_batch *b)
 static pet_status class_for(pet_batch *b, pet_state *s, BatchClass **out)
 {
     const int G = s->g->dev.G, arith = s->arith, KC = kc_of(s);
-    const int GC = G == 8 ? std::min(s->g->dev.NG, 4) : 0;
     for (BatchClass *c : b->classes)
-        if (c->G == G && c->arith == arith && c->KC == KC && c->GC == GC) { *out = c; return PET_OK; }
+        if (c->G == G && c->arith == arith && c->KC == KC) { *out = c; return PET_OK; }
     BatchClass *c = new BatchClass();
     c->G = G;
     c->arith = arith;
     c->KC = KC;
-    c->GC = GC;
     c->cap = b->capacity;
     c->slot.assign(c->cap, nullptr);
     c->objective.assign(c->cap, false);
@@ -249,7 +246,6 @@ static pet_status class_launches(pet_batch *b, BatchClass *c, const char *dev, c
     UpdateArgs us{};
     us.g.G = c->G;
     us.g.K = c->KC;
-    us.g.NG = std::max(1, c->GC);             // selects the staged update's tile (min(NG, 4))
     ImageArgs is{};
     is.g.G = c->G;
     is.g.K = c->KC;

@@ -171,18 +171,6 @@ static pet_status geometry_init(pet_geometry *g, cudaStream_t st)
     gd.G = d.nplanes == 1 ? 1 : 8;
     gd.Pp = (d.nplanes + gd.G - 1) / gd.G * gd.G;
     gd.NG = gd.Pp / gd.G;
-    {
-        // staged update window: a TX x TY tile spans at most |cx| (TX - 1) + |cy| (TY - 1) bins of
-        // a view; with the window starting one bin below the lowest first candidate bin, the
-        // second candidate of the highest pixel sits at most that extent + 3 bins above its start
-        // (+1 for fixed-point rounding at integer extents)
-        int GC, TX, TY;
-        stage_dims(gd.NG, GC, TX, TY);
-        double ext = 0.0;
-        for (const ViewGeo &vg : views)
-            ext = std::max(ext, fabs(vg.cx) * (TX - 1) + fabs(vg.cy) * (TY - 1));
-        gd.wb = (int)ceil(ext) + 5;
-    }
     gd.V = d.nviews;
     gd.NB = d.nbins;
     gd.M = d.nsubsets;

@@ -69,20 +69,10 @@ struct GeoDev {
     int N, P, Pp, G, NG;      // image side, planes, padded planes, group size, groups
     int V, NB, M, K;          // views, bins, subsets, max candidate bins per view in the gather
     int tuneS;                // forward projector chunks per ray picked by pet_autotune (0: heuristic)
-    int wb;                   // staged 8-plane update: bins of one view a pixel tile spans (+ margin)
     double scale;             // sens * pixel_mm
     const ViewGeo *views;     // [V] in subset order
     const RayGeo *rays;       // [V * NB] in subset order
 };
-
-// Tile of the staged 8-plane update kernel: TX x TY pixels x GC plane groups (256 threads or
-// fewer), GC = min(NG, 4).
-__host__ __device__ inline void stage_dims(int NG, int &GC, int &TX, int &TY)
-{
-    GC = NG < 4 ? NG : 4;
-    TX = GC <= 2 ? 16 : 8;
-    TY = 256 / (GC * TX);              // GC = 1: 16 x 16, 2: 16 x 8, 3: 8 x 10, 4: 8 x 8
-}
 
 struct Reducer {              // deterministic last-block reduction scratch
     double *partials;         // [capacity * nvals]

@@ -13,9 +13,6 @@
 #ifndef UPDATE_X8_BLOCKS
 #define UPDATE_X8_BLOCKS 3      // resident blocks per SM the packed update kernel is built for
 #endif
-#ifndef UPDATE_STAGED
-#define UPDATE_STAGED 1         // 8-plane FP32 update with the ratio rows staged in shared memory
-#endif
 
 namespace pet {
 
@@ -442,247 +439,6 @@ __global__ void __launch_bounds__(256, UPDATE_X8_BLOCKS) update_kernel_x8(
     }
 }
 
-// ------------------------------------------------------------------------------------------
-// Staged FP32 update for 8-plane groups with at most two candidate bins per view (KC = 2).
-// Same arithmetic, in the same order, as update_kernel_x8; what changes is where the gather
-// reads the ratio rows w from and the shape of a tile:
-//   - a tile is a TX x TY square of pixels times GC plane groups (GC = min(NG, 4); 8 x 8 x 4 for
-//     the stacked workload), so that the bins a tile's pixels project to in one view form one
-//     short window, and the 3 x 3 stencil's halo is mostly the tile's own pixels (L1 reuse);
-//   - for each view of the subset, the window of WB bins x the chunk's GC x 8 planes is copied
-//     into shared memory with cp.async (16-byte copies, zero-filled outside [0, NB)) while the
-//     stencil runs, so the gather's 2 x 12 dependent loads per (pixel, group) become shared-
-//     memory loads instead of L1/L2 gathers;
-//   - the (pixel, view) table holds the staged row offset of bin b0 and the two lengths.
-// Virtual blocks are (plane chunk, tile row, tile column) with the column fastest.
-// ------------------------------------------------------------------------------------------
-constexpr int kStageFloats = 6144;      // staged ratio rows: 24 KB
-constexpr int kStageEntries = 768;      // (pixel, view) table: 12 KB
-
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool valid)
-{
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
-                 :: "r"(sa), "l"(gmem), "r"(valid ? 16 : 0) : "memory");
-}
-
-template <int AR, int GC>
-__global__ void __launch_bounds__(256, UPDATE_X8_BLOCKS) update_kernel_x8s(
-    const __grid_constant__ UpdateArgs one, const Batch bt)
-{
-    static_assert(AR != AR_FP64, "FP32 arithmetic only");
-    constexpr int TX = GC <= 2 ? 16 : 8, TY = 256 / (GC * TX), npx = TX * TY, RS = GC * 8;
-    __shared__ __align__(16) float sw[kStageFloats];
-    __shared__ int4 tbl[kStageEntries];
-    __shared__ int blo[64];
-    const int total = total_vblocks(one, bt);
-    for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
-        int vloc, nv;
-        const UpdateArgs &a = *scan_of(one, bt, vb, vloc, nv);
-        const GeoDev &g = a.g;
-        const int N = g.N, NG = g.NG, NB = g.NB;
-        const unsigned Pp = (unsigned)g.Pp;
-        const int WB = g.wb;
-        const int ntx = (N + TX - 1) / TX, nty = (N + TY - 1) / TY, nch = (NG + GC - 1) / GC;
-        const int nt2 = ntx * nty, ntiles = nt2 * nch;
-        const int VC = max(1, min(min(a.nviews, 64), min(kStageEntries / npx, kStageFloats / (WB * RS))));
-        const int pl = threadIdx.x / GC, grp = threadIdx.x % GC;
-        const bool dyn = a.nu_mode == 1 || a.nu_mode == 2;
-        const double q = (double)N * N * g.P;
-        const float mean_f = dyn ? (float)*a.sum_f / (float)q : 1.f;
-        const float mean_mu = dyn ? (float)*a.sum_mu / (float)q : 1.f;
-        const float U = a.fs_U, tt = a.fs_t;
-        const float eps = fmaxf(a.fs_eps, 1e-30f);
-        const float *w_all = reinterpret_cast<const float *>(a.w);
-        const float *invp = reinterpret_cast<const float *>(a.invp);
-        float part = 0.f;
-        for (int tile = vloc * a.tpv; tile < min(ntiles, (vloc + 1) * a.tpv); ++tile) {
-            const int chunk = tile / nt2, t2 = tile - chunk * nt2;
-            const int x0 = (t2 % ntx) * TX, y0 = (t2 / ntx) * TY;
-            const int gidx = chunk * GC + grp;
-            const int ix = x0 + pl % TX, iy = y0 + pl / TX;
-            const bool active = pl < npx && gidx < NG && ix < N && iy < N;
-            const unsigned jc = (unsigned)(iy * N + ix);
-            const float *f = reinterpret_cast<const float *>(a.f) + gidx * 8;
-            // stage views [u0, u0 + nvc): window starts, async row copies, (pixel, view) table
-            auto stage = [&](int u0, int nvc) {
-                __syncthreads();                       // the previous views' rows are consumed
-                if ((int)threadIdx.x < nvc) {
-                    // window start: the smallest first candidate bin over the tile's corners
-                    const ViewGeo &vw = g.views[a.slot0 + u0 + threadIdx.x];
-                    const long long xe = (long long)min(x0 + TX, N) - 1, ye = (long long)min(y0 + TY, N) - 1;
-                    long long tq = vw.t0q + (long long)x0 * vw.cxq + (long long)y0 * vw.cyq;
-                    tq = min(tq, vw.t0q + xe * vw.cxq + (long long)y0 * vw.cyq);
-                    tq = min(tq, vw.t0q + (long long)x0 * vw.cxq + ye * vw.cyq);
-                    tq = min(tq, vw.t0q + xe * vw.cxq + ye * vw.cyq);
-                    blo[threadIdx.x] = (int)((tq - vw.hq) >> 32) - 1;
-                }
-                __syncthreads();
-                // stage rows [blo, blo + WB) x the chunk's planes of each view (16-byte copies)
-                const int q4 = RS / 4, per_view = WB * q4;
-                for (int e = threadIdx.x; e < nvc * per_view; e += blockDim.x) {
-                    const int uu = e / per_view, rem = e - uu * per_view;
-                    const int r = rem / q4, qq = rem - r * q4;
-                    const int b = blo[uu] + r;
-                    const bool ok = (unsigned)b < (unsigned)NB && chunk * GC * 8 + qq * 4 < NG * 8;
-                    const float *src = ok ? w_all + ((size_t)(u0 + uu) * NB + b) * Pp + chunk * GC * 8 + qq * 4
-                                          : w_all;
-                    cp_async16(sw + (uu * WB + r) * RS + qq * 4, src, ok);
-                }
-                asm volatile("cp.async.commit_group;" ::: "memory");
-                // (pixel, view) table: staged offset of the first candidate bin and the lengths
-                for (int e = threadIdx.x; e < npx * nvc; e += blockDim.x) {
-                    const int uu = e / npx, pp = e - uu * npx;
-                    const int ex = x0 + pp % TX, ey = y0 + pp / TX;
-                    int b0 = 0;
-                    float wv[2] = {0.f, 0.f};
-                    if (ex < N && ey < N) {
-                        const int slot = a.slot0 + u0 + uu;
-                        bp_weights<2, AR>(g, g.views[slot], slot, ex, ey, b0, wv);
-                    }
-                    const int r = min(max(b0 - blo[uu], 0), WB - 2);
-                    tbl[e] = make_int4((uu * WB + r) * RS, __float_as_int(wv[0]), __float_as_int(wv[1]), 0);
-                }
-            };
-            f2x A[4], B[4];
-            stage(0, min(VC, a.nviews));
-            if (active) {
-                // stencil, nu, and the step folded into A, B (as update_kernel_x8), while
-                // the copies are in flight
-                const unsigned xm = ix > 0 ? jc - 1 : jc, xp = ix < N - 1 ? jc + 1 : jc;
-                const unsigned ym = iy > 0 ? jc - N : jc, yp = iy < N - 1 ? jc + N : jc;
-                const f2x GR = vsplat(a.fs_gamma_r), EP = vsplat(eps), TWO = vsplat(2.f);
-                f2x c[4], ce[4], gr[4], g2[4], nb0[4], nb1[4];
-                load8x(f + jc * Pp, c);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) { ce[k] = vadd(c[k], EP); gr[k] = 0ull; }
-                auto rdp = [&](const f2x(&x)[4]) {
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const f2x d = vsub(c[k], x[k]);
-                        const f2x den = vfma(GR, vabs(d), vadd(ce[k], x[k]));
-                        const f2x num = vadd(den, vfma(TWO, x[k], EP));
-                        const f2x rr = vrcp(den);
-                        gr[k] = vfma(vmul(d, vmul(num, rr)), rr, gr[k]);
-                    }
-                };
-                load8x(f + xm * Pp, nb0);
-                load8x(f + xp * Pp, nb1);
-                rdp(nb0);
-                rdp(nb1);
-                if (dyn) {
-                    const f2x HX = vsplat((ix > 0 && ix < N - 1) ? 0.5f : 1.f);
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const f2x t = vmul(HX, vsub(nb1[k], nb0[k]));
-                        g2[k] = vmul(t, t);
-                    }
-                }
-                load8x(f + ym * Pp, nb0);
-                load8x(f + yp * Pp, nb1);
-                rdp(nb0);
-                rdp(nb1);
-                f2x nu[4];
-                if (dyn) {
-                    const f2x HY = vsplat((iy > 0 && iy < N - 1) ? 0.5f : 1.f);
-                    const float nu1 = a.fs_nu1, nu2 = a.fs_nu2;
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const f2x t = vmul(HY, vsub(nb1[k], nb0[k]));
-                        float r0, r1;
-                        vunpk(vrsqrt(vfma(t, t, g2[k])), r0, r1);
-                        r0 = fminf(100.f, r0 * mean_f);
-                        r1 = fminf(100.f, r1 * mean_f);
-                        nu[k] = vpk(fminf(fmaxf(mean_mu * r0, nu1), nu2),
-                                    fminf(fmaxf(mean_mu * r1, nu1), nu2));
-                    }
-                    if (a.nu_mode == 2)
-                        store8x(reinterpret_cast<float *>(a.nu_frozen) + jc * Pp + gidx * 8, nu);
-                } else if (a.nu_mode == 3) {
-                    load8x(reinterpret_cast<const float *>(a.nu_frozen) + jc * Pp + gidx * 8, nu);
-                } else {
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) nu[k] = vsplat(1.f);
-                }
-                const unsigned dm = iy > 0 ? jc - N : jc, dp = iy < N - 1 ? jc + N : jc;
-                load8x(f + (ix > 0 && iy > 0 ? dm - 1 : jc) * Pp, nb0);
-                load8x(f + (ix < N - 1 && iy > 0 ? dm + 1 : jc) * Pp, nb1);
-                rdp(nb0);
-                rdp(nb1);
-                load8x(f + (ix > 0 && iy < N - 1 ? dp - 1 : jc) * Pp, nb0);
-                load8x(f + (ix < N - 1 && iy < N - 1 ? dp + 1 : jc) * Pp, nb1);
-                rdp(nb0);
-                rdp(nb1);
-                const f2x NK = vsplat(-a.fs_lam * invp[jc] * a.fs_ips);
-                const f2x BM = vsplat(2.f * a.fs_bm), SC = vsplat(a.fs_scale);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    float c0, c1;
-                    vunpk(c[k], c0, c1);
-                    const f2x S = vpk(fminf(c0, U - c0), fminf(c1, U - c1));
-                    const f2x cn = vmul(vmul(nu[k], S), NK);
-                    A[k] = vfma(cn, vmul(BM, gr[k]), c[k]);
-                    B[k] = vmul(cn, SC);
-                }
-            }
-            f2x sm[4], er[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) { sm[k] = 0ull; er[k] = 0ull; }
-            for (int u0 = 0; u0 < a.nviews; u0 += VC) {
-                const int nvc = min(VC, a.nviews - u0);
-                if (u0 > 0) stage(u0, nvc);
-                asm volatile("cp.async.wait_all;" ::: "memory");
-                __syncthreads();
-                if (!active) continue;
-                // gather b = A_i^T w from the staged rows, view by view (the order of the
-                // unstaged kernel: same bits)
-                for (int uu = 0; uu < nvc; ++uu) {
-                    const int4 ent = tbl[uu * npx + pl];
-                    const float *row = sw + ent.x + grp * 8;
-                    f2x xa[4], xb[4];
-                    const ulonglong2 *r0 = reinterpret_cast<const ulonglong2 *>(row);
-                    const ulonglong2 *r1 = reinterpret_cast<const ulonglong2 *>(row + RS);
-                    ulonglong2 v;
-                    v = r0[0]; xa[0] = v.x; xa[1] = v.y;
-                    v = r0[1]; xa[2] = v.x; xa[3] = v.y;
-                    v = r1[0]; xb[0] = v.x; xb[1] = v.y;
-                    v = r1[1]; xb[2] = v.x; xb[3] = v.y;
-                    const f2x W0 = vsplat(__int_as_float(ent.y)), W1 = vsplat(__int_as_float(ent.z));
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        if constexpr (AR == AR_KAHAN) {
-                            const f2x y = vfma(W1, xb[k], vfma(W0, xa[k], er[k]));
-                            const f2x t = vadd(sm[k], y);
-                            er[k] = vsub(y, vsub(t, sm[k]));
-                            sm[k] = t;
-                        } else {
-                            sm[k] = vfma(W1, xb[k], vfma(W0, xa[k], sm[k]));
-                        }
-                    }
-                }
-            }
-            if (!active) continue;
-            f2x out[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const f2x b = AR == AR_KAHAN ? vadd(sm[k], er[k]) : sm[k];
-                float f0, f1;
-                vunpk(vfma(B[k], b, A[k]), f0, f1);
-                f0 = f0 <= 0.f ? tt : (f0 >= U ? U - tt : f0);
-                f1 = f1 <= 0.f ? tt : (f1 >= U ? U - tt : f1);
-                const int p0 = gidx * 8 + 2 * k;
-                f0 = p0 < g.P ? f0 : 0.f;
-                f1 = p0 + 1 < g.P ? f1 : 0.f;
-                part += f0 + f1;
-                out[k] = vpk(f0, f1);
-            }
-            store8x(reinterpret_cast<float *>(a.fout) + jc * Pp + gidx * 8, out);
-        }
-        double v[1] = {(double)part};
-        grid_reduce<1>(v, a.red, a.sum_fout, vloc, nv);
-    }
-}
-
 // Stand-alone gather backprojection (also the sensitivity, proj == nullptr); one pixel tile
 // per virtual block.
 template <int G, int KC, int AR>
@@ -838,35 +594,10 @@ GeoDev update_geo(const GeoDev &g) { return g; }
 // pixel tiles per virtual block so that a scan never needs more partial sums than its reducer
 int resident_blocks(const void *fn);
 
-template <int AR>
-static const void *staged_fn(int NG)
-{
-    switch (NG < 4 ? NG : 4) {
-    case 1: return (const void *)update_kernel_x8s<AR, 1>;
-    case 2: return (const void *)update_kernel_x8s<AR, 2>;
-    case 3: return (const void *)update_kernel_x8s<AR, 3>;
-    default: return (const void *)update_kernel_x8s<AR, 4>;
-    }
-}
-
-template <int AR>
-static void staged_launch(const UpdateArgs &a, const Batch &b, int grid, cudaStream_t st)
-{
-    switch (a.g.NG < 4 ? a.g.NG : 4) {
-    case 1: update_kernel_x8s<AR, 1><<<grid, 256, 0, st>>>(a, b); break;
-    case 2: update_kernel_x8s<AR, 2><<<grid, 256, 0, st>>>(a, b); break;
-    case 3: update_kernel_x8s<AR, 3><<<grid, 256, 0, st>>>(a, b); break;
-    default: update_kernel_x8s<AR, 4><<<grid, 256, 0, st>>>(a, b); break;
-    }
-}
-
 template <int G, int KC>
-static const void *update_fn(int arith, int NG = 4)
+static const void *update_fn(int arith)
 {
-    if constexpr (G == 8 && KC == 2 && UPDATE_STAGED) {
-        if (arith == AR_FP32) return staged_fn<AR_FP32>(NG);
-        if (arith == AR_KAHAN) return staged_fn<AR_KAHAN>(NG);
-    } else if constexpr (G == 8) {
+    if constexpr (G == 8) {
         if (arith == AR_FP32) return (const void *)update_kernel_x8<KC, AR_FP32>;
         if (arith == AR_KAHAN) return (const void *)update_kernel_x8<KC, AR_KAHAN>;
     } else {
@@ -879,22 +610,8 @@ static const void *update_fn(int arith, int NG = 4)
 // Pixel tiles per virtual block: each virtual block ends in a block reduction and a grid-wide
 // ticket, so the tiles are grouped into one wave of virtual blocks over the resident block
 // slots (and never more virtual blocks than the reducer has partial sums for).
-static bool staged_update(const GeoDev &g, int arith)
-{
-    return UPDATE_STAGED && g.G == 8 && g.K <= 2 && arith != AR_FP64;
-}
-
 void update_shape(UpdateArgs &a, int arith)
 {
-    if (staged_update(a.g, arith)) {
-        int GC, TX, TY;
-        stage_dims(a.g.NG, GC, TX, TY);
-        const int ntiles = ((a.g.N + TX - 1) / TX) * ((a.g.N + TY - 1) / TY) * ((a.g.NG + GC - 1) / GC);
-        const int slots = sm_count() * resident_blocks(update_fn<8, 2>(arith, a.g.NG));
-        a.tpv = std::max({1, (ntiles + a.red.capacity - 1) / a.red.capacity, (ntiles + slots - 1) / slots});
-        a.nvb = (ntiles + a.tpv - 1) / a.tpv;
-        return;
-    }
     const int TP = 256 / a.g.NG;
     const int ntiles = (a.g.N * a.g.N + TP - 1) / TP;
     const void *fn = a.g.G == 1 ? (a.g.K <= 2 ? update_fn<1, 2>(arith) : update_fn<1, 4>(arith))
@@ -921,11 +638,7 @@ static int persistent_grid(int nvb) { return std::max(1, std::min(nvb, sm_count(
 template <int G, int KC>
 static void update_dispatch(const UpdateArgs &a, const Batch &b, int arith, int grid, cudaStream_t st)
 {
-    if constexpr (G == 8 && KC == 2 && UPDATE_STAGED) {
-        if (arith == AR_FP32) staged_launch<AR_FP32>(a, b, grid, st);
-        else if (arith == AR_KAHAN) staged_launch<AR_KAHAN>(a, b, grid, st);
-        else update_kernel<G, KC, AR_FP64><<<grid, 256, 0, st>>>(a, b);
-    } else if constexpr (G == 8) {
+    if constexpr (G == 8) {
         if (arith == AR_FP32) update_kernel_x8<KC, AR_FP32><<<grid, 256, 0, st>>>(a, b);
         else if (arith == AR_KAHAN) update_kernel_x8<KC, AR_KAHAN><<<grid, 256, 0, st>>>(a, b);
         else update_kernel<G, KC, AR_FP64><<<grid, 256, 0, st>>>(a, b);

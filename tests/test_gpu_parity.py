@@ -243,10 +243,10 @@ def test_subiteration_parity_each_preconditioner(kind):
 
 @pytest.mark.parametrize("P", [5, 11, 20, 33])
 def test_update_tiles_and_plane_chunks(P):
-    """The 8-plane update kernel at every tile shape it has (1, 2, 3 and 4 plane groups per
-    tile; a ragged last plane chunk for 33 planes) on an image side (37) that no tile divides:
-    subiterations through J0, the dynamic-nu range, the freeze at J1 and beyond, against the
-    oracle."""
+    """The 8-plane update kernel with 1, 2, 3 and 5 plane groups (pixel tiles of 256 / groups
+    pixels, so tiles that straddle image rows and end raggedly; 33 planes leave 7 pad planes) on
+    an odd image side: subiterations through J0, the dynamic-nu range, the freeze at J1 and
+    beyond, against the oracle."""
     w = synth.Workload("t", 37, P, 8.0, 30, 53, 8.0, 5, 2e5 * P, "ellipsoid3d",
                        synth.AlgoParams(iterations=2, J0=2, J1=6, a=0.2), plane_mm=8.0, seed=P)
     scan = synth.make_scan(w)
