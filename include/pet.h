@@ -94,6 +94,11 @@ typedef struct {
     int J1;             /* nu frozen at its J1 value for J > J1 */
     int precond;        /* pet_precond */
     int precision;      /* pet_precision */
+    int rdp_3d;         /* 0: RDP over the 8 in-plane neighbours and nu from the in-plane gradient
+                           (Sec. IV-A); 1: the volume as one 3-D image (the fully 3-D
+                           reconstructions of Sec. IV-C): RDP over the 26 neighbours in the volume
+                           (Eqs. RDP, gradRD) and nu from the gradient with its component across
+                           the planes (Sec. III) */
 } pet_params;
 
 typedef struct pet_geometry pet_geometry;
@@ -214,6 +219,16 @@ pet_status pet_smoothness_nu(const pet_geometry *g, const float *d_img, double n
 pet_status pet_objective(const pet_geometry *g, const int32_t *d_counts, const float *d_gamma,
                          const float *d_img, double beta, double gamma_r, double eps,
                          double *h_phi, double *h_parts, void *stream);
+/* The same three calls with the fully 3-D prior (pet_params.rdp_3d = 1): RDP over the 26
+ * neighbours of each voxel in the volume, nu from the gradient including its component across
+ * the planes. */
+pet_status pet_rdp_gradient_3d(const pet_geometry *g, const float *d_img, double gamma_r,
+                               double eps, float *d_grad, void *stream);
+pet_status pet_smoothness_nu_3d(const pet_geometry *g, const float *d_img, double nu1, double nu2,
+                                float *d_nu, void *stream);
+pet_status pet_objective_3d(const pet_geometry *g, const int32_t *d_counts, const float *d_gamma,
+                            const float *d_img, double beta, double gamma_r, double eps,
+                            double *h_phi, double *h_parts, void *stream);
 
 /* ------------------------------------------------------------------------------------------
  * Batches (Table I for many independent scans at once; no counterpart in the paper).

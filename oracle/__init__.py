@@ -45,7 +45,8 @@ class Params(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int)] + [
         (k, ctypes.c_double) for k in ("beta", "gamma_r", "eps", "t", "U", "lambda0", "a",
                                        "rho", "delta1", "delta2", "nu1", "nu2")] + [
-        ("J0", ctypes.c_int), ("J1", ctypes.c_int), ("precond", ctypes.c_int)]
+        ("J0", ctypes.c_int), ("J1", ctypes.c_int), ("precond", ctypes.c_int),
+        ("rdp3d", ctypes.c_int)]
 
 
 def lib():
@@ -69,6 +70,14 @@ def lib():
             L.ora_rdp_grad.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_double, ctypes.c_double, dp]
             L.ora_matlab_gradient.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp]
             L.ora_nu_from_image.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_double, ctypes.c_double, dp]
+            L.ora_nu_from_image3.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_double, ctypes.c_double,
+                                             ctypes.c_int, dp]
+            L.ora_rdp_value3.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_double, ctypes.c_double]
+            L.ora_rdp_value3.restype = ctypes.c_double
+            L.ora_rdp_grad3.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_double, ctypes.c_double, dp]
+            L.ora_matlab_gradient_z.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp]
+            L.ora_objective3.argtypes = [gp, ip, fp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_int, dp]
             L.ora_alpha_nesterov.argtypes = [ctypes.c_int, dp]
             L.ora_alpha_km.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
             L.ora_objective.argtypes = [gp, ip, fp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
@@ -133,17 +142,21 @@ def sensitivity(g: Geom) -> np.ndarray:
     return out
 
 
-def rdp_value(f, gamma_r=2.0, eps=1e-12) -> float:
+def rdp_value(f, gamma_r=2.0, eps=1e-12, three_d=False) -> float:
+    """R(f) of Eq. RDP: 8 in-plane neighbours, or the 26 neighbours of the volume (three_d)."""
     f, fp = _d(f)
     P, N = (1,) + f.shape if f.ndim == 2 else f.shape[:2]
-    return lib().ora_rdp_value(N, P, fp, gamma_r, eps)
+    fn = lib().ora_rdp_value3 if three_d else lib().ora_rdp_value
+    return fn(N, P, fp, gamma_r, eps)
 
 
-def rdp_grad(f, gamma_r=2.0, eps=1e-12) -> np.ndarray:
+def rdp_grad(f, gamma_r=2.0, eps=1e-12, three_d=False) -> np.ndarray:
+    """dR/df of Eq. gradRD over the same neighbourhood as rdp_value."""
     f, fp = _d(f)
     P, N = (1,) + f.shape if f.ndim == 2 else f.shape[:2]
     out = np.zeros_like(f)
-    lib().ora_rdp_grad(N, P, fp, gamma_r, eps, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    fn = lib().ora_rdp_grad3 if three_d else lib().ora_rdp_grad
+    fn(N, P, fp, gamma_r, eps, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
     return out
 
 
@@ -156,11 +169,21 @@ def matlab_gradient(f):
     return gx, gy
 
 
-def nu_from_image(f, nu1, nu2) -> np.ndarray:
+def matlab_gradient_z(f) -> np.ndarray:
+    """Third component of Matlab's gradient of the volume (along the planes)."""
+    f, fp = _d(f)
+    P, N = f.shape[:2]
+    gz = np.zeros_like(f)
+    lib().ora_matlab_gradient_z(N, P, fp, gz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return gz
+
+
+def nu_from_image(f, nu1, nu2, three_d=False) -> np.ndarray:
     f, fp = _d(f)
     P, N = (1,) + f.shape if f.ndim == 2 else f.shape[:2]
     out = np.zeros_like(f)
-    lib().ora_nu_from_image(N, P, fp, nu1, nu2, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    lib().ora_nu_from_image3(N, P, fp, nu1, nu2, 1 if three_d else 0,
+                             out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
     return out
 
 
@@ -176,22 +199,23 @@ def alpha_km(nsub: int, rho: float, delta1: float, delta2: float) -> np.ndarray:
     return out
 
 
-def objective(g: Geom, counts, gamma, f, beta, gamma_r=2.0, eps=1e-12) -> dict:
+def objective(g: Geom, counts, gamma, f, beta, gamma_r=2.0, eps=1e-12, three_d=False) -> dict:
     """Phi(f) and its parts: sum(Af), sum(g ln(Af + gamma)), R(f)."""
     counts = np.ascontiguousarray(counts, dtype=np.int32)
     gamma = np.ascontiguousarray(gamma, dtype=np.float32)
     f, fp = _d(f)
     out = np.zeros(4)
-    lib().ora_objective(ctypes.byref(g), counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
-                        gamma.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), fp, beta, gamma_r,
-                        eps, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    lib().ora_objective3(ctypes.byref(g), counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                         gamma.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), fp, beta, gamma_r,
+                         eps, 1 if three_d else 0, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
     return dict(sum_af=out[0], sum_glog=out[1], rdp=out[2], phi=out[3])
 
 
 def params_from(p) -> Params:
     """Oracle parameters from an object with the AlgoParams attribute names."""
     return Params(p.iterations, p.beta, p.gamma_r, p.eps, p.t, p.U, p.lambda0, p.a, p.rho,
-                  p.delta1, p.delta2, p.nu1, p.nu2, p.J0, p.J1, p.precond)
+                  p.delta1, p.delta2, p.nu1, p.nu2, p.J0, p.J1, p.precond,
+                  int(getattr(p, "rdp3d", 0)))
 
 
 def reconstruct(g: Geom, counts, gamma, params, f0, nsub: int = -1, with_objective=False):

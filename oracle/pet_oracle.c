@@ -15,6 +15,8 @@
  *   - alpha (Nesterov / KM), mu, nu, lambda_k ......... Sec. III, Eqs. preconditioner:Nesterov,
  *                                                      preconditioner:KM, nuki; Theorem 2
  *   - grad F, dR/df_j ................................ Appendix A, Eq. gradRD
+ *   - fully 3-D RDP (26 neighbours) and 3-D smoothness map, for volumes reconstructed as one
+ *     3-D image (Sec. IV-C) ......................... Eqs. RDP, gradRD, nuki over 3-D neighbours
  *
  * System model: one line per detector bin, parallel beam; A_ij = sens * (length in mm of
  * ray i inside pixel j), where a pixel is the half-open square [x, x+1) x [y, y+1) in pixel
@@ -47,6 +49,7 @@ typedef struct {
     double beta, gamma_r, eps, t, U, lambda0, a, rho, delta1, delta2, nu1, nu2;
     int J0, J1;
     int precond;     /* 0 BSREM, 1 M1, 2 M2, 3 P1, 4 P2 */
+    int rdp3d;       /* 0: 8 in-plane neighbours (Sec. IV-A); 1: 26 neighbours in 3-D */
 } ora_params;
 
 /* ---------------------------------------------------------------------------------------
@@ -269,6 +272,54 @@ void ora_rdp_grad(int N, int P, const double *f, double gamma_r, double eps, dou
 }
 
 /*
+ * Fully 3-D RDP (Eq. RDP, Eq. gradRD with the neighbourhood N_j of voxel j taken as its 26
+ * neighbours in the volume: offsets (dx, dy, dz) in {-1, 0, 1}^3 other than 0, unweighted, absent
+ * outside the volume).  f: [P][N][N] with the planes as the third axis.
+ */
+double ora_rdp_value3(int N, int P, const double *f, double gamma_r, double eps)
+{
+    double R = 0.0;
+    for (int p = 0; p < P; ++p)
+        for (int iy = 0; iy < N; ++iy)
+            for (int ix = 0; ix < N; ++ix) {
+                const double fj = f[((size_t)p * N + iy) * N + ix];
+                for (int dz = -1; dz <= 1; ++dz)
+                    for (int dy = -1; dy <= 1; ++dy)
+                        for (int dx = -1; dx <= 1; ++dx) {
+                            if (!dx && !dy && !dz) continue;
+                            const int x = ix + dx, y = iy + dy, z = p + dz;
+                            if (x < 0 || y < 0 || z < 0 || x >= N || y >= N || z >= P) continue;
+                            const double fk = f[((size_t)z * N + y) * N + x];
+                            const double d = fj - fk;
+                            R += d * d / (fj + fk + gamma_r * fabs(d) + eps);
+                        }
+            }
+    return R;
+}
+
+void ora_rdp_grad3(int N, int P, const double *f, double gamma_r, double eps, double *grad)
+{
+    for (int p = 0; p < P; ++p)
+        for (int iy = 0; iy < N; ++iy)
+            for (int ix = 0; ix < N; ++ix) {
+                const double fj = f[((size_t)p * N + iy) * N + ix];
+                double acc = 0.0;
+                for (int dz = -1; dz <= 1; ++dz)
+                    for (int dy = -1; dy <= 1; ++dy)
+                        for (int dx = -1; dx <= 1; ++dx) {
+                            if (!dx && !dy && !dz) continue;
+                            const int x = ix + dx, y = iy + dy, z = p + dz;
+                            if (x < 0 || y < 0 || z < 0 || x >= N || y >= N || z >= P) continue;
+                            const double fk = f[((size_t)z * N + y) * N + x];
+                            const double d = fj - fk;
+                            const double den = fj + fk + gamma_r * fabs(d) + eps;
+                            acc += d * (gamma_r * fabs(d) + fj + 3.0 * fk + 2.0 * eps) / (den * den);
+                        }
+                grad[((size_t)p * N + iy) * N + ix] = 2.0 * acc;
+            }
+}
+
+/*
  * Numerical gradient of mat(f) along x and y (Sec. III, "gradient function in Matlab"):
  * central differences (f[j+1] - f[j-1]) / 2 inside, one-sided differences at the two edges,
  * unit spacing, in-plane.  gx along ix, gy along iy.
@@ -296,20 +347,43 @@ void ora_matlab_gradient(int N, int P, const double *f, double *gx, double *gy)
 }
 
 /*
- * nu from f (Sec. III): mu = max(0.01, grad(f) / mean(f)), nu = P_{nu1}^{nu2}(mean(mu) / mu),
- * with grad(f) = sqrt(gx^2 + gy^2) and means over all q = N^2 P pixels.
+ * The third component of Matlab's gradient of a 3-D array (planes as the third axis): central
+ * differences (f[z+1] - f[z-1]) / 2 between planes, one-sided at the first and last plane, zero
+ * for a single plane.
  */
-void ora_nu_from_image(int N, int P, const double *f, double nu1, double nu2, double *nu)
+void ora_matlab_gradient_z(int N, int P, const double *f, double *gz)
+{
+    const size_t np = (size_t)N * N;
+    for (int p = 0; p < P; ++p)
+        for (size_t j = 0; j < np; ++j) {
+            double d;
+            if (P == 1) d = 0.0;
+            else if (p == 0) d = f[np + j] - f[j];
+            else if (p == P - 1) d = f[(size_t)(P - 1) * np + j] - f[(size_t)(P - 2) * np + j];
+            else d = 0.5 * (f[(size_t)(p + 1) * np + j] - f[(size_t)(p - 1) * np + j]);
+            gz[(size_t)p * np + j] = d;
+        }
+}
+
+/*
+ * nu from f (Sec. III): mu = max(0.01, grad(f) / mean(f)), nu = P_{nu1}^{nu2}(mean(mu) / mu),
+ * with grad(f) = sqrt(gx^2 + gy^2) (+ gz^2 for a 3-D volume, three_d != 0) and means over all
+ * q = N^2 P pixels.
+ */
+void ora_nu_from_image3(int N, int P, const double *f, double nu1, double nu2, int three_d,
+                        double *nu)
 {
     size_t q = (size_t)N * N * P;
     double *gx = (double *)malloc(sizeof(double) * q), *gy = (double *)malloc(sizeof(double) * q);
+    double *gz = (double *)calloc(q, sizeof(double));
     ora_matlab_gradient(N, P, f, gx, gy);
+    if (three_d) ora_matlab_gradient_z(N, P, f, gz);
     double mf = 0.0;
     for (size_t j = 0; j < q; ++j) mf += f[j];
     mf /= (double)q;
     double mmu = 0.0;
     for (size_t j = 0; j < q; ++j) {
-        double mu = sqrt(gx[j] * gx[j] + gy[j] * gy[j]) / mf;
+        double mu = sqrt(gx[j] * gx[j] + gy[j] * gy[j] + gz[j] * gz[j]) / mf;
         if (mu < 0.01) mu = 0.01;
         gx[j] = mu;
         mmu += mu;
@@ -319,7 +393,12 @@ void ora_nu_from_image(int N, int P, const double *f, double nu1, double nu2, do
         double v = mmu / gx[j];
         nu[j] = v < nu1 ? nu1 : (v > nu2 ? nu2 : v);
     }
-    free(gx); free(gy);
+    free(gx); free(gy); free(gz);
+}
+
+void ora_nu_from_image(int N, int P, const double *f, double nu1, double nu2, double *nu)
+{
+    ora_nu_from_image3(N, P, f, nu1, nu2, 0, nu);
 }
 
 /* ---------------------------------------------------------------------------------------
@@ -348,8 +427,18 @@ void ora_alpha_km(int nsub, double rho, double delta1, double delta2, double *al
  * Objective Phi(f) = <Af, 1> - <ln(Af + gamma), g> + beta R(f)   (Eqs. FidelityTerm,
  * ObjectiveFunction, RDP).  out[0] = <Af,1>, out[1] = <ln(Af+gamma), g>, out[2] = R, out[3] = Phi.
  * ------------------------------------------------------------------------------------- */
+void ora_objective3(const ora_geom *g, const int *counts, const float *gamma, const double *f,
+                    double beta, double gamma_r, double eps, int three_d, double *out);
+
 void ora_objective(const ora_geom *g, const int *counts, const float *gamma, const double *f,
                    double beta, double gamma_r, double eps, double *out)
+{
+    ora_objective3(g, counts, gamma, f, beta, gamma_r, eps, 0, out);
+}
+
+/* As ora_objective; three_d != 0 takes R over the 26 neighbours of each voxel. */
+void ora_objective3(const ora_geom *g, const int *counts, const float *gamma, const double *f,
+                    double beta, double gamma_r, double eps, int three_d, double *out)
 {
     size_t nsino = (size_t)g->nplanes * g->nviews * g->nbins;
     double *y = (double *)malloc(sizeof(double) * nsino);
@@ -359,7 +448,8 @@ void ora_objective(const ora_geom *g, const int *counts, const float *gamma, con
         s1 += y[k];
         s2 += (double)counts[k] * log(y[k] + (double)gamma[k]);
     }
-    double R = ora_rdp_value(g->n, g->nplanes, f, gamma_r, eps);
+    double R = three_d ? ora_rdp_value3(g->n, g->nplanes, f, gamma_r, eps)
+                       : ora_rdp_value(g->n, g->nplanes, f, gamma_r, eps);
     out[0] = s1; out[1] = s2; out[2] = R; out[3] = s1 - s2 + beta * R;
     free(y);
 }
@@ -413,7 +503,8 @@ void ora_reconstruct_snap(const ora_geom *g, const int *counts, const float *gam
     int *views = (int *)malloc(sizeof(int) * g->nviews);
     double *ysub = (double *)malloc(sizeof(double) * (size_t)P * g->nviews * NB);
 
-    if (obj) { double o[4]; ora_objective(g, counts, gamma, f, prm->beta, prm->gamma_r, prm->eps, o); obj[0] = o[3]; }
+    const int z3 = prm->rdp3d;
+    if (obj) { double o[4]; ora_objective3(g, counts, gamma, f, prm->beta, prm->gamma_r, prm->eps, z3, o); obj[0] = o[3]; }
     for (int J = 1; J <= nsub; ++J) {
         const int k = (J - 1) / M, i = (J - 1) % M + 1;
         const double lambda = prm->lambda0 / (prm->a * k + 1.0);
@@ -422,7 +513,7 @@ void ora_reconstruct_snap(const ora_geom *g, const int *counts, const float *gam
         /* nu^{k,i} (Eq. nuki) from f^{k,i-1} */
         if (!use_nu || J <= prm->J0) { for (size_t j = 0; j < q; ++j) nu[j] = 1.0; }
         else if (J <= prm->J1) {
-            ora_nu_from_image(N, P, f, prm->nu1, prm->nu2, nu);
+            ora_nu_from_image3(N, P, f, prm->nu1, prm->nu2, z3, nu);
             if (J == prm->J1) { memcpy(nu_frozen, nu, sizeof(double) * q); have_frozen = 1; }
         } else {
             if (!have_frozen) { /* J1 < first dynamic J: nu^{k1,i1} with J_{k1,i1} = J1 <= J0 is 1 */
@@ -442,7 +533,8 @@ void ora_reconstruct_snap(const ora_geom *g, const int *counts, const float *gam
                 }
         ora_back(g, subset, ysub, grad);
         /* penalty term (beta / M) grad R  (Eq. SubObjFunc, Eq. gradRD) */
-        ora_rdp_grad(N, P, f, prm->gamma_r, prm->eps, rgrad);
+        if (z3) ora_rdp_grad3(N, P, f, prm->gamma_r, prm->eps, rgrad);
+        else ora_rdp_grad(N, P, f, prm->gamma_r, prm->eps, rgrad);
         for (size_t j = 0; j < q; ++j) {
             const double d = grad[j] + prm->beta / M * rgrad[j];
             const double fj = f[j], pjj = pj[j % npix];
@@ -454,7 +546,7 @@ void ora_reconstruct_snap(const ora_geom *g, const int *counts, const float *gam
         }
         if (obj && i == M) {
             double o[4];
-            ora_objective(g, counts, gamma, f, prm->beta, prm->gamma_r, prm->eps, o);
+            ora_objective3(g, counts, gamma, f, prm->beta, prm->gamma_r, prm->eps, z3, o);
             obj[k + 1] = o[3];
         }
         if (snaps && i == M) memcpy(snaps + (size_t)k * q, f, sizeof(double) * q);

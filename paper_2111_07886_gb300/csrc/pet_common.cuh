@@ -163,6 +163,7 @@ struct UpdateArgs {
     Reducer red;
     int tpv;                   // pixel tiles per virtual block
     int nvb;                   // virtual blocks of this scan
+    int z3;                    // 1: RDP over the 26 neighbours in 3-D, nu from the 3-D gradient
     // the scalars above as FP32 for the FP32 kernels (converted once on the host: a conversion
     // from double on the device runs on the narrow FP64 pipe)
     float fs_lam, fs_bm, fs_gamma_r, fs_eps, fs_t, fs_U, fs_nu1, fs_nu2, fs_ips, fs_scale;
@@ -185,6 +186,7 @@ struct ImageArgs {
     double *result;            // reductions
     Reducer red;
     int ipt, nvb;              // items per thread, virtual blocks of this scan
+    int z3;                    // 1: RDP over the 26 neighbours in 3-D, gradient with its z part
 };
 pet_status launch_sum(const ImageArgs &a, int arith, cudaStream_t st);        // result[0] = sum f
 pet_status launch_mu_sum(const ImageArgs &a, int arith, cudaStream_t st);     // result[0] = sum mu

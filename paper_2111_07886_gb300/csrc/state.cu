@@ -27,11 +27,11 @@ pet_status pet::check_params(const pet_params *p)
         !(p->U > 0) || !(p->t > 0) || !(p->t < p->U) || !(p->lambda0 > 0) || !(p->a >= 0) ||
         !(p->nu1 > 0) || !(p->nu2 >= p->nu1) || p->precond < 0 || p->precond > 4 ||
         p->precision < 0 || p->precision > 2 || !(p->delta1 > 0) || !(p->rho > 0) ||
-        !(p->delta2 > 0) || p->J0 < 0 || p->J1 < p->J0)
+        !(p->delta2 > 0) || p->J0 < 0 || p->J1 < p->J0 || p->rdp_3d < 0 || p->rdp_3d > 1)
         return fail(PET_ERR_INVALID,
                     "invalid pet_params (need iterations >= 0, beta, gamma_r, a >= 0, eps, "
                     "lambda0, rho, delta1, delta2 > 0, 0 < t < U, 0 < nu1 <= nu2, "
-                    "0 <= J0 <= J1, precond in 0..4, precision in 0..2)");
+                    "0 <= J0 <= J1, precond in 0..4, precision in 0..2, rdp_3d in 0..1)");
     return PET_OK;
 }
 
@@ -204,6 +204,7 @@ void pet::plan_subiter(pet_state *s, SubiterPlan *pl, bool with_objective)
     a.sum_f = s->sums + s->cur;
     a.result = s->sums + 2;
     a.red = s->red;
+    a.z3 = p.rdp_3d;
     mu_shape(a, s->arith);
     FwdArgs &fa = pl->fwd;
     fa.g = gd;
@@ -237,6 +238,7 @@ void pet::plan_subiter(pet_state *s, SubiterPlan *pl, bool with_objective)
     ua.sum_mu = s->sums + 2;
     ua.sum_fout = s->sums + (1 - s->cur);
     ua.red = s->red;
+    ua.z3 = p.rdp_3d;
     update_shape(ua, s->arith);
     update_fp32_scalars(ua);
     if (nu_mode == 2) s->have_frozen = true;
@@ -300,6 +302,7 @@ void pet::objective_args(pet_state *s, double *out3, FwdArgs *fa, ImageArgs *ra)
     ra->eps = s->prm.eps;
     ra->result = out3 + 2;
     ra->red = s->red;
+    ra->z3 = s->prm.rdp_3d;
     image_shape(*ra);
 }
 
@@ -754,8 +757,8 @@ static pet_status stage_image(const pet_geometry *g, const float *d_img, void **
     return to_internal_image(gd, d_img, *img_i, 0, 0, st);
 }
 
-extern "C" pet_status pet_rdp_gradient(const pet_geometry *g, const float *d_img, double gamma_r,
-                                       double eps, float *d_grad, void *stream)
+static pet_status rdp_gradient_any(const pet_geometry *g, const float *d_img, double gamma_r,
+                                   double eps, float *d_grad, void *stream, int z3)
 {
     if (!g || !d_img || !d_grad) return fail(PET_ERR_INVALID, "pet_rdp_gradient: NULL argument");
     cudaStream_t st = as_stream(stream);
@@ -768,12 +771,25 @@ extern "C" pet_status pet_rdp_gradient(const pet_geometry *g, const float *d_img
     a.gamma_r = gamma_r;
     a.eps = eps;
     a.red = g->red;
+    a.z3 = z3;
     PET_TRY(launch_rdp_grad(a, AR_FP32, st));
     return from_internal_image(g->dev, out_i, d_grad, 0, 0, st);
 }
 
-extern "C" pet_status pet_smoothness_nu(const pet_geometry *g, const float *d_img, double nu1,
-                                        double nu2, float *d_nu, void *stream)
+extern "C" pet_status pet_rdp_gradient(const pet_geometry *g, const float *d_img, double gamma_r,
+                                       double eps, float *d_grad, void *stream)
+{
+    return rdp_gradient_any(g, d_img, gamma_r, eps, d_grad, stream, 0);
+}
+
+extern "C" pet_status pet_rdp_gradient_3d(const pet_geometry *g, const float *d_img, double gamma_r,
+                                          double eps, float *d_grad, void *stream)
+{
+    return rdp_gradient_any(g, d_img, gamma_r, eps, d_grad, stream, 1);
+}
+
+static pet_status smoothness_nu_any(const pet_geometry *g, const float *d_img, double nu1,
+                                    double nu2, float *d_nu, void *stream, int z3)
 {
     if (!g || !d_img || !d_nu) return fail(PET_ERR_INVALID, "pet_smoothness_nu: NULL argument");
     if (!(nu1 > 0) || !(nu2 >= nu1)) return fail(PET_ERR_INVALID, "pet_smoothness_nu: need 0 < nu1 <= nu2");
@@ -787,6 +803,7 @@ extern "C" pet_status pet_smoothness_nu(const pet_geometry *g, const float *d_im
     a.nu1 = nu1;
     a.nu2 = nu2;
     a.red = g->red;
+    a.z3 = z3;
     a.result = g->d_sums;
     PET_TRY(launch_sum(a, AR_FP32, st));                  // d_sums[0] = sum f
     a.sum_f = g->d_sums;
@@ -797,10 +814,22 @@ extern "C" pet_status pet_smoothness_nu(const pet_geometry *g, const float *d_im
     return from_internal_image(g->dev, out_i, d_nu, 0, 0, st);
 }
 
-extern "C" pet_status pet_objective(const pet_geometry *g, const int32_t *d_counts,
-                                    const float *d_gamma, const float *d_img, double beta,
-                                    double gamma_r, double eps, double *h_phi, double *h_parts,
-                                    void *stream)
+extern "C" pet_status pet_smoothness_nu(const pet_geometry *g, const float *d_img, double nu1,
+                                        double nu2, float *d_nu, void *stream)
+{
+    return smoothness_nu_any(g, d_img, nu1, nu2, d_nu, stream, 0);
+}
+
+extern "C" pet_status pet_smoothness_nu_3d(const pet_geometry *g, const float *d_img, double nu1,
+                                           double nu2, float *d_nu, void *stream)
+{
+    return smoothness_nu_any(g, d_img, nu1, nu2, d_nu, stream, 1);
+}
+
+static pet_status objective_any(const pet_geometry *g, const int32_t *d_counts,
+                                const float *d_gamma, const float *d_img, double beta,
+                                double gamma_r, double eps, double *h_phi, double *h_parts,
+                                void *stream, int z3)
 {
     if (!g || !d_counts || !d_gamma || !d_img || !h_phi)
         return fail(PET_ERR_INVALID, "pet_objective: NULL argument");
@@ -835,6 +864,7 @@ extern "C" pet_status pet_objective(const pet_geometry *g, const int32_t *d_coun
     a.eps = eps;
     a.red = g->red;
     a.result = g->d_sums + 6;
+    a.z3 = z3;
     PET_TRY(launch_rdp_value(a, AR_FP32, st));
     double h[3];
     PET_CUDA(cudaMemcpyAsync(h, g->d_sums + 4, sizeof(h), cudaMemcpyDeviceToHost, st));
@@ -842,4 +872,20 @@ extern "C" pet_status pet_objective(const pet_geometry *g, const int32_t *d_coun
     *h_phi = h[0] - h[1] + beta * h[2];
     if (h_parts) { h_parts[0] = h[0]; h_parts[1] = h[1]; h_parts[2] = h[2]; }
     return PET_OK;
+}
+
+extern "C" pet_status pet_objective(const pet_geometry *g, const int32_t *d_counts,
+                                    const float *d_gamma, const float *d_img, double beta,
+                                    double gamma_r, double eps, double *h_phi, double *h_parts,
+                                    void *stream)
+{
+    return objective_any(g, d_counts, d_gamma, d_img, beta, gamma_r, eps, h_phi, h_parts, stream, 0);
+}
+
+extern "C" pet_status pet_objective_3d(const pet_geometry *g, const int32_t *d_counts,
+                                       const float *d_gamma, const float *d_img, double beta,
+                                       double gamma_r, double eps, double *h_phi, double *h_parts,
+                                       void *stream)
+{
+    return objective_any(g, d_counts, d_gamma, d_img, beta, gamma_r, eps, h_phi, h_parts, stream, 1);
 }

@@ -22,6 +22,10 @@ namespace pet {
 //   MU: gx_p, gy_p of the Matlab-style gradient: central differences inside, one-sided at
 //       the edges (the missing side counts as the centre value)
 //   RV: rv_p = sum_k (f_j - f_k)^2 / den
+// z3: the neighbourhood is the 26 voxels around (ix, iy, plane) in the volume (neighbours
+// outside it are absent), and MU also gives gz_p, the gradient across the planes (central
+// inside, one-sided at the first and last plane, 0 for one plane).  Each position's plane group
+// is loaded with the planes just below and above it.
 template <int G, int AR, bool RG, bool MU, bool RV>
 __device__ __forceinline__ void stencil(const GeoDev &g, const typename ArithT<AR>::T *f, int grp,
                                         int ix, int iy, typename ArithT<AR>::T gamma_r,
@@ -30,7 +34,8 @@ __device__ __forceinline__ void stencil(const GeoDev &g, const typename ArithT<A
                                         typename ArithT<AR>::T (&gr)[G],
                                         typename ArithT<AR>::T (&gx)[G],
                                         typename ArithT<AR>::T (&gy)[G],
-                                        typename ArithT<AR>::T (&rv)[G])
+                                        typename ArithT<AR>::T (&rv)[G],
+                                        bool z3 = false, typename ArithT<AR>::T *gz = nullptr)
 {
     using T = typename ArithT<AR>::T;
     const int N = g.N, Pp = g.Pp;
@@ -48,16 +53,59 @@ __device__ __forceinline__ void stencil(const GeoDev &g, const typename ArithT<A
 #pragma unroll
         for (int p = 0; p < G; ++p) { gx[p] = sx * fc[p]; gy[p] = sy * fc[p]; }
     }
+    // one (centre, neighbour) pair of Eq. RDP / Eq. gradRD
+    auto pair = [&](int p, T c, T k) {
+        const T d = c - k;
+        const T ad = d < T(0) ? -d : d;
+        const T den = c + k + gamma_r * ad + eps;
+        if constexpr (RG) {
+            const T num = d * (gamma_r * ad + c + T(3) * k + T(2) * eps);
+            if constexpr (AR == AR_FP64) gr[p] += num / (den * den);
+            else gr[p] += __fdividef(num, den * den);
+        }
+        if constexpr (RV) {
+            if constexpr (AR == AR_FP64) rv[p] += d * d / den;
+            else rv[p] += __fdividef(d * d, den);
+        }
+    };
+    const int z0 = grp * G;                  // plane of element 0 of the group
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
         const int dx = q % 3 - 1, dy = q / 3 - 1;
-        if (q == 4) continue;
+        if (q == 4 && !z3) continue;
         if (!RG && !RV && dx != 0 && dy != 0) continue;    // gradient only: axial neighbours
         const int x = ix + dx, y = iy + dy;
         if (x < 0 || y < 0 || x >= N || y >= N) continue;
+        const unsigned jn = (unsigned)((int)jc + dy * N + dx) * (unsigned)Pp;
         T fk[G];
-        load_group<G, T>(base + (unsigned)((int)jc + dy * N + dx) * (unsigned)Pp, fk);
-        if constexpr (RG && AR != AR_FP64 && G % 2 == 0) {
+        if (q == 4) {
+#pragma unroll
+            for (int p = 0; p < G; ++p) fk[p] = fc[p];
+        } else {
+            load_group<G, T>(base + jn, fk);
+        }
+        if (z3) {
+            // the planes just below and above this position's group
+            const T lo = z0 > 0 ? f[jn + z0 - 1] : T(0);
+            const T hi = z0 + G < g.P ? f[jn + z0 + G] : T(0);
+#pragma unroll
+            for (int p = 0; p < G; ++p) {
+                const int z = z0 + p;
+                if (z >= g.P) continue;
+                if (RG || RV) {
+                    if (q != 4) pair(p, fc[p], fk[p]);
+                    if (z > 0) pair(p, fc[p], p > 0 ? fk[p - 1] : lo);
+                    if (z + 1 < g.P) pair(p, fc[p], p + 1 < G ? fk[p + 1] : hi);
+                }
+                if constexpr (MU) {
+                    if (q == 4 && gz) {
+                        const T dn = z > 0 ? (p > 0 ? fk[p - 1] : lo) : fc[p];
+                        const T up = z + 1 < g.P ? (p + 1 < G ? fk[p + 1] : hi) : fc[p];
+                        gz[p] = (z > 0 && z + 1 < g.P ? T(0.5) : T(1)) * (up - dn);
+                    }
+                }
+            }
+        } else if constexpr (RG && AR != AR_FP64 && G % 2 == 0) {
             // packed FP32x2: two planes per instruction; 1/den^2 from the fast reciprocal
             const float2 GR = make_float2(gamma_r, gamma_r), THREE = make_float2(3.f, 3.f);
 #pragma unroll
@@ -69,28 +117,16 @@ __device__ __forceinline__ void stencil(const GeoDev &g, const typename ArithT<A
                 const float2 t = fma2(GR, ad, fma2(THREE, k2, add2(c2, make_float2(2.f * eps, 2.f * eps))));
                 const float2 num = mul2(d, t);
                 const float2 den2 = mul2(den, den);
-                const float2 q = make_float2(__fdividef(num.x, den2.x), __fdividef(num.y, den2.y));
-                gr[p] += q.x;
-                gr[p + 1] += q.y;
+                const float2 qq = make_float2(__fdividef(num.x, den2.x), __fdividef(num.y, den2.y));
+                gr[p] += qq.x;
+                gr[p + 1] += qq.y;
             }
         } else if constexpr (RG || RV) {
 #pragma unroll
-            for (int p = 0; p < G; ++p) {
-                const T d = fc[p] - fk[p];
-                const T ad = d < T(0) ? -d : d;
-                const T den = fc[p] + fk[p] + gamma_r * ad + eps;
-                if constexpr (RG) {
-                    const T num = d * (gamma_r * ad + fc[p] + T(3) * fk[p] + T(2) * eps);
-                    if constexpr (AR == AR_FP64) gr[p] += num / (den * den);
-                    else gr[p] += __fdividef(num, den * den);
-                }
-                if constexpr (RV) {
-                    if constexpr (AR == AR_FP64) rv[p] += d * d / den;
-                    else rv[p] += __fdividef(d * d, den);
-                }
-            }
+            for (int p = 0; p < G; ++p) pair(p, fc[p], fk[p]);
         }
         if constexpr (MU) {
+            if (q == 4) continue;
             if (dy == 0) {
                 const T sgn = dx < 0 ? -hx : hx;
 #pragma unroll
@@ -127,11 +163,20 @@ __device__ __forceinline__ T grad_norm(T gx, T gy)
     else return x > 0.f ? x * rsqrtf(x) : 0.f;
 }
 
+// |(gx, gy, gz)|
+template <typename T>
+__device__ __forceinline__ T grad_norm3(T gx, T gy, T gz)
+{
+    const T x = gx * gx + gy * gy + gz * gz;
+    if constexpr (sizeof(T) == 8) return sqrt(x);
+    else return x > 0.f ? x * rsqrtf(x) : 0.f;
+}
+
 // mu = max(0.01, |grad f| / mean(f)); nu = P_{nu1}^{nu2}(mean(mu) / mu)
 template <typename T>
-__device__ __forceinline__ T nu_of(T gx, T gy, T inv_mean_f, T mean_mu, T nu1, T nu2)
+__device__ __forceinline__ T nu_of(T gx, T gy, T gz, T inv_mean_f, T mean_mu, T nu1, T nu2)
 {
-    T mu = grad_norm(gx, gy) * inv_mean_f;
+    T mu = grad_norm3(gx, gy, gz) * inv_mean_f;
     mu = mu < T(0.01) ? T(0.01) : mu;
     return clampT<T>(fast_div(mean_mu, mu), nu1, nu2);
 }
@@ -202,10 +247,12 @@ __global__ void __launch_bounds__(256, 3) update_kernel(const __grid_constant__ 
             T fc[G], coef[G], rg[G];
             if (active) {
                 const int ix = j % N, iy = j / N;
-                T gr[G], gx[G], gy[G], rv[G];
+                T gr[G], gx[G], gy[G], rv[G], gz[G];
+#pragma unroll
+                for (int p = 0; p < G; ++p) gz[p] = T(0);
                 const T gam_r = scal<T>(a.gamma_r, a.fs_gamma_r), eps_t = scal<T>(a.eps, a.fs_eps);
-                if (dyn) stencil<G, AR, true, true, false>(g, f, grp, ix, iy, gam_r, eps_t, fc, gr, gx, gy, rv);
-                else stencil<G, AR, true, false, false>(g, f, grp, ix, iy, gam_r, eps_t, fc, gr, gx, gy, rv);
+                if (dyn) stencil<G, AR, true, true, false>(g, f, grp, ix, iy, gam_r, eps_t, fc, gr, gx, gy, rv, a.z3, gz);
+                else stencil<G, AR, true, false, false>(g, f, grp, ix, iy, gam_r, eps_t, fc, gr, gx, gy, rv, a.z3, gz);
                 T nu[G];
                 if (a.nu_mode == 3) {
                     load_group<G, T>(reinterpret_cast<const T *>(a.nu_frozen) + (unsigned)j * (unsigned)Pp + grp * G, nu);
@@ -214,7 +261,7 @@ __global__ void __launch_bounds__(256, 3) update_kernel(const __grid_constant__ 
                     for (int p = 0; p < G; ++p) nu[p] = T(1);
                 } else {
 #pragma unroll
-                    for (int p = 0; p < G; ++p) nu[p] = nu_of<T>(gx[p], gy[p], inv_mean_f, mean_mu, nu1, nu2);
+                    for (int p = 0; p < G; ++p) nu[p] = nu_of<T>(gx[p], gy[p], gz[p], inv_mean_f, mean_mu, nu1, nu2);
                     if (a.nu_mode == 2)
                         store_group<G, T>(reinterpret_cast<T *>(a.nu_frozen) + (unsigned)j * (unsigned)Pp + grp * G, nu);
                 }
@@ -499,16 +546,18 @@ __global__ void __launch_bounds__(256) image_kernel(const __grid_constant__ Imag
             const int grp = NG == 1 ? 0 : (int)(tid % (unsigned)NG);
             const int j = NG == 1 ? (int)tid : (int)(tid / (unsigned)NG);
             const int ix = j % N, iy = j / N;
-            T fc[G], gr[G], gx[G], gy[G], rv[G], out[G];
+            T fc[G], gr[G], gx[G], gy[G], rv[G], out[G], gz[G];
+#pragma unroll
+            for (int p = 0; p < G; ++p) gz[p] = T(0);
             if constexpr (KIND == 0) {
                 load_group<G, T>(f + (size_t)j * Pp + (size_t)grp * G, fc);
 #pragma unroll
                 for (int p = 0; p < G; ++p) part += (grp * G + p < g.P) ? fc[p] : T(0);
             } else if constexpr (KIND == 1 || KIND == 2) {
-                stencil<G, AR, false, true, false>(g, f, grp, ix, iy, T(0), T(0), fc, gr, gx, gy, rv);
+                stencil<G, AR, false, true, false>(g, f, grp, ix, iy, T(0), T(0), fc, gr, gx, gy, rv, a.z3, gz);
 #pragma unroll
                 for (int p = 0; p < G; ++p) {
-                    T mu = grad_norm(gx[p], gy[p]) * inv_mean_f;
+                    T mu = grad_norm3(gx[p], gy[p], gz[p]) * inv_mean_f;
                     mu = mu < T(0.01) ? T(0.01) : mu;
                     if constexpr (KIND == 1) {
                         part += (grp * G + p < g.P) ? mu : T(0);
@@ -519,12 +568,12 @@ __global__ void __launch_bounds__(256) image_kernel(const __grid_constant__ Imag
                 if constexpr (KIND == 2)
                     store_group<G, T>(reinterpret_cast<T *>(a.out) + (size_t)j * Pp + (size_t)grp * G, out);
             } else if constexpr (KIND == 3) {
-                stencil<G, AR, true, false, false>(g, f, grp, ix, iy, (T)a.gamma_r, (T)a.eps, fc, gr, gx, gy, rv);
+                stencil<G, AR, true, false, false>(g, f, grp, ix, iy, (T)a.gamma_r, (T)a.eps, fc, gr, gx, gy, rv, a.z3, gz);
 #pragma unroll
                 for (int p = 0; p < G; ++p) out[p] = grp * G + p < g.P ? gr[p] : T(0);
                 store_group<G, T>(reinterpret_cast<T *>(a.out) + (size_t)j * Pp + (size_t)grp * G, out);
             } else {
-                stencil<G, AR, false, false, true>(g, f, grp, ix, iy, (T)a.gamma_r, (T)a.eps, fc, gr, gx, gy, rv);
+                stencil<G, AR, false, false, true>(g, f, grp, ix, iy, (T)a.gamma_r, (T)a.eps, fc, gr, gx, gy, rv, a.z3, gz);
 #pragma unroll
                 for (int p = 0; p < G; ++p) part += (grp * G + p < g.P) ? rv[p] : T(0);
             }
@@ -595,9 +644,11 @@ GeoDev update_geo(const GeoDev &g) { return g; }
 int resident_blocks(const void *fn);
 
 template <int G, int KC>
-static const void *update_fn(int arith)
+static const void *update_fn(int arith, int z3 = 0)
 {
     if constexpr (G == 8) {
+        if (z3 && arith == AR_FP32) return (const void *)update_kernel<G, KC, AR_FP32>;
+        if (z3 && arith == AR_KAHAN) return (const void *)update_kernel<G, KC, AR_KAHAN>;
         if (arith == AR_FP32) return (const void *)update_kernel_x8<KC, AR_FP32>;
         if (arith == AR_KAHAN) return (const void *)update_kernel_x8<KC, AR_KAHAN>;
     } else {
@@ -615,7 +666,7 @@ void update_shape(UpdateArgs &a, int arith)
     const int TP = 256 / a.g.NG;
     const int ntiles = (a.g.N * a.g.N + TP - 1) / TP;
     const void *fn = a.g.G == 1 ? (a.g.K <= 2 ? update_fn<1, 2>(arith) : update_fn<1, 4>(arith))
-                                : (a.g.K <= 2 ? update_fn<8, 2>(arith) : update_fn<8, 4>(arith));
+                                : (a.g.K <= 2 ? update_fn<8, 2>(arith, a.z3) : update_fn<8, 4>(arith, a.z3));
     const int slots = sm_count() * resident_blocks(fn);
     a.tpv = std::max({1, (ntiles + a.red.capacity - 1) / a.red.capacity, (ntiles + slots - 1) / slots});
     a.nvb = (ntiles + a.tpv - 1) / a.tpv;
@@ -639,7 +690,10 @@ template <int G, int KC>
 static void update_dispatch(const UpdateArgs &a, const Batch &b, int arith, int grid, cudaStream_t st)
 {
     if constexpr (G == 8) {
-        if (arith == AR_FP32) update_kernel_x8<KC, AR_FP32><<<grid, 256, 0, st>>>(a, b);
+        // the packed kernel has the in-plane stencil only; the 3-D prior runs the generic kernel
+        if (a.z3 && arith == AR_FP32) update_kernel<G, KC, AR_FP32><<<grid, 256, 0, st>>>(a, b);
+        else if (a.z3 && arith == AR_KAHAN) update_kernel<G, KC, AR_KAHAN><<<grid, 256, 0, st>>>(a, b);
+        else if (arith == AR_FP32) update_kernel_x8<KC, AR_FP32><<<grid, 256, 0, st>>>(a, b);
         else if (arith == AR_KAHAN) update_kernel_x8<KC, AR_KAHAN><<<grid, 256, 0, st>>>(a, b);
         else update_kernel<G, KC, AR_FP64><<<grid, 256, 0, st>>>(a, b);
     } else {
@@ -734,7 +788,7 @@ pet_status launch_sum(const ImageArgs &a, int arith, cudaStream_t st) { return l
 // items-per-thread shape of image_kernel.
 void mu_shape(ImageArgs &a, int arith)
 {
-    if (a.g.G != 8 || arith == AR_FP64) {
+    if (a.g.G != 8 || arith == AR_FP64 || a.z3) {
         image_shape(a);
         return;
     }
@@ -748,7 +802,7 @@ void mu_shape(ImageArgs &a, int arith)
 
 static pet_status mu_any(const ImageArgs &a, const Batch &b, int arith, int grid, cudaStream_t st)
 {
-    if (a.g.G != 8 || arith == AR_FP64) return image_any<1>(a, b, arith, grid, st);
+    if (a.g.G != 8 || arith == AR_FP64 || a.z3) return image_any<1>(a, b, arith, grid, st);
     LaunchScope ls(PET_K_MU_SUM, st);
     mu_kernel_x8<<<grid, 256, 0, st>>>(a, b);
     cudaError_t e = cudaGetLastError();

@@ -38,7 +38,7 @@ class Params(ctypes.Structure):
         (k, ctypes.c_double) for k in ("beta", "gamma_r", "eps", "t", "U", "lambda0", "a",
                                        "rho", "delta1", "delta2", "nu1", "nu2")] + [
         ("J0", ctypes.c_int), ("J1", ctypes.c_int), ("precond", ctypes.c_int),
-        ("precision", ctypes.c_int)]
+        ("precision", ctypes.c_int), ("rdp_3d", ctypes.c_int)]
 
 
 class Request(ctypes.Structure):
@@ -88,6 +88,9 @@ SIGNATURES = {
     "pet_smoothness_nu": (_I, [_VP, _VP, _D, _D, _VP, _VP]),
     "pet_objective": (_I, [_VP, _VP, _VP, _VP, _D, _D, _D, _DP, _DP, _VP]),
     "pet_objective_static": (_I, [_VP, _VP, _VP, _VP, _D, _D, _D, _DP, _DP, _VP]),
+    "pet_rdp_gradient_3d": (_I, [_VP, _VP, _D, _D, _VP, _VP]),
+    "pet_smoothness_nu_3d": (_I, [_VP, _VP, _D, _D, _VP, _VP]),
+    "pet_objective_3d": (_I, [_VP, _VP, _VP, _VP, _D, _D, _D, _DP, _DP, _VP]),
     "pet_batch_create": (_I, [_I, _I, ctypes.POINTER(_VP)]),
     "pet_batch_add": (_I, [_VP, _VP, _I, _VP]),
     "pet_batch_remove": (_I, [_VP, _VP]),
@@ -155,7 +158,7 @@ def make_params(p, precision: int | None = None) -> Params:
     """Params from an object with AlgoParams attribute names."""
     return Params(p.iterations, p.beta, p.gamma_r, p.eps, p.t, p.U, p.lambda0, p.a, p.rho,
                   p.delta1, p.delta2, p.nu1, p.nu2, p.J0, p.J1, p.precond,
-                  p.precision if precision is None else precision)
+                  p.precision if precision is None else precision, int(getattr(p, "rdp3d", 0)))
 
 
 class Geometry:
@@ -285,19 +288,22 @@ def reconstruct_host(g: Geometry, h_counts, h_gamma, params: Params, h_img_inout
     return list(obj) if objective else None
 
 
-def rdp_gradient(g: Geometry, d_img, gamma_r, eps, d_grad, stream=None):
-    _check(lib().pet_rdp_gradient(g.handle, _ptr(d_img), gamma_r, eps, _ptr(d_grad), _stream(stream)))
+def rdp_gradient(g: Geometry, d_img, gamma_r, eps, d_grad, stream=None, three_d=False):
+    fn = lib().pet_rdp_gradient_3d if three_d else lib().pet_rdp_gradient
+    _check(fn(g.handle, _ptr(d_img), gamma_r, eps, _ptr(d_grad), _stream(stream)))
 
 
-def smoothness_nu(g: Geometry, d_img, nu1, nu2, d_nu, stream=None):
-    _check(lib().pet_smoothness_nu(g.handle, _ptr(d_img), nu1, nu2, _ptr(d_nu), _stream(stream)))
+def smoothness_nu(g: Geometry, d_img, nu1, nu2, d_nu, stream=None, three_d=False):
+    fn = lib().pet_smoothness_nu_3d if three_d else lib().pet_smoothness_nu
+    _check(fn(g.handle, _ptr(d_img), nu1, nu2, _ptr(d_nu), _stream(stream)))
 
 
-def objective(g: Geometry, d_counts, d_gamma, d_img, beta, gamma_r, eps, stream=None):
+def objective(g: Geometry, d_counts, d_gamma, d_img, beta, gamma_r, eps, stream=None, three_d=False):
     phi = ctypes.c_double()
     parts = (ctypes.c_double * 3)()
-    _check(lib().pet_objective(g.handle, _ptr(d_counts), _ptr(d_gamma), _ptr(d_img), beta, gamma_r,
-                               eps, ctypes.byref(phi), parts, _stream(stream)))
+    fn = lib().pet_objective_3d if three_d else lib().pet_objective
+    _check(fn(g.handle, _ptr(d_counts), _ptr(d_gamma), _ptr(d_img), beta, gamma_r,
+              eps, ctypes.byref(phi), parts, _stream(stream)))
     return phi.value, list(parts)
 
 

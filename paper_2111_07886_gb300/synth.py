@@ -58,6 +58,7 @@ class AlgoParams:
     J1: int = 1000                # Sec. IV-A prints "J_2 = 1000"; Eq. nuki uses J_1
     precond: int = PRECOND_P2
     precision: int = PREC_FP32_KAHAN
+    rdp3d: int = 0                # 0: 8 in-plane neighbours (Sec. IV-A); 1: 26 neighbours in 3-D
 
 
 @dataclasses.dataclass
