@@ -243,7 +243,10 @@ pet_status pet_objective_3d(const pet_geometry *g, const int32_t *d_counts, cons
  * pet_batch_add: the state joins at its current subiteration (Phi(f^0) is enqueued on `stream`
  *   when requested and J = 0); PET_ERR_OOM if the batch is full.
  * pet_batch_step: *running_after (optional) = states still running after this step.  The step is
- *   asynchronous; the host waits only to reuse its double-buffered descriptor memory.
+ *   asynchronous; the host waits only to reuse its descriptor memory (four buffers per class, so
+ *   up to four steps are in flight).  A class with a single running state launches that state's
+ *   kernels directly (as pet_subiter does); with more, only the running states' arguments are
+ *   uploaded and the replayed graph runs just the kernels the step needs.
  * pet_batch_remove: detach a state (waits for in-flight steps that read its descriptors).
  * pet_batch_size: running states.  The batch does not own the states.
  * pet_state_objective_history: h_obj[k] = Phi(f^k) for k = 0..T recorded so far (synchronises);

@@ -12,6 +12,8 @@
 // tick's graph may still read the other.  Each scan keeps its own launch shapes and reduction
 // scratch, so its results are bitwise the same alone or in any mix.
 //
+// A class with a single running scan skips all of this and launches that scan's kernels directly
+// (the launches of pet_subiter): at light load a served scan then runs as fast as alone.
 // Descriptor buffers rotate over kBufs per class (the host may run that many ticks ahead of the
 // GPU).  Before each replay the tick's kernel nodes are fitted to its work: a kernel that no scan
 // needs this tick (the mu pass outside the dynamic-nu range, the objective between iteration ends)
@@ -51,23 +53,35 @@ struct BatchClass {
     // the instantiated graph (enabled, grid)
     cudaGraphNode_t knode[kBufs][kKinds] = {};
     cudaKernelNodeParams kparams[kBufs][kKinds] = {};
-    int kgrid[kBufs][kKinds] = {};
+    int kgrid[kBufs][kKinds] = {};            // grid each kernel node is set to (0: disabled)
     int next = 0;                             // descriptor buffer of the next tick
 
-    // layout of one descriptor buffer
-    size_t off_fwd = 0, off_upd = 0, off_mu = 0, off_objf = 0, off_objr = 0, off_pre = 0;
-    void layout()
+    cudaGraphNode_t mnode[kBufs] = {};       // the captured descriptor copy
+    int knsc[kBufs] = {};                     // scans each buffer's kernel nodes were set for
+
+    // Layout of a descriptor buffer holding n scans: the five prefix tables first, then the
+    // per-kind argument arrays.  The running scans of a tick are packed at positions 0..n-1,
+    // so only the first `bytes` of the buffer travel to the device.
+    struct Layout {
+        size_t off_pre, off[kKinds], bytes;   // kinds: mu, forward, update, objective x2
+        int n;
+    };
+    static Layout layout_for(int n)
     {
+        Layout L{};
         size_t o = 0;
-        auto take = [&](size_t n) { size_t r = o; o = (o + n + 255) / 256 * 256; return r; };
-        off_fwd = take(sizeof(FwdArgs) * cap);
-        off_upd = take(sizeof(UpdateArgs) * cap);
-        off_mu = take(sizeof(ImageArgs) * cap);
-        off_objf = take(sizeof(FwdArgs) * cap);
-        off_objr = take(sizeof(ImageArgs) * cap);
-        off_pre = take(sizeof(int) * 5 * (cap + 1));
-        bytes = o;
+        auto take = [&](size_t b) { size_t r = o; o = (o + b + 255) / 256 * 256; return r; };
+        L.n = n;
+        L.off_pre = take(sizeof(int) * kKinds * (n + 1));
+        L.off[0] = take(sizeof(ImageArgs) * n);
+        L.off[1] = take(sizeof(FwdArgs) * n);
+        L.off[2] = take(sizeof(UpdateArgs) * n);
+        L.off[3] = take(sizeof(FwdArgs) * n);
+        L.off[4] = take(sizeof(ImageArgs) * n);
+        L.bytes = o;
+        return L;
     }
+    void layout() { bytes = layout_for(cap).bytes; }
 };
 
 static int kc_of(const pet_state *s) { return s->g->dev.K <= 2 ? 2 : 4; }
@@ -232,15 +246,20 @@ extern "C" int pet_batch_size(const pet_batch *b)
     return n;
 }
 
-// The five batched launches of one class tick, reading descriptor buffer `dev`.  n: virtual
-// blocks per kind, or nullptr (graph capture: every kernel at the full persistent grid; the
-// replay fits them to each tick).  Without a graph a kernel with no work is skipped and the
-// others get grids of min(virtual blocks, persistent grid).
-static pet_status class_launches(pet_batch *b, BatchClass *c, const char *dev, const int *n,
-                                 cudaStream_t st, int *launched)
+// The Batch argument of kind t for descriptor layout L in device buffer `dev`.
+static Batch batch_arg(const BatchClass::Layout &L, const char *dev, int t, int grid)
 {
-    const int cap = c->cap;
-    const int *pre = reinterpret_cast<const int *>(dev + c->off_pre);
+    const int *pre = reinterpret_cast<const int *>(dev + L.off_pre);
+    return Batch{dev + L.off[t], pre + t * (L.n + 1), L.n, grid};
+}
+
+// The five batched launches of one class tick, reading descriptor buffer `dev` laid out as L.
+// n: virtual blocks per kind, or nullptr (graph capture: every kernel at the full persistent
+// grid; the replay fits them to each tick).  Without a graph a kernel with no work is skipped
+// and the others get grids of min(virtual blocks, persistent grid).
+static pet_status class_launches(pet_batch *b, BatchClass *c, const BatchClass::Layout &L,
+                                 const char *dev, const int *n, cudaStream_t st, int *launched)
+{
     // the shape structs only select the kernel instantiation (G, K); contents come from `dev`
     FwdArgs fs{};
     fs.g.G = c->G;
@@ -255,78 +274,112 @@ static pet_status class_launches(pet_batch *b, BatchClass *c, const char *dev, c
     is.z3 = c->z3;
     auto grid = [&](int t) { return n ? std::min(n[t], b->grid) : b->grid; };
     auto on = [&](int t) { return !n || n[t] > 0; };
-    Batch bm{dev + c->off_mu, pre + 0 * (cap + 1), cap, grid(0)};
-    Batch bf{dev + c->off_fwd, pre + 1 * (cap + 1), cap, grid(1)};
-    Batch bu{dev + c->off_upd, pre + 2 * (cap + 1), cap, grid(2)};
-    Batch bo{dev + c->off_objf, pre + 3 * (cap + 1), cap, grid(3)};
-    Batch br{dev + c->off_objr, pre + 4 * (cap + 1), cap, grid(4)};
     int cnt = 0;
     // mu passes on the side stream, joined before the update (a parallel branch in the graph)
     if (on(0)) {
         PET_CUDA(cudaEventRecord(b->ev_fork, st));
         PET_CUDA(cudaStreamWaitEvent(b->side, b->ev_fork, 0));
-        PET_TRY(launch_mu_sum_batch(is, bm, c->arith, b->side));
+        PET_TRY(launch_mu_sum_batch(is, batch_arg(L, dev, 0, grid(0)), c->arith, b->side));
         PET_CUDA(cudaEventRecord(b->ev_join, b->side));
         ++cnt;
     }
-    if (on(1)) { PET_TRY(launch_forward_batch(fs, bf, FWD_RATIO, c->arith, st)); ++cnt; }
+    if (on(1)) { PET_TRY(launch_forward_batch(fs, batch_arg(L, dev, 1, grid(1)), FWD_RATIO, c->arith, st)); ++cnt; }
     if (on(0)) PET_CUDA(cudaStreamWaitEvent(st, b->ev_join, 0));
-    if (on(2)) { PET_TRY(launch_update_batch(us, bu, c->arith, st)); ++cnt; }
-    if (on(3)) { PET_TRY(launch_forward_batch(fs, bo, FWD_OBJECTIVE, c->arith, st)); ++cnt; }
-    if (on(4)) { PET_TRY(launch_rdp_value_batch(is, br, c->arith, st)); ++cnt; }
+    if (on(2)) { PET_TRY(launch_update_batch(us, batch_arg(L, dev, 2, grid(2)), c->arith, st)); ++cnt; }
+    if (on(3)) { PET_TRY(launch_forward_batch(fs, batch_arg(L, dev, 3, grid(3)), FWD_OBJECTIVE, c->arith, st)); ++cnt; }
+    if (on(4)) { PET_TRY(launch_rdp_value_batch(is, batch_arg(L, dev, 4, grid(4)), c->arith, st)); ++cnt; }
     if (launched) *launched = cnt;
     return PET_OK;
 }
 
-// Finds the captured graph's kernel node of each kind (by the descriptor array its Batch
-// argument points to) and keeps its parameters for the per-tick updates.
-static pet_status index_kernel_nodes(BatchClass *c, int buf)
+// Finds the captured graph's descriptor copy and the kernel node of each kind (by the argument
+// array its Batch argument points to, in the capture layout L) and keeps the kernel parameters
+// for the per-tick updates.
+static pet_status index_nodes(BatchClass *c, int buf, const BatchClass::Layout &L)
 {
     size_t nn = 0;
     PET_CUDA(cudaGraphGetNodes(c->graph[buf], nullptr, &nn));
     std::vector<cudaGraphNode_t> nodes(nn);
     PET_CUDA(cudaGraphGetNodes(c->graph[buf], nodes.data(), &nn));
-    const size_t off[kKinds] = {c->off_mu, c->off_fwd, c->off_upd, c->off_objf, c->off_objr};
     int found = 0;
+    c->mnode[buf] = nullptr;
     for (cudaGraphNode_t nd : nodes) {
         cudaGraphNodeType ty;
         PET_CUDA(cudaGraphNodeGetType(nd, &ty));
+        if (ty == cudaGraphNodeTypeMemcpy) { c->mnode[buf] = nd; continue; }
         if (ty != cudaGraphNodeTypeKernel) continue;
         cudaKernelNodeParams kp;
         PET_CUDA(cudaGraphKernelNodeGetParams(nd, &kp));
         const Batch *bt = reinterpret_cast<const Batch *>(kp.kernelParams[1]);
         for (int t = 0; t < kKinds; ++t)
-            if (bt->args == c->dev[buf] + off[t]) {
+            if (bt->args == c->dev[buf] + L.off[t]) {
                 c->knode[buf][t] = nd;
                 c->kparams[buf][t] = kp;
                 c->kgrid[buf][t] = (int)kp.gridDim.x;
                 ++found;
             }
     }
-    if (found != kKinds) return fail(PET_ERR_CUDA, "pet_batch: captured graph lacks a kernel node");
+    c->knsc[buf] = L.n;
+    if (found != kKinds || !c->mnode[buf])
+        return fail(PET_ERR_CUDA, "pet_batch: captured graph lacks a node");
     return PET_OK;
 }
 
-// Fits the instantiated graph of buffer `buf` to this tick: kernels without work disabled,
-// the others' grids cut to their virtual blocks.  Returns the kernels that will run.
-static pet_status fit_graph(pet_batch *b, BatchClass *c, int buf, const int *n, int *launched)
+// Fits the instantiated graph of buffer `buf` to this tick: the descriptor copy to the packed
+// layout L, kernels without work disabled, the others pointed at L and their grids cut to their
+// virtual blocks.  Returns the kernels that will run.
+static pet_status fit_graph(pet_batch *b, BatchClass *c, int buf, const BatchClass::Layout &L,
+                            const int *n, int *launched)
 {
+    PET_CUDA(cudaGraphExecMemcpyNodeSetParams1D(c->exec[buf], c->mnode[buf], c->dev[buf],
+                                                c->host[buf], L.bytes, cudaMemcpyHostToDevice));
+    const bool relayout = c->knsc[buf] != L.n;
     int cnt = 0;
     for (int t = 0; t < kKinds; ++t) {
         const int want = n[t] > 0 ? std::min(n[t], b->grid) : 0;
-        if (want == c->kgrid[buf][t]) { cnt += want > 0; continue; }
         if (want == 0) {
-            PET_CUDA(cudaGraphNodeSetEnabled(c->exec[buf], c->knode[buf][t], 0));
-        } else {
-            if (c->kgrid[buf][t] == 0) PET_CUDA(cudaGraphNodeSetEnabled(c->exec[buf], c->knode[buf][t], 1));
-            cudaKernelNodeParams kp = c->kparams[buf][t];
-            kp.gridDim.x = (unsigned)want;
-            PET_CUDA(cudaGraphExecKernelNodeSetParams(c->exec[buf], c->knode[buf][t], &kp));
-            ++cnt;
+            if (c->kgrid[buf][t] != 0)
+                PET_CUDA(cudaGraphNodeSetEnabled(c->exec[buf], c->knode[buf][t], 0));
+            c->kgrid[buf][t] = 0;
+            continue;
         }
+        ++cnt;
+        if (want == c->kgrid[buf][t] && !relayout) continue;
+        if (c->kgrid[buf][t] == 0) PET_CUDA(cudaGraphNodeSetEnabled(c->exec[buf], c->knode[buf][t], 1));
+        cudaKernelNodeParams kp = c->kparams[buf][t];
+        Batch arg = batch_arg(L, c->dev[buf], t, want);
+        void *params[2] = {kp.kernelParams[0], &arg};
+        kp.kernelParams = params;
+        kp.gridDim.x = (unsigned)want;
+        PET_CUDA(cudaGraphExecKernelNodeSetParams(c->exec[buf], c->knode[buf][t], &kp));
         c->kgrid[buf][t] = want;
     }
+    // a disabled node keeps its old arguments; it is re-pointed when it is enabled again
+    c->knsc[buf] = L.n;
     *launched = cnt;
+    return PET_OK;
+}
+
+// A class with one running scan: the scan's own launches (the kernels and shapes of
+// pet_subiter, so the same bits), without descriptor upload or graph replay.
+static pet_status solo_tick(pet_batch *b, BatchClass *c, int k, cudaStream_t st)
+{
+    pet_state *s = c->slot[k];
+    SubiterPlan pl;
+    plan_subiter(s, &pl, c->objective[k]);
+    if (pl.mu) {
+        PET_CUDA(cudaEventRecord(b->ev_fork, st));
+        PET_CUDA(cudaStreamWaitEvent(b->side, b->ev_fork, 0));
+        PET_TRY(launch_mu_sum(pl.mu_args, pl.arith, b->side));
+        PET_CUDA(cudaEventRecord(b->ev_join, b->side));
+    }
+    PET_TRY(launch_forward(pl.fwd, FWD_RATIO, pl.arith, st));
+    if (pl.mu) PET_CUDA(cudaStreamWaitEvent(st, b->ev_join, 0));
+    PET_TRY(launch_update(pl.upd, pl.arith, st));
+    if (pl.objective) {
+        PET_TRY(launch_forward(pl.obj_fwd, FWD_OBJECTIVE, pl.arith, st));
+        PET_TRY(launch_rdp_value(pl.obj_rdp, pl.arith, st));
+    }
     return PET_OK;
 }
 
@@ -336,36 +389,49 @@ static pet_status class_tick(pet_batch *b, BatchClass *c, cudaStream_t st, int *
     const int buf = c->next;
     c->next = (c->next + 1) % kBufs;
     if (c->used[buf]) PET_CUDA(cudaEventSynchronize(c->done[buf]));   // host may now overwrite it
+    int nrun = 0, solo = -1;
+    for (int k = 0; k < cap; ++k)
+        if (running(c->slot[k])) { ++nrun; solo = k; }
+    if (nrun == 1) {
+        PET_TRY(solo_tick(b, c, solo, st));
+        if (running(c->slot[solo])) ++*running_after;
+        PET_CUDA(cudaEventRecord(c->done[buf], st));
+        c->used[buf] = true;
+        return PET_OK;
+    }
+    // pack the running scans' arguments at positions 0..nrun-1 of the tick's layout
+    const BatchClass::Layout L = BatchClass::layout_for(nrun);
     char *h = c->host[buf];
-    FwdArgs *fwd = reinterpret_cast<FwdArgs *>(h + c->off_fwd);
-    UpdateArgs *upd = reinterpret_cast<UpdateArgs *>(h + c->off_upd);
-    ImageArgs *mu = reinterpret_cast<ImageArgs *>(h + c->off_mu);
-    FwdArgs *objf = reinterpret_cast<FwdArgs *>(h + c->off_objf);
-    ImageArgs *objr = reinterpret_cast<ImageArgs *>(h + c->off_objr);
-    int *pre = reinterpret_cast<int *>(h + c->off_pre);
+    ImageArgs *mu = reinterpret_cast<ImageArgs *>(h + L.off[0]);
+    FwdArgs *fwd = reinterpret_cast<FwdArgs *>(h + L.off[1]);
+    UpdateArgs *upd = reinterpret_cast<UpdateArgs *>(h + L.off[2]);
+    FwdArgs *objf = reinterpret_cast<FwdArgs *>(h + L.off[3]);
+    ImageArgs *objr = reinterpret_cast<ImageArgs *>(h + L.off[4]);
+    int *pre = reinterpret_cast<int *>(h + L.off_pre);
     int n[kKinds] = {0, 0, 0, 0, 0};
-    for (int k = 0; k <= cap; ++k) {
-        for (int t = 0; t < kKinds; ++t) pre[t * (cap + 1) + k] = n[t];
-        if (k == cap) break;
+    int pos = 0;
+    for (int k = 0; k < cap; ++k) {
         pet_state *s = c->slot[k];
         if (!running(s)) continue;
+        for (int t = 0; t < kKinds; ++t) pre[t * (nrun + 1) + pos] = n[t];
         SubiterPlan pl;
         plan_subiter(s, &pl, c->objective[k]);
-        mu[k] = pl.mu_args;
-        fwd[k] = pl.fwd;
-        upd[k] = pl.upd;
+        mu[pos] = pl.mu_args;
+        fwd[pos] = pl.fwd;
+        upd[pos] = pl.upd;
         if (pl.mu) n[0] += pl.mu_args.nvb;
         n[1] += pl.fwd.nvb;
         n[2] += pl.upd.nvb;
         if (pl.objective) {
-            objf[k] = pl.obj_fwd;
-            objr[k] = pl.obj_rdp;
+            objf[pos] = pl.obj_fwd;
+            objr[pos] = pl.obj_rdp;
             n[3] += pl.obj_fwd.nvb;
             n[4] += pl.obj_rdp.nvb;
         }
         if (running(s)) ++*running_after;
+        ++pos;
     }
-    // prefix tables must close at the totals; the loop above wrote pre[t][cap] = n[t]
+    for (int t = 0; t < kKinds; ++t) pre[t * (nrun + 1) + nrun] = n[t];   // tables close at the totals
     int launched = 0;
     if (b->use_graph && st != nullptr) {       // the legacy default stream cannot be captured
         if (!c->exec[buf] || c->exec_stream[buf] != st) {
@@ -375,25 +441,25 @@ static pet_status class_tick(pet_batch *b, BatchClass *c, cudaStream_t st, int *
             c->graph[buf] = nullptr;
             cudaGraph_t graph = nullptr;
             PET_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-            cudaError_t e = cudaMemcpyAsync(c->dev[buf], c->host[buf], c->bytes,
+            cudaError_t e = cudaMemcpyAsync(c->dev[buf], c->host[buf], L.bytes,
                                             cudaMemcpyHostToDevice, st);
-            pet_status ls = e == cudaSuccess ? class_launches(b, c, c->dev[buf], nullptr, st, nullptr)
+            pet_status ls = e == cudaSuccess ? class_launches(b, c, L, c->dev[buf], nullptr, st, nullptr)
                                              : cuda_fail(e, "pet_batch: descriptor copy");
             cudaError_t ec = cudaStreamEndCapture(st, &graph);
             if (ls != PET_OK) { if (graph) cudaGraphDestroy(graph); return ls; }
             if (ec != cudaSuccess) return cuda_fail(ec, "pet_batch: end capture");
-            c->graph[buf] = graph;                 // kept: its nodes address the kernel updates
-            PET_TRY(index_kernel_nodes(c, buf));
+            c->graph[buf] = graph;                 // kept: its nodes address the per-tick updates
+            PET_TRY(index_nodes(c, buf, L));
             e = cudaGraphInstantiate(&c->exec[buf], graph, 0);
             if (e != cudaSuccess) return cuda_fail(e, "pet_batch: graph instantiate");
             c->exec_stream[buf] = st;
         }
-        PET_TRY(fit_graph(b, c, buf, n, &launched));
+        PET_TRY(fit_graph(b, c, buf, L, n, &launched));
         PET_CUDA(cudaGraphLaunch(c->exec[buf], st));
         count_launches(launched);
     } else {
-        PET_CUDA(cudaMemcpyAsync(c->dev[buf], c->host[buf], c->bytes, cudaMemcpyHostToDevice, st));
-        PET_TRY(class_launches(b, c, c->dev[buf], n, st, &launched));
+        PET_CUDA(cudaMemcpyAsync(c->dev[buf], c->host[buf], L.bytes, cudaMemcpyHostToDevice, st));
+        PET_TRY(class_launches(b, c, L, c->dev[buf], n, st, &launched));
     }
     PET_CUDA(cudaEventRecord(c->done[buf], st));
     c->used[buf] = true;
