@@ -99,7 +99,20 @@ typedef struct {
                            reconstructions of Sec. IV-C): RDP over the 26 neighbours in the volume
                            (Eqs. RDP, gradRD) and nu from the gradient with its component across
                            the planes (Sec. III) */
+    int regularizer;    /* pet_regularizer: PET_REG_RDP (the paper's prior, by its gradient) or
+                           PET_REG_TV (no counterpart in the paper's method, which names TV only as
+                           a non-smooth example): R_TV(f) = sum_j |(D f)_j|, D the in-plane forward
+                           differences, entering each subiteration through a proximal step in the
+                           metric of the step sizes, W = lambda_k alpha_{k,i} nu S(f):
+                           z = f - W grad F_i(f); f = P_t(argmin_x 1/2 |x - z|^2_{W^-1}
+                           + (beta/M) R_TV(x)), the argmin approximated by tv_iters primal-dual
+                           (Chambolle-Pock) iterations warm-started from the previous dual
+                           variable.  TV runs through pet_subiter / pet_reconstruct (not in
+                           batches or the server), in-plane only (rdp_3d = 0). */
+    int tv_iters;       /* primal-dual iterations per subiteration (PET_REG_TV), 1..10000 */
 } pet_params;
+
+typedef enum { PET_REG_RDP = 0, PET_REG_TV = 1 } pet_regularizer;
 
 typedef struct pet_geometry pet_geometry;
 typedef struct pet_state pet_state;
@@ -229,6 +242,17 @@ pet_status pet_smoothness_nu_3d(const pet_geometry *g, const float *d_img, doubl
 pet_status pet_objective_3d(const pet_geometry *g, const int32_t *d_counts, const float *d_gamma,
                             const float *d_img, double beta, double gamma_r, double eps,
                             double *h_phi, double *h_parts, void *stream);
+/* TV variant (pet_params.regularizer = PET_REG_TV; no counterpart in the paper's method).
+ * pet_objective_tv: Phi with R = R_TV; h_parts[2] = R_TV(d_img).  Synchronises.
+ * pet_tv_prox: d_x = the primal-dual approximation (iters Chambolle-Pock iterations, steps
+ *   sigma = 1/(2b), tau = 1/(4b)) of argmin_x 1/2 sum_j (x_j - z_j)^2 / W_j + b R_TV(x), from
+ *   x = z and the dual variable (d_px, d_py), which is updated in place.  All arrays float
+ *   [P][N][N]; W > 0; b >= 0 (b = 0 copies z). */
+pet_status pet_objective_tv(const pet_geometry *g, const int32_t *d_counts, const float *d_gamma,
+                            const float *d_img, double beta, double *h_phi, double *h_parts,
+                            void *stream);
+pet_status pet_tv_prox(const pet_geometry *g, const float *d_z, const float *d_w, double b,
+                       int iters, float *d_px, float *d_py, float *d_x, void *stream);
 
 /* ------------------------------------------------------------------------------------------
  * Batches (Table I for many independent scans at once; no counterpart in the paper).

@@ -46,7 +46,7 @@ class Params(ctypes.Structure):
         (k, ctypes.c_double) for k in ("beta", "gamma_r", "eps", "t", "U", "lambda0", "a",
                                        "rho", "delta1", "delta2", "nu1", "nu2")] + [
         ("J0", ctypes.c_int), ("J1", ctypes.c_int), ("precond", ctypes.c_int),
-        ("rdp3d", ctypes.c_int)]
+        ("rdp3d", ctypes.c_int), ("reg", ctypes.c_int), ("tv_iters", ctypes.c_int)]
 
 
 def lib():
@@ -78,6 +78,10 @@ def lib():
             L.ora_matlab_gradient_z.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp]
             L.ora_objective3.argtypes = [gp, ip, fp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                          ctypes.c_int, dp]
+            L.ora_tv_value.argtypes = [ctypes.c_int, ctypes.c_int, dp]
+            L.ora_tv_value.restype = ctypes.c_double
+            L.ora_tv_prox.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_double, ctypes.c_int,
+                                      dp, dp, dp]
             L.ora_alpha_nesterov.argtypes = [ctypes.c_int, dp]
             L.ora_alpha_km.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
             L.ora_objective.argtypes = [gp, ip, fp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
@@ -187,6 +191,28 @@ def nu_from_image(f, nu1, nu2, three_d=False) -> np.ndarray:
     return out
 
 
+def tv_value(f) -> float:
+    """R_TV(f): isotropic total variation, in-plane forward differences (TV variant)."""
+    f, fp = _d(f)
+    P, N = (1,) + f.shape if f.ndim == 2 else f.shape[:2]
+    return lib().ora_tv_value(N, P, fp)
+
+
+def tv_prox(z, W, b, iters, p=None):
+    """Primal-dual approximation of argmin_x 1/2 sum (x - z)^2 / W + b R_TV(x); returns
+    (x, (px, py)) with the dual variable updated from `p` (zeros if None)."""
+    z, zp = _d(z)
+    W, Wp = _d(W)
+    P, N = z.shape[:2]
+    px = np.zeros_like(z) if p is None else np.array(p[0], dtype=np.float64, order="C")
+    py = np.zeros_like(z) if p is None else np.array(p[1], dtype=np.float64, order="C")
+    x = np.zeros_like(z)
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib().ora_tv_prox(N, P, zp, Wp, b, iters, px.ctypes.data_as(dp), py.ctypes.data_as(dp),
+                      x.ctypes.data_as(dp))
+    return x, (px, py)
+
+
 def alpha_nesterov(nsub: int) -> np.ndarray:
     out = np.zeros(nsub)
     lib().ora_alpha_nesterov(nsub, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
@@ -199,15 +225,17 @@ def alpha_km(nsub: int, rho: float, delta1: float, delta2: float) -> np.ndarray:
     return out
 
 
-def objective(g: Geom, counts, gamma, f, beta, gamma_r=2.0, eps=1e-12, three_d=False) -> dict:
-    """Phi(f) and its parts: sum(Af), sum(g ln(Af + gamma)), R(f)."""
+def objective(g: Geom, counts, gamma, f, beta, gamma_r=2.0, eps=1e-12, three_d=False,
+              tv=False) -> dict:
+    """Phi(f) and its parts: sum(Af), sum(g ln(Af + gamma)), R(f) (R_TV with tv)."""
     counts = np.ascontiguousarray(counts, dtype=np.int32)
     gamma = np.ascontiguousarray(gamma, dtype=np.float32)
     f, fp = _d(f)
     out = np.zeros(4)
     lib().ora_objective3(ctypes.byref(g), counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
                          gamma.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), fp, beta, gamma_r,
-                         eps, 1 if three_d else 0, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+                         eps, 2 if tv else (1 if three_d else 0),
+                         out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
     return dict(sum_af=out[0], sum_glog=out[1], rdp=out[2], phi=out[3])
 
 
@@ -215,7 +243,8 @@ def params_from(p) -> Params:
     """Oracle parameters from an object with the AlgoParams attribute names."""
     return Params(p.iterations, p.beta, p.gamma_r, p.eps, p.t, p.U, p.lambda0, p.a, p.rho,
                   p.delta1, p.delta2, p.nu1, p.nu2, p.J0, p.J1, p.precond,
-                  int(getattr(p, "rdp3d", 0)))
+                  int(getattr(p, "rdp3d", 0)), int(getattr(p, "reg", 0)),
+                  int(getattr(p, "tv_iters", 10)))
 
 
 def reconstruct(g: Geom, counts, gamma, params, f0, nsub: int = -1, with_objective=False):

@@ -17,6 +17,9 @@
  *   - grad F, dR/df_j ................................ Appendix A, Eq. gradRD
  *   - fully 3-D RDP (26 neighbours) and 3-D smoothness map, for volumes reconstructed as one
  *     3-D image (Sec. IV-C) ......................... Eqs. RDP, gradRD, nuki over 3-D neighbours
+ *   - TV variant: total variation (named in Sec. I as the typical non-smooth prior) entering
+ *     Table I's step through a proximal step in the preconditioner's metric, computed by the
+ *     primal-dual method of Chambolle and Pock (2011) ...... see ora_tv_prox
  *
  * System model: one line per detector bin, parallel beam; A_ij = sens * (length in mm of
  * ray i inside pixel j), where a pixel is the half-open square [x, x+1) x [y, y+1) in pixel
@@ -50,6 +53,8 @@ typedef struct {
     int J0, J1;
     int precond;     /* 0 BSREM, 1 M1, 2 M2, 3 P1, 4 P2 */
     int rdp3d;       /* 0: 8 in-plane neighbours (Sec. IV-A); 1: 26 neighbours in 3-D */
+    int reg;         /* 0: RDP by its gradient (the paper); 1: TV by a proximal step */
+    int tv_iters;    /* primal-dual iterations per proximal step (reg = 1) */
 } ora_params;
 
 /* ---------------------------------------------------------------------------------------
@@ -402,6 +407,78 @@ void ora_nu_from_image(int N, int P, const double *f, double nu1, double nu2, do
 }
 
 /* ---------------------------------------------------------------------------------------
+ * TV variant.  R_TV(f) = sum_j |(D f)_j| (isotropic total variation, in-plane): (D f)_j =
+ * (f_{j+x} - f_j, f_{j+y} - f_j), a component being 0 across the last column / row, |.| the
+ * Euclidean norm.  The paper handles its smooth prior by the gradient; a non-smooth prior enters
+ * the same preconditioned step through its proximal operator in the metric of the step sizes:
+ *   z = f - W grad F_i(f),   W_j = lambda_k alpha_{k,i} nu_j S_jj(f)
+ *   x = argmin_x 1/2 sum_j (x_j - z_j)^2 / W_j + b R_TV(x),   b = beta / M,   f+ = P_t(x)
+ * ora_tv_prox approximates x by `iters` iterations of the first-order primal-dual algorithm of
+ * Chambolle and Pock (J. Math. Imaging Vis. 40, 2011) for min_x G(x) + F(K x), G the weighted
+ * quadratic, K = b D, F the sum of Euclidean norms, with the diagonal step sizes of Pock and
+ * Chambolle (ICCV 2011) for this K: sigma = 1 / (2 b) for every dual component (each row of K
+ * holds b and -b) and tau = 1 / (4 b) for every voxel (a column holds at most four entries
+ * +-b).  One iteration, from x = xbar = z and the dual p (one 2-vector per voxel):
+ *   p    <- proj_{|p_j| <= 1}(p + sigma K xbar)            (sigma K = D / 2)
+ *   x'    = (x - tau K^T p + (tau / W) z) / (1 + tau / W)  (tau K^T p = -div(p) / 4)
+ *   xbar  = 2 x' - x,   x = x'
+ * div(p)_j = p^x_j - p^x_{j-x} + p^y_j - p^y_{j-y}, terms outside the plane are 0.  p is in/out:
+ * the loop keeps it from one subiteration to the next (0 at the start).  b = 0 gives x = z.
+ * ------------------------------------------------------------------------------------- */
+double ora_tv_value(int N, int P, const double *f)
+{
+    double R = 0.0;
+    for (int p = 0; p < P; ++p) {
+        const double *fp = f + (size_t)p * N * N;
+        for (int iy = 0; iy < N; ++iy)
+            for (int ix = 0; ix < N; ++ix) {
+                const double c = fp[iy * N + ix];
+                const double gx = ix + 1 < N ? fp[iy * N + ix + 1] - c : 0.0;
+                const double gy = iy + 1 < N ? fp[(iy + 1) * N + ix] - c : 0.0;
+                R += sqrt(gx * gx + gy * gy);
+            }
+    }
+    return R;
+}
+
+void ora_tv_prox(int N, int P, const double *z, const double *W, double b, int iters,
+                 double *px, double *py, double *x)
+{
+    const size_t q = (size_t)N * N * P;
+    memcpy(x, z, sizeof(double) * q);
+    if (!(b > 0.0)) return;
+    double *xbar = (double *)malloc(sizeof(double) * q);
+    memcpy(xbar, z, sizeof(double) * q);
+    const double sigma_b = 0.5, tau = 1.0 / (4.0 * b);
+    for (int it = 0; it < iters; ++it) {
+        for (int p = 0; p < P; ++p)
+            for (int iy = 0; iy < N; ++iy)
+                for (int ix = 0; ix < N; ++ix) {
+                    const size_t j = ((size_t)p * N + iy) * N + ix;
+                    const double gx = ix + 1 < N ? xbar[j + 1] - xbar[j] : 0.0;
+                    const double gy = iy + 1 < N ? xbar[j + N] - xbar[j] : 0.0;
+                    const double qx = px[j] + sigma_b * gx, qy = py[j] + sigma_b * gy;
+                    const double nq = sqrt(qx * qx + qy * qy);
+                    const double sc = nq > 1.0 ? 1.0 / nq : 1.0;
+                    px[j] = qx * sc;
+                    py[j] = qy * sc;
+                }
+        for (int p = 0; p < P; ++p)
+            for (int iy = 0; iy < N; ++iy)
+                for (int ix = 0; ix < N; ++ix) {
+                    const size_t j = ((size_t)p * N + iy) * N + ix;
+                    const double div = px[j] - (ix > 0 ? px[j - 1] : 0.0) + py[j] -
+                                       (iy > 0 ? py[j - N] : 0.0);
+                    const double r = tau / W[j];
+                    const double xn = (x[j] + 0.25 * div + r * z[j]) / (1.0 + r);
+                    xbar[j] = 2.0 * xn - x[j];
+                    x[j] = xn;
+                }
+    }
+    free(xbar);
+}
+
+/* ---------------------------------------------------------------------------------------
  * Scalar schedules (Sec. III).  alpha for subiterations J = 1..nsub in order.
  * ------------------------------------------------------------------------------------- */
 /* Eq. preconditioner:Nesterov: alpha = 1 + (t_J - 1) / t_{J+1}, t_{J+1} = (1 + sqrt(1 + 4 t_J^2)) / 2,
@@ -436,7 +513,8 @@ void ora_objective(const ora_geom *g, const int *counts, const float *gamma, con
     ora_objective3(g, counts, gamma, f, beta, gamma_r, eps, 0, out);
 }
 
-/* As ora_objective; three_d != 0 takes R over the 26 neighbours of each voxel. */
+/* As ora_objective; three_d == 1 takes R over the 26 neighbours of each voxel, three_d == 2
+   takes R = R_TV (the TV variant). */
 void ora_objective3(const ora_geom *g, const int *counts, const float *gamma, const double *f,
                     double beta, double gamma_r, double eps, int three_d, double *out)
 {
@@ -448,8 +526,9 @@ void ora_objective3(const ora_geom *g, const int *counts, const float *gamma, co
         s1 += y[k];
         s2 += (double)counts[k] * log(y[k] + (double)gamma[k]);
     }
-    double R = three_d ? ora_rdp_value3(g->n, g->nplanes, f, gamma_r, eps)
-                       : ora_rdp_value(g->n, g->nplanes, f, gamma_r, eps);
+    double R = three_d == 2 ? ora_tv_value(g->n, g->nplanes, f)
+               : three_d ? ora_rdp_value3(g->n, g->nplanes, f, gamma_r, eps)
+                         : ora_rdp_value(g->n, g->nplanes, f, gamma_r, eps);
     out[0] = s1; out[1] = s2; out[2] = R; out[3] = s1 - s2 + beta * R;
     free(y);
 }
@@ -503,8 +582,16 @@ void ora_reconstruct_snap(const ora_geom *g, const int *counts, const float *gam
     int *views = (int *)malloc(sizeof(int) * g->nviews);
     double *ysub = (double *)malloc(sizeof(double) * (size_t)P * g->nviews * NB);
 
-    const int z3 = prm->rdp3d;
-    if (obj) { double o[4]; ora_objective3(g, counts, gamma, f, prm->beta, prm->gamma_r, prm->eps, z3, o); obj[0] = o[3]; }
+    const int z3 = prm->rdp3d, tv = prm->reg == 1;
+    const int rmode = tv ? 2 : z3;                      /* regulariser of the objective */
+    double *px = NULL, *py = NULL, *W = NULL, *zz = NULL;
+    if (tv) {
+        px = (double *)calloc(q, sizeof(double));
+        py = (double *)calloc(q, sizeof(double));
+        W = (double *)malloc(sizeof(double) * q);
+        zz = (double *)malloc(sizeof(double) * q);
+    }
+    if (obj) { double o[4]; ora_objective3(g, counts, gamma, f, prm->beta, prm->gamma_r, prm->eps, rmode, o); obj[0] = o[3]; }
     for (int J = 1; J <= nsub; ++J) {
         const int k = (J - 1) / M, i = (J - 1) % M + 1;
         const double lambda = prm->lambda0 / (prm->a * k + 1.0);
@@ -532,6 +619,20 @@ void ora_reconstruct_snap(const ora_geom *g, const int *counts, const float *gam
                     ysub[ks] = 1.0 - (double)counts[kf] / (ysub[ks] + (double)gamma[kf]);
                 }
         ora_back(g, subset, ysub, grad);
+        if (tv) {
+            /* TV variant: the data step, then the proximal step of (beta / M) R_TV */
+            for (size_t j = 0; j < q; ++j) {
+                const double fj = f[j], pjj = pj[j % npix];
+                const double S = fj < 0.5 * prm->U ? fj / pjj : (prm->U - fj) / pjj;
+                W[j] = lambda * alpha[J - 1] * nu[j] * S;
+                zz[j] = fj - W[j] * grad[j];
+            }
+            ora_tv_prox(N, P, zz, W, prm->beta / M, prm->tv_iters, px, py, f);
+            for (size_t j = 0; j < q; ++j) {
+                if (f[j] <= 0.0) f[j] = prm->t;
+                else if (f[j] >= prm->U) f[j] = prm->U - prm->t;
+            }
+        } else {
         /* penalty term (beta / M) grad R  (Eq. SubObjFunc, Eq. gradRD) */
         if (z3) ora_rdp_grad3(N, P, f, prm->gamma_r, prm->eps, rgrad);
         else ora_rdp_grad(N, P, f, prm->gamma_r, prm->eps, rgrad);
@@ -544,13 +645,14 @@ void ora_reconstruct_snap(const ora_geom *g, const int *counts, const float *gam
             else if (ft >= prm->U) ft = prm->U - prm->t;
             f[j] = ft;
         }
+        }
         if (obj && i == M) {
             double o[4];
-            ora_objective3(g, counts, gamma, f, prm->beta, prm->gamma_r, prm->eps, z3, o);
+            ora_objective3(g, counts, gamma, f, prm->beta, prm->gamma_r, prm->eps, rmode, o);
             obj[k + 1] = o[3];
         }
         if (snaps && i == M) memcpy(snaps + (size_t)k * q, f, sizeof(double) * q);
     }
     free(pj); free(alpha); free(nu); free(nu_frozen); free(grad); free(rgrad);
-    free(views); free(ysub);
+    free(views); free(ysub); free(px); free(py); free(W); free(zz);
 }

@@ -179,6 +179,8 @@ static pet_status class_for(pet_batch *b, pet_state *s, BatchClass **out)
 extern "C" pet_status pet_batch_add(pet_batch *b, pet_state *s, int with_objective, void *stream)
 {
     if (!b || !s) return fail(PET_ERR_INVALID, "pet_batch_add: NULL argument");
+    if (s->prm.regularizer == PET_REG_TV)
+        return fail(PET_ERR_INVALID, "pet_batch_add: the TV variant runs through pet_subiter / pet_reconstruct");
     for (BatchClass *c : b->classes)
         for (pet_state *x : c->slot)
             if (x == s) return fail(PET_ERR_INVALID, "pet_batch_add: state already in the batch");

@@ -164,6 +164,8 @@ struct UpdateArgs {
     int tpv;                   // pixel tiles per virtual block
     int nvb;                   // virtual blocks of this scan
     int z3;                    // 1: RDP over the 26 neighbours in 3-D, nu from the 3-D gradient
+    int tv;                    // 1: TV variant: write z = f - W grad F_i (no clamp) to fout and
+    void *zbuf, *wbuf;         //    zbuf, and W = lambda alpha nu S to wbuf ([N*N][Pp])
     // the scalars above as FP32 for the FP32 kernels (converted once on the host: a conversion
     // from double on the device runs on the narrow FP64 pipe)
     float fs_lam, fs_bm, fs_gamma_r, fs_eps, fs_t, fs_U, fs_nu1, fs_nu2, fs_ips, fs_scale;
@@ -187,6 +189,7 @@ struct ImageArgs {
     Reducer red;
     int ipt, nvb;              // items per thread, virtual blocks of this scan
     int z3;                    // 1: RDP over the 26 neighbours in 3-D, gradient with its z part
+    int tv;                    // RDP value kernel: the total variation R_TV instead
 };
 pet_status launch_sum(const ImageArgs &a, int arith, cudaStream_t st);        // result[0] = sum f
 pet_status launch_mu_sum(const ImageArgs &a, int arith, cudaStream_t st);     // result[0] = sum mu
@@ -213,6 +216,7 @@ struct pet_state {
     float *gamma = nullptr;
     void *nu_frozen = nullptr;
     bool have_frozen = false;
+    void *tvmem = nullptr;          // TV variant: z, W, xbar, px, py (each q_bytes)
     double *sums = nullptr;         // [0..1] sum f (ping-pong), [2] sum mu, [3..5] objective
     double *objhist = nullptr;      // [(T+1) * 3] objective parts per outer iteration
     int objcap = 0;
@@ -239,8 +243,27 @@ struct pet_state {
 
 namespace pet {
 
+// Proximal step of the TV variant: primal-dual iterations on internal images [N*N][Pp].
+struct TvArgs {
+    GeoDev g;
+    void *x;                   // in: z, out: the proximal point (clamped by P_t on the last step)
+    void *xbar;                // extrapolated primal iterate
+    const void *z, *w;         // z = f - W grad F_i and the metric W
+    void *px, *py;             // dual variable (kept across subiterations)
+    double b;                  // beta / M
+    double t, U;               // P_t
+    Reducer red;
+    double *sum_out;           // sum of the clamped result (last step)
+    int ipt, nvb;
+};
+void tv_shape(TvArgs &a);
+pet_status launch_tv_prox(const TvArgs &a, int iters, int arith, cudaStream_t st);
+
 struct SubiterPlan {
     int arith;
+    bool tv;                   // TV variant: proximal step after the update
+    int tv_iters;
+    TvArgs tv_args;
     bool mu;                   // mu pass needed (dynamic nu)
     ImageArgs mu_args;
     FwdArgs fwd;               // subset forward projection + ratio

@@ -475,6 +475,8 @@ extern "C" pet_status pet_serve_submit(pet_server *sv, const pet_request *rq, ui
         d.nsubsets > d.nviews || !(d.pixel_mm > 0) || !(d.bin_mm > 0) || !(d.sens > 0))
         return fail(PET_ERR_INVALID, "pet_serve_submit: invalid geometry description");
     PET_TRY(check_params(&rq->params));
+    if (rq->params.regularizer == PET_REG_TV)
+        return fail(PET_ERR_INVALID, "pet_serve_submit: the TV variant runs through pet_reconstruct");
     const size_t nsino = (size_t)d.nplanes * d.nviews * d.nbins, nimg = (size_t)d.nplanes * d.n * d.n;
     for (size_t k = 0; k < nsino; ++k)
         if (rq->h_counts[k] < 0 || !(rq->h_gamma[k] > 0.f) || !isfinite(rq->h_gamma[k]))

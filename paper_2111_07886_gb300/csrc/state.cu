@@ -27,11 +27,14 @@ pet_status pet::check_params(const pet_params *p)
         !(p->U > 0) || !(p->t > 0) || !(p->t < p->U) || !(p->lambda0 > 0) || !(p->a >= 0) ||
         !(p->nu1 > 0) || !(p->nu2 >= p->nu1) || p->precond < 0 || p->precond > 4 ||
         p->precision < 0 || p->precision > 2 || !(p->delta1 > 0) || !(p->rho > 0) ||
-        !(p->delta2 > 0) || p->J0 < 0 || p->J1 < p->J0 || p->rdp_3d < 0 || p->rdp_3d > 1)
+        !(p->delta2 > 0) || p->J0 < 0 || p->J1 < p->J0 || p->rdp_3d < 0 || p->rdp_3d > 1 ||
+        p->regularizer < 0 || p->regularizer > 1 ||
+        (p->regularizer == PET_REG_TV && (p->tv_iters < 1 || p->tv_iters > 10000 || p->rdp_3d)))
         return fail(PET_ERR_INVALID,
                     "invalid pet_params (need iterations >= 0, beta, gamma_r, a >= 0, eps, "
                     "lambda0, rho, delta1, delta2 > 0, 0 < t < U, 0 < nu1 <= nu2, "
-                    "0 <= J0 <= J1, precond in 0..4, precision in 0..2, rdp_3d in 0..1)");
+                    "0 <= J0 <= J1, precond in 0..4, precision in 0..2, rdp_3d in 0..1, "
+                    "regularizer in 0..1, TV: 1 <= tv_iters <= 10000 and rdp_3d = 0)");
     return PET_OK;
 }
 
@@ -81,6 +84,8 @@ static void state_free(pet_state *s)
     rel(s->objhist);
     rel(s->redmem);
     rel(s->flag);
+    rel(s->tvmem);
+    s->tvmem = nullptr;
     s->f[0] = s->f[1] = s->w = s->nu_frozen = s->redmem = nullptr;
     s->counts = nullptr;
     s->gamma = nullptr;
@@ -88,8 +93,10 @@ static void state_free(pet_state *s)
     s->flag = nullptr;
 }
 
-// (Re)allocate the state's buffers for geometry g and arithmetic `arith` (no-op when they fit).
-static pet_status state_alloc(pet_state *s, const pet_geometry *g, int arith, int iterations)
+// (Re)allocate the state's buffers for geometry g and arithmetic `arith` (no-op when they fit);
+// tv: also the buffers of the TV variant's proximal step (z, W, xbar and the dual variable).
+static pet_status state_alloc(pet_state *s, const pet_geometry *g, int arith, int iterations,
+                              bool tv = false)
 {
     const GeoDev &gd = g->dev;
     const size_t esz = arith == AR_FP64 ? 8 : 4;
@@ -98,7 +105,7 @@ static pet_status state_alloc(pet_state *s, const pet_geometry *g, int arith, in
     for (int i = 0; i < gd.M; ++i) maxv = std::max(maxv, g->voff[i + 1] - g->voff[i]);
     const size_t w_bytes = (size_t)maxv * gd.NB * gd.Pp * esz;
     const size_t sino = (size_t)gd.V * gd.NB * gd.Pp;
-    if (s->g == g && s->esz == esz && s->f[0] && s->objcap >= iterations + 1) {
+    if (s->g == g && s->esz == esz && s->f[0] && s->objcap >= iterations + 1 && (!tv || s->tvmem)) {
         s->arith = arith;
         return PET_OK;
     }
@@ -126,7 +133,17 @@ static pet_status state_alloc(pet_state *s, const pet_geometry *g, int arith, in
     PET_CUDA(cudaMemsetAsync(s->redmem, 0, reducer_bytes(kRedCap, 2), as));
     reducer_bind(s->red, s->redmem, kRedCap, 2);
     PET_CUDA(get((void **)&s->flag, sizeof(int)));
+    if (tv) PET_CUDA(get(&s->tvmem, 5 * q_bytes));
     if (!as) PET_CUDA(cudaStreamSynchronize(nullptr));
+    return PET_OK;
+}
+
+// TV variant: the dual variable starts at zero with every (re)started reconstruction.
+static pet_status tv_reset(pet_state *s, cudaStream_t st)
+{
+    if (s->prm.regularizer != PET_REG_TV) return PET_OK;
+    if (!s->tvmem) return fail(PET_ERR_INVALID, "TV variant: state has no TV buffers");
+    PET_CUDA(cudaMemsetAsync(reinterpret_cast<char *>(s->tvmem) + 3 * s->q_bytes, 0, 2 * s->q_bytes, st));
     return PET_OK;
 }
 
@@ -164,6 +181,7 @@ static pet_status state_load(pet_state *s, const int32_t *d_counts, const float 
     s->k = s->i = s->J = 0;
     s->tn = 1.0;
     s->have_frozen = false;
+    PET_TRY(tv_reset(s, st));
     return state_sum_f(s, st);
 }
 
@@ -239,6 +257,30 @@ void pet::plan_subiter(pet_state *s, SubiterPlan *pl, bool with_objective)
     ua.sum_fout = s->sums + (1 - s->cur);
     ua.red = s->red;
     ua.z3 = p.rdp_3d;
+    pl->tv = p.regularizer == PET_REG_TV;
+    if (pl->tv) {
+        // TV variant: the update writes z = f - W grad F_i and W; the proximal step follows
+        char *tvm = reinterpret_cast<char *>(s->tvmem);
+        ua.tv = 1;
+        ua.beta_over_M = 0.0;
+        ua.zbuf = tvm;
+        ua.wbuf = tvm + s->q_bytes;
+        TvArgs &ta = pl->tv_args;
+        ta.g = gd;
+        ta.x = ua.fout;
+        ta.z = tvm;
+        ta.w = tvm + s->q_bytes;
+        ta.xbar = tvm + 2 * s->q_bytes;
+        ta.px = tvm + 3 * s->q_bytes;
+        ta.py = tvm + 4 * s->q_bytes;
+        ta.b = p.beta / M;
+        ta.t = p.t;
+        ta.U = p.U;
+        ta.red = s->red;
+        ta.sum_out = ua.sum_fout;
+        tv_shape(ta);
+        pl->tv_iters = ta.b > 0 ? p.tv_iters : 0;
+    }
     update_shape(ua, s->arith);
     update_fp32_scalars(ua);
     if (nu_mode == 2) s->have_frozen = true;
@@ -250,6 +292,13 @@ void pet::plan_subiter(pet_state *s, SubiterPlan *pl, bool with_objective)
     if (pl->objective) objective_args(s, s->objhist + 3 * s->k, &pl->obj_fwd, &pl->obj_rdp);
 }
 
+// TV variant: the proximal step on the update's z (beta = 0: P_t(z)).
+static pet_status tv_step(const SubiterPlan &pl, cudaStream_t st)
+{
+    if (!pl.tv) return PET_OK;
+    return launch_tv_prox(pl.tv_args, pl.tv_iters, pl.arith, st);
+}
+
 // The mu pass and the forward projection only read f^{k,i-1}: the mu pass runs on a side stream
 // forked from `st` and joined before the update.
 static pet_status state_subiter(pet_state *s, cudaStream_t st)
@@ -259,7 +308,8 @@ static pet_status state_subiter(pet_state *s, cudaStream_t st)
     if (pl.mu && profile_active()) {
         PET_TRY(launch_mu_sum(pl.mu_args, pl.arith, st));
         PET_TRY(launch_forward(pl.fwd, FWD_RATIO, pl.arith, st));
-        return launch_update(pl.upd, pl.arith, st);
+        PET_TRY(launch_update(pl.upd, pl.arith, st));
+        return tv_step(pl, st);
     }
     if (pl.mu) {
         if (!s->side) {
@@ -276,7 +326,8 @@ static pet_status state_subiter(pet_state *s, cudaStream_t st)
     }
     PET_TRY(launch_forward(pl.fwd, FWD_RATIO, pl.arith, st));
     if (pl.mu) PET_CUDA(cudaStreamWaitEvent(st, s->ev_join, 0));
-    return launch_update(pl.upd, pl.arith, st);
+    PET_TRY(launch_update(pl.upd, pl.arith, st));
+    return tv_step(pl, st);
 }
 
 // Argument structs for Phi(current f): parts sum(Af), sum(g ln(Af+gamma)) -> out3[0..1],
@@ -303,6 +354,7 @@ void pet::objective_args(pet_state *s, double *out3, FwdArgs *fa, ImageArgs *ra)
     ra->result = out3 + 2;
     ra->red = s->red;
     ra->z3 = s->prm.rdp_3d;
+    ra->tv = s->prm.regularizer == PET_REG_TV;
     image_shape(*ra);
 }
 
@@ -389,7 +441,8 @@ extern "C" pet_status pet_state_create(const pet_geometry *g, const int32_t *d_c
     PET_TRY(check_params(params));
     cudaStream_t st = as_stream(stream);
     pet_state *s = new pet_state();
-    pet_status r = state_alloc(s, g, arith_of(params->precision), params->iterations);
+    pet_status r = state_alloc(s, g, arith_of(params->precision), params->iterations,
+                               params->regularizer == PET_REG_TV);
     if (r == PET_OK) r = state_load(s, d_counts, d_gamma, params, d_img_init, st, true);
     if (r == PET_OK) {
         cudaError_t e = cudaStreamSynchronize(st);
@@ -450,6 +503,7 @@ extern "C" pet_status pet_state_reset(pet_state *s, const float *d_img_init, voi
     s->k = s->i = s->J = 0;
     s->tn = 1.0;
     s->have_frozen = false;
+    PET_TRY(tv_reset(s, st));
     return state_sum_f(s, st);
 }
 
@@ -606,7 +660,8 @@ extern "C" pet_status pet_reconstruct(const pet_geometry *g, const int32_t *d_co
     cudaStream_t st = as_stream(stream);
     GeoWorkspace *ws = workspace_of(g);
     pet_state *s = &ws->st;
-    PET_TRY(state_alloc(s, g, arith_of(params->precision), params->iterations));
+    PET_TRY(state_alloc(s, g, arith_of(params->precision), params->iterations,
+                        params->regularizer == PET_REG_TV));
     PET_TRY(state_load(s, d_counts, d_gamma, params, d_img_inout, st, true));
     PET_TRY(run_reconstruct(s, h_objective, st));
     PET_TRY(from_internal_image(g->dev, s->f[s->cur], d_img_inout, s->arith == AR_FP64, 0, st));
@@ -647,7 +702,8 @@ extern "C" pet_status pet_reconstruct_host(const pet_geometry *g, const int32_t 
     PET_CUDA(cudaMemcpyAsync(ws->gamma, h_gamma, nsino * sizeof(float), cudaMemcpyHostToDevice, st));
     PET_CUDA(cudaMemcpyAsync(ws->img, h_img_inout, nimg * sizeof(float), cudaMemcpyHostToDevice, st));
     pet_state *s = &ws->st;
-    PET_TRY(state_alloc(s, g, arith_of(params->precision), params->iterations));
+    PET_TRY(state_alloc(s, g, arith_of(params->precision), params->iterations,
+                        params->regularizer == PET_REG_TV));
     PET_TRY(state_load(s, ws->counts, ws->gamma, params, ws->img, st, true));
     PET_TRY(run_reconstruct(s, h_objective, st));
     PET_TRY(from_internal_image(gd, s->f[s->cur], ws->img, s->arith == AR_FP64, 0, st));
@@ -829,7 +885,7 @@ extern "C" pet_status pet_smoothness_nu_3d(const pet_geometry *g, const float *d
 static pet_status objective_any(const pet_geometry *g, const int32_t *d_counts,
                                 const float *d_gamma, const float *d_img, double beta,
                                 double gamma_r, double eps, double *h_phi, double *h_parts,
-                                void *stream, int z3)
+                                void *stream, int z3, int tv = 0)
 {
     if (!g || !d_counts || !d_gamma || !d_img || !h_phi)
         return fail(PET_ERR_INVALID, "pet_objective: NULL argument");
@@ -865,6 +921,7 @@ static pet_status objective_any(const pet_geometry *g, const int32_t *d_counts,
     a.red = g->red;
     a.result = g->d_sums + 6;
     a.z3 = z3;
+    a.tv = tv;
     PET_TRY(launch_rdp_value(a, AR_FP32, st));
     double h[3];
     PET_CUDA(cudaMemcpyAsync(h, g->d_sums + 4, sizeof(h), cudaMemcpyDeviceToHost, st));
@@ -888,4 +945,11 @@ extern "C" pet_status pet_objective_3d(const pet_geometry *g, const int32_t *d_c
                                        void *stream)
 {
     return objective_any(g, d_counts, d_gamma, d_img, beta, gamma_r, eps, h_phi, h_parts, stream, 1);
+}
+
+extern "C" pet_status pet_objective_tv(const pet_geometry *g, const int32_t *d_counts,
+                                       const float *d_gamma, const float *d_img, double beta,
+                                       double *h_phi, double *h_parts, void *stream)
+{
+    return objective_any(g, d_counts, d_gamma, d_img, beta, 2.0, 1e-12, h_phi, h_parts, stream, 0, 1);
 }

@@ -284,18 +284,25 @@ __global__ void __launch_bounds__(256, 3) update_kernel(const __grid_constant__ 
                 if (active) bp_accumulate<G, KC, AR>(g, tb, w, TP, nvc, pl, grp, bp);
             }
             if (!active) continue;
-            // 3. step and clamp P_t
-            T out[G];
+            // 3. step and clamp P_t (TV variant: the unclamped z and the metric W = coef, for the
+            //    proximal step that follows)
+            T out[G], wv[G];
 #pragma unroll
             for (int p = 0; p < G; ++p) {
                 const T d = scale * bp.value(p) + rg[p];
                 T ft = fc[p] - coef[p] * d;
-                ft = ft <= T(0) ? tt : (ft >= U ? U - tt : ft);
+                if (!a.tv) ft = ft <= T(0) ? tt : (ft >= U ? U - tt : ft);
                 const bool valid = grp * G + p < g.P;
                 out[p] = valid ? ft : T(0);
+                wv[p] = valid ? coef[p] : T(1);
                 part += out[p];
             }
-            store_group<G, T>(reinterpret_cast<T *>(a.fout) + (unsigned)j * (unsigned)Pp + grp * G, out);
+            const unsigned o = (unsigned)j * (unsigned)Pp + grp * G;
+            store_group<G, T>(reinterpret_cast<T *>(a.fout) + o, out);
+            if (a.tv) {
+                store_group<G, T>(reinterpret_cast<T *>(a.zbuf) + o, out);
+                store_group<G, T>(reinterpret_cast<T *>(a.wbuf) + o, wv);
+            }
         }
         double v[1] = {(double)part};
         grid_reduce<1>(v, a.red, a.sum_fout, vloc, nv);
@@ -572,6 +579,18 @@ __global__ void __launch_bounds__(256) image_kernel(const __grid_constant__ Imag
 #pragma unroll
                 for (int p = 0; p < G; ++p) out[p] = grp * G + p < g.P ? gr[p] : T(0);
                 store_group<G, T>(reinterpret_cast<T *>(a.out) + (size_t)j * Pp + (size_t)grp * G, out);
+            } else if (a.tv) {
+                // R_TV: |(f_{j+x} - f_j, f_{j+y} - f_j)|, a component 0 across the last column / row
+                T fx[G], fy[G];
+                load_group<G, T>(f + (size_t)j * Pp + (size_t)grp * G, fc);
+                if (ix + 1 < N) load_group<G, T>(f + (size_t)(j + 1) * Pp + (size_t)grp * G, fx);
+                if (iy + 1 < N) load_group<G, T>(f + (size_t)(j + N) * Pp + (size_t)grp * G, fy);
+#pragma unroll
+                for (int p = 0; p < G; ++p) {
+                    const T dx = ix + 1 < N ? fx[p] - fc[p] : T(0);
+                    const T dy = iy + 1 < N ? fy[p] - fc[p] : T(0);
+                    part += (grp * G + p < g.P) ? sqrt(dx * dx + dy * dy) : T(0);
+                }
             } else {
                 stencil<G, AR, false, false, true>(g, f, grp, ix, iy, (T)a.gamma_r, (T)a.eps, fc, gr, gx, gy, rv, a.z3, gz);
 #pragma unroll
@@ -666,7 +685,8 @@ void update_shape(UpdateArgs &a, int arith)
     const int TP = 256 / a.g.NG;
     const int ntiles = (a.g.N * a.g.N + TP - 1) / TP;
     const void *fn = a.g.G == 1 ? (a.g.K <= 2 ? update_fn<1, 2>(arith) : update_fn<1, 4>(arith))
-                                : (a.g.K <= 2 ? update_fn<8, 2>(arith, a.z3) : update_fn<8, 4>(arith, a.z3));
+                                : (a.g.K <= 2 ? update_fn<8, 2>(arith, a.z3 || a.tv)
+                                              : update_fn<8, 4>(arith, a.z3 || a.tv));
     const int slots = sm_count() * resident_blocks(fn);
     a.tpv = std::max({1, (ntiles + a.red.capacity - 1) / a.red.capacity, (ntiles + slots - 1) / slots});
     a.nvb = (ntiles + a.tpv - 1) / a.tpv;
@@ -690,9 +710,11 @@ template <int G, int KC>
 static void update_dispatch(const UpdateArgs &a, const Batch &b, int arith, int grid, cudaStream_t st)
 {
     if constexpr (G == 8) {
-        // the packed kernel has the in-plane stencil only; the 3-D prior runs the generic kernel
-        if (a.z3 && arith == AR_FP32) update_kernel<G, KC, AR_FP32><<<grid, 256, 0, st>>>(a, b);
-        else if (a.z3 && arith == AR_KAHAN) update_kernel<G, KC, AR_KAHAN><<<grid, 256, 0, st>>>(a, b);
+        // the packed kernel has the in-plane RDP step only; the 3-D prior and the TV variant run
+        // the generic kernel
+        const bool gen = a.z3 || a.tv;
+        if (gen && arith == AR_FP32) update_kernel<G, KC, AR_FP32><<<grid, 256, 0, st>>>(a, b);
+        else if (gen && arith == AR_KAHAN) update_kernel<G, KC, AR_KAHAN><<<grid, 256, 0, st>>>(a, b);
         else if (arith == AR_FP32) update_kernel_x8<KC, AR_FP32><<<grid, 256, 0, st>>>(a, b);
         else if (arith == AR_KAHAN) update_kernel_x8<KC, AR_KAHAN><<<grid, 256, 0, st>>>(a, b);
         else update_kernel<G, KC, AR_FP64><<<grid, 256, 0, st>>>(a, b);

@@ -38,7 +38,8 @@ class Params(ctypes.Structure):
         (k, ctypes.c_double) for k in ("beta", "gamma_r", "eps", "t", "U", "lambda0", "a",
                                        "rho", "delta1", "delta2", "nu1", "nu2")] + [
         ("J0", ctypes.c_int), ("J1", ctypes.c_int), ("precond", ctypes.c_int),
-        ("precision", ctypes.c_int), ("rdp_3d", ctypes.c_int)]
+        ("precision", ctypes.c_int), ("rdp_3d", ctypes.c_int), ("regularizer", ctypes.c_int),
+        ("tv_iters", ctypes.c_int)]
 
 
 class Request(ctypes.Structure):
@@ -91,6 +92,8 @@ SIGNATURES = {
     "pet_rdp_gradient_3d": (_I, [_VP, _VP, _D, _D, _VP, _VP]),
     "pet_smoothness_nu_3d": (_I, [_VP, _VP, _D, _D, _VP, _VP]),
     "pet_objective_3d": (_I, [_VP, _VP, _VP, _VP, _D, _D, _D, _DP, _DP, _VP]),
+    "pet_objective_tv": (_I, [_VP, _VP, _VP, _VP, _D, _DP, _DP, _VP]),
+    "pet_tv_prox": (_I, [_VP, _VP, _VP, _D, _I, _VP, _VP, _VP, _VP]),
     "pet_batch_create": (_I, [_I, _I, ctypes.POINTER(_VP)]),
     "pet_batch_add": (_I, [_VP, _VP, _I, _VP]),
     "pet_batch_remove": (_I, [_VP, _VP]),
@@ -158,7 +161,8 @@ def make_params(p, precision: int | None = None) -> Params:
     """Params from an object with AlgoParams attribute names."""
     return Params(p.iterations, p.beta, p.gamma_r, p.eps, p.t, p.U, p.lambda0, p.a, p.rho,
                   p.delta1, p.delta2, p.nu1, p.nu2, p.J0, p.J1, p.precond,
-                  p.precision if precision is None else precision, int(getattr(p, "rdp3d", 0)))
+                  p.precision if precision is None else precision, int(getattr(p, "rdp3d", 0)),
+                  int(getattr(p, "reg", 0)), int(getattr(p, "tv_iters", 10)))
 
 
 class Geometry:
@@ -305,6 +309,21 @@ def objective(g: Geometry, d_counts, d_gamma, d_img, beta, gamma_r, eps, stream=
     _check(fn(g.handle, _ptr(d_counts), _ptr(d_gamma), _ptr(d_img), beta, gamma_r,
               eps, ctypes.byref(phi), parts, _stream(stream)))
     return phi.value, list(parts)
+
+
+def objective_tv(g: Geometry, d_counts, d_gamma, d_img, beta, stream=None):
+    """Phi with the TV variant's R_TV (parts[2] = R_TV(d_img))."""
+    phi = ctypes.c_double()
+    parts = (ctypes.c_double * 3)()
+    _check(lib().pet_objective_tv(g.handle, _ptr(d_counts), _ptr(d_gamma), _ptr(d_img), beta,
+                                  ctypes.byref(phi), parts, _stream(stream)))
+    return phi.value, list(parts)
+
+
+def tv_prox(g: Geometry, d_z, d_w, b, iters, d_px, d_py, d_x, stream=None):
+    """The TV variant's proximal step (primal-dual iterations); d_px, d_py updated in place."""
+    _check(lib().pet_tv_prox(g.handle, _ptr(d_z), _ptr(d_w), float(b), int(iters), _ptr(d_px),
+                             _ptr(d_py), _ptr(d_x), _stream(stream)))
 
 
 def objective_static(g: Geometry, d_counts, d_gamma, d_img, beta, gamma_r, eps, stream=None):

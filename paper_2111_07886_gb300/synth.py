@@ -59,6 +59,8 @@ class AlgoParams:
     precond: int = PRECOND_P2
     precision: int = PREC_FP32_KAHAN
     rdp3d: int = 0                # 0: 8 in-plane neighbours (Sec. IV-A); 1: 26 neighbours in 3-D
+    reg: int = 0                  # 0: RDP by its gradient (the paper); 1: TV by a proximal step
+    tv_iters: int = 10            # primal-dual iterations per proximal step (reg = 1)
 
 
 @dataclasses.dataclass
