@@ -575,6 +575,28 @@ __device__ __forceinline__ const A *scan_of(const A &one, const Batch &b, int vb
     return reinterpret_cast<const A *>(b.args) + lo;
 }
 
+// As scan_of, for a whole block: in a batched launch the scan's argument struct is copied into
+// the block's shared memory `sh` (one cooperative copy per virtual block; the kernel's field
+// reads are then shared-memory loads instead of global ones); a single scan's arguments are
+// used where they are (the kernel parameters).  Every thread of the block must call it with the
+// same vb.
+template <class A>
+__device__ __forceinline__ const A &scan_args(const A &one, const Batch &b, int vb, int &local,
+                                              int &count, A &sh)
+{
+    const A *src = scan_of(one, b, vb, local, count);
+    if (b.nscans == 0) return one;
+    static_assert(sizeof(A) % 4 == 0, "argument structs are copied as 32-bit words");
+    __syncthreads();                                  // the previous virtual block is done with sh
+    const int nthr = blockDim.x * blockDim.y;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const unsigned *s = reinterpret_cast<const unsigned *>(src);
+    unsigned *d = reinterpret_cast<unsigned *>(&sh);
+    for (int k = tid; k < (int)(sizeof(A) / 4); k += nthr) d[k] = __ldg(s + k);
+    __syncthreads();
+    return sh;
+}
+
 template <class A>
 __device__ __forceinline__ int total_vblocks(const A &one, const Batch &b)
 {

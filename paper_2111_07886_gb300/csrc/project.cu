@@ -16,7 +16,7 @@
 #include "profile.cuh"
 
 #ifndef FWD_FAST
-#define FWD_FAST 0
+#define FWD_FAST 1               // blocked compensated walk (see the G == 8 branch of fwd_kernel)
 #endif
 
 namespace pet {
@@ -33,9 +33,10 @@ __global__ void __launch_bounds__(256, 3) fwd_kernel(const __grid_constant__ Fwd
     __shared__ T comb_s[256 * G];
     __shared__ T comb_e[256 * G];
     const int total = total_vblocks(one, bt);
+    __shared__ FwdArgs sh_args;
     for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
         int vloc, nv;
-        const FwdArgs &a = *scan_of(one, bt, vb, vloc, nv);
+        const FwdArgs &a = scan_args(one, bt, vb, vloc, nv, sh_args);
         const GeoDev &g = a.g;
         const int NG = g.NG, NB = g.NB, N = g.N, Pp = g.Pp, S = a.S, R = a.R;
         const int nrays = a.nviews * NB;

@@ -216,9 +216,10 @@ __global__ void __launch_bounds__(256, 3) update_kernel(const __grid_constant__ 
     using T = typename ArithT<AR>::T;
     __shared__ BpTable<KC, AR> tb;
     const int total = total_vblocks(one, bt);
+    __shared__ UpdateArgs sh_args;
     for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
         int vloc, nv;
-        const UpdateArgs &a = *scan_of(one, bt, vb, vloc, nv);
+        const UpdateArgs &a = scan_args(one, bt, vb, vloc, nv, sh_args);
         const GeoDev &g = a.g;
         const int N = g.N, NG = g.NG, Pp = g.Pp, npix = N * N;
         const int TP = 256 / NG;
@@ -328,9 +329,10 @@ __global__ void __launch_bounds__(256, UPDATE_X8_BLOCKS) update_kernel_x8(
     using Table = BpTable<KC, AR, 1024 / (KC > 2 ? 2 : 1)>;
     __shared__ Table tb;
     const int total = total_vblocks(one, bt);
+    __shared__ UpdateArgs sh_args;
     for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
         int vloc, nv;
-        const UpdateArgs &a = *scan_of(one, bt, vb, vloc, nv);
+        const UpdateArgs &a = scan_args(one, bt, vb, vloc, nv, sh_args);
         const GeoDev &g = a.g;
         const int N = g.N, NG = g.NG, npix = N * N;
         const unsigned Pp = (unsigned)g.Pp;
@@ -536,9 +538,10 @@ __global__ void __launch_bounds__(256) image_kernel(const __grid_constant__ Imag
 {
     using T = typename ArithT<AR>::T;
     const int total = total_vblocks(one, bt);
+    __shared__ ImageArgs sh_args;
     for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
         int vloc, nv;
-        const ImageArgs &a = *scan_of(one, bt, vb, vloc, nv);
+        const ImageArgs &a = scan_args(one, bt, vb, vloc, nv, sh_args);
         const GeoDev &g = a.g;
         const int N = g.N, NG = g.NG, Pp = g.Pp;
         const unsigned items = (unsigned)N * (unsigned)N * (unsigned)NG;    // < 2^32 (geometry limits)
@@ -611,9 +614,10 @@ __global__ void __launch_bounds__(256) image_kernel(const __grid_constant__ Imag
 __global__ void __launch_bounds__(256) mu_kernel_x8(const __grid_constant__ ImageArgs one, const Batch bt)
 {
     const int total = total_vblocks(one, bt);
+    __shared__ ImageArgs sh_args;
     for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
         int vloc, nv;
-        const ImageArgs &a = *scan_of(one, bt, vb, vloc, nv);
+        const ImageArgs &a = scan_args(one, bt, vb, vloc, nv, sh_args);
         const GeoDev &g = a.g;
         const int N = g.N, NG = g.NG, npix = N * N;
         const unsigned Pp = (unsigned)g.Pp;
