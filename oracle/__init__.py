@@ -38,7 +38,7 @@ class Geom(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("nplanes", ctypes.c_int), ("nviews", ctypes.c_int),
                 ("nbins", ctypes.c_int), ("nsubsets", ctypes.c_int),
                 ("pixel_mm", ctypes.c_double), ("bin_mm", ctypes.c_double),
-                ("sens", ctypes.c_double)]
+                ("sens", ctypes.c_double), ("subrays", ctypes.c_int)]
 
 
 class Params(ctypes.Structure):
@@ -60,6 +60,8 @@ def lib():
             gp = ctypes.POINTER(Geom)
             L.ora_ray_pieces.argtypes = [gp, ctypes.c_int, ctypes.c_int, ip, dp]
             L.ora_ray_pieces.restype = ctypes.c_int
+            L.ora_bin_pieces.argtypes = [gp, ctypes.c_int, ctypes.c_int, ip, dp]
+            L.ora_bin_pieces.restype = ctypes.c_int
             L.ora_subset_size.argtypes = [gp, ctypes.c_int]
             L.ora_subset_size.restype = ctypes.c_int
             L.ora_forward.argtypes = [gp, ctypes.c_int, dp, dp]
@@ -96,15 +98,16 @@ def _d(a):
     return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
-def geom(n, nplanes, nviews, nbins, nsubsets, pixel_mm=1.0, bin_mm=None, sens=1.0) -> Geom:
+def geom(n, nplanes, nviews, nbins, nsubsets, pixel_mm=1.0, bin_mm=None, sens=1.0,
+         subrays=1) -> Geom:
     return Geom(n, nplanes, nviews, nbins, nsubsets, pixel_mm,
-                pixel_mm if bin_mm is None else bin_mm, sens)
+                pixel_mm if bin_mm is None else bin_mm, sens, subrays)
 
 
 def geom_from(geometry: dict, sens: float) -> Geom:
     g = geometry
     return Geom(g["n"], g["nplanes"], g["nviews"], g["nbins"], g["nsubsets"],
-                g["pixel_mm"], g["bin_mm"], sens)
+                g["pixel_mm"], g["bin_mm"], sens, int(g.get("subrays", 1)))
 
 
 def subset_size(g: Geom, subset: int) -> int:
@@ -117,6 +120,17 @@ def ray_pieces(g: Geom, v: int, b: int):
     pix = np.zeros(cap, np.int32)
     ln = np.zeros(cap, np.float64)
     k = lib().ora_ray_pieces(ctypes.byref(g), v, b,
+                             pix.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                             ln.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return pix[:k].copy(), ln[:k].copy()
+
+
+def bin_pieces(g: Geom, v: int, b: int):
+    """Pieces of bin (v, b) under the sub-ray model: every sub-ray's Siddon pieces, lengths / R."""
+    cap = max(1, g.subrays) * (2 * g.n + 2)
+    pix = np.zeros(cap, np.int32)
+    ln = np.zeros(cap, np.float64)
+    k = lib().ora_bin_pieces(ctypes.byref(g), v, b,
                              pix.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
                              ln.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
     return pix[:k].copy(), ln[:k].copy()

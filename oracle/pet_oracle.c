@@ -23,7 +23,11 @@
  *
  * System model: one line per detector bin, parallel beam; A_ij = sens * (length in mm of
  * ray i inside pixel j), where a pixel is the half-open square [x, x+1) x [y, y+1) in pixel
- * units (a ray lying on a pixel edge belongs to the pixel on its + side only).  Lengths are
+ * units (a ray lying on a pixel edge belongs to the pixel on its + side only).  With R > 1
+ * sub-rays (the "parallel rays per detector pair" of the paper's ray-driven system model,
+ * Sec. IV-A, 32 there) bin i is R parallel lines spread uniformly across its width, at offsets
+ * ((s + 1/2) / R - 1/2) bin_mm from its centre, s = 0..R-1, and A_ij = sens / R * (the sum of
+ * their lengths in mm inside pixel j).  Lengths are
  * found by Siddon's method: all crossings of the ray with the grid lines are sorted, and each
  * piece between consecutive crossings is charged to the pixel that contains its midpoint.
  *
@@ -45,6 +49,7 @@ typedef struct {
     double pixel_mm;
     double bin_mm;
     double sens;     /* A_ij = sens * length_mm */
+    int subrays;     /* R parallel lines per bin (<= 1: one line at the bin centre) */
 } ora_geom;
 
 typedef struct {
@@ -94,12 +99,41 @@ static int cmp_double(const void *a, const void *b)
  * (length in pixel units) and returns the number of pieces.  Buffers need 2N+2 entries.
  * The ray is P(tau) = r (c, s) + tau (-s, c); the image is [-N/2, N/2]^2 in pixel units.
  */
+static int line_pieces(const ora_geom *g, int v, double r, int *pix, double *len);
+
 int ora_ray_pieces(const ora_geom *g, int v, int b, int *pix, double *len)
+{
+    return line_pieces(g, v, bin_offset(g, b), pix, len);
+}
+
+static int nsub_of(const ora_geom *g) { return g->subrays > 1 ? g->subrays : 1; }
+
+/*
+ * Pieces of bin (v, b) under the sub-ray model: the Siddon pieces of each of its R lines, each
+ * length divided by R (pixels may repeat).  Buffers need R (2N + 2) entries.
+ */
+int ora_bin_pieces(const ora_geom *g, int v, int b, int *pix, double *len)
+{
+    const int R = nsub_of(g), N = g->n;
+    if (R == 1) return ora_ray_pieces(g, v, b, pix, len);
+    const double rho = g->bin_mm / g->pixel_mm;
+    int np = 0;
+    for (int s = 0; s < R; ++s) {
+        const double r = bin_offset(g, b) + ((s + 0.5) / R - 0.5) * rho;
+        const int k = line_pieces(g, v, r, pix + np, len + np);
+        for (int m = np; m < np + k; ++m) len[m] /= R;
+        np += k;
+    }
+    (void)N;
+    return np;
+}
+
+/* Siddon's method for the line of view v at offset r (pixel units) from the centre. */
+static int line_pieces(const ora_geom *g, int v, double r, int *pix, double *len)
 {
     const int N = g->n;
     double c, s;
     view_dir(g, v, &c, &s);
-    const double r = bin_offset(g, b);
     const double half = 0.5 * N;
     double *tau = (double *)malloc(sizeof(double) * (2 * N + 2));
     int nt = 0;
@@ -140,13 +174,13 @@ typedef struct { int *pix; double *len; int *cnt; int stride; } piece_table;
 static void build_pieces(const ora_geom *g, const int *views, int nv, piece_table *tb)
 {
     const int N = g->n, NB = g->nbins;
-    tb->stride = 2 * N + 2;
+    tb->stride = nsub_of(g) * (2 * N + 2);
     tb->pix = (int *)malloc(sizeof(int) * (size_t)nv * NB * tb->stride);
     tb->len = (double *)malloc(sizeof(double) * (size_t)nv * NB * tb->stride);
     tb->cnt = (int *)malloc(sizeof(int) * (size_t)nv * NB);
     #pragma omp parallel for schedule(dynamic)
     for (int ray = 0; ray < nv * NB; ++ray)
-        tb->cnt[ray] = ora_ray_pieces(g, views[ray / NB], ray % NB,
+        tb->cnt[ray] = ora_bin_pieces(g, views[ray / NB], ray % NB,
                                       tb->pix + (size_t)ray * tb->stride,
                                       tb->len + (size_t)ray * tb->stride);
 }

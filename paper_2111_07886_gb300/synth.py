@@ -78,11 +78,12 @@ class Workload:
     params: AlgoParams
     plane_mm: float = 0.0
     seed: int = 0
+    subrays: int = 1              # parallel lines per bin of the system model (Sec. IV-A: 32)
 
     def geometry(self) -> dict:
         return dict(n=self.n, nplanes=self.nplanes, pixel_mm=self.pixel_mm,
                     nviews=self.nviews, nbins=self.nbins, bin_mm=self.bin_mm,
-                    nsubsets=self.nsubsets)
+                    nsubsets=self.nsubsets, subrays=self.subrays)
 
 
 # SDP-P2 settings of the workloads.  Table II's rows were tuned on the paper's brain phantom;
