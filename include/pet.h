@@ -13,7 +13,8 @@
  *     pixel units, so a ray lying on a pixel edge belongs to the pixel on its + side only;
  *   - views theta_v = v pi / V, v = 0..V-1; bins at offsets r_b = (b - (n_b - 1)/2) bin_mm;
  *     ray (v, b) is the line {x cos theta_v + y sin theta_v = r_b};
- *   - system matrix A_ij = sens * (length in mm of ray i inside pixel j);
+ *   - system matrix A_ij = sens * (length in mm of ray i inside pixel j) (or the mean over
+ *     desc.subrays parallel lines across the bin, see pet_geometry_desc);
  *   - ordered subsets (Sec. II-B): subset i (0-based) holds the views v with v mod M == i,
  *     processed i = 0..M-1 within an iteration; subset projections list the subset's views
  *     in increasing order.
@@ -62,6 +63,11 @@ typedef struct {
     double bin_mm;      /* bin spacing */
     int nsubsets;       /* M ordered subsets, 1 <= M <= V */
     double sens;        /* A_ij = sens * length_mm (counts per activity per mm), > 0 */
+    int subrays;        /* R parallel lines per bin, spread uniformly across its width (offsets
+                           ((s + 1/2)/R - 1/2) bin_mm from its centre, s = 0..R-1), and
+                           A_ij = sens / R * (sum of their lengths in mm inside pixel j): the
+                           paper's ray-driven model with parallel rays per detector pair
+                           (Sec. IV-A, 32 there).  0 or 1: one line at the bin centre; at most 64 */
 } pet_geometry_desc;
 
 typedef enum {
@@ -126,7 +132,8 @@ const char *pet_last_error(void);
  * uploads them, and computes the sensitivity p_j of Eq. pj (one backprojection of ones over all
  * views) on the device.  Synchronises `stream` before returning.  PET_ERR_INVALID for a bad desc
  * (limits: 1 <= n <= 8192, 1 <= nplanes <= 2048, nbins >= 4, 1 <= nsubsets <= nviews,
- * bin_mm >= 0.36 pixel_mm, fewer than 4e9 image or sinogram elements).
+ * bin_mm >= 0.36 pixel_mm, 0 <= subrays <= 64, at most 4 bins per view in a pixel's footprint,
+ * fewer than 4e9 image or sinogram elements).
  * ---------------------------------------------------------------------------------------- */
 pet_status pet_geometry_create(const pet_geometry_desc *desc, void *stream, pet_geometry **out);
 void pet_geometry_destroy(pet_geometry *g);

@@ -2,7 +2,7 @@
 //
 // Every tick advances each running scan of the batch by one subiteration.  The scans are grouped
 // into classes that share one kernel instantiation (plane-group size G, arithmetic, candidate
-// bins per view, in-plane or 3-D prior); for each class the per-scan argument structs of the tick are packed, with
+// bins per view, in-plane or 3-D prior, one line or sub-rays per bin); for each class the per-scan argument structs of the tick are packed, with
 // per-kernel virtual-block prefix tables, into one pinned buffer and copied to the device, and
 // five persistent kernels (mu pass, forward + ratio, fused update, objective projection, RDP
 // value) stride over the virtual blocks of all scans of the class.  A scan that skips a kernel
@@ -37,6 +37,7 @@ constexpr int kKinds = 5;                     // mu pass, forward + ratio, updat
 struct BatchClass {
     int G = 0, arith = 0, KC = 0;
     int z3 = 0;                               // 3-D prior (the generic update and mu kernels)
+    int sub = 0;                              // sub-ray geometry (the sub-ray update kernel)
     int cap = 0;                              // scan slots of this class
     std::vector<pet_state *> slot;            // nullptr = empty
     std::vector<bool> objective;              // per slot: plan objectives
@@ -150,13 +151,18 @@ extern "C" void pet_batch_destroy(pet_batch *b)
 static pet_status class_for(pet_batch *b, pet_state *s, BatchClass **out)
 {
     const int G = s->g->dev.G, arith = s->arith, KC = kc_of(s), z3 = s->prm.rdp_3d;
+    const int sub = s->g->dev.R > 1;
     for (BatchClass *c : b->classes)
-        if (c->G == G && c->arith == arith && c->KC == KC && c->z3 == z3) { *out = c; return PET_OK; }
+        if (c->G == G && c->arith == arith && c->KC == KC && c->z3 == z3 && c->sub == sub) {
+            *out = c;
+            return PET_OK;
+        }
     BatchClass *c = new BatchClass();
     c->G = G;
     c->arith = arith;
     c->KC = KC;
     c->z3 = z3;
+    c->sub = sub;
     c->cap = b->capacity;
     c->slot.assign(c->cap, nullptr);
     c->objective.assign(c->cap, false);
@@ -266,9 +272,11 @@ static pet_status class_launches(pet_batch *b, BatchClass *c, const BatchClass::
     FwdArgs fs{};
     fs.g.G = c->G;
     fs.g.K = c->KC;
+    fs.g.R = c->sub ? 2 : 1;                  // selects the sub-ray projector
     UpdateArgs us{};
     us.g.G = c->G;
     us.g.K = c->KC;
+    us.g.R = c->sub ? 2 : 1;                  // selects the sub-ray kernel (the count comes per scan)
     us.z3 = c->z3;
     ImageArgs is{};
     is.g.G = c->G;

@@ -82,6 +82,7 @@ static pet_status build_tables(pet_geometry *g, std::vector<ViewGeo> &views,
 {
     const pet_geometry_desc &d = g->desc;
     const int N = d.n, V = d.nviews, NB = d.nbins, M = d.nsubsets;
+    const int R = d.subrays > 1 ? d.subrays : 1;
     const double rho = d.bin_mm / d.pixel_mm;
     const double half = 0.5 * N;
     g->voff.assign(M + 1, 0);
@@ -125,15 +126,20 @@ static pet_status build_tables(pet_geometry *g, std::vector<ViewGeo> &views,
         vg.axis = minor == 0.0 ? 1 : 0;
         vg.wslope = minor > 0.0 ? rho / (major * minor) : 0.0;
         vg.wslopef = (float)vg.wslope;
-        K = std::max(K, (int)floor(2.0 * vg.h) + 1);
-        views[u] = vg;
         // forward walk: cross coordinate (grid units) at the start of driving step 0
         const double a = vg.xdrive ? s : c;        // divisor
         const double o = vg.xdrive ? c : s;        // other component
-        for (int b = 0; b < NB; ++b) {
-            const double r = ((double)b - 0.5 * (NB - 1)) * rho;
+        vg.half = R > 1 ? rho / (2.0 * R * a) : 0.0;
+        vg.halfq = to_q32(vg.half);
+        // candidate bins of a pixel's footprint: one line per bin, or sub-lines within
+        // (R - 1) / (2 R) bins of the bin centre on either side (first candidate floor(t - hh))
+        if (R == 1) K = std::max(K, (int)floor(2.0 * vg.h) + 1);
+        else K = std::max(K, (int)floor(2.0 * (vg.h + 0.5 - 0.5 / R)) + 2);
+        views[u] = vg;
+        // driving steps the line at offset r meets the image (+- one step of margin)
+        auto range = [&](double r, long long &dlo, long long &dhi, double &LO0) {
             const double A0 = (r + half * o) / a + half;
-            const double LO0 = A0 + std::min(0.0, B);
+            LO0 = A0 + std::min(0.0, B);
             const double aB = fabs(B);
             double lower, upper;
             if (B > 0) { lower = (-LO0 - aB) / B; upper = (N - LO0) / B; }
@@ -142,8 +148,27 @@ static pet_status build_tables(pet_geometry *g, std::vector<ViewGeo> &views,
                 lower = (LO0 >= -1.0 && LO0 < N + 1.0) ? 0.0 : 1e30;
                 upper = (LO0 >= -1.0 && LO0 < N + 1.0) ? N : -1e30;
             }
-            long long dlo = (long long)floor(std::max(-1e9, lower)) - 1;
-            long long dhi = (long long)ceil(std::min(1e9, upper)) + 1;
+            dlo = (long long)floor(std::max(-1e9, lower)) - 1;
+            dhi = (long long)ceil(std::min(1e9, upper)) + 1;
+        };
+        for (int b = 0; b < NB; ++b) {
+            const double r = ((double)b - 0.5 * (NB - 1)) * rho;
+            long long dlo, dhi;
+            double LO0;
+            range(r, dlo, dhi, LO0);
+            if (R > 1) {
+                // the union of the ranges of the bin's outermost sub-lines and its centre line
+                const double e = (0.5 - 0.5 / R) * rho;
+                for (double rr : {r - e, r + e}) {
+                    long long l2, h2;
+                    double unused;
+                    range(rr, l2, h2, unused);
+                    if (l2 <= h2) {
+                        if (dlo > dhi) { dlo = l2; dhi = h2; }
+                        else { dlo = std::min(dlo, l2); dhi = std::max(dhi, h2); }
+                    }
+                }
+            }
             dlo = std::max(0LL, dlo);
             dhi = std::min((long long)N - 1, dhi);
             RayGeo rg;
@@ -155,7 +180,9 @@ static pet_status build_tables(pet_geometry *g, std::vector<ViewGeo> &views,
             rays[(size_t)u * NB + b] = rg;
         }
     }
-    g->dev.K = K;
+    g->dev.K = R > 1 ? std::max(K, 3) : K;   // sub-ray kernels are built for 4 candidates
+    g->dev.R = R;
+    g->dev.offq = to_q32(0.5 / R);
     return PET_OK;
 }
 
@@ -166,6 +193,9 @@ static pet_status geometry_init(pet_geometry *g, cudaStream_t st)
     std::vector<RayGeo> rays;
     PET_TRY(build_tables(g, views, rays));
     GeoDev &gd = g->dev;
+    if (gd.K > 4)
+        return fail(PET_ERR_INVALID, "pet_geometry_create: a pixel's footprint spans more than 4 "
+                                     "bins of one view (bins too fine for the sub-ray width)");
     gd.N = d.n;
     gd.P = d.nplanes;
     gd.G = d.nplanes == 1 ? 1 : 8;
@@ -174,7 +204,7 @@ static pet_status geometry_init(pet_geometry *g, cudaStream_t st)
     gd.V = d.nviews;
     gd.NB = d.nbins;
     gd.M = d.nsubsets;
-    gd.scale = d.sens * d.pixel_mm;
+    gd.scale = d.sens * d.pixel_mm / gd.R;
     PET_CUDA(cudaMalloc(&g->d_views, sizeof(ViewGeo) * views.size()));
     PET_CUDA(cudaMalloc(&g->d_rays, sizeof(RayGeo) * rays.size()));
     PET_CUDA(cudaMalloc(&g->d_view_of_slot, sizeof(int) * g->view_of_slot.size()));
@@ -236,6 +266,8 @@ extern "C" pet_status pet_geometry_create(const pet_geometry_desc *desc, void *s
                                      "1 <= nsubsets <= nviews, pixel_mm, bin_mm, sens > 0)");
     if (d.nplanes > 2048)
         return fail(PET_ERR_INVALID, "pet_geometry_create: at most 2048 planes");
+    if (d.subrays < 0 || d.subrays > 64)
+        return fail(PET_ERR_INVALID, "pet_geometry_create: subrays must be in 0..64");
     if (d.bin_mm < 0.36 * d.pixel_mm)
         return fail(PET_ERR_INVALID, "pet_geometry_create: bin_mm must be >= 0.36 pixel_mm "
                                      "(at most 4 rays of one view cross a pixel)");

@@ -345,12 +345,85 @@ template <int KC, int AR, int CAPX = 0> struct BpTable {
     E e[CAP];
 };
 
+// Sub-ray model (g.R > 1): the weight of bin b is the sum over its R lines, at offsets
+// (2 s + 1 - R) / (2 R) bins from its centre, of the single-line length (the trapezoid of oblique
+// views; for views along an axis, L for each line whose forward-walk start coordinate lies in the
+// pixel's column, the forward projector's own membership test); scale carries the 1 / R.  The
+// first candidate is floor(t - h - (R - 1) / (2 R)).
 template <int KC, int AR>
+__device__ __forceinline__ void bp_weights_sub(const GeoDev &g, const ViewGeo &vw, int slot, int ix,
+                                            int iy, int &b0, typename ArithT<AR>::T (&w)[KC])
+{
+    using T = typename ArithT<AR>::T;
+    const int NB = g.NB, R = g.R;
+#pragma unroll
+    for (int k = 0; k < KC; ++k) w[k] = T(0);
+    if constexpr (AR == AR_FP64) {
+        const double t = vw.t0 + (double)ix * vw.cx + (double)iy * vw.cy;
+        b0 = (int)floor(t - vw.h - (0.5 - 0.5 / R));
+    } else {
+        const long long tq = vw.t0q + (long long)ix * vw.cxq + (long long)iy * vw.cyq;
+        b0 = (int)((tq - vw.hq - (long long)(R - 1) * g.offq) >> 32);
+    }
+    if (vw.axis) {
+        const int cross = vw.xdrive ? iy : ix;
+        const RayGeo *rr = g.rays + (size_t)slot * NB;
+#pragma unroll
+        for (int k = 0; k < KC; ++k) {
+            const int b = b0 + k;
+            if ((unsigned)b >= (unsigned)NB) continue;
+            int cnt = 0;
+            for (int sr = 0; sr < R; ++sr) {
+                if constexpr (AR == AR_FP64) cnt += (int)floor(rr[b].lo + (2 * sr + 1 - R) * vw.half) == cross;
+                else cnt += (int)((rr[b].loq + (long long)(2 * sr + 1 - R) * vw.halfq) >> 32) == cross;
+            }
+            w[k] = (T)cnt * (T)vw.L;
+        }
+        return;
+    }
+    if constexpr (AR == AR_FP64) {
+        const double t = vw.t0 + (double)ix * vw.cx + (double)iy * vw.cy;
+#pragma unroll
+        for (int k = 0; k < KC; ++k) {
+            const int b = b0 + k;
+            if ((unsigned)b >= (unsigned)NB) continue;
+            double ww = 0.0;
+            for (int sr = 0; sr < R; ++sr) {
+                const double dd = vw.h - fabs((double)b + (2 * sr + 1 - R) * (0.5 / R) - t);
+                ww += dd > 0.0 ? fmin(vw.L, dd * vw.wslope) : 0.0;
+            }
+            w[k] = ww;
+        }
+    } else {
+        const long long tq = vw.t0q + (long long)ix * vw.cxq + (long long)iy * vw.cyq;
+        const float ws = vw.wslopef * (kQ32 * 256.f);
+#pragma unroll
+        for (int k = 0; k < KC; ++k) {
+            const int b = b0 + k;
+            if ((unsigned)b >= (unsigned)NB) continue;
+            float ww = 0.f;
+            for (int sr = 0; sr < R; ++sr) {
+                const long long dq = ((long long)b << 32) + (long long)(2 * sr + 1 - R) * g.offq - tq;
+                const long long dd = vw.hq - (dq < 0 ? -dq : dq);
+                ww += dd > 0 ? fminf(vw.Lf, __int2float_rn((int)(dd >> 8)) * ws) : 0.f;
+            }
+            w[k] = ww;
+        }
+    }
+}
+
+// SUB: the kernel instantiation that serves sub-ray geometries (g.R > 1); the others never
+// contain the sub-ray code
+template <int KC, int AR, bool SUB = false>
 __device__ __forceinline__ void bp_weights(const GeoDev &g, const ViewGeo &vw, int slot, int ix,
                                            int iy, int &b0, typename ArithT<AR>::T (&w)[KC])
 {
     using T = typename ArithT<AR>::T;
     const int NB = g.NB;
+    if constexpr (SUB) {
+        bp_weights_sub<KC, AR>(g, vw, slot, ix, iy, b0, w);
+        return;
+    }
     if (vw.axis) {
         const int cross = vw.xdrive ? iy : ix;
         const RayGeo *rr = g.rays + (size_t)slot * NB;
@@ -397,7 +470,7 @@ __device__ __forceinline__ void bp_weights(const GeoDev &g, const ViewGeo &vw, i
 }
 
 // One table entry: pixel (ix, iy) (inside the image when `in`) against view u of the subset.
-template <int KC, int AR, int CAPX>
+template <int KC, int AR, int CAPX, bool SUB = false>
 __device__ __forceinline__ typename BpTable<KC, AR, CAPX>::E bp_entry(const GeoDev &g, int slot0, int u,
                                                                     bool in, int ix, int iy)
 {
@@ -405,7 +478,7 @@ __device__ __forceinline__ typename BpTable<KC, AR, CAPX>::E bp_entry(const GeoD
     int b0 = 0;
     T w[KC];
     if (in) {
-        bp_weights<KC, AR>(g, g.views[slot0 + u], slot0 + u, ix, iy, b0, w);
+        bp_weights<KC, AR, SUB>(g, g.views[slot0 + u], slot0 + u, ix, iy, b0, w);
     } else {
 #pragma unroll
         for (int k = 0; k < KC; ++k) w[k] = T(0);
@@ -430,7 +503,7 @@ __device__ __forceinline__ typename BpTable<KC, AR, CAPX>::E bp_entry(const GeoD
 // pixel pl and view u0 + uu is tb.e[uu * np + pl], so that threads of consecutive pixels touch
 // consecutive entries.  With one pixel per thread (single-plane images) each thread computes its
 // pixel's coordinates once and walks the views.
-template <int KC, int AR, int CAPX>
+template <int KC, int AR, int CAPX, bool SUB = false>
 __device__ __forceinline__ void bp_fill(const GeoDev &g, int slot0, int u0, int nvc, int j0,
                                         int np, BpTable<KC, AR, CAPX> &tb)
 {
@@ -440,14 +513,14 @@ __device__ __forceinline__ void bp_fill(const GeoDev &g, int slot0, int u0, int 
         const bool in = j < npix;
         const int ix = in ? j % g.N : 0, iy = in ? j / g.N : 0;
         for (int uu = 0; uu < nvc; ++uu)
-            tb.e[uu * np + pl] = bp_entry<KC, AR, CAPX>(g, slot0, u0 + uu, in, ix, iy);
+            tb.e[uu * np + pl] = bp_entry<KC, AR, CAPX, SUB>(g, slot0, u0 + uu, in, ix, iy);
         return;
     }
     for (int e = threadIdx.x; e < np * nvc; e += nthr) {
         const int uu = e / np, pl = e - uu * np;
         const int j = j0 + pl;
         const bool in = j < npix;
-        tb.e[e] = bp_entry<KC, AR, CAPX>(g, slot0, u0 + uu, in, in ? j % g.N : 0, in ? j / g.N : 0);
+        tb.e[e] = bp_entry<KC, AR, CAPX, SUB>(g, slot0, u0 + uu, in, in ? j % g.N : 0, in ? j / g.N : 0);
     }
 }
 

@@ -56,6 +56,11 @@ struct ViewGeo {
     double wslope;        // length per bin unit of (h - |delta|): rho / (major * minor)
     float wslopef;
     int axis;             // minor == 0: half-open rule, length L for delta in [-h, h)
+    // sub-ray model: cross-coordinate shift of half a sub-ray spacing (rho / (2 R a), a the
+    // driving component of the view's direction), grid units; sub-ray s of a bin starts
+    // (2 s + 1 - R) of them away from the bin's centre line
+    long long halfq;
+    double half;
 };
 
 struct RayGeo {
@@ -69,6 +74,8 @@ struct GeoDev {
     int N, P, Pp, G, NG;      // image side, planes, padded planes, group size, groups
     int V, NB, M, K;          // views, bins, subsets, max candidate bins per view in the gather
     int tuneS;                // forward projector chunks per ray picked by pet_autotune (0: heuristic)
+    int R;                    // sub-rays per bin (1: one line); scale includes the 1 / R
+    long long offq;           // half a sub-ray spacing in bin units, Q32.32 (2^32 / (2 R))
     double scale;             // sens * pixel_mm
     const ViewGeo *views;     // [V] in subset order
     const RayGeo *rays;       // [V * NB] in subset order

@@ -26,7 +26,7 @@ namespace pet {
 // [c Lc, (c + 1) Lc) of its ray, Lc = ceil(nd / S), so that short subsets still fill the GPU; the
 // S partial sums of a (ray, group) are combined in chunk order through shared memory
 // (deterministic).  A persistent grid strides over the virtual blocks of one scan or a batch.
-template <int G, int AR, int MODE>
+template <int G, int AR, int MODE, bool SUB = false>
 __global__ void __launch_bounds__(256, 3) fwd_kernel(const __grid_constant__ FwdArgs one, const Batch bt)
 {
     using T = typename ArithT<AR>::T;
@@ -60,11 +60,14 @@ __global__ void __launch_bounds__(256, 3) fwd_kernel(const __grid_constant__ Fwd
             const T *img = reinterpret_cast<const T *>(a.img) + (size_t)grp * G;
             const int Lc = (rg.nd + S - 1) / S;
             const int k0 = c * Lc, k1 = min(rg.nd, k0 + Lc);
+            // sub-rays of the bin (SUB instantiations only; the others walk its centre line)
+            const int nsr = SUB ? g.R : 1;
             if constexpr (AR == AR_FP64) {
                 const double step = vw.step, ast = fabs(vw.step), L = vw.L, im = vw.inv_minor;
+                for (int sr = 0; sr < nsr; ++sr)
                 for (int k = k0; k < k1; ++k) {
                     const int d = rg.d0 + k;
-                    const double lo = fma((double)k, step, rg.lo);
+                    const double lo = fma((double)k, step, rg.lo + (2 * sr + 1 - nsr) * vw.half);
                     const double hi = lo + ast;
                     const double f0 = floor(lo), f1 = floor(hi);
                     const int r0 = (int)f0, r1 = (int)f1;
@@ -88,8 +91,6 @@ __global__ void __launch_bounds__(256, 3) fwd_kernel(const __grid_constant__ Fwd
                 const float L = vw.Lf, imb = vw.inv_minorf;
                 const float *imf = reinterpret_cast<const float *>(img);
                 const unsigned dstep = (unsigned)ds * (unsigned)Pp, cstep = (unsigned)cs * (unsigned)Pp;
-                unsigned base = (unsigned)(rg.d0 + k0) * dstep;
-                long long lo = rg.loq + (long long)k0 * stp;
                 f2x sm[4], er[4], bl[4];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) { sm[q] = 0ull; er[q] = 0ull; bl[q] = 0ull; }
@@ -108,6 +109,9 @@ __global__ void __launch_bounds__(256, 3) fwd_kernel(const __grid_constant__ Fwd
                     }
                 };
                 int nb = 0;
+                for (int sr = 0; sr < nsr; ++sr) {
+                unsigned base = (unsigned)(rg.d0 + k0) * dstep;
+                long long lo = rg.loq + (long long)(2 * sr + 1 - nsr) * vw.halfq + (long long)k0 * stp;
                 for (int k = k0; k < k1; ++k) {
                     const long long hi = lo + ast;
                     const int r0 = (int)(lo >> 32), r1 = (int)(hi >> 32);
@@ -130,6 +134,7 @@ __global__ void __launch_bounds__(256, 3) fwd_kernel(const __grid_constant__ Fwd
                     lo += stp;
                     base += dstep;
                 }
+                }
                 merge();
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
@@ -145,10 +150,11 @@ __global__ void __launch_bounds__(256, 3) fwd_kernel(const __grid_constant__ Fwd
                 const long long stp = vw.stepq, ast = vw.absstepq;
                 const float L = vw.Lf, im = vw.inv_minorf * kQ32;
                 const float *imf = reinterpret_cast<const float *>(img);
-                long long lo = rg.loq + (long long)k0 * stp;
                 f2x sm[4], er[4];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) { sm[q] = 0ull; er[q] = 0ull; }
+                for (int sr = 0; sr < nsr; ++sr) {
+                long long lo = rg.loq + (long long)(2 * sr + 1 - nsr) * vw.halfq + (long long)k0 * stp;
                 for (int k = k0; k < k1; ++k) {
                     const int d = rg.d0 + k;
                     const long long hi = lo + ast;
@@ -174,6 +180,7 @@ __global__ void __launch_bounds__(256, 3) fwd_kernel(const __grid_constant__ Fwd
                     }
                     lo += stp;
                 }
+                }
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     float a0, a1, b0, b1;
@@ -185,7 +192,8 @@ __global__ void __launch_bounds__(256, 3) fwd_kernel(const __grid_constant__ Fwd
             } else {
                 const long long stp = vw.stepq, ast = vw.absstepq;
                 const float L = vw.Lf, im = vw.inv_minorf * kQ32;
-                long long lo = rg.loq + (long long)k0 * stp;
+                for (int sr = 0; sr < nsr; ++sr) {
+                long long lo = rg.loq + (long long)(2 * sr + 1 - nsr) * vw.halfq + (long long)k0 * stp;
                 for (int k = k0; k < k1; ++k) {
                     const int d = rg.d0 + k;
                     const long long hi = lo + ast;
@@ -200,6 +208,7 @@ __global__ void __launch_bounds__(256, 3) fwd_kernel(const __grid_constant__ Fwd
                     load_group<G, T>(img + (unsigned)(d * ds + (ok1 ? r1 : 0) * cs) * (unsigned)Pp, x1);
                     acc.add2terms(l0, x0, l1, x1);
                     lo += stp;
+                }
                 }
             }
         }
@@ -281,6 +290,12 @@ __global__ void __launch_bounds__(256, 3) fwd_kernel(const __grid_constant__ Fwd
 template <int G, int AR>
 static void fwd_dispatch_mode(const FwdArgs &a, const Batch &b, int mode, int grid, cudaStream_t st)
 {
+    if (a.g.R > 1) {
+        if (mode == FWD_PLAIN) fwd_kernel<G, AR, FWD_PLAIN, true><<<grid, 256, 0, st>>>(a, b);
+        else if (mode == FWD_RATIO) fwd_kernel<G, AR, FWD_RATIO, true><<<grid, 256, 0, st>>>(a, b);
+        else fwd_kernel<G, AR, FWD_OBJECTIVE, true><<<grid, 256, 0, st>>>(a, b);
+        return;
+    }
     if (mode == FWD_PLAIN) fwd_kernel<G, AR, FWD_PLAIN><<<grid, 256, 0, st>>>(a, b);
     else if (mode == FWD_RATIO) fwd_kernel<G, AR, FWD_RATIO><<<grid, 256, 0, st>>>(a, b);
     else fwd_kernel<G, AR, FWD_OBJECTIVE><<<grid, 256, 0, st>>>(a, b);
@@ -296,19 +311,24 @@ static void fwd_dispatch(const FwdArgs &a, const Batch &b, int mode, int arith, 
 }
 
 template <int G, int AR>
-static const void *fwd_fn_mode(int mode)
+static const void *fwd_fn_mode(int mode, int sub)
 {
+    if (sub) {
+        if (mode == FWD_PLAIN) return (const void *)fwd_kernel<G, AR, FWD_PLAIN, true>;
+        if (mode == FWD_RATIO) return (const void *)fwd_kernel<G, AR, FWD_RATIO, true>;
+        return (const void *)fwd_kernel<G, AR, FWD_OBJECTIVE, true>;
+    }
     if (mode == FWD_PLAIN) return (const void *)fwd_kernel<G, AR, FWD_PLAIN>;
     if (mode == FWD_RATIO) return (const void *)fwd_kernel<G, AR, FWD_RATIO>;
     return (const void *)fwd_kernel<G, AR, FWD_OBJECTIVE>;
 }
 
 template <int G>
-static const void *fwd_fn_g(int mode, int arith)
+static const void *fwd_fn_g(int mode, int arith, int sub)
 {
-    if (arith == AR_FP32) return fwd_fn_mode<G, AR_FP32>(mode);
-    if (arith == AR_KAHAN) return fwd_fn_mode<G, AR_KAHAN>(mode);
-    return fwd_fn_mode<G, AR_FP64>(mode);
+    if (arith == AR_FP32) return fwd_fn_mode<G, AR_FP32>(mode, sub);
+    if (arith == AR_KAHAN) return fwd_fn_mode<G, AR_KAHAN>(mode, sub);
+    return fwd_fn_mode<G, AR_FP64>(mode, sub);
 }
 
 // Resident 256-thread blocks per SM of one kernel instantiation (cached per function).
@@ -359,7 +379,7 @@ void forward_shape(FwdArgs &a, int mode, int arith)
     a.tpv = 1;
     if (mode == FWD_OBJECTIVE) {
         // each virtual block ends in a block reduction and a grid-wide ticket: one wave of them
-        const void *fn = a.g.G == 1 ? fwd_fn_g<1>(mode, arith) : fwd_fn_g<8>(mode, arith);
+        const void *fn = a.g.G == 1 ? fwd_fn_g<1>(mode, arith, a.g.R > 1) : fwd_fn_g<8>(mode, arith, a.g.R > 1);
         const long long slots = (long long)sm_count() * resident_blocks(fn);
         long long tpv = (ntiles + slots - 1) / slots;
         if (a.red.capacity > 0) tpv = std::max(tpv, (ntiles + a.red.capacity - 1) / a.red.capacity);

@@ -73,11 +73,12 @@ struct SrvClass {
     std::vector<Request *> running;
 };
 
-typedef std::tuple<int, int, double, int, int, double, int> GeoKey;   // desc without sens
+typedef std::tuple<int, int, double, int, int, double, int, int> GeoKey;   // desc without sens
 
 GeoKey key_of(const pet_geometry_desc &d)
 {
-    return GeoKey(d.n, d.nplanes, d.pixel_mm, d.nviews, d.nbins, d.bin_mm, d.nsubsets);
+    return GeoKey(d.n, d.nplanes, d.pixel_mm, d.nviews, d.nbins, d.bin_mm, d.nsubsets,
+                  d.subrays > 1 ? d.subrays : 1);
 }
 
 size_t geometry_bytes(const pet_geometry_desc &d)
@@ -472,7 +473,8 @@ extern "C" pet_status pet_serve_submit(pet_server *sv, const pet_request *rq, ui
         return fail(PET_ERR_INVALID, "pet_serve_submit: NULL argument");
     const pet_geometry_desc &d = rq->geom;
     if (d.n < 1 || d.nplanes < 1 || d.nviews < 1 || d.nbins < 1 || d.nsubsets < 1 ||
-        d.nsubsets > d.nviews || !(d.pixel_mm > 0) || !(d.bin_mm > 0) || !(d.sens > 0))
+        d.nsubsets > d.nviews || !(d.pixel_mm > 0) || !(d.bin_mm > 0) || !(d.sens > 0) ||
+        d.subrays < 0 || d.subrays > 64)
         return fail(PET_ERR_INVALID, "pet_serve_submit: invalid geometry description");
     PET_TRY(check_params(&rq->params));
     if (rq->params.regularizer == PET_REG_TV)

@@ -30,7 +30,7 @@ class PetError(RuntimeError):
 class GeometryDesc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("nplanes", ctypes.c_int), ("pixel_mm", ctypes.c_double),
                 ("nviews", ctypes.c_int), ("nbins", ctypes.c_int), ("bin_mm", ctypes.c_double),
-                ("nsubsets", ctypes.c_int), ("sens", ctypes.c_double)]
+                ("nsubsets", ctypes.c_int), ("sens", ctypes.c_double), ("subrays", ctypes.c_int)]
 
 
 class Params(ctypes.Structure):
@@ -168,8 +168,9 @@ def make_params(p, precision: int | None = None) -> Params:
 class Geometry:
     """pet_geometry handle (Sec. II-A/B geometry, subsets, sensitivity)."""
 
-    def __init__(self, n, nplanes, pixel_mm, nviews, nbins, bin_mm, nsubsets, sens, stream=None):
-        self.desc = GeometryDesc(n, nplanes, pixel_mm, nviews, nbins, bin_mm, nsubsets, sens)
+    def __init__(self, n, nplanes, pixel_mm, nviews, nbins, bin_mm, nsubsets, sens, stream=None,
+                 subrays=1):
+        self.desc = GeometryDesc(n, nplanes, pixel_mm, nviews, nbins, bin_mm, nsubsets, sens, subrays)
         h = _VP()
         _check(lib().pet_geometry_create(ctypes.byref(self.desc), _stream(stream), ctypes.byref(h)))
         self.handle = h
@@ -179,7 +180,7 @@ class Geometry:
     def from_dict(cls, geometry: dict, sens: float, stream=None):
         g = geometry
         return cls(g["n"], g["nplanes"], g["pixel_mm"], g["nviews"], g["nbins"], g["bin_mm"],
-                   g["nsubsets"], sens, stream)
+                   g["nsubsets"], sens, stream, int(g.get("subrays", 1)))
 
     def close(self):
         if getattr(self, "handle", None):
@@ -410,7 +411,7 @@ class Server:
         import numpy as np
         g = geometry
         desc = GeometryDesc(g["n"], g["nplanes"], g["pixel_mm"], g["nviews"], g["nbins"], g["bin_mm"],
-                            g["nsubsets"], sens)
+                            g["nsubsets"], sens, int(g.get("subrays", 1)))
         counts = np.ascontiguousarray(counts, dtype=np.int32)
         gamma = np.ascontiguousarray(gamma, dtype=np.float32)
         img0 = None if img0 is None else np.ascontiguousarray(img0, dtype=np.float32)
