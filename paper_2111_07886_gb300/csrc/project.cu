@@ -15,6 +15,9 @@
 #include "kernels.cuh"
 #include "profile.cuh"
 
+#ifndef FWD_MAX_CHUNKS
+#define FWD_MAX_CHUNKS 8        // most threads sharing one ray in the built-in chunking
+#endif
 #ifndef FWD_FAST
 #define FWD_FAST 1               // blocked compensated walk (see the G == 8 branch of fwd_kernel)
 #endif
@@ -369,7 +372,7 @@ void forward_shape(FwdArgs &a, int mode, int arith)
     const long long nrays = (long long)a.nviews * a.g.NB;
     const long long want = (long long)sm_count() * 2048;
     const long long have = std::max<long long>(1, nrays * a.g.NG);
-    int S = (int)std::min<long long>(8, std::max<long long>(1, (want + have - 1) / have));
+    int S = (int)std::min<long long>(FWD_MAX_CHUNKS, std::max<long long>(1, (want + have - 1) / have));
     S = std::max(1, std::min(S, a.g.N / 16));
     if (a.g.tuneS > 0 && mode != FWD_OBJECTIVE) S = a.g.tuneS;
     while (S > 1 && (256 / a.g.NG) % S) --S;          // S divides the rays-per-block budget

@@ -10,6 +10,9 @@
 #include "kernels.cuh"
 #include "profile.cuh"
 
+#ifndef UPDATE_G1_BLOCKS
+#define UPDATE_G1_BLOCKS 3      // resident blocks per SM the single-plane update kernel is built for
+#endif
 #ifndef UPDATE_X8_BLOCKS
 #define UPDATE_X8_BLOCKS 3      // resident blocks per SM the packed update kernel is built for
 #endif
@@ -210,8 +213,8 @@ __device__ __forceinline__ T scal(double d, float f)
 // group); the (pixel, view) weights of each tile are computed once into shared memory.  A
 // persistent grid strides over the virtual blocks of one scan or of a batch of scans.
 template <int G, int KC, int AR, bool SUB = false>
-__global__ void __launch_bounds__(256, 3) update_kernel(const __grid_constant__ UpdateArgs one,
-                                                     const Batch bt)
+__global__ void __launch_bounds__(256, G == 1 ? UPDATE_G1_BLOCKS : 3) update_kernel(
+    const __grid_constant__ UpdateArgs one, const Batch bt)
 {
     using T = typename ArithT<AR>::T;
     __shared__ BpTable<KC, AR> tb;
