@@ -153,7 +153,7 @@ pet_status pet_autotune_batch(pet_geometry *g, int concurrent, void *stream, int
 /* Sets the forward projector's ray chunks S directly (no counterpart in the paper): a choice
  * taken from an earlier pet_autotune, or fixed for a profiling run, where the profiler's own
  * per-launch cost distorts the autotuner's timings.  S = 0 returns to the built-in heuristic.
- * PET_ERR_INVALID unless S == 0 or 1 <= S <= 8 with S dividing 256 / ceil(nplanes / 8) (256 for
+ * PET_ERR_INVALID unless S == 0 or 1 <= S <= 16 with S dividing 256 / ceil(nplanes / 8) (256 for
  * one plane).  Same rule as pet_autotune: set it before creating states on the geometry. */
 pet_status pet_set_ray_chunks(pet_geometry *g, int S);
 

@@ -16,7 +16,7 @@
 #include "profile.cuh"
 
 #ifndef FWD_MAX_CHUNKS
-#define FWD_MAX_CHUNKS 8        // most threads sharing one ray in the built-in chunking
+#define FWD_MAX_CHUNKS 16       // most threads sharing one ray (built-in chunking and autotuner)
 #endif
 #ifndef FWD_FAST
 #define FWD_FAST 1               // blocked compensated walk (see the G == 8 branch of fwd_kernel)
@@ -363,8 +363,8 @@ int sm_count()
     return n;
 }
 
-// Chunks per ray (S) so that one subset projection has about one full-occupancy wave of
-// threads, with >= 16 driving steps per chunk; R rays per 256-thread virtual block.  The
+// Chunks per ray (S, at most FWD_MAX_CHUNKS) so that one subset projection has about one
+// full-occupancy wave of threads, with >= 16 driving steps per chunk; R rays per 256-thread virtual block.  The
 // objective mode groups its ray tiles into one wave of virtual blocks (each ends in a reduction
 // step), never more than its reducer holds partial sums for.
 void forward_shape(FwdArgs &a, int mode, int arith)
@@ -426,7 +426,7 @@ pet_status launch_forward_batch(const FwdArgs &shape, const Batch &b, int mode, 
 using namespace pet;
 
 // Autotuner: times the subset-0 forward projection of an image of ones for every admissible
-// chunk count S (1..8, dividing the 256-thread block budget) and keeps the fastest in the
+// chunk count S (1..16, dividing the 256-thread block budget) and keeps the fastest in the
 // geometry.  `concurrent` copies of the projection run as one batched launch (the persistent
 // grid of pet_batch), so that a geometry whose scans run in a batch is tuned with the GPU shared
 // the way the batch shares it; concurrent = 1 is a scan alone.  The choice is per geometry, so
@@ -455,7 +455,7 @@ static pet_status autotune_any(pet_geometry *g, int concurrent, cudaStream_t st,
     int bestS = 0;
     const int save = gd.tuneS;
     pet_status r = PET_OK;
-    for (int S = 1; S <= 8 && r == PET_OK; ++S) {
+    for (int S = 1; S <= FWD_MAX_CHUNKS && r == PET_OK; ++S) {
         if ((256 / gd.NG) % S) continue;
         gd.tuneS = S;
         FwdArgs fa{};
@@ -518,8 +518,8 @@ extern "C" pet_status pet_autotune_batch(pet_geometry *g, int concurrent, void *
 extern "C" pet_status pet_set_ray_chunks(pet_geometry *g, int S)
 {
     if (!g) return fail(PET_ERR_INVALID, "pet_set_ray_chunks: NULL geometry");
-    if (S < 0 || S > 8 || (S > 0 && (256 / g->dev.NG) % S))
-        return fail(PET_ERR_INVALID, "pet_set_ray_chunks: S must be 0 or in 1..8 and divide 256 / plane groups");
+    if (S < 0 || S > FWD_MAX_CHUNKS || (S > 0 && (256 / g->dev.NG) % S))
+        return fail(PET_ERR_INVALID, "pet_set_ray_chunks: S must be 0 or in 1..16 and divide 256 / plane groups");
     g->dev.tuneS = S;
     return PET_OK;
 }

@@ -11,7 +11,7 @@
 #include "profile.cuh"
 
 #ifndef UPDATE_G1_BLOCKS
-#define UPDATE_G1_BLOCKS 3      // resident blocks per SM the single-plane update kernel is built for
+#define UPDATE_G1_BLOCKS 4      // resident blocks per SM the single-plane update kernel is built for
 #endif
 #ifndef UPDATE_X8_BLOCKS
 #define UPDATE_X8_BLOCKS 3      // resident blocks per SM the packed update kernel is built for

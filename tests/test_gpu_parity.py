@@ -77,13 +77,13 @@ def test_set_ray_chunks():
     """Pinned ray chunks: invalid counts are rejected; every admissible count (and 0, the
     heuristic) gives the same projection within the parity bound."""
     g, og = _geoms(48, 11, 30, 69, 7, 1.0)            # 2 plane groups: S must divide 128
-    for bad in (3, 9, -1):
+    for bad in (3, 9, 17, 32, -1):
         with pytest.raises(pet.PetError) as e:
             g.set_ray_chunks(bad)
         assert e.value.status == pet.ERR_INVALID
     x = f32(synth.random_image((11, 48, 48), seed=21))
     ref = oracle.forward(og, 2, x)
-    for S in (1, 2, 8, 0):
+    for S in (1, 2, 8, 16, 0):
         g.set_ray_chunks(S)
         out = torch.empty(ref.shape, device=DEV)
         pet.forward_subset(g, 2, to_dev(x), out)
