@@ -207,6 +207,16 @@ pet_status pet_state_read_image(const pet_state *s, float *d_img, void *stream);
 pet_status pet_state_read_image_f64(const pet_state *s, double *d_img, void *stream);
 pet_status pet_state_objective(pet_state *s, double *h_phi, double *h_parts, void *stream);
 int pet_state_subiters(const pet_state *s);
+/* Checkpoint / resume (no counterpart in the paper).  pet_state_export: with h_buf NULL,
+ * *bytes = the size of the state's checkpoint; otherwise writes it to h_buf (*bytes >= that
+ * size; host memory, caller-owned) and synchronises `stream`.  The checkpoint holds the position
+ * (k, i), the Nesterov t, the current image, the frozen nu, the FP64 sums, the objective history
+ * and the TV dual variable.  pet_state_import: loads a checkpoint into a state created for the
+ * same geometry and parameters (same data: counts and gamma are not in the checkpoint);
+ * PET_ERR_INVALID for another geometry or parameters or a truncated buffer.  Subiterations after
+ * an import give the same bits as the uninterrupted run.  Synchronises `stream`. */
+pet_status pet_state_export(const pet_state *s, void *h_buf, size_t *bytes, void *stream);
+pet_status pet_state_import(pet_state *s, const void *h_buf, size_t bytes, void *stream);
 pet_status pet_state_reset(pet_state *s, const float *d_img_init, void *stream);
 void pet_state_destroy(pet_state *s);
 

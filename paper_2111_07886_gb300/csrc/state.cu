@@ -509,6 +509,105 @@ extern "C" pet_status pet_state_reset(pet_state *s, const float *d_img_init, voi
 
 extern "C" int pet_state_subiters(const pet_state *s) { return s ? s->J : -1; }
 
+// ------------------------------------------------------------------------------------------
+// Checkpoint / resume: everything a state carries from one subiteration to the next (schedule
+// position, Nesterov t, the current image in the internal layout, the frozen nu, the FP64 sums,
+// the objective history, the TV dual variable), as one host blob.
+// ------------------------------------------------------------------------------------------
+namespace {
+struct CkptHeader {
+    char magic[8];                  // "PETCKPT1"
+    int n, nplanes, nviews, nbins, nsubsets, subrays, precision, regularizer, rdp_3d, iterations;
+    int k, i, J, cur, have_frozen, objcap;
+    double tn;
+    unsigned long long q_bytes, tv_bytes;
+};
+const char kMagic[8] = {'P', 'E', 'T', 'C', 'K', 'P', 'T', '1'};
+
+size_t ckpt_bytes(const pet_state *s)
+{
+    const size_t tv = s->prm.regularizer == PET_REG_TV ? 2 * s->q_bytes : 0;
+    return sizeof(CkptHeader) + 2 * s->q_bytes + 16 * sizeof(double) +
+           (size_t)s->objcap * 3 * sizeof(double) + tv;
+}
+}  // namespace
+
+extern "C" pet_status pet_state_export(const pet_state *s, void *h_buf, size_t *bytes, void *stream)
+{
+    if (!s || !bytes) return fail(PET_ERR_INVALID, "pet_state_export: NULL argument");
+    const size_t need = ckpt_bytes(s);
+    if (!h_buf) { *bytes = need; return PET_OK; }
+    if (*bytes < need) return fail(PET_ERR_INVALID, "pet_state_export: buffer too small");
+    cudaStream_t st = as_stream(stream);
+    const pet_geometry_desc &d = s->g->desc;
+    CkptHeader h{};
+    memcpy(h.magic, kMagic, 8);
+    h.n = d.n; h.nplanes = d.nplanes; h.nviews = d.nviews; h.nbins = d.nbins;
+    h.nsubsets = d.nsubsets; h.subrays = s->g->dev.R; h.precision = s->prm.precision;
+    h.regularizer = s->prm.regularizer; h.rdp_3d = s->prm.rdp_3d; h.iterations = s->prm.iterations;
+    h.k = s->k; h.i = s->i; h.J = s->J; h.cur = s->cur; h.have_frozen = s->have_frozen;
+    h.objcap = s->objcap; h.tn = s->tn;
+    h.q_bytes = s->q_bytes;
+    h.tv_bytes = s->prm.regularizer == PET_REG_TV ? 2 * s->q_bytes : 0;
+    char *o = reinterpret_cast<char *>(h_buf);
+    memcpy(o, &h, sizeof(h));
+    o += sizeof(h);
+    PET_CUDA(cudaMemcpyAsync(o, s->f[s->cur], s->q_bytes, cudaMemcpyDeviceToHost, st));
+    o += s->q_bytes;
+    PET_CUDA(cudaMemcpyAsync(o, s->nu_frozen, s->q_bytes, cudaMemcpyDeviceToHost, st));
+    o += s->q_bytes;
+    PET_CUDA(cudaMemcpyAsync(o, s->sums, 16 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    o += 16 * sizeof(double);
+    PET_CUDA(cudaMemcpyAsync(o, s->objhist, (size_t)s->objcap * 3 * sizeof(double),
+                             cudaMemcpyDeviceToHost, st));
+    o += (size_t)s->objcap * 3 * sizeof(double);
+    if (h.tv_bytes)
+        PET_CUDA(cudaMemcpyAsync(o, reinterpret_cast<char *>(s->tvmem) + 3 * s->q_bytes, h.tv_bytes,
+                                 cudaMemcpyDeviceToHost, st));
+    PET_CUDA(cudaStreamSynchronize(st));
+    *bytes = need;
+    return PET_OK;
+}
+
+extern "C" pet_status pet_state_import(pet_state *s, const void *h_buf, size_t bytes, void *stream)
+{
+    if (!s || !h_buf) return fail(PET_ERR_INVALID, "pet_state_import: NULL argument");
+    if (bytes < sizeof(CkptHeader)) return fail(PET_ERR_INVALID, "pet_state_import: truncated checkpoint");
+    CkptHeader h;
+    memcpy(&h, h_buf, sizeof(h));
+    const pet_geometry_desc &d = s->g->desc;
+    if (memcmp(h.magic, kMagic, 8) != 0)
+        return fail(PET_ERR_INVALID, "pet_state_import: not a checkpoint of this library");
+    if (h.n != d.n || h.nplanes != d.nplanes || h.nviews != d.nviews || h.nbins != d.nbins ||
+        h.nsubsets != d.nsubsets || h.subrays != s->g->dev.R || h.precision != s->prm.precision ||
+        h.regularizer != s->prm.regularizer || h.rdp_3d != s->prm.rdp_3d ||
+        h.iterations != s->prm.iterations || h.q_bytes != s->q_bytes || h.objcap != s->objcap)
+        return fail(PET_ERR_INVALID, "pet_state_import: checkpoint of another geometry or parameters");
+    if (bytes < ckpt_bytes(s)) return fail(PET_ERR_INVALID, "pet_state_import: truncated checkpoint");
+    cudaStream_t st = as_stream(stream);
+    const char *o = reinterpret_cast<const char *>(h_buf) + sizeof(h);
+    s->cur = h.cur;
+    PET_CUDA(cudaMemcpyAsync(s->f[s->cur], o, s->q_bytes, cudaMemcpyHostToDevice, st));
+    o += s->q_bytes;
+    PET_CUDA(cudaMemcpyAsync(s->nu_frozen, o, s->q_bytes, cudaMemcpyHostToDevice, st));
+    o += s->q_bytes;
+    PET_CUDA(cudaMemcpyAsync(s->sums, o, 16 * sizeof(double), cudaMemcpyHostToDevice, st));
+    o += 16 * sizeof(double);
+    PET_CUDA(cudaMemcpyAsync(s->objhist, o, (size_t)s->objcap * 3 * sizeof(double),
+                             cudaMemcpyHostToDevice, st));
+    o += (size_t)s->objcap * 3 * sizeof(double);
+    if (h.tv_bytes)
+        PET_CUDA(cudaMemcpyAsync(reinterpret_cast<char *>(s->tvmem) + 3 * s->q_bytes, o, h.tv_bytes,
+                                 cudaMemcpyHostToDevice, st));
+    PET_CUDA(cudaStreamSynchronize(st));
+    s->k = h.k;
+    s->i = h.i;
+    s->J = h.J;
+    s->tn = h.tn;
+    s->have_frozen = h.have_frozen != 0;
+    return PET_OK;
+}
+
 extern "C" pet_status pet_state_objective_history(pet_state *s, double *h_obj, void *stream)
 {
     if (!s || !h_obj) return fail(PET_ERR_INVALID, "pet_state_objective_history: NULL argument");

@@ -81,6 +81,8 @@ SIGNATURES = {
     "pet_state_read_image_f64": (_I, [_VP, _VP, _VP]),
     "pet_state_objective": (_I, [_VP, _DP, _DP, _VP]),
     "pet_state_subiters": (_I, [_VP]),
+    "pet_state_export": (_I, [_VP, _VP, ctypes.POINTER(ctypes.c_size_t), _VP]),
+    "pet_state_import": (_I, [_VP, _VP, ctypes.c_size_t, _VP]),
     "pet_state_reset": (_I, [_VP, _VP, _VP]),
     "pet_state_destroy": (None, [_VP]),
     "pet_reconstruct": (_I, [_VP, _VP, _VP, ctypes.POINTER(Params), _VP, _DP, _VP]),
@@ -256,6 +258,19 @@ class State:
     @property
     def subiters(self) -> int:
         return lib().pet_state_subiters(self.handle)
+
+    def export(self, stream=None) -> bytes:
+        """The state's checkpoint (host bytes)."""
+        n = ctypes.c_size_t()
+        _check(lib().pet_state_export(self.handle, None, ctypes.byref(n), _stream(stream)))
+        buf = ctypes.create_string_buffer(n.value)
+        _check(lib().pet_state_export(self.handle, buf, ctypes.byref(n), _stream(stream)))
+        return buf.raw[:n.value]
+
+    def load(self, blob: bytes, stream=None):
+        """Resume from a checkpoint written by export() for the same geometry and parameters."""
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        _check(lib().pet_state_import(self.handle, buf, len(blob), _stream(stream)))
 
     def objective_history(self, stream=None):
         """Phi(f^k), k = 0..T, recorded so far (NaN where not computed)."""
