@@ -88,6 +88,10 @@ def lib():
             L.ora_alpha_km.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
             L.ora_objective.argtypes = [gp, ip, fp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
             L.ora_reconstruct.argtypes = [gp, ip, fp, ctypes.POINTER(Params), dp, ctypes.c_int, dp]
+            L.ora_reconstruct_m.argtypes = [gp, ip, fp, fp, ctypes.POINTER(Params), dp, ctypes.c_int, dp, dp]
+            L.ora_objective_m.argtypes = [gp, ip, fp, fp, dp, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_int, dp]
+            L.ora_sensitivity_m.argtypes = [gp, fp, dp]
             L.ora_reconstruct_snap.argtypes = [gp, ip, fp, ctypes.POINTER(Params), dp, ctypes.c_int, dp, dp]
             _lib = L
     return _lib
@@ -157,6 +161,22 @@ def sensitivity(g: Geom) -> np.ndarray:
     """p_j of Eq. pj, [N][N]."""
     out = np.zeros((g.n, g.n))
     lib().ora_sensitivity(ctypes.byref(g), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return out
+
+
+def _fptr(a):
+    """float32 [P][V][n_b] per-bin detection factors (or None: all ones) as a C pointer."""
+    if a is None:
+        return None, None
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def sensitivity_m(g: Geom, mult) -> np.ndarray:
+    """p_j of Eq. pj for the system matrix diag(mult) A: (A^T mult)_j / M per voxel, [P][N][N]."""
+    keep, mp = _fptr(mult)
+    out = np.zeros((g.nplanes, g.n, g.n))
+    lib().ora_sensitivity_m(ctypes.byref(g), mp, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
     return out
 
 
@@ -240,16 +260,18 @@ def alpha_km(nsub: int, rho: float, delta1: float, delta2: float) -> np.ndarray:
 
 
 def objective(g: Geom, counts, gamma, f, beta, gamma_r=2.0, eps=1e-12, three_d=False,
-              tv=False) -> dict:
-    """Phi(f) and its parts: sum(Af), sum(g ln(Af + gamma)), R(f) (R_TV with tv)."""
+              tv=False, mult=None) -> dict:
+    """Phi(f) and its parts: sum(Af), sum(g ln(Af + gamma)), R(f) (R_TV with tv); with
+    ``mult`` the system matrix is diag(mult) A."""
     counts = np.ascontiguousarray(counts, dtype=np.int32)
     gamma = np.ascontiguousarray(gamma, dtype=np.float32)
+    keep, mp = _fptr(mult)
     f, fp = _d(f)
     out = np.zeros(4)
-    lib().ora_objective3(ctypes.byref(g), counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
-                         gamma.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), fp, beta, gamma_r,
-                         eps, 2 if tv else (1 if three_d else 0),
-                         out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    lib().ora_objective_m(ctypes.byref(g), counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                          gamma.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), mp, fp, beta,
+                          gamma_r, eps, 2 if tv else (1 if three_d else 0),
+                          out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
     return dict(sum_af=out[0], sum_glog=out[1], rdp=out[2], phi=out[3])
 
 
@@ -261,19 +283,24 @@ def params_from(p) -> Params:
                   int(getattr(p, "tv_iters", 10)))
 
 
-def reconstruct(g: Geom, counts, gamma, params, f0, nsub: int = -1, with_objective=False):
-    """Run SDP-BSREM (Table I) for ``nsub`` subiterations (all T M when -1).
+def reconstruct(g: Geom, counts, gamma, params, f0, nsub: int = -1, with_objective=False,
+                mult=None):
+    """Run SDP-BSREM (Table I) for ``nsub`` subiterations (all T M when -1); with ``mult``
+    ([P][V][n_b] float32) the system matrix is diag(mult) A.
 
     Returns (f, objective history or None)."""
     counts = np.ascontiguousarray(counts, dtype=np.int32)
     gamma = np.ascontiguousarray(gamma, dtype=np.float32)
+    keep, mp = _fptr(mult)
     f = np.array(f0, dtype=np.float64, copy=True, order="C")
     prm = params if isinstance(params, Params) else params_from(params)
     obj = np.full(prm.iterations + 1, np.nan) if with_objective else None
-    lib().ora_reconstruct(ctypes.byref(g), counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
-                          gamma.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), ctypes.byref(prm),
-                          f.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), nsub,
-                          obj.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if obj is not None else None)
+    lib().ora_reconstruct_m(ctypes.byref(g), counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                            gamma.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), mp,
+                            ctypes.byref(prm), f.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                            nsub,
+                            obj.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if obj is not None else None,
+                            None)
     return f, obj
 
 

@@ -31,6 +31,11 @@
  * found by Siddon's method: all crossings of the ray with the grid lines are sorted, and each
  * piece between consecutive crossings is charged to the pixel that contains its midpoint.
  *
+ * Per-bin detection factors (the simulated system of Sec. IV-A includes uniform water
+ * attenuation): given a_i > 0 for every bin i, the system matrix is diag(a) A, i.e. the mean
+ * data are a_i (A f)_i + gamma_i, its transpose weights bin i by a_i, and p_j of Eq. pj becomes
+ * (A^T a)_j / M, which differs from plane to plane.  a = NULL stands for a_i = 1.
+ *
  * Layouts: images [P][N][N] (x fastest), full sinograms [P][V][n_b], subset sinograms
  * [P][V_i][n_b] with the subset's views in increasing order.  Subset i (0-based) holds the
  * views v with v mod M == i.
@@ -260,6 +265,20 @@ void ora_sensitivity(const ora_geom *g, double *pj)
     for (int j = 0; j < N * N; ++j)
         pj[j] = pj[j] > 0.0 ? pj[j] / g->nsubsets : 1.0 / g->nsubsets;
     free(ones);
+}
+
+/* p_j of Eq. pj for the system matrix diag(a) A: (A^T a)_j / M, or 1/M where it is 0.
+   a: [P][V][n_b] (NULL: a_i = 1); p: [P][N][N], one value per voxel. */
+void ora_sensitivity_m(const ora_geom *g, const float *a, double *pj)
+{
+    const size_t q = (size_t)g->nplanes * g->n * g->n;
+    const size_t nsino = (size_t)g->nplanes * g->nviews * g->nbins;
+    double *ad = (double *)malloc(sizeof(double) * nsino);
+    for (size_t k = 0; k < nsino; ++k) ad[k] = a ? (double)a[k] : 1.0;
+    ora_back(g, -1, ad, pj);
+    for (size_t j = 0; j < q; ++j)
+        pj[j] = pj[j] > 0.0 ? pj[j] / g->nsubsets : 1.0 / g->nsubsets;
+    free(ad);
 }
 
 /* ---------------------------------------------------------------------------------------
@@ -538,13 +557,14 @@ void ora_alpha_km(int nsub, double rho, double delta1, double delta2, double *al
  * Objective Phi(f) = <Af, 1> - <ln(Af + gamma), g> + beta R(f)   (Eqs. FidelityTerm,
  * ObjectiveFunction, RDP).  out[0] = <Af,1>, out[1] = <ln(Af+gamma), g>, out[2] = R, out[3] = Phi.
  * ------------------------------------------------------------------------------------- */
-void ora_objective3(const ora_geom *g, const int *counts, const float *gamma, const double *f,
-                    double beta, double gamma_r, double eps, int three_d, double *out);
+void ora_objective_m(const ora_geom *g, const int *counts, const float *gamma, const float *a,
+                     const double *f, double beta, double gamma_r, double eps, int three_d,
+                     double *out);
 
 void ora_objective(const ora_geom *g, const int *counts, const float *gamma, const double *f,
                    double beta, double gamma_r, double eps, double *out)
 {
-    ora_objective3(g, counts, gamma, f, beta, gamma_r, eps, 0, out);
+    ora_objective_m(g, counts, gamma, NULL, f, beta, gamma_r, eps, 0, out);
 }
 
 /* As ora_objective; three_d == 1 takes R over the 26 neighbours of each voxel, three_d == 2
@@ -552,9 +572,20 @@ void ora_objective(const ora_geom *g, const int *counts, const float *gamma, con
 void ora_objective3(const ora_geom *g, const int *counts, const float *gamma, const double *f,
                     double beta, double gamma_r, double eps, int three_d, double *out)
 {
+    ora_objective_m(g, counts, gamma, NULL, f, beta, gamma_r, eps, three_d, out);
+}
+
+/* As ora_objective3 for the system matrix diag(a) A (a: [P][V][n_b], NULL: a_i = 1): the sums
+   run over a_i (A f)_i. */
+void ora_objective_m(const ora_geom *g, const int *counts, const float *gamma, const float *a,
+                     const double *f, double beta, double gamma_r, double eps, int three_d,
+                     double *out)
+{
     size_t nsino = (size_t)g->nplanes * g->nviews * g->nbins;
     double *y = (double *)malloc(sizeof(double) * nsino);
     ora_forward(g, -1, f, y);
+    if (a)
+        for (size_t k = 0; k < nsino; ++k) y[k] *= (double)a[k];
     double s1 = 0.0, s2 = 0.0;
     for (size_t k = 0; k < nsino; ++k) {
         s1 += y[k];
@@ -580,13 +611,13 @@ void ora_objective3(const ora_geom *g, const int *counts, const float *gamma, co
  *   f      = P_t(f~)                                                           (Eq. OperatorPt)
  * nu is computed from f^{k,i-1}, the iterate the preconditioner is applied to.
  * ------------------------------------------------------------------------------------- */
-void ora_reconstruct_snap(const ora_geom *g, const int *counts, const float *gamma,
-                          const ora_params *prm, double *f, int nsub, double *obj, double *snaps);
+void ora_reconstruct_m(const ora_geom *g, const int *counts, const float *gamma, const float *a,
+                       const ora_params *prm, double *f, int nsub, double *obj, double *snaps);
 
 void ora_reconstruct(const ora_geom *g, const int *counts, const float *gamma,
                      const ora_params *prm, double *f, int nsub, double *obj)
 {
-    ora_reconstruct_snap(g, counts, gamma, prm, f, nsub, obj, NULL);
+    ora_reconstruct_m(g, counts, gamma, NULL, prm, f, nsub, obj, NULL);
 }
 
 /* As ora_reconstruct; snaps (optional, T x q doubles) receives f^{k+1} after each completed
@@ -594,13 +625,22 @@ void ora_reconstruct(const ora_geom *g, const int *counts, const float *gamma,
 void ora_reconstruct_snap(const ora_geom *g, const int *counts, const float *gamma,
                           const ora_params *prm, double *f, int nsub, double *obj, double *snaps)
 {
+    ora_reconstruct_m(g, counts, gamma, NULL, prm, f, nsub, obj, snaps);
+}
+
+/* As ora_reconstruct_snap for the system matrix diag(a) A (a: [P][V][n_b], NULL: a_i = 1):
+   the forward projection is scaled by a_i before the ratio, the backprojected ratio carries
+   a_i, and p_j is (A^T a)_j / M per voxel. */
+void ora_reconstruct_m(const ora_geom *g, const int *counts, const float *gamma, const float *a,
+                       const ora_params *prm, double *f, int nsub, double *obj, double *snaps)
+{
     const int N = g->n, P = g->nplanes, M = g->nsubsets, NB = g->nbins;
-    const size_t q = (size_t)N * N * P, npix = (size_t)N * N;
+    const size_t q = (size_t)N * N * P;
     const int T = prm->iterations;
     const int total = T * M;
     if (nsub < 0 || nsub > total) nsub = total;
-    double *pj = (double *)malloc(sizeof(double) * npix);
-    ora_sensitivity(g, pj);
+    double *pj = (double *)malloc(sizeof(double) * q);
+    ora_sensitivity_m(g, a, pj);
     double *alpha = (double *)malloc(sizeof(double) * (total > 0 ? total : 1));
     int kind = prm->precond;
     if (kind == 1 || kind == 3) ora_alpha_nesterov(total, alpha);
@@ -625,7 +665,7 @@ void ora_reconstruct_snap(const ora_geom *g, const int *counts, const float *gam
         W = (double *)malloc(sizeof(double) * q);
         zz = (double *)malloc(sizeof(double) * q);
     }
-    if (obj) { double o[4]; ora_objective3(g, counts, gamma, f, prm->beta, prm->gamma_r, prm->eps, rmode, o); obj[0] = o[3]; }
+    if (obj) { double o[4]; ora_objective_m(g, counts, gamma, a, f, prm->beta, prm->gamma_r, prm->eps, rmode, o); obj[0] = o[3]; }
     for (int J = 1; J <= nsub; ++J) {
         const int k = (J - 1) / M, i = (J - 1) % M + 1;
         const double lambda = prm->lambda0 / (prm->a * k + 1.0);
@@ -643,20 +683,26 @@ void ora_reconstruct_snap(const ora_geom *g, const int *counts, const float *gam
             }
             memcpy(nu, nu_frozen, sizeof(double) * q);
         }
-        /* data term of grad Phi_i: A_i^T (1 - g_i / (A_i f + gamma_i))  (App. A) */
+        /* data term of grad Phi_i: A_i^T (1 - g_i / (A_i f + gamma_i))  (App. A); with factors
+           the matrix is diag(a_i) A_i: A_i^T diag(a_i) (1 - g_i / (a_i A_i f + gamma_i)) */
         ora_forward(g, subset, f, ysub);
         for (int p = 0; p < P; ++p)
             for (int u = 0; u < nv; ++u)
                 for (int b = 0; b < NB; ++b) {
                     size_t ks = ((size_t)p * nv + u) * NB + b;
                     size_t kf = ((size_t)p * g->nviews + views[u]) * NB + b;
-                    ysub[ks] = 1.0 - (double)counts[kf] / (ysub[ks] + (double)gamma[kf]);
+                    if (a) {
+                        const double ai = (double)a[kf];
+                        ysub[ks] = ai * (1.0 - (double)counts[kf] / (ai * ysub[ks] + (double)gamma[kf]));
+                    } else {
+                        ysub[ks] = 1.0 - (double)counts[kf] / (ysub[ks] + (double)gamma[kf]);
+                    }
                 }
         ora_back(g, subset, ysub, grad);
         if (tv) {
             /* TV variant: the data step, then the proximal step of (beta / M) R_TV */
             for (size_t j = 0; j < q; ++j) {
-                const double fj = f[j], pjj = pj[j % npix];
+                const double fj = f[j], pjj = pj[j];
                 const double S = fj < 0.5 * prm->U ? fj / pjj : (prm->U - fj) / pjj;
                 W[j] = lambda * alpha[J - 1] * nu[j] * S;
                 zz[j] = fj - W[j] * grad[j];
@@ -672,7 +718,7 @@ void ora_reconstruct_snap(const ora_geom *g, const int *counts, const float *gam
         else ora_rdp_grad(N, P, f, prm->gamma_r, prm->eps, rgrad);
         for (size_t j = 0; j < q; ++j) {
             const double d = grad[j] + prm->beta / M * rgrad[j];
-            const double fj = f[j], pjj = pj[j % npix];
+            const double fj = f[j], pjj = pj[j];
             const double S = fj < 0.5 * prm->U ? fj / pjj : (prm->U - fj) / pjj;
             double ft = fj - lambda * alpha[J - 1] * nu[j] * S * d;
             if (ft <= 0.0) ft = prm->t;
@@ -682,7 +728,7 @@ void ora_reconstruct_snap(const ora_geom *g, const int *counts, const float *gam
         }
         if (obj && i == M) {
             double o[4];
-            ora_objective3(g, counts, gamma, f, prm->beta, prm->gamma_r, prm->eps, rmode, o);
+            ora_objective_m(g, counts, gamma, a, f, prm->beta, prm->gamma_r, prm->eps, rmode, o);
             obj[k + 1] = o[3];
         }
         if (snaps && i == M) memcpy(snaps + (size_t)k * q, f, sizeof(double) * q);
