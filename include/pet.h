@@ -142,7 +142,8 @@ void pet_geometry_destroy(pet_geometry *g);
  * admissible number of ray chunks (threads sharing one ray) and keeps the fastest in the
  * geometry; *best_S (optional) receives it.  Tune before creating states on the geometry (the
  * chunking changes the order of the ray sums, within rounding).  The projection is timed on an
- * image of ones, best of 5 after a warm-up.  Synchronises `stream`.
+ * image of ones, best of 7 runs of 4 launches after a warm-up; a larger chunk count replaces a
+ * smaller one only when it is more than 3 % faster.  Synchronises `stream`.
  * pet_autotune_batch: the same, with `concurrent` (1..4096) copies of the projection running as
  * one batched launch, as they do when that many scans of the geometry step together in a
  * pet_batch or a server; the choice is kept in the geometry and used alone and in batches alike,
