@@ -203,6 +203,19 @@ pet_status pet_back_subset_f64(const pet_geometry *g, int subset, const double *
 pet_status pet_state_create(const pet_geometry *g, const int32_t *d_counts, const float *d_gamma,
                             const pet_params *params, const float *d_img_init, void *stream,
                             pet_state **out);
+/* pet_state_create_attn: a scan whose system matrix carries per-bin detection factors a_i
+ * (attenuation, times normalisation where wanted; the simulated system of Sec. IV-A includes
+ * uniform water attenuation): A becomes diag(a) A, so the mean data are a_i (A f)_i + gamma_i,
+ * the ratio term backprojected by each subiteration is a_i (1 - g_i / (a_i (A f)_i + gamma_i)),
+ * and p_j of Eq. pj is (A^T a)_j / M for every voxel (1/M where it is 0), computed once at
+ * creation by an FP64 backprojection of a.  d_mult: float [P][V][NB] like gamma, finite and
+ * >= 0 (PET_ERR_INVALID otherwise), copied into the state.  Objectives of the state
+ * (pet_state_objective, the objective history) use diag(a) A.  Such states step alone and in
+ * batches; the server does not take them.  Synchronises `stream`. */
+pet_status pet_state_create_attn(const pet_geometry *g, const int32_t *d_counts,
+                                 const float *d_gamma, const float *d_mult,
+                                 const pet_params *params, const float *d_img_init, void *stream,
+                                 pet_state **out);
 pet_status pet_subiter(pet_state *s, void *stream);
 pet_status pet_state_read_image(const pet_state *s, float *d_img, void *stream);
 pet_status pet_state_read_image_f64(const pet_state *s, double *d_img, void *stream);
@@ -213,7 +226,8 @@ int pet_state_subiters(const pet_state *s);
  * size; host memory, caller-owned) and synchronises `stream`.  The checkpoint holds the position
  * (k, i), the Nesterov t, the current image, the frozen nu, the FP64 sums, the objective history
  * and the TV dual variable.  pet_state_import: loads a checkpoint into a state created for the
- * same geometry and parameters (same data: counts and gamma are not in the checkpoint);
+ * same geometry and parameters (same data: counts, gamma and detection factors are not in the
+ * checkpoint, but whether the scan has detection factors is checked);
  * PET_ERR_INVALID for another geometry or parameters or a truncated buffer.  Subiterations after
  * an import give the same bits as the uninterrupted run.  Synchronises `stream`. */
 pet_status pet_state_export(const pet_state *s, void *h_buf, size_t *bytes, void *stream);
@@ -226,6 +240,8 @@ void pet_state_destroy(pet_state *s);
  * d_img_inout: f^0 in, f^T out (float [P][N][N]).  h_objective: NULL, or T+1 doubles receiving
  * Phi(f^k), k = 0..T.  Synchronises `stream`.
  * pet_reconstruct_host: the same from host buffers (copies in and out inside the call).
+ * pet_reconstruct_attn: the same for a scan with per-bin detection factors d_mult (float
+ *   [P][V][NB], device; see pet_state_create_attn).
  * ---------------------------------------------------------------------------------------- */
 pet_status pet_reconstruct(const pet_geometry *g, const int32_t *d_counts, const float *d_gamma,
                            const pet_params *params, float *d_img_inout, double *h_objective,
@@ -233,6 +249,10 @@ pet_status pet_reconstruct(const pet_geometry *g, const int32_t *d_counts, const
 pet_status pet_reconstruct_host(const pet_geometry *g, const int32_t *h_counts,
                                 const float *h_gamma, const pet_params *params,
                                 float *h_img_inout, double *h_objective, void *stream);
+pet_status pet_reconstruct_attn(const pet_geometry *g, const int32_t *d_counts,
+                                const float *d_gamma, const float *d_mult,
+                                const pet_params *params, float *d_img_inout,
+                                double *h_objective, void *stream);
 
 /* ------------------------------------------------------------------------------------------
  * Single steps of the hot path, for parity checks (same kernels as pet_subiter).

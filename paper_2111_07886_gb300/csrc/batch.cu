@@ -38,6 +38,7 @@ struct BatchClass {
     int G = 0, arith = 0, KC = 0;
     int z3 = 0;                               // 3-D prior (the generic update and mu kernels)
     int sub = 0;                              // sub-ray geometry (the sub-ray update kernel)
+    int vox = 0;                              // detection factors: p per voxel (generic update)
     int cap = 0;                              // scan slots of this class
     std::vector<pet_state *> slot;            // nullptr = empty
     std::vector<bool> objective;              // per slot: plan objectives
@@ -151,9 +152,10 @@ extern "C" void pet_batch_destroy(pet_batch *b)
 static pet_status class_for(pet_batch *b, pet_state *s, BatchClass **out)
 {
     const int G = s->g->dev.G, arith = s->arith, KC = kc_of(s), z3 = s->prm.rdp_3d;
-    const int sub = s->g->dev.R > 1;
+    const int sub = s->g->dev.R > 1, vox = s->attn ? 1 : 0;
     for (BatchClass *c : b->classes)
-        if (c->G == G && c->arith == arith && c->KC == KC && c->z3 == z3 && c->sub == sub) {
+        if (c->G == G && c->arith == arith && c->KC == KC && c->z3 == z3 && c->sub == sub &&
+            c->vox == vox) {
             *out = c;
             return PET_OK;
         }
@@ -163,6 +165,7 @@ static pet_status class_for(pet_batch *b, pet_state *s, BatchClass **out)
     c->KC = KC;
     c->z3 = z3;
     c->sub = sub;
+    c->vox = vox;
     c->cap = b->capacity;
     c->slot.assign(c->cap, nullptr);
     c->objective.assign(c->cap, false);
@@ -278,6 +281,7 @@ static pet_status class_launches(pet_batch *b, BatchClass *c, const BatchClass::
     us.g.K = c->KC;
     us.g.R = c->sub ? 2 : 1;                  // selects the sub-ray kernel (the count comes per scan)
     us.z3 = c->z3;
+    us.vox = c->vox;
     ImageArgs is{};
     is.g.G = c->G;
     is.g.K = c->KC;

@@ -30,10 +30,10 @@ __global__ void img_from_internal(const S *src, D *dst, int npix, int P, int Pp)
 }
 
 // full [P][V][NB] (original view order) or subset [P][nviews][NB] -> [nviews][NB][Pp]
-template <typename E>
-__global__ void sino_to_internal(const E *src, E *dst, const int *view_of_slot, int slot0,
+template <typename E, typename D = E>
+__global__ void sino_to_internal(const E *src, D *dst, const int *view_of_slot, int slot0,
                                  int nviews, int V, int NB, int P, int Pp, int src_is_subset,
-                                 E pad)
+                                 D pad)
 {
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (tid >= (long long)nviews * NB * Pp) return;
@@ -44,7 +44,7 @@ __global__ void sino_to_internal(const E *src, E *dst, const int *view_of_slot, 
     if (p >= P) { dst[tid] = pad; return; }
     const int v = src_is_subset ? u : view_of_slot[slot0 + u];
     const int vn = src_is_subset ? nviews : V;
-    dst[tid] = src[((size_t)p * vn + v) * NB + b];
+    dst[tid] = (D)src[((size_t)p * vn + v) * NB + b];
 }
 
 // [nviews][NB][Pp] -> [P][nviews][NB], or -> [P][V][NB] in original view order when
@@ -78,6 +78,14 @@ __global__ void check_data(const int *counts, const float *gamma, size_t n, int 
     if (i >= n) return;
     const float gm = gamma[i];
     if (counts[i] < 0 || !(gm > 0.f) || !isfinite(gm)) atomicOr(flag, 1);
+}
+
+__global__ void check_factors(const float *mult, size_t n, int *flag)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float a = mult[i];
+    if (!(a >= 0.f) || !isfinite(a)) atomicOr(flag, 1);
 }
 
 static inline unsigned blocks(long long n) { return (unsigned)((n + 255) / 256); }
@@ -117,8 +125,11 @@ pet_status to_internal_sino(const GeoDev &g, const int *d_view_of_slot, int slot
     const long long n = (long long)nviews * g.NB * g.Pp;
     if (n == 0) return PET_OK;
     LaunchScope ls(PET_K_LAYOUT, st);
-    // elem: 0 int32 counts (pad 0), 1 float gamma (pad 1), 2 float data (pad 0), 3 double data
-    if (elem == 0)
+    // elem: 0 int32 counts (pad 0), 1 float gamma (pad 1), 2 float data (pad 0), 3 double
+    // data, 4 float data to double (pad 0)
+    if (elem == 4)
+        sino_to_internal<float, double><<<blocks(n), 256, 0, st>>>((const float *)src, (double *)dst, d_view_of_slot, slot0, nviews, g.V, g.NB, g.P, g.Pp, src_is_subset, 0.0);
+    else if (elem == 0)
         sino_to_internal<int><<<blocks(n), 256, 0, st>>>((const int *)src, (int *)dst, d_view_of_slot, slot0, nviews, g.V, g.NB, g.P, g.Pp, src_is_subset, 0);
     else if (elem == 1)
         sino_to_internal<float><<<blocks(n), 256, 0, st>>>((const float *)src, (float *)dst, d_view_of_slot, slot0, nviews, g.V, g.NB, g.P, g.Pp, src_is_subset, 1.f);
@@ -150,6 +161,16 @@ pet_status fill_internal_ones(const GeoDev &g, void *dst, int is_double, cudaStr
     else img_ones_internal<float><<<blocks(n), 256, 0, st>>>((float *)dst, n, g.P, g.Pp);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? PET_OK : cuda_fail(e, "img_ones_internal");
+}
+
+// Per-bin detection factors: finite and >= 0 (sets *d_flag, which the caller cleared, else).
+pet_status validate_factors(const float *mult, size_t n, int *d_flag, cudaStream_t st)
+{
+    if (n == 0) return PET_OK;
+    LaunchScope ls(PET_K_LAYOUT, st);
+    check_factors<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(mult, n, d_flag);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? PET_OK : cuda_fail(e, "check_factors");
 }
 
 pet_status validate_data(const GeoDev &g, const int *counts, const float *gamma, size_t n,

@@ -127,6 +127,8 @@ struct FwdArgs {
     void *out;                 // [nviews*NB][Pp]: y, or w = 1 - counts/(y + gamma)
     const int *counts;         // [nviews*NB][Pp] (ratio / objective modes)
     const float *gamma;        // [nviews*NB][Pp]
+    const float *mult;         // [nviews*NB][Pp] per-bin detection factors a_i (ratio /
+                               // objective modes; NULL: a_i = 1): y = a_i (A f)_i + gamma_i
     Reducer red;               // objective mode
     double *result;            // objective mode: 2 doubles (sum y, sum g ln(y + gamma))
     int S, R;                  // launch shape: chunks per ray, rays per ray tile
@@ -158,7 +160,8 @@ struct UpdateArgs {
     const void *w;             // subset ratio term [nviews*NB][Pp]
     const void *f;             // f^{k,i-1} [N*N][Pp]
     void *fout;                // f^{k,i}
-    const void *invp;          // [N*N] (float or double)
+    const void *invp;          // [N*N], or [N*N][Pp] when vox (float or double)
+    int vox;                   // 1: p differs per voxel (a scan with per-bin detection factors)
     double invp_scale;         // multiplies invp (a scan whose sens differs from the geometry's)
     void *nu_frozen;           // [N*N][Pp]
     int nu_mode;               // 0: nu = 1, 1: from f, 2: from f and stored, 3: frozen
@@ -221,6 +224,9 @@ struct pet_state {
     void *w = nullptr;              // ratio term of the largest subset
     int *counts = nullptr;          // [V][NB][Pp], views sorted by subset
     float *gamma = nullptr;
+    float *mult = nullptr;          // per-bin detection factors [V][NB][Pp] (buffer)
+    bool attn = false;              // the loaded scan has per-bin detection factors (mult)
+    void *invp_vox = nullptr;       // 1 / p_j per voxel [N*N][Pp] for diag(a) A (with mult)
     void *nu_frozen = nullptr;
     bool have_frozen = false;
     void *tvmem = nullptr;          // TV variant: z, W, xbar, px, py (each q_bytes)
@@ -299,6 +305,7 @@ pet_status to_internal_sino(const GeoDev &g, const int *d_view_of_slot, int slot
                             cudaStream_t st);
 pet_status from_internal_sino(const GeoDev &g, const int *d_view_of_slot, int nviews,
                               const void *src, void *dst, int is_double, cudaStream_t st);
+pet_status validate_factors(const float *mult, size_t n, int *d_flag, cudaStream_t st);
 pet_status validate_data(const GeoDev &g, const int *counts, const float *gamma, size_t n,
                          int *d_flag, cudaStream_t st);
 

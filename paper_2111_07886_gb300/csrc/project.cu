@@ -21,6 +21,12 @@
 #ifndef FWD_FAST
 #define FWD_FAST 1               // blocked compensated walk (see the G == 8 branch of fwd_kernel)
 #endif
+#ifndef FWD_TILE_ORDER
+#define FWD_TILE_ORDER 0         // 1: ray tiles within one view, centre bins first (long rays first)
+#endif
+#ifndef FWD_ANY_S
+#define FWD_ANY_S 0              // 1: any chunk count S <= 16 (R = floor(256 / (S NG)) rays a block)
+#endif
 
 namespace pet {
 
@@ -43,15 +49,31 @@ __global__ void __launch_bounds__(256, 3) fwd_kernel(const __grid_constant__ Fwd
         const GeoDev &g = a.g;
         const int NG = g.NG, NB = g.NB, N = g.N, Pp = g.Pp, S = a.S, R = a.R;
         const int nrays = a.nviews * NB;
+#if FWD_TILE_ORDER
+        const int tpv_view = (NB + R - 1) / R;       // tiles of one view
+        const int ntiles = a.nviews * tpv_view;
+#else
         const int ntiles = (nrays + R - 1) / R;
+#endif
         const bool lane_ok = (int)threadIdx.x < R * S * NG;
         double obj[2] = {0.0, 0.0};
         for (int tile = vloc * a.tpv; tile < min(ntiles, (vloc + 1) * a.tpv); ++tile) {
         const int grp = threadIdx.x % NG;
         const int c = (threadIdx.x / NG) % S;
         const int rl = threadIdx.x / (NG * S);
+#if FWD_TILE_ORDER
+        // tile rank t -> (view, tile of the view) with the view's tiles taken from its centre
+        // outwards (c, c + 1, c - 1, c + 2, ...; c the lower middle), so that the longest rays
+        // run first and the launch ends on short ones
+        const int tu = tile % a.nviews, tr = tile / a.nviews;
+        const int tb = (tpv_view - 1) / 2 + ((tr & 1) ? (tr + 1) / 2 : -(tr / 2));
+        const int bin = tb * R + rl;
+        const int ray = tu * NB + bin;               // subset-local ray index u * NB + b
+        const bool live = lane_ok && bin < NB;
+#else
         const int ray = tile * R + rl;               // subset-local ray index u * NB + b
         const bool live = lane_ok && ray < nrays;
+#endif
         GroupSum<G, AR> acc;
         acc.zero();
         if (live) {
@@ -260,12 +282,17 @@ __global__ void __launch_bounds__(256, 3) fwd_kernel(const __grid_constant__ Fwd
                 float gam[G];
                 load_group_i<G>(a.counts + o, cnt);
                 load_group<G, float>(a.gamma + o, gam);
+                // per-bin detection factors: the system matrix is diag(a) A, so the mean is
+                // a_i (A f)_i + gamma_i and the backprojected ratio carries a_i (a_i = 1, exact
+                // in the products, without factors)
+                const float *mp = a.mult ? a.mult + o : nullptr;
                 if constexpr (MODE == FWD_RATIO) {
                     T w[G];
 #pragma unroll
                     for (int p = 0; p < G; ++p) {
-                        const T y = scale * tot[p] + (T)gam[p];
-                        w[p] = (grp * G + p < g.P) ? T(1) - (T)cnt[p] / y : T(0);
+                        const T m = mp ? (T)__ldg(mp + p) : T(1);
+                        const T y = scale * (tot[p] * m) + (T)gam[p];
+                        w[p] = (grp * G + p < g.P) ? m * (T(1) - (T)cnt[p] / y) : T(0);
                     }
                     store_group<G, T>(reinterpret_cast<T *>(a.out) + o, w);
                 } else {
@@ -275,7 +302,7 @@ __global__ void __launch_bounds__(256, 3) fwd_kernel(const __grid_constant__ Fwd
 #pragma unroll
                     for (int p = 0; p < G; ++p) {
                         if (grp * G + p < g.P) {
-                            const T af = scale * tot[p];
+                            const T af = scale * (mp ? tot[p] * (T)__ldg(mp + p) : tot[p]);
                             s_af += af;
                             if (cnt[p] != 0) s_gl += (double)cnt[p] * log((double)af + (double)gam[p]);
                         }
@@ -375,10 +402,17 @@ void forward_shape(FwdArgs &a, int mode, int arith)
     int S = (int)std::min<long long>(FWD_MAX_CHUNKS, std::max<long long>(1, (want + have - 1) / have));
     S = std::max(1, std::min(S, a.g.N / 16));
     if (a.g.tuneS > 0 && mode != FWD_OBJECTIVE) S = a.g.tuneS;
+#if !FWD_ANY_S
     while (S > 1 && (256 / a.g.NG) % S) --S;          // S divides the rays-per-block budget
+#endif
+    S = std::max(1, std::min(S, 256 / a.g.NG));       // S NG threads share a ray tile
     a.S = S;
     a.R = std::max(1, 256 / (S * a.g.NG));
+#if FWD_TILE_ORDER
+    const long long ntiles = (long long)a.nviews * ((a.g.NB + a.R - 1) / a.R);
+#else
     const long long ntiles = (nrays + a.R - 1) / a.R;
+#endif
     a.tpv = 1;
     if (mode == FWD_OBJECTIVE) {
         // each virtual block ends in a block reduction and a grid-wide ticket: one wave of them
@@ -457,7 +491,8 @@ static pet_status autotune_any(pet_geometry *g, int concurrent, cudaStream_t st,
     const int save = gd.tuneS;
     pet_status r = PET_OK;
     for (int S = 1; S <= FWD_MAX_CHUNKS && r == PET_OK; ++S) {
-        if ((256 / gd.NG) % S) continue;
+        if (!FWD_ANY_S && (256 / gd.NG) % S) continue;
+        if (S * gd.NG > 256) break;
         gd.tuneS = S;
         FwdArgs fa{};
         fa.g = gd;
@@ -521,7 +556,8 @@ extern "C" pet_status pet_autotune_batch(pet_geometry *g, int concurrent, void *
 extern "C" pet_status pet_set_ray_chunks(pet_geometry *g, int S)
 {
     if (!g) return fail(PET_ERR_INVALID, "pet_set_ray_chunks: NULL geometry");
-    if (S < 0 || S > FWD_MAX_CHUNKS || (S > 0 && (256 / g->dev.NG) % S))
+    if (S < 0 || S > FWD_MAX_CHUNKS || (S > 0 && !FWD_ANY_S && (256 / g->dev.NG) % S) ||
+        S * g->dev.NG > 256)
         return fail(PET_ERR_INVALID, "pet_set_ray_chunks: S must be 0 or in 1..16 and divide 256 / plane groups");
     g->dev.tuneS = S;
     return PET_OK;

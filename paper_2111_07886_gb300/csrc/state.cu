@@ -85,7 +85,12 @@ static void state_free(pet_state *s)
     rel(s->redmem);
     rel(s->flag);
     rel(s->tvmem);
+    rel(s->mult);
+    rel(s->invp_vox);
     s->tvmem = nullptr;
+    s->mult = nullptr;
+    s->invp_vox = nullptr;
+    s->attn = false;
     s->f[0] = s->f[1] = s->w = s->nu_frozen = s->redmem = nullptr;
     s->counts = nullptr;
     s->gamma = nullptr;
@@ -94,9 +99,10 @@ static void state_free(pet_state *s)
 }
 
 // (Re)allocate the state's buffers for geometry g and arithmetic `arith` (no-op when they fit);
-// tv: also the buffers of the TV variant's proximal step (z, W, xbar and the dual variable).
+// tv: also the buffers of the TV variant's proximal step (z, W, xbar and the dual variable);
+// attn: also the per-bin detection factors and the per-voxel 1 / p_j they imply.
 static pet_status state_alloc(pet_state *s, const pet_geometry *g, int arith, int iterations,
-                              bool tv = false)
+                              bool tv = false, bool attn = false)
 {
     const GeoDev &gd = g->dev;
     const size_t esz = arith == AR_FP64 ? 8 : 4;
@@ -105,7 +111,8 @@ static pet_status state_alloc(pet_state *s, const pet_geometry *g, int arith, in
     for (int i = 0; i < gd.M; ++i) maxv = std::max(maxv, g->voff[i + 1] - g->voff[i]);
     const size_t w_bytes = (size_t)maxv * gd.NB * gd.Pp * esz;
     const size_t sino = (size_t)gd.V * gd.NB * gd.Pp;
-    if (s->g == g && s->esz == esz && s->f[0] && s->objcap >= iterations + 1 && (!tv || s->tvmem)) {
+    if (s->g == g && s->esz == esz && s->f[0] && s->objcap >= iterations + 1 && (!tv || s->tvmem) &&
+        (!attn || s->mult)) {
         s->arith = arith;
         return PET_OK;
     }
@@ -134,6 +141,10 @@ static pet_status state_alloc(pet_state *s, const pet_geometry *g, int arith, in
     reducer_bind(s->red, s->redmem, kRedCap, 2);
     PET_CUDA(get((void **)&s->flag, sizeof(int)));
     if (tv) PET_CUDA(get(&s->tvmem, 5 * q_bytes));
+    if (attn) {
+        PET_CUDA(get((void **)&s->mult, sino * sizeof(float)));
+        PET_CUDA(get(&s->invp_vox, q_bytes));
+    }
     if (!as) PET_CUDA(cudaStreamSynchronize(nullptr));
     return PET_OK;
 }
@@ -157,25 +168,78 @@ static pet_status state_sum_f(pet_state *s, cudaStream_t st)
     return launch_sum(a, s->arith, st);
 }
 
-// Load data (counts, gamma: [P][V][NB], device) and f^0 ([P][N][N] float, device) into an
-// allocated state and reset the schedule to (k, i) = (0, 1).  Validates the data (synchronises).
+// 1 / p_j per voxel from the FP64 backprojection bp = A^T a (Eq. pj for diag(a) A).
+template <typename T>
+__global__ void finish_sensitivity_vox(const double *bp, size_t q, int M, T *invp)
+{
+    const size_t j = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= q) return;
+    const double v = bp[j];
+    invp[j] = (T)(1.0 / (v > 0.0 ? v / M : 1.0 / M));
+}
+
+// The per-bin detection factors of a scan ([P][V][NB], device): their internal copy, and
+// p_j = (A^T a)_j / M per voxel (1/M where it is 0) by one FP64 backprojection of a over all
+// views, kept as 1 / p_j in the state's arithmetic.
+static pet_status load_factors(pet_state *s, const float *d_mult, cudaStream_t st)
+{
+    const pet_geometry *g = s->g;
+    const GeoDev &gd = g->dev;
+    PET_TRY(to_internal_sino(gd, g->d_view_of_slot, 0, gd.V, d_mult, s->mult, 2, 0, st));
+    const size_t nsino = (size_t)gd.V * gd.NB * gd.Pp, q = (size_t)gd.N * gd.N * gd.Pp;
+    double *ad = nullptr, *bp = nullptr;
+    PET_CUDA(cudaMallocAsync((void **)&ad, nsino * sizeof(double), st));
+    pet_status r = cuda_ok(cudaMallocAsync((void **)&bp, q * sizeof(double), st),
+                           "per-voxel sensitivity");
+    if (r == PET_OK) r = to_internal_sino(gd, g->d_view_of_slot, 0, gd.V, d_mult, ad, 4, 0, st);
+    if (r == PET_OK) {
+        BackArgs ba{};
+        ba.g = gd;
+        ba.slot0 = 0;
+        ba.nviews = gd.V;
+        ba.proj = ad;
+        ba.img = bp;
+        r = launch_back(ba, AR_FP64, st);
+    }
+    if (r == PET_OK) {
+        LaunchScope ls(PET_K_OTHER, st);
+        const unsigned blk = (unsigned)((q + 255) / 256);
+        if (s->arith == AR_FP64)
+            finish_sensitivity_vox<double><<<blk, 256, 0, st>>>(bp, q, gd.M, (double *)s->invp_vox);
+        else
+            finish_sensitivity_vox<float><<<blk, 256, 0, st>>>(bp, q, gd.M, (float *)s->invp_vox);
+        r = cuda_ok(cudaGetLastError(), "finish_sensitivity_vox");
+    }
+    if (ad) cudaFreeAsync(ad, st);
+    if (bp) cudaFreeAsync(bp, st);
+    return r;
+}
+
+// Load data (counts, gamma and, when not NULL, the per-bin detection factors mult: [P][V][NB],
+// device) and f^0 ([P][N][N] float, device) into an allocated state and reset the schedule to
+// (k, i) = (0, 1).  Validates the data (synchronises).
 static pet_status state_load(pet_state *s, const int32_t *d_counts, const float *d_gamma,
-                             const pet_params *p, const float *d_img, cudaStream_t st,
-                             bool validate)
+                             const float *d_mult, const pet_params *p, const float *d_img,
+                             cudaStream_t st, bool validate)
 {
     const pet_geometry *g = s->g;
     const GeoDev &gd = g->dev;
     s->prm = *p;
+    if (d_mult && !s->mult) return fail(PET_ERR_INVALID, "state has no buffers for detection factors");
     if (validate) {
         const size_t n = (size_t)gd.P * gd.V * gd.NB;
         PET_TRY(validate_data(gd, d_counts, d_gamma, n, s->flag, st));
+        if (d_mult) PET_TRY(validate_factors(d_mult, n, s->flag, st));
         int h = 0;
         PET_CUDA(cudaMemcpyAsync(&h, s->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
         PET_CUDA(cudaStreamSynchronize(st));
-        if (h) return fail(PET_ERR_INVALID, "data check failed: need counts >= 0 and 0 < gamma < inf");
+        if (h) return fail(PET_ERR_INVALID, "data check failed: need counts >= 0, 0 < gamma < inf "
+                                            "and finite detection factors >= 0");
     }
     PET_TRY(to_internal_sino(gd, g->d_view_of_slot, 0, gd.V, d_counts, s->counts, 0, 0, st));
     PET_TRY(to_internal_sino(gd, g->d_view_of_slot, 0, gd.V, d_gamma, s->gamma, 1, 0, st));
+    s->attn = d_mult != nullptr;
+    if (d_mult) PET_TRY(load_factors(s, d_mult, st));
     s->cur = 0;
     PET_TRY(to_internal_image(gd, d_img, s->f[0], 0, s->arith == AR_FP64, st));
     s->k = s->i = s->J = 0;
@@ -232,6 +296,7 @@ void pet::plan_subiter(pet_state *s, SubiterPlan *pl, bool with_objective)
     fa.out = s->w;
     fa.counts = s->counts + (size_t)slot0 * gd.NB * gd.Pp;
     fa.gamma = s->gamma + (size_t)slot0 * gd.NB * gd.Pp;
+    fa.mult = s->attn ? s->mult + (size_t)slot0 * gd.NB * gd.Pp : nullptr;
     forward_shape(fa, FWD_RATIO, s->arith);
     UpdateArgs &ua = pl->upd;
     ua.g = update_geo(gd);
@@ -240,7 +305,9 @@ void pet::plan_subiter(pet_state *s, SubiterPlan *pl, bool with_objective)
     ua.w = s->w;
     ua.f = s->f[s->cur];
     ua.fout = s->f[1 - s->cur];
-    ua.invp = s->arith == AR_FP64 ? (const void *)g->d_invp64 : (const void *)g->d_invp;
+    ua.invp = s->attn ? (const void *)s->invp_vox
+                      : (s->arith == AR_FP64 ? (const void *)g->d_invp64 : (const void *)g->d_invp);
+    ua.vox = s->attn ? 1 : 0;
     ua.invp_scale = 1.0 / s->sens_ratio;
     ua.nu_frozen = s->nu_frozen;
     ua.nu_mode = nu_mode;
@@ -343,6 +410,7 @@ void pet::objective_args(pet_state *s, double *out3, FwdArgs *fa, ImageArgs *ra)
     fa->img = s->f[s->cur];
     fa->counts = s->counts;
     fa->gamma = s->gamma;
+    fa->mult = s->attn ? s->mult : nullptr;
     fa->red = s->red;
     fa->result = out3;
     forward_shape(*fa, FWD_OBJECTIVE, s->arith);
@@ -387,7 +455,7 @@ pet_status pet::state_create_loaded(const pet_geometry *g, double sens, const in
     if (r == PET_OK) {
         s->sens_ratio = sens / g->desc.sens;
         if (d_img) {
-            r = state_load(s, d_counts, d_gamma, p, d_img, st, false);
+            r = state_load(s, d_counts, d_gamma, nullptr, p, d_img, st, false);
         } else {
             // f^0 = 1: fill the internal image, then load data
             s->prm = *p;
@@ -431,9 +499,10 @@ void pet::state_release(pet_state *s, cudaStream_t st)
     delete s;
 }
 
-extern "C" pet_status pet_state_create(const pet_geometry *g, const int32_t *d_counts,
-                                       const float *d_gamma, const pet_params *params,
-                                       const float *d_img_init, void *stream, pet_state **out)
+static pet_status state_create_any(const pet_geometry *g, const int32_t *d_counts,
+                                   const float *d_gamma, const float *d_mult,
+                                   const pet_params *params, const float *d_img_init,
+                                   void *stream, pet_state **out)
 {
     if (!g || !d_counts || !d_gamma || !d_img_init || !out)
         return fail(PET_ERR_INVALID, "pet_state_create: NULL argument");
@@ -442,8 +511,8 @@ extern "C" pet_status pet_state_create(const pet_geometry *g, const int32_t *d_c
     cudaStream_t st = as_stream(stream);
     pet_state *s = new pet_state();
     pet_status r = state_alloc(s, g, arith_of(params->precision), params->iterations,
-                               params->regularizer == PET_REG_TV);
-    if (r == PET_OK) r = state_load(s, d_counts, d_gamma, params, d_img_init, st, true);
+                               params->regularizer == PET_REG_TV, d_mult != nullptr);
+    if (r == PET_OK) r = state_load(s, d_counts, d_gamma, d_mult, params, d_img_init, st, true);
     if (r == PET_OK) {
         cudaError_t e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) r = cuda_fail(e, "pet_state_create");
@@ -456,6 +525,22 @@ extern "C" pet_status pet_state_create(const pet_geometry *g, const int32_t *d_c
     }
     *out = s;
     return PET_OK;
+}
+
+extern "C" pet_status pet_state_create(const pet_geometry *g, const int32_t *d_counts,
+                                       const float *d_gamma, const pet_params *params,
+                                       const float *d_img_init, void *stream, pet_state **out)
+{
+    return state_create_any(g, d_counts, d_gamma, nullptr, params, d_img_init, stream, out);
+}
+
+extern "C" pet_status pet_state_create_attn(const pet_geometry *g, const int32_t *d_counts,
+                                            const float *d_gamma, const float *d_mult,
+                                            const pet_params *params, const float *d_img_init,
+                                            void *stream, pet_state **out)
+{
+    if (!d_mult) return fail(PET_ERR_INVALID, "pet_state_create_attn: NULL detection factors");
+    return state_create_any(g, d_counts, d_gamma, d_mult, params, d_img_init, stream, out);
 }
 
 extern "C" pet_status pet_subiter(pet_state *s, void *stream)
@@ -518,6 +603,7 @@ namespace {
 struct CkptHeader {
     char magic[8];                  // "PETCKPT1"
     int n, nplanes, nviews, nbins, nsubsets, subrays, precision, regularizer, rdp_3d, iterations;
+    int attn;                       // the scan has per-bin detection factors
     int k, i, J, cur, have_frozen, objcap;
     double tn;
     unsigned long long q_bytes, tv_bytes;
@@ -545,6 +631,7 @@ extern "C" pet_status pet_state_export(const pet_state *s, void *h_buf, size_t *
     h.n = d.n; h.nplanes = d.nplanes; h.nviews = d.nviews; h.nbins = d.nbins;
     h.nsubsets = d.nsubsets; h.subrays = s->g->dev.R; h.precision = s->prm.precision;
     h.regularizer = s->prm.regularizer; h.rdp_3d = s->prm.rdp_3d; h.iterations = s->prm.iterations;
+    h.attn = s->attn ? 1 : 0;
     h.k = s->k; h.i = s->i; h.J = s->J; h.cur = s->cur; h.have_frozen = s->have_frozen;
     h.objcap = s->objcap; h.tn = s->tn;
     h.q_bytes = s->q_bytes;
@@ -581,7 +668,8 @@ extern "C" pet_status pet_state_import(pet_state *s, const void *h_buf, size_t b
     if (h.n != d.n || h.nplanes != d.nplanes || h.nviews != d.nviews || h.nbins != d.nbins ||
         h.nsubsets != d.nsubsets || h.subrays != s->g->dev.R || h.precision != s->prm.precision ||
         h.regularizer != s->prm.regularizer || h.rdp_3d != s->prm.rdp_3d ||
-        h.iterations != s->prm.iterations || h.q_bytes != s->q_bytes || h.objcap != s->objcap)
+        h.iterations != s->prm.iterations || h.q_bytes != s->q_bytes || h.objcap != s->objcap ||
+        h.attn != (s->attn ? 1 : 0))
         return fail(PET_ERR_INVALID, "pet_state_import: checkpoint of another geometry or parameters");
     if (bytes < ckpt_bytes(s)) return fail(PET_ERR_INVALID, "pet_state_import: truncated checkpoint");
     cudaStream_t st = as_stream(stream);
@@ -749,9 +837,10 @@ void workspace_free(void *w)
 }
 }  // namespace pet
 
-extern "C" pet_status pet_reconstruct(const pet_geometry *g, const int32_t *d_counts,
-                                      const float *d_gamma, const pet_params *params,
-                                      float *d_img_inout, double *h_objective, void *stream)
+static pet_status reconstruct_any(const pet_geometry *g, const int32_t *d_counts,
+                                  const float *d_gamma, const float *d_mult,
+                                  const pet_params *params, float *d_img_inout,
+                                  double *h_objective, void *stream)
 {
     if (!g || !d_counts || !d_gamma || !d_img_inout)
         return fail(PET_ERR_INVALID, "pet_reconstruct: NULL argument");
@@ -760,13 +849,29 @@ extern "C" pet_status pet_reconstruct(const pet_geometry *g, const int32_t *d_co
     GeoWorkspace *ws = workspace_of(g);
     pet_state *s = &ws->st;
     PET_TRY(state_alloc(s, g, arith_of(params->precision), params->iterations,
-                        params->regularizer == PET_REG_TV));
-    PET_TRY(state_load(s, d_counts, d_gamma, params, d_img_inout, st, true));
+                        params->regularizer == PET_REG_TV, d_mult != nullptr));
+    PET_TRY(state_load(s, d_counts, d_gamma, d_mult, params, d_img_inout, st, true));
     PET_TRY(run_reconstruct(s, h_objective, st));
     PET_TRY(from_internal_image(g->dev, s->f[s->cur], d_img_inout, s->arith == AR_FP64, 0, st));
     PET_TRY(finish_objective(s, h_objective, st));
     PET_CUDA(cudaStreamSynchronize(st));
     return PET_OK;
+}
+
+extern "C" pet_status pet_reconstruct(const pet_geometry *g, const int32_t *d_counts,
+                                      const float *d_gamma, const pet_params *params,
+                                      float *d_img_inout, double *h_objective, void *stream)
+{
+    return reconstruct_any(g, d_counts, d_gamma, nullptr, params, d_img_inout, h_objective, stream);
+}
+
+extern "C" pet_status pet_reconstruct_attn(const pet_geometry *g, const int32_t *d_counts,
+                                           const float *d_gamma, const float *d_mult,
+                                           const pet_params *params, float *d_img_inout,
+                                           double *h_objective, void *stream)
+{
+    if (!d_mult) return fail(PET_ERR_INVALID, "pet_reconstruct_attn: NULL detection factors");
+    return reconstruct_any(g, d_counts, d_gamma, d_mult, params, d_img_inout, h_objective, stream);
 }
 
 extern "C" pet_status pet_reconstruct_host(const pet_geometry *g, const int32_t *h_counts,
@@ -803,7 +908,7 @@ extern "C" pet_status pet_reconstruct_host(const pet_geometry *g, const int32_t 
     pet_state *s = &ws->st;
     PET_TRY(state_alloc(s, g, arith_of(params->precision), params->iterations,
                         params->regularizer == PET_REG_TV));
-    PET_TRY(state_load(s, ws->counts, ws->gamma, params, ws->img, st, true));
+    PET_TRY(state_load(s, ws->counts, ws->gamma, nullptr, params, ws->img, st, true));
     PET_TRY(run_reconstruct(s, h_objective, st));
     PET_TRY(from_internal_image(gd, s->f[s->cur], ws->img, s->arith == AR_FP64, 0, st));
     PET_CUDA(cudaMemcpyAsync(h_img_inout, ws->img, nimg * sizeof(float), cudaMemcpyDeviceToHost, st));

@@ -269,10 +269,19 @@ __global__ void __launch_bounds__(256, G == 1 ? UPDATE_G1_BLOCKS : 3) update_ker
                     if (a.nu_mode == 2)
                         store_group<G, T>(reinterpret_cast<T *>(a.nu_frozen) + (unsigned)j * (unsigned)Pp + grp * G, nu);
                 }
-                const T ip = invp[j] * scal<T>(a.invp_scale, a.fs_ips);
+                T ipv[G];
+                if (a.vox) {
+                    load_group<G, T>(invp + (unsigned)j * (unsigned)Pp + grp * G, ipv);
+#pragma unroll
+                    for (int p = 0; p < G; ++p) ipv[p] *= scal<T>(a.invp_scale, a.fs_ips);
+                } else {
+                    const T ip = invp[j] * scal<T>(a.invp_scale, a.fs_ips);
+#pragma unroll
+                    for (int p = 0; p < G; ++p) ipv[p] = ip;
+                }
 #pragma unroll
                 for (int p = 0; p < G; ++p) {
-                    const T S = (fc[p] < halfU ? fc[p] : U - fc[p]) * ip;
+                    const T S = (fc[p] < halfU ? fc[p] : U - fc[p]) * ipv[p];
                     coef[p] = lam * nu[p] * S;
                     rg[p] = bm * gr[p];
                 }
@@ -698,8 +707,8 @@ void update_shape(UpdateArgs &a, int arith)
     const int ntiles = (a.g.N * a.g.N + TP - 1) / TP;
     const int sub = a.g.R > 1;
     const void *fn = a.g.G == 1 ? (a.g.K <= 2 ? update_fn<1, 2>(arith, 0, sub) : update_fn<1, 4>(arith, 0, sub))
-                                : (a.g.K <= 2 ? update_fn<8, 2>(arith, a.z3 || a.tv, sub)
-                                              : update_fn<8, 4>(arith, a.z3 || a.tv, sub));
+                                : (a.g.K <= 2 ? update_fn<8, 2>(arith, a.z3 || a.tv || a.vox, sub)
+                                              : update_fn<8, 4>(arith, a.z3 || a.tv || a.vox, sub));
     const int slots = sm_count() * resident_blocks(fn);
     a.tpv = std::max({1, (ntiles + a.red.capacity - 1) / a.red.capacity, (ntiles + slots - 1) / slots});
     a.nvb = (ntiles + a.tpv - 1) / a.tpv;
@@ -729,9 +738,9 @@ static void update_dispatch(const UpdateArgs &a, const Batch &b, int arith, int 
         return;
     }
     if constexpr (G == 8) {
-        // the packed kernel has the in-plane RDP step only; the 3-D prior and the TV variant run
-        // the generic kernel
-        const bool gen = a.z3 || a.tv;
+        // the packed kernel has the in-plane RDP step and p per pixel only; the 3-D prior, the
+        // TV variant and scans with detection factors (p per voxel) run the generic kernel
+        const bool gen = a.z3 || a.tv || a.vox;
         if (gen && arith == AR_FP32) update_kernel<G, KC, AR_FP32><<<grid, 256, 0, st>>>(a, b);
         else if (gen && arith == AR_KAHAN) update_kernel<G, KC, AR_KAHAN><<<grid, 256, 0, st>>>(a, b);
         else if (arith == AR_FP32) update_kernel_x8<KC, AR_FP32><<<grid, 256, 0, st>>>(a, b);

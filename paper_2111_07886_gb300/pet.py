@@ -76,6 +76,8 @@ SIGNATURES = {
     "pet_forward_subset_f64": (_I, [_VP, _I, _VP, _VP, _VP]),
     "pet_back_subset_f64": (_I, [_VP, _I, _VP, _VP, _VP]),
     "pet_state_create": (_I, [_VP, _VP, _VP, ctypes.POINTER(Params), _VP, _VP, ctypes.POINTER(_VP)]),
+    "pet_state_create_attn": (_I, [_VP, _VP, _VP, _VP, ctypes.POINTER(Params), _VP, _VP,
+                                   ctypes.POINTER(_VP)]),
     "pet_subiter": (_I, [_VP, _VP]),
     "pet_state_read_image": (_I, [_VP, _VP, _VP]),
     "pet_state_read_image_f64": (_I, [_VP, _VP, _VP]),
@@ -86,6 +88,7 @@ SIGNATURES = {
     "pet_state_reset": (_I, [_VP, _VP, _VP]),
     "pet_state_destroy": (None, [_VP]),
     "pet_reconstruct": (_I, [_VP, _VP, _VP, ctypes.POINTER(Params), _VP, _DP, _VP]),
+    "pet_reconstruct_attn": (_I, [_VP, _VP, _VP, _VP, ctypes.POINTER(Params), _VP, _DP, _VP]),
     "pet_reconstruct_host": (_I, [_VP, _VP, _VP, ctypes.POINTER(Params), _VP, _DP, _VP]),
     "pet_rdp_gradient": (_I, [_VP, _VP, _D, _D, _VP, _VP]),
     "pet_smoothness_nu": (_I, [_VP, _VP, _D, _D, _VP, _VP]),
@@ -232,11 +235,19 @@ def back_subset(g: Geometry, subset: int, d_proj, d_img, stream=None):
 class State:
     """pet_state handle: resident reconstruction state (Table I)."""
 
-    def __init__(self, g: Geometry, d_counts, d_gamma, params: Params, d_img_init, stream=None):
+    def __init__(self, g: Geometry, d_counts, d_gamma, params: Params, d_img_init, stream=None,
+                 d_mult=None):
+        """d_mult: per-bin detection factors (float32 [P][V][NB], device) for the system matrix
+        diag(a) A (pet_state_create_attn), or None."""
         h = _VP()
         self.params = params
-        _check(lib().pet_state_create(g.handle, _ptr(d_counts), _ptr(d_gamma), ctypes.byref(params),
-                                      _ptr(d_img_init), _stream(stream), ctypes.byref(h)))
+        if d_mult is None:
+            _check(lib().pet_state_create(g.handle, _ptr(d_counts), _ptr(d_gamma), ctypes.byref(params),
+                                          _ptr(d_img_init), _stream(stream), ctypes.byref(h)))
+        else:
+            _check(lib().pet_state_create_attn(g.handle, _ptr(d_counts), _ptr(d_gamma), _ptr(d_mult),
+                                               ctypes.byref(params), _ptr(d_img_init), _stream(stream),
+                                               ctypes.byref(h)))
         self.handle = h
 
     def subiter(self, stream=None):
@@ -291,11 +302,17 @@ class State:
 
 
 def reconstruct(g: Geometry, d_counts, d_gamma, params: Params, d_img_inout, objective=False,
-                stream=None):
-    """f^0 -> f^T in place; returns the objective history (T+1 values) if requested."""
+                stream=None, d_mult=None):
+    """f^0 -> f^T in place; returns the objective history (T+1 values) if requested.  d_mult:
+    per-bin detection factors (pet_reconstruct_attn), or None."""
     obj = (ctypes.c_double * (params.iterations + 1))() if objective else None
-    _check(lib().pet_reconstruct(g.handle, _ptr(d_counts), _ptr(d_gamma), ctypes.byref(params),
-                                 _ptr(d_img_inout), obj, _stream(stream)))
+    if d_mult is None:
+        _check(lib().pet_reconstruct(g.handle, _ptr(d_counts), _ptr(d_gamma), ctypes.byref(params),
+                                     _ptr(d_img_inout), obj, _stream(stream)))
+    else:
+        _check(lib().pet_reconstruct_attn(g.handle, _ptr(d_counts), _ptr(d_gamma), _ptr(d_mult),
+                                          ctypes.byref(params), _ptr(d_img_inout), obj,
+                                          _stream(stream)))
     return list(obj) if objective else None
 
 

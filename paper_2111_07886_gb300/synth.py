@@ -29,7 +29,7 @@ __all__ = [
     "Workload", "AlgoParams", "config_2d_128", "config_stacked_256x89",
     "mixed_2d_scans", "make_scan", "ellipse_phantom_2d", "ellipsoid_phantom_3d",
     "rasterize", "random_image", "uniform_phantom_2d", "uniform_phantom_rois",
-    "brain_standin_2d",
+    "brain_standin_2d", "make_scan_paper",
 ]
 
 # Preconditioner kinds (Sec. III: BSREM, momentum-only M1/M2, SDP P1/P2).
@@ -322,6 +322,75 @@ def make_scan(w: Workload) -> dict:
     lam = sens * sino + gamma.astype(np.float64)
     counts = rng.poisson(lam).astype(np.int32)
     return dict(counts=counts, gamma=gamma, sens=float(sens), planes=planes)
+
+
+def _gauss_blur_r(prof: np.ndarray, step_mm: float, fwhm_mm: float) -> np.ndarray:
+    """Gaussian blur (FWHM ``fwhm_mm``) of profiles sampled every ``step_mm`` along the last
+    axis (zero outside), as a normalised discrete convolution."""
+    sigma = fwhm_mm / (2.0 * math.sqrt(2.0 * math.log(2.0))) / step_mm
+    half = int(math.ceil(5.0 * sigma))
+    k = np.exp(-0.5 * (np.arange(-half, half + 1) / sigma) ** 2)
+    k /= k.sum()
+    flat = prof.reshape(-1, prof.shape[-1])
+    out = np.stack([np.convolve(row, k, mode="same") for row in flat])
+    return out.reshape(prof.shape)
+
+
+PAPER_PSF_FWHM_MM = 6.59        # Sec. IV-A: shift-invariant Gaussian PSF of the data
+PAPER_MU_WATER_PER_MM = 0.0096  # Sec. IV-A: water attenuation 0.096 / cm
+PAPER_SF = PAPER_RF = 0.25      # Sec. IV-A: scatter and random fractions
+
+
+def make_scan_paper(w: Workload, psf_fwhm_mm: float = PAPER_PSF_FWHM_MM,
+                    mu_per_mm: float = PAPER_MU_WATER_PER_MM, sf: float = PAPER_SF,
+                    rf: float = PAPER_RF, scatter_fwhm_mm: float = 150.0,
+                    oversample: int = 8) -> dict:
+    """The data model of the paper's simulations (Sec. IV-A) for workload ``w``:
+
+      * trues: the projection of the phantom convolved with a Gaussian PSF of FWHM
+        ``psf_fwhm_mm``; for an isotropic Gaussian the line integrals of the blurred image are the
+        analytic line integrals blurred by the same 1-D Gaussian along the detector axis
+        (projection-slice theorem), computed on a grid ``oversample`` times finer than the bins
+        and sampled at the bin centres; attenuated by a_i = exp(-mu L_i), L_i the chord of the
+        phantom's body (its first, outline shape: uniform water on the image's support);
+      * scatter: the (unattenuated) projection of the phantom smoothed by a Gaussian of FWHM
+        ``scatter_fwhm_mm`` along the detector axis ("highly smoothed"), scaled so that the
+        scatter fraction S / (T + S) is ``sf``;
+      * randoms: uniform over the sinogram, scaled so that R / (T + S + R) is ``rf``;
+      * the total T + S + R is ``w.counts``; counts = Poisson(T + S + R).
+
+    Returns counts (int32), gamma = S + R (float32, the known background), mult = a (float32,
+    the per-bin detection factors of the system matrix diag(a) sens L), sens and the phantom.
+    The reconstruction model keeps one line per bin (or the workload's sub-rays) and no PSF."""
+    if w.phantom == "ellipses2d":
+        planes = ellipse_phantom_2d(w.n, w.pixel_mm, w.seed)
+    else:
+        planes = ellipsoid_phantom_3d(w.n, w.nplanes, w.pixel_mm, w.plane_mm, w.seed)
+    fine = w.bin_mm / oversample
+    margin = int(math.ceil(3.0 * max(psf_fwhm_mm, scatter_fwhm_mm) / fine))
+    nfine = w.nbins * oversample + 2 * margin
+    # fine grid centred like the bins: fine sample m sits at (m - (nfine - 1) / 2) * fine
+    proj_f = analytic_sinogram(planes, w.nviews, nfine, fine)
+    centre = (np.arange(w.nbins) - (w.nbins - 1) / 2.0) * w.bin_mm
+    idx = np.rint(centre / fine + (nfine - 1) / 2.0).astype(int)
+    trues_shape = _gauss_blur_r(proj_f, fine, psf_fwhm_mm)[..., idx]
+    scatter_shape = _gauss_blur_r(proj_f, fine, scatter_fwhm_mm)[..., idx]
+    body = [[sh[0]] if sh else [] for sh in planes]
+    chord = analytic_sinogram([[(cx, cy, a, b, phi, 1.0) for (cx, cy, a, b, phi, _) in sh]
+                               for sh in body], w.nviews, w.nbins, w.bin_mm)
+    mult = np.exp(-mu_per_mm * chord)
+    t_sino = mult * trues_shape                      # trues per unit sens
+    s_scale = sf / (1.0 - sf) * t_sino.sum() / scatter_shape.sum()
+    s_sino = s_scale * scatter_shape
+    r_total = rf / (1.0 - rf) * (t_sino.sum() + s_sino.sum())
+    r_sino = np.full(t_sino.shape, r_total / t_sino.size)
+    sens = w.counts / (t_sino.sum() + s_sino.sum() + r_total)
+    trues = sens * t_sino
+    gamma = (sens * (s_sino + r_sino)).astype(np.float32)
+    rng = np.random.Generator(np.random.PCG64(w.seed + 7919))
+    counts = rng.poisson(trues + gamma.astype(np.float64)).astype(np.int32)
+    return dict(counts=counts, gamma=gamma, mult=mult.astype(np.float32), sens=float(sens),
+                planes=planes, trues=trues, scatter=sens * s_sino, randoms=sens * r_sino)
 
 
 def random_image(shape, seed: int, lo: float = 0.1, hi: float = 2.0) -> np.ndarray:
