@@ -38,7 +38,9 @@ class Geom(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("nplanes", ctypes.c_int), ("nviews", ctypes.c_int),
                 ("nbins", ctypes.c_int), ("nsubsets", ctypes.c_int),
                 ("pixel_mm", ctypes.c_double), ("bin_mm", ctypes.c_double),
-                ("sens", ctypes.c_double), ("subrays", ctypes.c_int)]
+                ("sens", ctypes.c_double), ("subrays", ctypes.c_int),
+                ("tof_bins", ctypes.c_int), ("tof_bin_mm", ctypes.c_double),
+                ("tof_fwhm_mm", ctypes.c_double)]
 
 
 class Params(ctypes.Structure):
@@ -92,6 +94,8 @@ def lib():
             L.ora_objective_m.argtypes = [gp, ip, fp, fp, dp, ctypes.c_double, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_int, dp]
             L.ora_sensitivity_m.argtypes = [gp, fp, dp]
+            L.ora_tof_weight.argtypes = [gp, ctypes.c_int, ctypes.c_double]
+            L.ora_tof_weight.restype = ctypes.c_double
             L.ora_reconstruct_snap.argtypes = [gp, ip, fp, ctypes.POINTER(Params), dp, ctypes.c_int, dp, dp]
             _lib = L
     return _lib
@@ -103,15 +107,27 @@ def _d(a):
 
 
 def geom(n, nplanes, nviews, nbins, nsubsets, pixel_mm=1.0, bin_mm=None, sens=1.0,
-         subrays=1) -> Geom:
+         subrays=1, tof_bins=0, tof_bin_mm=0.0, tof_fwhm_mm=0.0) -> Geom:
     return Geom(n, nplanes, nviews, nbins, nsubsets, pixel_mm,
-                pixel_mm if bin_mm is None else bin_mm, sens, subrays)
+                pixel_mm if bin_mm is None else bin_mm, sens, subrays, tof_bins, tof_bin_mm,
+                tof_fwhm_mm)
 
 
 def geom_from(geometry: dict, sens: float) -> Geom:
     g = geometry
     return Geom(g["n"], g["nplanes"], g["nviews"], g["nbins"], g["nsubsets"],
-                g["pixel_mm"], g["bin_mm"], sens, int(g.get("subrays", 1)))
+                g["pixel_mm"], g["bin_mm"], sens, int(g.get("subrays", 1)),
+                int(g.get("tof_bins", 0)), float(g.get("tof_bin_mm", 0.0)),
+                float(g.get("tof_fwhm_mm", 0.0)))
+
+
+def ntof(g: Geom) -> int:
+    return g.tof_bins if g.tof_bins > 1 else 1
+
+
+def tof_weight(g: Geom, t: int, tau_mm: float) -> float:
+    """h_t(tau): the Gaussian timing kernel integrated over TOF bin t, at tau mm along a line."""
+    return lib().ora_tof_weight(ctypes.byref(g), t, tau_mm)
 
 
 def subset_size(g: Geom, subset: int) -> int:
@@ -141,16 +157,17 @@ def bin_pieces(g: Geom, v: int, b: int):
 
 
 def forward(g: Geom, subset: int, f) -> np.ndarray:
-    """y = A_i f, f [P][N][N] -> [P][V_i][n_b] (subset -1: all views, [P][V][n_b])."""
+    """y = A_i f, f [P][N][N] -> [P][V_i][n_b] (subset -1: all views, [P][V][n_b]); with TOF
+    bins [P][V_i][n_b][T]."""
     f, fp = _d(f)
     nv = g.nviews if subset < 0 else subset_size(g, subset)
-    y = np.zeros((g.nplanes, nv, g.nbins))
+    y = np.zeros((g.nplanes, nv, g.nbins) + ((ntof(g),) if ntof(g) > 1 else ()))
     lib().ora_forward(ctypes.byref(g), subset, fp, y.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
     return y
 
 
 def back(g: Geom, subset: int, y) -> np.ndarray:
-    """A_i^T y, y [P][V_i][n_b] -> [P][N][N]."""
+    """A_i^T y, y [P][V_i][n_b] ([P][V_i][n_b][T] with TOF bins) -> [P][N][N]."""
     y, yp = _d(y)
     out = np.zeros((g.nplanes, g.n, g.n))
     lib().ora_back(ctypes.byref(g), subset, yp, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))

@@ -31,6 +31,15 @@
  * found by Siddon's method: all crossings of the ray with the grid lines are sorted, and each
  * piece between consecutive crossings is charged to the pixel that contains its midpoint.
  *
+ * Time of flight (the clinical reconstructions of Sec. IV-C use TOF data): with T > 1 TOF bins,
+ * bin i = (v, b) splits into (v, b, t), t = 0..T-1, centred at tau_t = (t - (T-1)/2) dtau along
+ * the line from its point nearest the centre, and A_{(v,b,t) j} = A_{(v,b) j} h_t(tau_j), where
+ * tau_j is the position of the centre of pixel j along the line and
+ * h_t(tau) = Phi((tau - tau_t + dtau/2) / sigma) - Phi((tau - tau_t - dtau/2) / sigma) is the
+ * Gaussian timing kernel (sigma = FWHM / (2 sqrt(2 ln 2))) integrated over the TOF bin.  When
+ * the TOF bins cover the image with margin, sum_t h_t = 1 and the TOF bins add up to A.
+ * Sinograms then hold [P][V][n_b][T].
+ *
  * Per-bin detection factors (the simulated system of Sec. IV-A includes uniform water
  * attenuation): given a_i > 0 for every bin i, the system matrix is diag(a) A, i.e. the mean
  * data are a_i (A f)_i + gamma_i, its transpose weights bin i by a_i, and p_j of Eq. pj becomes
@@ -55,6 +64,9 @@ typedef struct {
     double bin_mm;
     double sens;     /* A_ij = sens * length_mm */
     int subrays;     /* R parallel lines per bin (<= 1: one line at the bin centre) */
+    int tof_bins;    /* T time-of-flight bins per bin (<= 1: no TOF) */
+    double tof_bin_mm;   /* width of a TOF bin along the line */
+    double tof_fwhm_mm;  /* FWHM of the Gaussian timing kernel, as a distance along the line */
 } ora_geom;
 
 typedef struct {
@@ -165,6 +177,36 @@ static int line_pieces(const ora_geom *g, int v, double r, int *pix, double *len
     return np;
 }
 
+/* TOF bins per bin (1 without TOF) and "bins" per view of the sinogram (n_b T) */
+static int ntof(const ora_geom *g) { return g->tof_bins > 1 ? g->tof_bins : 1; }
+static int nbt(const ora_geom *g) { return g->nbins * ntof(g); }
+
+/* h_t(tau) for TOF bin t at position tau (mm) along the line, in the form without cancellation */
+double ora_tof_weight(const ora_geom *g, int t, double tau_mm)
+{
+    const int T = ntof(g);
+    if (T == 1) return 1.0;
+    const double sigma = g->tof_fwhm_mm / (2.0 * sqrt(2.0 * log(2.0)));
+    const double c = ((double)t - 0.5 * (T - 1)) * g->tof_bin_mm;
+    const double k = 1.0 / (sigma * sqrt(2.0));
+    const double a = (tau_mm - c - 0.5 * g->tof_bin_mm) * k;   /* lower edge, scaled */
+    const double b = (tau_mm - c + 0.5 * g->tof_bin_mm) * k;   /* upper edge, scaled */
+    /* h = Phi(b') - Phi(a') with Phi(z) = erfc(-z / sqrt 2) / 2 */
+    if (a > 0.0) return 0.5 * (erfc(a) - erfc(b));
+    if (b < 0.0) return 0.5 * (erfc(-b) - erfc(-a));
+    return 0.5 * (erf(b) - erf(a));
+}
+
+/* position (mm) of the centre of pixel j along the lines of view v */
+static double pixel_tau_mm(const ora_geom *g, int v, int j)
+{
+    double c, s;
+    view_dir(g, v, &c, &s);
+    const double X = (double)(j % g->n) + 0.5 - 0.5 * g->n;
+    const double Y = (double)(j / g->n) + 0.5 - 0.5 * g->n;
+    return (-X * s + Y * c) * g->pixel_mm;
+}
+
 /* views of subset `subset` in increasing order; returns count */
 static int subset_views(const ora_geom *g, int subset, int *views)
 {
@@ -178,16 +220,29 @@ typedef struct { int *pix; double *len; int *cnt; int stride; } piece_table;
 
 static void build_pieces(const ora_geom *g, const int *views, int nv, piece_table *tb)
 {
-    const int N = g->n, NB = g->nbins;
+    const int N = g->n, NB = g->nbins, T = ntof(g);
     tb->stride = nsub_of(g) * (2 * N + 2);
-    tb->pix = (int *)malloc(sizeof(int) * (size_t)nv * NB * tb->stride);
-    tb->len = (double *)malloc(sizeof(double) * (size_t)nv * NB * tb->stride);
-    tb->cnt = (int *)malloc(sizeof(int) * (size_t)nv * NB);
+    tb->pix = (int *)malloc(sizeof(int) * (size_t)nv * NB * T * tb->stride);
+    tb->len = (double *)malloc(sizeof(double) * (size_t)nv * NB * T * tb->stride);
+    tb->cnt = (int *)malloc(sizeof(int) * (size_t)nv * NB * T);
+    /* ray index (u * n_b + b) * T + t: the pieces of bin (u, b), weighted by h_t at each
+       piece's pixel centre */
     #pragma omp parallel for schedule(dynamic)
-    for (int ray = 0; ray < nv * NB; ++ray)
-        tb->cnt[ray] = ora_bin_pieces(g, views[ray / NB], ray % NB,
-                                      tb->pix + (size_t)ray * tb->stride,
-                                      tb->len + (size_t)ray * tb->stride);
+    for (int ray = 0; ray < nv * NB; ++ray) {
+        int *pix0 = tb->pix + (size_t)ray * T * tb->stride;
+        double *len0 = tb->len + (size_t)ray * T * tb->stride;
+        const int cnt = ora_bin_pieces(g, views[ray / NB], ray % NB, pix0, len0);
+        for (int t = T - 1; t >= 0; --t) {
+            int *pix = pix0 + (size_t)t * tb->stride;
+            double *len = len0 + (size_t)t * tb->stride;
+            for (int m = 0; m < cnt; ++m) {
+                pix[m] = pix0[m];
+                len[m] = T > 1 ? len0[m] * ora_tof_weight(g, t, pixel_tau_mm(g, views[ray / NB], pix0[m]))
+                               : len0[m];
+            }
+            tb->cnt[(size_t)ray * T + t] = cnt;
+        }
+    }
 }
 
 static void free_pieces(piece_table *tb) { free(tb->pix); free(tb->len); free(tb->cnt); }
@@ -200,11 +255,12 @@ static int view_list(const ora_geom *g, int subset, int *views)
 
 /*
  * Forward projection of one subset: y = A_i f  (Sec. II-B, the row block A_i of A).
- * f: [P][N][N]; y: [P][V_i][n_b].  subset = -1 projects all views into [P][V][n_b].
+ * f: [P][N][N]; y: [P][V_i][n_b] ([P][V_i][n_b][T] with TOF).  subset = -1 projects all
+ * views into [P][V][n_b] ([P][V][n_b][T]).
  */
 void ora_forward(const ora_geom *g, int subset, const double *f, double *y)
 {
-    const int N = g->n, P = g->nplanes, NB = g->nbins;
+    const int N = g->n, P = g->nplanes, NB = nbt(g);   /* bins x TOF bins */
     int *views = (int *)malloc(sizeof(int) * g->nviews);
     const int nv = view_list(g, subset, views);
     const double scale = g->sens * g->pixel_mm;
@@ -231,7 +287,7 @@ void ora_forward(const ora_geom *g, int subset, const double *f, double *y)
  */
 void ora_back(const ora_geom *g, int subset, const double *y, double *out)
 {
-    const int N = g->n, P = g->nplanes, NB = g->nbins;
+    const int N = g->n, P = g->nplanes, NB = nbt(g);   /* bins x TOF bins */
     int *views = (int *)malloc(sizeof(int) * g->nviews);
     const int nv = view_list(g, subset, views);
     const double scale = g->sens * g->pixel_mm;
@@ -259,8 +315,8 @@ void ora_sensitivity(const ora_geom *g, double *pj)
     ora_geom g1 = *g;
     g1.nplanes = 1;
     const int N = g->n;
-    double *ones = (double *)malloc(sizeof(double) * (size_t)g->nviews * g->nbins);
-    for (size_t k = 0; k < (size_t)g->nviews * g->nbins; ++k) ones[k] = 1.0;
+    double *ones = (double *)malloc(sizeof(double) * (size_t)g->nviews * nbt(g));
+    for (size_t k = 0; k < (size_t)g->nviews * nbt(g); ++k) ones[k] = 1.0;
     ora_back(&g1, -1, ones, pj);
     for (int j = 0; j < N * N; ++j)
         pj[j] = pj[j] > 0.0 ? pj[j] / g->nsubsets : 1.0 / g->nsubsets;
@@ -272,7 +328,7 @@ void ora_sensitivity(const ora_geom *g, double *pj)
 void ora_sensitivity_m(const ora_geom *g, const float *a, double *pj)
 {
     const size_t q = (size_t)g->nplanes * g->n * g->n;
-    const size_t nsino = (size_t)g->nplanes * g->nviews * g->nbins;
+    const size_t nsino = (size_t)g->nplanes * g->nviews * nbt(g);
     double *ad = (double *)malloc(sizeof(double) * nsino);
     for (size_t k = 0; k < nsino; ++k) ad[k] = a ? (double)a[k] : 1.0;
     ora_back(g, -1, ad, pj);
@@ -581,7 +637,7 @@ void ora_objective_m(const ora_geom *g, const int *counts, const float *gamma, c
                      const double *f, double beta, double gamma_r, double eps, int three_d,
                      double *out)
 {
-    size_t nsino = (size_t)g->nplanes * g->nviews * g->nbins;
+    size_t nsino = (size_t)g->nplanes * g->nviews * nbt(g);
     double *y = (double *)malloc(sizeof(double) * nsino);
     ora_forward(g, -1, f, y);
     if (a)
@@ -634,7 +690,7 @@ void ora_reconstruct_snap(const ora_geom *g, const int *counts, const float *gam
 void ora_reconstruct_m(const ora_geom *g, const int *counts, const float *gamma, const float *a,
                        const ora_params *prm, double *f, int nsub, double *obj, double *snaps)
 {
-    const int N = g->n, P = g->nplanes, M = g->nsubsets, NB = g->nbins;
+    const int N = g->n, P = g->nplanes, M = g->nsubsets, NB = nbt(g);   /* bins x TOF bins */
     const size_t q = (size_t)N * N * P;
     const int T = prm->iterations;
     const int total = T * M;
