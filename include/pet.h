@@ -68,6 +68,15 @@ typedef struct {
                            A_ij = sens / R * (sum of their lengths in mm inside pixel j): the
                            paper's ray-driven model with parallel rays per detector pair
                            (Sec. IV-A, 32 there).  0 or 1: one line at the bin centre; at most 64 */
+    int tof_bins;       /* T time-of-flight bins per bin (the TOF data of the clinical
+                           reconstructions, Sec. IV-C); 0 or 1: no TOF.  TOF bin t of bin i is
+                           centred at tau_t = (t - (T-1)/2) tof_bin_mm along the line from its
+                           point nearest the centre, and A_{(i,t) j} = A_ij h_t(tau_j) with tau_j
+                           the position of pixel j's centre along the line and h_t the Gaussian
+                           timing kernel (FWHM tof_fwhm_mm) integrated over the TOF bin.
+                           Sinograms then hold [P][V][n_b][T].  At most 64; with subrays <= 1 */
+    double tof_bin_mm;  /* TOF bin width along the line (> 0 with TOF) */
+    double tof_fwhm_mm; /* FWHM of the timing kernel as a distance along the line (> 0 with TOF) */
 } pet_geometry_desc;
 
 typedef enum {
@@ -132,8 +141,11 @@ const char *pet_last_error(void);
  * uploads them, and computes the sensitivity p_j of Eq. pj (one backprojection of ones over all
  * views) on the device.  Synchronises `stream` before returning.  PET_ERR_INVALID for a bad desc
  * (limits: 1 <= n <= 8192, 1 <= nplanes <= 2048, nbins >= 4, 1 <= nsubsets <= nviews,
- * bin_mm >= 0.36 pixel_mm, 0 <= subrays <= 64, at most 4 bins per view in a pixel's footprint,
- * fewer than 4e9 image or sinogram elements).
+ * bin_mm >= 0.36 pixel_mm, 0 <= subrays <= 64, 0 <= tof_bins <= 64 (TOF with subrays <= 1),
+ * at most 4 bins per view in a pixel's footprint, fewer than 4e9 image or sinogram elements).
+ * With TOF bins every sinogram argument and result of the library is [P][V][n_b][T]; TOF
+ * scans run through pet_subiter / pet_reconstruct and the single-step calls (not in batches or
+ * the server).
  * ---------------------------------------------------------------------------------------- */
 pet_status pet_geometry_create(const pet_geometry_desc *desc, void *stream, pet_geometry **out);
 void pet_geometry_destroy(pet_geometry *g);
@@ -142,8 +154,9 @@ void pet_geometry_destroy(pet_geometry *g);
  * admissible number of ray chunks (threads sharing one ray) and keeps the fastest in the
  * geometry; *best_S (optional) receives it.  Tune before creating states on the geometry (the
  * chunking changes the order of the ray sums, within rounding).  The projection is timed on an
- * image of ones, best of 7 runs of 4 launches after a warm-up; a larger chunk count replaces a
- * smaller one only when it is more than 3 % faster.  Synchronises `stream`.
+ * image of ones, best of 7 runs of 4 launches after a warm-up (pet_autotune_batch: best of 5
+ * single batched launches); a larger chunk count replaces a smaller one only when it is more
+ * than 3 % faster.  Synchronises `stream`.  TOF geometries have no ray chunking (*best_S = 1).
  * pet_autotune_batch: the same, with `concurrent` (1..4096) copies of the projection running as
  * one batched launch, as they do when that many scans of the geometry step together in a
  * pet_batch or a server; the choice is kept in the geometry and used alone and in batches alike,

@@ -190,6 +190,8 @@ extern "C" pet_status pet_batch_add(pet_batch *b, pet_state *s, int with_objecti
     if (!b || !s) return fail(PET_ERR_INVALID, "pet_batch_add: NULL argument");
     if (s->prm.regularizer == PET_REG_TV)
         return fail(PET_ERR_INVALID, "pet_batch_add: the TV variant runs through pet_subiter / pet_reconstruct");
+    if (s->g->dev.T > 1)
+        return fail(PET_ERR_INVALID, "pet_batch_add: TOF scans run through pet_subiter / pet_reconstruct");
     for (BatchClass *c : b->classes)
         for (pet_state *x : c->slot)
             if (x == s) return fail(PET_ERR_INVALID, "pet_batch_add: state already in the batch");

@@ -131,6 +131,18 @@ static pet_status build_tables(pet_geometry *g, std::vector<ViewGeo> &views,
         const double o = vg.xdrive ? c : s;        // other component
         vg.half = R > 1 ? rho / (2.0 * R * a) : 0.0;
         vg.halfq = to_q32(vg.half);
+        // time of flight: the line is r (c, s) + tau (-s, c); pixel centre (X, Y) lies at
+        // tau = -X s + Y c, X = ix + 1/2 - N/2, Y = iy + 1/2 - N/2 (pixel units)
+        vg.taux = -s;
+        vg.tauy = c;
+        vg.tau0 = (0.5 - half) * (c - s);
+        if (vg.xdrive) {           // X = d + 1/2 - N/2 on the line: tau = (r c - X) / s
+            vg.tdr = c / s; vg.tdc = -(0.5 - half) / s; vg.tdd = -1.0 / s;
+        } else {                   // Y = d + 1/2 - N/2: tau = (Y - r s) / c
+            vg.tdr = -s / c; vg.tdc = (0.5 - half) / c; vg.tdd = 1.0 / c;
+        }
+        vg.tau0f = (float)vg.tau0; vg.tauxf = (float)vg.taux; vg.tauyf = (float)vg.tauy;
+        vg.tdrf = (float)vg.tdr; vg.tdcf = (float)vg.tdc; vg.tddf = (float)vg.tdd;
         // candidate bins of a pixel's footprint: one line per bin, or sub-lines within
         // (R - 1) / (2 R) bins of the bin centre on either side (first candidate floor(t - hh))
         if (R == 1) K = std::max(K, (int)floor(2.0 * vg.h) + 1);
@@ -205,6 +217,19 @@ static pet_status geometry_init(pet_geometry *g, cudaStream_t st)
     gd.NB = d.nbins;
     gd.M = d.nsubsets;
     gd.scale = d.sens * d.pixel_mm / gd.R;
+    gd.rho = d.bin_mm / d.pixel_mm;
+    gd.T = d.tof_bins > 1 ? d.tof_bins : 1;
+    gd.SB = gd.NB * gd.T;
+    if (gd.T > 1) {
+        // h_t(tau) < 1e-12 farther than 7.1 sigma beyond the bin's edges
+        const double sigma = d.tof_fwhm_mm / (2.0 * sqrt(2.0 * log(2.0))) / d.pixel_mm;
+        gd.tof_d = d.tof_bin_mm / d.pixel_mm;
+        gd.tof_k = 1.0 / (sigma * sqrt(2.0));
+        gd.tof_w = 0.5 * gd.tof_d + 7.1 * sigma;
+    } else {
+        gd.tof_d = gd.tof_k = gd.tof_w = 0.0;
+    }
+    gd.tof_df = (float)gd.tof_d; gd.tof_kf = (float)gd.tof_k; gd.tof_wf = (float)gd.tof_w;
     PET_CUDA(cudaMalloc(&g->d_views, sizeof(ViewGeo) * views.size()));
     PET_CUDA(cudaMalloc(&g->d_rays, sizeof(RayGeo) * rays.size()));
     PET_CUDA(cudaMalloc(&g->d_view_of_slot, sizeof(int) * g->view_of_slot.size()));
@@ -271,8 +296,15 @@ extern "C" pet_status pet_geometry_create(const pet_geometry_desc *desc, void *s
     if (d.bin_mm < 0.36 * d.pixel_mm)
         return fail(PET_ERR_INVALID, "pet_geometry_create: bin_mm must be >= 0.36 pixel_mm "
                                      "(at most 4 rays of one view cross a pixel)");
+    if (d.tof_bins < 0 || d.tof_bins > 64 ||
+        (d.tof_bins > 1 && (!(d.tof_bin_mm > 0) || !(d.tof_fwhm_mm > 0) ||
+                            !std::isfinite(d.tof_bin_mm) || !std::isfinite(d.tof_fwhm_mm) ||
+                            d.subrays > 1)))
+        return fail(PET_ERR_INVALID, "pet_geometry_create: tof_bins must be in 0..64, with "
+                                     "tof_bin_mm, tof_fwhm_mm > 0 and subrays <= 1 when > 1");
     if ((double)d.n * d.n * ((d.nplanes + 7) / 8 * 8) > 4.0e9 ||
-        (double)d.nviews * d.nbins * ((d.nplanes + 7) / 8 * 8) > 4.0e9)
+        (double)d.nviews * d.nbins * (d.tof_bins > 1 ? d.tof_bins : 1) *
+                ((d.nplanes + 7) / 8 * 8) > 4.0e9)
         return fail(PET_ERR_INVALID, "pet_geometry_create: problem too large (> 4e9 elements)");
     pet_geometry *g = new pet_geometry();
     g->desc = d;

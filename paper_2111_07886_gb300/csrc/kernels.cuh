@@ -557,6 +557,86 @@ __device__ __forceinline__ void bp_accumulate(const GeoDev &g, const BpTable<KC,
 }
 
 // ------------------------------------------------------------------------------------------
+// Time of flight.  TOF bin t of a line spans [e_t, e_t+1) along it, e_t = (t - T/2) d, and
+// h_t(tau) = Phi((e_t+1 - tau) / sigma) - Phi((e_t - tau) / sigma) is the Gaussian timing kernel
+// at position tau integrated over the bin.  With z = (e - tau) / (sigma sqrt 2) at the two edges
+// (z0 < z1), h = (erfc(-z1) - erfc(-z0)) / 2, taken from the tail masses in the form that has
+// no cancellation.
+// ------------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T tof_h(T z0, T z1)
+{
+    if constexpr (sizeof(T) == 8) {
+        if (z0 >= 0.0) return 0.5 * (erfc(z0) - erfc(z1));
+        if (z1 <= 0.0) return 0.5 * (erfc(-z1) - erfc(-z0));
+        return 1.0 - 0.5 * (erfc(-z0) + erfc(z1));
+    } else {
+        if (z0 >= 0.f) return 0.5f * (erfcf(z0) - erfcf(z1));
+        if (z1 <= 0.f) return 0.5f * (erfcf(-z1) - erfcf(-z0));
+        return 1.f - 0.5f * (erfcf(-z0) + erfcf(z1));
+    }
+}
+
+// h_t(tau) for one TOF bin (tau in pixel units)
+template <typename T>
+__device__ __forceinline__ T tof_weight(const GeoDev &g, int t, T tau)
+{
+    const T d = sizeof(T) == 8 ? (T)g.tof_d : (T)g.tof_df, k = sizeof(T) == 8 ? (T)g.tof_k : (T)g.tof_kf;
+    const T e0 = (T)(2 * t - g.T) * T(0.5) * d;
+    return tof_h<T>((e0 - tau) * k, (e0 + d - tau) * k);
+}
+
+// TOF form of bp_accumulate: rows [u][NB][T][Pp]; for each view the pixel's centre position
+// tau along the view's lines picks the TOF bins within the kernel's window, each weighted by
+// h_t(tau) (its bin edges evaluated once and shared by neighbouring bins).  ix, iy: the pixel;
+// slot0 + u0: the table's first view.
+template <int G, int KC, int AR, int CAPX>
+__device__ __forceinline__ void bp_accumulate_tof(const GeoDev &g, const BpTable<KC, AR, CAPX> &tb,
+                                                  const typename ArithT<AR>::T *__restrict__ proj,
+                                                  int np, int nvc, int pl, int grp,
+                                                  GroupSum<G, AR> &acc, int ix, int iy, int slot0,
+                                                  int u0)
+{
+    using T = typename ArithT<AR>::T;
+    constexpr bool D = AR == AR_FP64;
+    const unsigned Pp = (unsigned)g.Pp, TT = (unsigned)g.T;
+    const T d = D ? (T)g.tof_d : (T)g.tof_df, kk = D ? (T)g.tof_k : (T)g.tof_kf;
+    const T W = D ? (T)g.tof_w : (T)g.tof_wf;
+    const T *base = proj + grp * G;
+    for (int uu = 0; uu < nvc; ++uu) {
+        const typename BpTable<KC, AR, CAPX>::E ent = tb.e[uu * np + pl];
+        const ViewGeo &vw = g.views[slot0 + u0 + uu];
+        const T tau = D ? (T)(vw.tau0 + ix * vw.taux + iy * vw.tauy)
+                        : (T)vw.tau0f + (T)ix * (T)vw.tauxf + (T)iy * (T)vw.tauyf;
+        // bins whose centre (t - (T-1)/2) d lies within W of tau
+        const T tc = tau / d + T(0.5) * (T)(g.T - 1);
+        const int t_lo = max(0, (int)ceil(tc - W / d));
+        const int t_hi = min(g.T - 1, (int)floor(tc + W / d));
+        T z0 = ((T)(2 * t_lo - g.T) * T(0.5) * d - tau) * kk;
+        for (int t = t_lo; t <= t_hi; ++t) {
+            const T z1 = ((T)(2 * t + 2 - g.T) * T(0.5) * d - tau) * kk;
+            const T h = tof_h<T>(z0, z1);
+            z0 = z1;
+            if (proj == nullptr) {
+                T sw = T(0);
+#pragma unroll
+                for (int k = 0; k < KC; ++k) sw += ent.w[k];
+                acc.add_scalar(h * sw);
+                continue;
+            }
+            const T *row = base + ent.off * TT + (unsigned)t * Pp;
+#pragma unroll
+            for (int k = 0; k < KC; k += 2) {
+                T x0[G], x1[G];
+                load_group<G, T>(row + (unsigned)k * TT * Pp, x0);
+                load_group<G, T>(row + (unsigned)(k + 1) * TT * Pp, x1);
+                acc.add2terms(h * ent.w[k], x0, h * ent.w[k + 1], x1);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
 // Deterministic FP64 reduction of NV values over the whole grid: each block writes its
 // partial, the last block to finish (atomic ticket) adds the partials in block order and
 // writes result[0..NV).  No waits.  blockDim.x must be a multiple of 32, <= 1024.

@@ -122,21 +122,21 @@ pet_status to_internal_sino(const GeoDev &g, const int *d_view_of_slot, int slot
                             const void *src, void *dst, int elem, int src_is_subset,
                             cudaStream_t st)
 {
-    const long long n = (long long)nviews * g.NB * g.Pp;
+    const long long n = (long long)nviews * g.SB * g.Pp;    // SB: bins x TOF bins
     if (n == 0) return PET_OK;
     LaunchScope ls(PET_K_LAYOUT, st);
     // elem: 0 int32 counts (pad 0), 1 float gamma (pad 1), 2 float data (pad 0), 3 double
     // data, 4 float data to double (pad 0)
     if (elem == 4)
-        sino_to_internal<float, double><<<blocks(n), 256, 0, st>>>((const float *)src, (double *)dst, d_view_of_slot, slot0, nviews, g.V, g.NB, g.P, g.Pp, src_is_subset, 0.0);
+        sino_to_internal<float, double><<<blocks(n), 256, 0, st>>>((const float *)src, (double *)dst, d_view_of_slot, slot0, nviews, g.V, g.SB, g.P, g.Pp, src_is_subset, 0.0);
     else if (elem == 0)
-        sino_to_internal<int><<<blocks(n), 256, 0, st>>>((const int *)src, (int *)dst, d_view_of_slot, slot0, nviews, g.V, g.NB, g.P, g.Pp, src_is_subset, 0);
+        sino_to_internal<int><<<blocks(n), 256, 0, st>>>((const int *)src, (int *)dst, d_view_of_slot, slot0, nviews, g.V, g.SB, g.P, g.Pp, src_is_subset, 0);
     else if (elem == 1)
-        sino_to_internal<float><<<blocks(n), 256, 0, st>>>((const float *)src, (float *)dst, d_view_of_slot, slot0, nviews, g.V, g.NB, g.P, g.Pp, src_is_subset, 1.f);
+        sino_to_internal<float><<<blocks(n), 256, 0, st>>>((const float *)src, (float *)dst, d_view_of_slot, slot0, nviews, g.V, g.SB, g.P, g.Pp, src_is_subset, 1.f);
     else if (elem == 2)
-        sino_to_internal<float><<<blocks(n), 256, 0, st>>>((const float *)src, (float *)dst, d_view_of_slot, slot0, nviews, g.V, g.NB, g.P, g.Pp, src_is_subset, 0.f);
+        sino_to_internal<float><<<blocks(n), 256, 0, st>>>((const float *)src, (float *)dst, d_view_of_slot, slot0, nviews, g.V, g.SB, g.P, g.Pp, src_is_subset, 0.f);
     else
-        sino_to_internal<double><<<blocks(n), 256, 0, st>>>((const double *)src, (double *)dst, d_view_of_slot, slot0, nviews, g.V, g.NB, g.P, g.Pp, src_is_subset, 0.0);
+        sino_to_internal<double><<<blocks(n), 256, 0, st>>>((const double *)src, (double *)dst, d_view_of_slot, slot0, nviews, g.V, g.SB, g.P, g.Pp, src_is_subset, 0.0);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? PET_OK : cuda_fail(e, "sino_to_internal");
 }
@@ -144,11 +144,11 @@ pet_status to_internal_sino(const GeoDev &g, const int *d_view_of_slot, int slot
 pet_status from_internal_sino(const GeoDev &g, const int *d_view_of_slot, int nviews,
                               const void *src, void *dst, int is_double, cudaStream_t st)
 {
-    const long long n = (long long)g.P * nviews * g.NB;
+    const long long n = (long long)g.P * nviews * g.SB;
     if (n == 0) return PET_OK;
     LaunchScope ls(PET_K_LAYOUT, st);
-    if (is_double) sino_from_internal<double><<<blocks(n), 256, 0, st>>>((const double *)src, (double *)dst, d_view_of_slot, nviews, g.NB, g.P, g.Pp);
-    else sino_from_internal<float><<<blocks(n), 256, 0, st>>>((const float *)src, (float *)dst, d_view_of_slot, nviews, g.NB, g.P, g.Pp);
+    if (is_double) sino_from_internal<double><<<blocks(n), 256, 0, st>>>((const double *)src, (double *)dst, d_view_of_slot, nviews, g.SB, g.P, g.Pp);
+    else sino_from_internal<float><<<blocks(n), 256, 0, st>>>((const float *)src, (float *)dst, d_view_of_slot, nviews, g.SB, g.P, g.Pp);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? PET_OK : cuda_fail(e, "sino_from_internal");
 }

@@ -61,6 +61,11 @@ struct ViewGeo {
     // (2 s + 1 - R) of them away from the bin's centre line
     long long halfq;
     double half;
+    // time of flight: position along the line (pixel units) of pixel (ix, iy)'s centre,
+    // tau = tau0 + ix taux + iy tauy; and of the line at the centre of driving column d,
+    // tau = tdr r + tdc + d tdd (r the line's offset in pixel units)
+    double tau0, taux, tauy, tdr, tdc, tdd;
+    float tau0f, tauxf, tauyf, tdrf, tdcf, tddf;
 };
 
 struct RayGeo {
@@ -75,6 +80,11 @@ struct GeoDev {
     int V, NB, M, K;          // views, bins, subsets, max candidate bins per view in the gather
     int tuneS;                // forward projector chunks per ray picked by pet_autotune (0: heuristic)
     int R;                    // sub-rays per bin (1: one line); scale includes the 1 / R
+    int T;                    // TOF bins per bin (1: no TOF)
+    int SB;                   // sinogram entries per view and plane: NB T
+    double rho;               // bin spacing / pixel size
+    double tof_d, tof_k, tof_w;   // TOF bin width, 1 / (sigma sqrt 2), window half-width
+    float tof_df, tof_kf, tof_wf; //   (pixel units; h_t < 1e-12 beyond the window)
     long long offq;           // half a sub-ray spacing in bin units, Q32.32 (2^32 / (2 R))
     double scale;             // sens * pixel_mm
     const ViewGeo *views;     // [V] in subset order
@@ -141,6 +151,9 @@ enum Arith { AR_FP32 = 0, AR_KAHAN = 1, AR_FP64 = 2 };
 
 pet_status launch_forward(const FwdArgs &a, int mode, int arith, cudaStream_t st);
 void forward_shape(FwdArgs &a, int mode, int arith);      // fills S, R, tpv, nvb
+// time-of-flight geometries (g.T > 1; launch_forward / forward_shape forward to these)
+pet_status launch_forward_tof(const FwdArgs &a, int mode, int arith, cudaStream_t st);
+void forward_shape_tof(FwdArgs &a, int mode, int arith);
 pet_status launch_forward_batch(const FwdArgs &shape, const Batch &b, int mode, int arith,
                                 cudaStream_t st);
 

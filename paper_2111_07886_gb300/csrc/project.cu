@@ -22,11 +22,8 @@
 #define FWD_FAST 1               // blocked compensated walk (see the G == 8 branch of fwd_kernel)
 #endif
 #ifndef FWD_TILE_ORDER
-#define FWD_TILE_ORDER 0         // 1: ray tiles within one view, centre bins first (long rays first)
-#endif
-#ifndef FWD_ANY_S
-#define FWD_ANY_S 0              // 1: any chunk count S <= 16 (R = floor(256 / (S NG)) rays a block)
-#endif
+#define FWD_TILE_ORDER 1         // ray tiles within one view, centre bins first (long rays first),
+#endif                           // in the ratio mode (2: in the objective mode too; 0: neither)
 
 namespace pet {
 
@@ -49,31 +46,27 @@ __global__ void __launch_bounds__(256, 3) fwd_kernel(const __grid_constant__ Fwd
         const GeoDev &g = a.g;
         const int NG = g.NG, NB = g.NB, N = g.N, Pp = g.Pp, S = a.S, R = a.R;
         const int nrays = a.nviews * NB;
-#if FWD_TILE_ORDER
+        constexpr bool kOrder = FWD_TILE_ORDER && (MODE != FWD_OBJECTIVE || FWD_TILE_ORDER > 1);
         const int tpv_view = (NB + R - 1) / R;       // tiles of one view
-        const int ntiles = a.nviews * tpv_view;
-#else
-        const int ntiles = (nrays + R - 1) / R;
-#endif
+        const int ntiles = kOrder ? a.nviews * tpv_view : (nrays + R - 1) / R;
         const bool lane_ok = (int)threadIdx.x < R * S * NG;
         double obj[2] = {0.0, 0.0};
-        for (int tile = vloc * a.tpv; tile < min(ntiles, (vloc + 1) * a.tpv); ++tile) {
+        // with the centre-first order, virtual block v of a scan takes tiles v, v + nv, ...: a
+        // mix of long and short rays in every block (the objective mode's blocks hold several)
+        const int t_end = kOrder ? ntiles : min(ntiles, (vloc + 1) * a.tpv);
+        for (int tile = kOrder ? vloc : vloc * a.tpv; tile < t_end; tile += kOrder ? nv : 1) {
         const int grp = threadIdx.x % NG;
         const int c = (threadIdx.x / NG) % S;
         const int rl = threadIdx.x / (NG * S);
-#if FWD_TILE_ORDER
-        // tile rank t -> (view, tile of the view) with the view's tiles taken from its centre
-        // outwards (c, c + 1, c - 1, c + 2, ...; c the lower middle), so that the longest rays
-        // run first and the launch ends on short ones
-        const int tu = tile % a.nviews, tr = tile / a.nviews;
+        // centre-first order: tile rank t -> (view, tile of the view) with the view's tiles
+        // taken from its centre outwards (c, c + 1, c - 1, c + 2, ...; c the lower middle), so
+        // that the longest rays run first and the launch ends on short ones
+        const int tr = kOrder ? tile / a.nviews : 0;
         const int tb = (tpv_view - 1) / 2 + ((tr & 1) ? (tr + 1) / 2 : -(tr / 2));
         const int bin = tb * R + rl;
-        const int ray = tu * NB + bin;               // subset-local ray index u * NB + b
-        const bool live = lane_ok && bin < NB;
-#else
-        const int ray = tile * R + rl;               // subset-local ray index u * NB + b
-        const bool live = lane_ok && ray < nrays;
-#endif
+        // subset-local ray index u * NB + b
+        const int ray = kOrder ? (tile % a.nviews) * NB + bin : tile * R + rl;
+        const bool live = lane_ok && (kOrder ? bin < NB : ray < nrays);
         GroupSum<G, AR> acc;
         acc.zero();
         if (live) {
@@ -396,23 +389,19 @@ int sm_count()
 // step), never more than its reducer holds partial sums for.
 void forward_shape(FwdArgs &a, int mode, int arith)
 {
+    if (a.g.T > 1) { forward_shape_tof(a, mode, arith); return; }
     const long long nrays = (long long)a.nviews * a.g.NB;
     const long long want = (long long)sm_count() * 2048;
     const long long have = std::max<long long>(1, nrays * a.g.NG);
     int S = (int)std::min<long long>(FWD_MAX_CHUNKS, std::max<long long>(1, (want + have - 1) / have));
     S = std::max(1, std::min(S, a.g.N / 16));
     if (a.g.tuneS > 0 && mode != FWD_OBJECTIVE) S = a.g.tuneS;
-#if !FWD_ANY_S
     while (S > 1 && (256 / a.g.NG) % S) --S;          // S divides the rays-per-block budget
-#endif
-    S = std::max(1, std::min(S, 256 / a.g.NG));       // S NG threads share a ray tile
     a.S = S;
     a.R = std::max(1, 256 / (S * a.g.NG));
-#if FWD_TILE_ORDER
-    const long long ntiles = (long long)a.nviews * ((a.g.NB + a.R - 1) / a.R);
-#else
-    const long long ntiles = (nrays + a.R - 1) / a.R;
-#endif
+    const bool order = FWD_TILE_ORDER && (mode != FWD_OBJECTIVE || FWD_TILE_ORDER > 1);
+    const long long ntiles = order ? (long long)a.nviews * ((a.g.NB + a.R - 1) / a.R)
+                                   : (nrays + a.R - 1) / a.R;
     a.tpv = 1;
     if (mode == FWD_OBJECTIVE) {
         // each virtual block ends in a block reduction and a grid-wide ticket: one wave of them
@@ -427,6 +416,7 @@ void forward_shape(FwdArgs &a, int mode, int arith)
 
 pet_status launch_forward(const FwdArgs &a0, int mode, int arith, cudaStream_t st)
 {
+    if (a0.g.T > 1) return launch_forward_tof(a0, mode, arith, st);
     FwdArgs a = a0;
     const long long nrays = (long long)a.nviews * a.g.NB;
     if (nrays == 0) return PET_OK;
@@ -460,7 +450,8 @@ pet_status launch_forward_batch(const FwdArgs &shape, const Batch &b, int mode, 
 using namespace pet;
 
 // Autotuner: times the subset-0 forward projection of an image of ones for every admissible
-// chunk count S (1..16, dividing the 256-thread block budget; best of 7 runs of 4 launches) and
+// chunk count S (1..16, dividing the 256-thread block budget; best of 7 runs of 4 launches, or
+// of 5 single launches of the batched copies) and
 // keeps the fastest in the geometry, a larger S only when it is faster by more than 3 %.
 // `concurrent` copies of the projection run as one batched launch (the persistent grid of
 // pet_batch), so that a geometry whose scans run in a batch is tuned with the GPU shared the way
@@ -469,6 +460,11 @@ using namespace pet;
 static pet_status autotune_any(pet_geometry *g, int concurrent, cudaStream_t st, int *best_S)
 {
     GeoDev &gd = g->dev;
+    if (gd.T > 1) {                      // the TOF projector has no ray chunking to tune
+        gd.tuneS = 0;
+        if (best_S) *best_S = 1;
+        return PET_OK;
+    }
     const int nv = g->voff[1] - g->voff[0];
     const size_t qb = ((size_t)gd.N * gd.N * gd.Pp * 4 + 255) / 256 * 256;
     const size_t pb = ((size_t)nv * gd.NB * gd.Pp * 4 + 255) / 256 * 256;
@@ -491,8 +487,7 @@ static pet_status autotune_any(pet_geometry *g, int concurrent, cudaStream_t st,
     const int save = gd.tuneS;
     pet_status r = PET_OK;
     for (int S = 1; S <= FWD_MAX_CHUNKS && r == PET_OK; ++S) {
-        if (!FWD_ANY_S && (256 / gd.NG) % S) continue;
-        if (S * gd.NG > 256) break;
+        if ((256 / gd.NG) % S) continue;
         gd.tuneS = S;
         FwdArgs fa{};
         fa.g = gd;
@@ -518,9 +513,12 @@ static pet_status autotune_any(pet_geometry *g, int concurrent, cudaStream_t st,
         };
         if (r == PET_OK) r = once();                         // warm-up
         float tmin = 1e30f;
-        for (int rep = 0; rep < 7 && r == PET_OK; ++rep) {
+        // a scan alone: runs of 4 launches (one is ~50 us); batched copies: one launch a run
+        // (each takes milliseconds, and a server tunes every geometry it meets)
+        const int per_run = concurrent == 1 ? 4 : 1;
+        for (int rep = 0; rep < (concurrent == 1 ? 7 : 5) && r == PET_OK; ++rep) {
             cudaEventRecord(a, st);
-            for (int k = 0; k < 4 && r == PET_OK; ++k) r = once();
+            for (int k = 0; k < per_run && r == PET_OK; ++k) r = once();
             cudaEventRecord(b, st);
             if (r == PET_OK) r = cuda_ok(cudaEventSynchronize(b), "pet_autotune: timing");
             float ms = 0.f;
@@ -556,8 +554,7 @@ extern "C" pet_status pet_autotune_batch(pet_geometry *g, int concurrent, void *
 extern "C" pet_status pet_set_ray_chunks(pet_geometry *g, int S)
 {
     if (!g) return fail(PET_ERR_INVALID, "pet_set_ray_chunks: NULL geometry");
-    if (S < 0 || S > FWD_MAX_CHUNKS || (S > 0 && !FWD_ANY_S && (256 / g->dev.NG) % S) ||
-        S * g->dev.NG > 256)
+    if (S < 0 || S > FWD_MAX_CHUNKS || (S > 0 && (256 / g->dev.NG) % S))
         return fail(PET_ERR_INVALID, "pet_set_ray_chunks: S must be 0 or in 1..16 and divide 256 / plane groups");
     g->dev.tuneS = S;
     return PET_OK;

@@ -476,6 +476,8 @@ extern "C" pet_status pet_serve_submit(pet_server *sv, const pet_request *rq, ui
         d.nsubsets > d.nviews || !(d.pixel_mm > 0) || !(d.bin_mm > 0) || !(d.sens > 0) ||
         d.subrays < 0 || d.subrays > 64)
         return fail(PET_ERR_INVALID, "pet_serve_submit: invalid geometry description");
+    if (d.tof_bins > 1)
+        return fail(PET_ERR_INVALID, "pet_serve_submit: TOF scans run through pet_reconstruct");
     PET_TRY(check_params(&rq->params));
     if (rq->params.regularizer == PET_REG_TV)
         return fail(PET_ERR_INVALID, "pet_serve_submit: the TV variant runs through pet_reconstruct");

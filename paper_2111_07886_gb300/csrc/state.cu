@@ -109,8 +109,8 @@ static pet_status state_alloc(pet_state *s, const pet_geometry *g, int arith, in
     const size_t q_bytes = (size_t)gd.N * gd.N * gd.Pp * esz;
     int maxv = 0;
     for (int i = 0; i < gd.M; ++i) maxv = std::max(maxv, g->voff[i + 1] - g->voff[i]);
-    const size_t w_bytes = (size_t)maxv * gd.NB * gd.Pp * esz;
-    const size_t sino = (size_t)gd.V * gd.NB * gd.Pp;
+    const size_t w_bytes = (size_t)maxv * gd.SB * gd.Pp * esz;
+    const size_t sino = (size_t)gd.V * gd.SB * gd.Pp;
     if (s->g == g && s->esz == esz && s->f[0] && s->objcap >= iterations + 1 && (!tv || s->tvmem) &&
         (!attn || s->mult)) {
         s->arith = arith;
@@ -186,7 +186,7 @@ static pet_status load_factors(pet_state *s, const float *d_mult, cudaStream_t s
     const pet_geometry *g = s->g;
     const GeoDev &gd = g->dev;
     PET_TRY(to_internal_sino(gd, g->d_view_of_slot, 0, gd.V, d_mult, s->mult, 2, 0, st));
-    const size_t nsino = (size_t)gd.V * gd.NB * gd.Pp, q = (size_t)gd.N * gd.N * gd.Pp;
+    const size_t nsino = (size_t)gd.V * gd.SB * gd.Pp, q = (size_t)gd.N * gd.N * gd.Pp;
     double *ad = nullptr, *bp = nullptr;
     PET_CUDA(cudaMallocAsync((void **)&ad, nsino * sizeof(double), st));
     pet_status r = cuda_ok(cudaMallocAsync((void **)&bp, q * sizeof(double), st),
@@ -227,7 +227,7 @@ static pet_status state_load(pet_state *s, const int32_t *d_counts, const float 
     s->prm = *p;
     if (d_mult && !s->mult) return fail(PET_ERR_INVALID, "state has no buffers for detection factors");
     if (validate) {
-        const size_t n = (size_t)gd.P * gd.V * gd.NB;
+        const size_t n = (size_t)gd.P * gd.V * gd.SB;
         PET_TRY(validate_data(gd, d_counts, d_gamma, n, s->flag, st));
         if (d_mult) PET_TRY(validate_factors(d_mult, n, s->flag, st));
         int h = 0;
@@ -294,9 +294,9 @@ void pet::plan_subiter(pet_state *s, SubiterPlan *pl, bool with_objective)
     fa.nviews = nv;
     fa.img = s->f[s->cur];
     fa.out = s->w;
-    fa.counts = s->counts + (size_t)slot0 * gd.NB * gd.Pp;
-    fa.gamma = s->gamma + (size_t)slot0 * gd.NB * gd.Pp;
-    fa.mult = s->attn ? s->mult + (size_t)slot0 * gd.NB * gd.Pp : nullptr;
+    fa.counts = s->counts + (size_t)slot0 * gd.SB * gd.Pp;
+    fa.gamma = s->gamma + (size_t)slot0 * gd.SB * gd.Pp;
+    fa.mult = s->attn ? s->mult + (size_t)slot0 * gd.SB * gd.Pp : nullptr;
     forward_shape(fa, FWD_RATIO, s->arith);
     UpdateArgs &ua = pl->upd;
     ua.g = update_geo(gd);
@@ -487,8 +487,8 @@ size_t pet::state_bytes(const pet_geometry *g, int precision, int iterations)
     const size_t q = (size_t)gd.N * gd.N * gd.Pp * esz;
     int maxv = 0;
     for (int i = 0; i < gd.M; ++i) maxv = std::max(maxv, g->voff[i + 1] - g->voff[i]);
-    const size_t sino = (size_t)gd.V * gd.NB * gd.Pp;
-    return 3 * q + (size_t)maxv * gd.NB * gd.Pp * esz + sino * 8 + reducer_bytes(kRedCap, 2) +
+    const size_t sino = (size_t)gd.V * gd.SB * gd.Pp;
+    return 3 * q + (size_t)maxv * gd.SB * gd.Pp * esz + sino * 8 + reducer_bytes(kRedCap, 2) +
            (size_t)(iterations + 1) * 24 + 1024;
 }
 
@@ -884,7 +884,7 @@ extern "C" pet_status pet_reconstruct_host(const pet_geometry *g, const int32_t 
     cudaStream_t st = as_stream(stream);
     GeoWorkspace *ws = workspace_of(g);
     const GeoDev &gd = g->dev;
-    const size_t nsino = (size_t)gd.P * gd.V * gd.NB, nimg = (size_t)gd.P * gd.N * gd.N;
+    const size_t nsino = (size_t)gd.P * gd.V * gd.SB, nimg = (size_t)gd.P * gd.N * gd.N;
     if (ws->cap_counts < nsino) {
         cudaFree(ws->counts);
         cudaFree(ws->gamma);
@@ -939,7 +939,7 @@ static pet_status forward_any(const pet_geometry *g, int subset, const void *d_i
     cudaStream_t st = as_stream(stream);
     const GeoDev &gd = g->dev;
     const size_t esz = is_double ? 8 : 4;
-    const size_t qb = (size_t)gd.N * gd.N * gd.Pp * esz, pb = (size_t)nv * gd.NB * gd.Pp * esz;
+    const size_t qb = (size_t)gd.N * gd.N * gd.Pp * esz, pb = (size_t)nv * gd.SB * gd.Pp * esz;
     void *scr = nullptr;
     PET_TRY(geometry_scratch(g, qb + pb + 256, &scr));
     void *img_i = scr, *proj_i = reinterpret_cast<char *>(scr) + ((qb + 255) / 256) * 256;
@@ -964,7 +964,7 @@ static pet_status back_any(const pet_geometry *g, int subset, const void *d_proj
     cudaStream_t st = as_stream(stream);
     const GeoDev &gd = g->dev;
     const size_t esz = is_double ? 8 : 4;
-    const size_t qb = (size_t)gd.N * gd.N * gd.Pp * esz, pb = (size_t)nv * gd.NB * gd.Pp * esz;
+    const size_t qb = (size_t)gd.N * gd.N * gd.Pp * esz, pb = (size_t)nv * gd.SB * gd.Pp * esz;
     void *scr = nullptr;
     PET_TRY(geometry_scratch(g, qb + pb + 256, &scr));
     void *img_i = scr, *proj_i = reinterpret_cast<char *>(scr) + ((qb + 255) / 256) * 256;
@@ -1096,7 +1096,7 @@ static pet_status objective_any(const pet_geometry *g, const int32_t *d_counts,
     cudaStream_t st = as_stream(stream);
     const GeoDev &gd = g->dev;
     const size_t qb = ((size_t)gd.N * gd.N * gd.Pp * 4 + 255) / 256 * 256;
-    const size_t sino = (size_t)gd.V * gd.NB * gd.Pp;
+    const size_t sino = (size_t)gd.V * gd.SB * gd.Pp;
     const size_t sb = (sino * 4 + 255) / 256 * 256;
     void *scr = nullptr;
     PET_TRY(geometry_scratch(g, qb + 2 * sb, &scr));

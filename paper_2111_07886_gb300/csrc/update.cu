@@ -212,7 +212,7 @@ __device__ __forceinline__ T scal(double d, float f)
 // Virtual block: tpv tiles of TP consecutive pixels x NG plane groups (thread = pixel * NG +
 // group); the (pixel, view) weights of each tile are computed once into shared memory.  A
 // persistent grid strides over the virtual blocks of one scan or of a batch of scans.
-template <int G, int KC, int AR, bool SUB = false>
+template <int G, int KC, int AR, bool SUB = false, bool TOF = false>
 __global__ void __launch_bounds__(256, G == 1 ? UPDATE_G1_BLOCKS : 3) update_kernel(
     const __grid_constant__ UpdateArgs one, const Batch bt)
 {
@@ -294,7 +294,12 @@ __global__ void __launch_bounds__(256, G == 1 ? UPDATE_G1_BLOCKS : 3) update_ker
                 __syncthreads();
                 bp_fill<KC, AR, 0, SUB>(g, a.slot0, u0, nvc, j0, TP, tb);
                 __syncthreads();
-                if (active) bp_accumulate<G, KC, AR>(g, tb, w, TP, nvc, pl, grp, bp);
+                if (!active) continue;
+                if constexpr (TOF)
+                    bp_accumulate_tof<G, KC, AR>(g, tb, w, TP, nvc, pl, grp, bp, j % N, j / N,
+                                                 a.slot0, u0);
+                else
+                    bp_accumulate<G, KC, AR>(g, tb, w, TP, nvc, pl, grp, bp);
             }
             if (!active) continue;
             // 3. step and clamp P_t (TV variant: the unclamped z and the metric W = coef, for the
@@ -509,7 +514,7 @@ __global__ void __launch_bounds__(256, UPDATE_X8_BLOCKS) update_kernel_x8(
 
 // Stand-alone gather backprojection (also the sensitivity, proj == nullptr); one pixel tile
 // per virtual block.
-template <int G, int KC, int AR, bool SUB = false>
+template <int G, int KC, int AR, bool SUB = false, bool TOF = false>
 __global__ void __launch_bounds__(256) back_kernel(const __grid_constant__ BackArgs a)
 {
     using T = typename ArithT<AR>::T;
@@ -531,7 +536,12 @@ __global__ void __launch_bounds__(256) back_kernel(const __grid_constant__ BackA
             __syncthreads();
             bp_fill<KC, AR, 0, SUB>(g, a.slot0, u0, nvc, j0, TP, tb);
             __syncthreads();
-            if (active) bp_accumulate<G, KC, AR>(g, tb, proj, TP, nvc, pl, grp, acc);
+            if (!active) continue;
+            if constexpr (TOF)
+                bp_accumulate_tof<G, KC, AR>(g, tb, proj, TP, nvc, pl, grp, acc, j % N, j / N,
+                                             a.slot0, u0);
+            else
+                bp_accumulate<G, KC, AR>(g, tb, proj, TP, nvc, pl, grp, acc);
         }
         if (!active) continue;
         T b[G];
@@ -679,8 +689,13 @@ GeoDev update_geo(const GeoDev &g) { return g; }
 int resident_blocks(const void *fn);
 
 template <int G, int KC>
-static const void *update_fn(int arith, int z3 = 0, int sub = 0)
+static const void *update_fn(int arith, int z3 = 0, int sub = 0, int tof = 0)
 {
+    if (tof) {                                   // TOF geometries: KC = 4, generic kernel
+        if (arith == AR_FP32) return (const void *)update_kernel<G, 4, AR_FP32, false, true>;
+        if (arith == AR_KAHAN) return (const void *)update_kernel<G, 4, AR_KAHAN, false, true>;
+        return (const void *)update_kernel<G, 4, AR_FP64, false, true>;
+    }
     if (sub) {                                   // sub-ray geometries: KC = 4, generic kernel
         if (arith == AR_FP32) return (const void *)update_kernel<G, 4, AR_FP32, true>;
         if (arith == AR_KAHAN) return (const void *)update_kernel<G, 4, AR_KAHAN, true>;
@@ -705,10 +720,10 @@ void update_shape(UpdateArgs &a, int arith)
 {
     const int TP = 256 / a.g.NG;
     const int ntiles = (a.g.N * a.g.N + TP - 1) / TP;
-    const int sub = a.g.R > 1;
-    const void *fn = a.g.G == 1 ? (a.g.K <= 2 ? update_fn<1, 2>(arith, 0, sub) : update_fn<1, 4>(arith, 0, sub))
-                                : (a.g.K <= 2 ? update_fn<8, 2>(arith, a.z3 || a.tv || a.vox, sub)
-                                              : update_fn<8, 4>(arith, a.z3 || a.tv || a.vox, sub));
+    const int sub = a.g.R > 1, tof = a.g.T > 1;
+    const void *fn = a.g.G == 1 ? (a.g.K <= 2 ? update_fn<1, 2>(arith, 0, sub, tof) : update_fn<1, 4>(arith, 0, sub, tof))
+                                : (a.g.K <= 2 ? update_fn<8, 2>(arith, a.z3 || a.tv || a.vox, sub, tof)
+                                              : update_fn<8, 4>(arith, a.z3 || a.tv || a.vox, sub, tof));
     const int slots = sm_count() * resident_blocks(fn);
     a.tpv = std::max({1, (ntiles + a.red.capacity - 1) / a.red.capacity, (ntiles + slots - 1) / slots});
     a.nvb = (ntiles + a.tpv - 1) / a.tpv;
@@ -731,6 +746,12 @@ static int persistent_grid(int nvb) { return std::max(1, std::min(nvb, sm_count(
 template <int G, int KC>
 static void update_dispatch(const UpdateArgs &a, const Batch &b, int arith, int grid, cudaStream_t st)
 {
+    if (a.g.T > 1) {                             // TOF geometries: KC = 4, generic kernel
+        if (arith == AR_FP32) update_kernel<G, 4, AR_FP32, false, true><<<grid, 256, 0, st>>>(a, b);
+        else if (arith == AR_KAHAN) update_kernel<G, 4, AR_KAHAN, false, true><<<grid, 256, 0, st>>>(a, b);
+        else update_kernel<G, 4, AR_FP64, false, true><<<grid, 256, 0, st>>>(a, b);
+        return;
+    }
     if (a.g.R > 1) {                             // sub-ray geometries: KC = 4, generic kernel
         if (arith == AR_FP32) update_kernel<G, 4, AR_FP32, true><<<grid, 256, 0, st>>>(a, b);
         else if (arith == AR_KAHAN) update_kernel<G, 4, AR_KAHAN, true><<<grid, 256, 0, st>>>(a, b);
@@ -784,6 +805,12 @@ pet_status launch_update_batch(const UpdateArgs &shape, const Batch &b, int arit
 template <int G, int KC>
 static void back_dispatch(const BackArgs &a, int arith, int grid, cudaStream_t st)
 {
+    if (a.g.T > 1) {
+        if (arith == AR_FP32) back_kernel<G, 4, AR_FP32, false, true><<<grid, 256, 0, st>>>(a);
+        else if (arith == AR_KAHAN) back_kernel<G, 4, AR_KAHAN, false, true><<<grid, 256, 0, st>>>(a);
+        else back_kernel<G, 4, AR_FP64, false, true><<<grid, 256, 0, st>>>(a);
+        return;
+    }
     if (a.g.R > 1) {
         if (arith == AR_FP32) back_kernel<G, 4, AR_FP32, true><<<grid, 256, 0, st>>>(a);
         else if (arith == AR_KAHAN) back_kernel<G, 4, AR_KAHAN, true><<<grid, 256, 0, st>>>(a);

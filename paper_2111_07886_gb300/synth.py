@@ -29,7 +29,7 @@ __all__ = [
     "Workload", "AlgoParams", "config_2d_128", "config_stacked_256x89",
     "mixed_2d_scans", "make_scan", "ellipse_phantom_2d", "ellipsoid_phantom_3d",
     "rasterize", "random_image", "uniform_phantom_2d", "uniform_phantom_rois",
-    "brain_standin_2d", "make_scan_paper",
+    "brain_standin_2d", "make_scan_paper", "analytic_tof_sinogram",
 ]
 
 # Preconditioner kinds (Sec. III: BSREM, momentum-only M1/M2, SDP P1/P2).
@@ -79,11 +79,15 @@ class Workload:
     plane_mm: float = 0.0
     seed: int = 0
     subrays: int = 1              # parallel lines per bin of the system model (Sec. IV-A: 32)
+    tof_bins: int = 0             # time-of-flight bins per bin (0: no TOF)
+    tof_bin_mm: float = 0.0       # TOF bin width along the line
+    tof_fwhm_mm: float = 0.0      # FWHM of the timing kernel along the line
 
     def geometry(self) -> dict:
         return dict(n=self.n, nplanes=self.nplanes, pixel_mm=self.pixel_mm,
                     nviews=self.nviews, nbins=self.nbins, bin_mm=self.bin_mm,
-                    nsubsets=self.nsubsets, subrays=self.subrays)
+                    nsubsets=self.nsubsets, subrays=self.subrays, tof_bins=self.tof_bins,
+                    tof_bin_mm=self.tof_bin_mm, tof_fwhm_mm=self.tof_fwhm_mm)
 
 
 # SDP-P2 settings of the workloads.  Table II's rows were tuned on the paper's brain phantom;
@@ -286,6 +290,45 @@ def analytic_sinogram(planes, nviews: int, nbins: int, bin_mm: float) -> np.ndar
     return out
 
 
+def analytic_tof_sinogram(planes, nviews: int, nbins: int, bin_mm: float, tof_bins: int,
+                          tof_bin_mm: float, tof_fwhm_mm: float) -> np.ndarray:
+    """Exact TOF line integrals [P][V][n_b][T] of the continuous phantom: for every ellipse and
+    line, the chord [tau1, tau2] along the line (tau measured from the line's point nearest the
+    centre along (-sin t, cos t)) weighted by the TOF bin's kernel h_t(tau) (a Gaussian of FWHM
+    ``tof_fwhm_mm`` integrated over the bin), integrated in closed form:
+    int Phi((e - tau) / s) dtau = -s Psi((e - tau) / s), Psi(x) = x Phi(x) + phi(x)."""
+    from scipy.special import ndtr
+    theta = np.arange(nviews) * math.pi / nviews
+    ct, st = np.cos(theta)[:, None], np.sin(theta)[:, None]
+    r = ((np.arange(nbins) - (nbins - 1) / 2.0) * bin_mm)[None, :]
+    sig = tof_fwhm_mm / (2.0 * math.sqrt(2.0 * math.log(2.0)))
+    edges = (np.arange(tof_bins + 1) - tof_bins / 2.0) * tof_bin_mm
+
+    def psi(x):
+        return x * ndtr(x) + np.exp(-0.5 * x * x) / math.sqrt(2.0 * math.pi)
+
+    out = np.zeros((len(planes), nviews, nbins, tof_bins))
+    for p, shapes in enumerate(planes):
+        for (cx, cy, a, b, phi, val) in shapes:
+            ux, uy, wx, wy = math.cos(phi), math.sin(phi), -math.sin(phi), math.cos(phi)
+            p0x, p0y = r * ct - cx, r * st - cy                 # line point at tau = 0, from C
+            dx, dy = -st, ct                                    # line direction
+            du, dw = dx * ux + dy * uy, dx * wx + dy * wy
+            pu, pw = p0x * ux + p0y * uy, p0x * wx + p0y * wy
+            A = du * du / a ** 2 + dw * dw / b ** 2
+            B = 2.0 * (pu * du / a ** 2 + pw * dw / b ** 2)
+            C = pu * pu / a ** 2 + pw * pw / b ** 2 - 1.0
+            disc = B * B - 4.0 * A * C
+            hit = disc > 0
+            sq = np.sqrt(np.where(hit, disc, 0.0))
+            t1 = np.where(hit, (-B - sq) / (2.0 * A), 0.0)
+            t2 = np.where(hit, (-B + sq) / (2.0 * A), 0.0)
+            # int_{t1}^{t2} Phi((e - tau) / sig) dtau at every edge e
+            F = np.stack([sig * (psi((e - t1) / sig) - psi((e - t2) / sig)) for e in edges], -1)
+            out[p] += val * (F[..., 1:] - F[..., :-1])
+    return out
+
+
 def rasterize(planes, n: int, pixel_mm: float, supersample: int = 4) -> np.ndarray:
     """Pixel image [P][N][N] of the phantom (partial volume by supersampling)."""
     s = supersample
@@ -313,7 +356,11 @@ def make_scan(w: Workload) -> dict:
         planes = ellipse_phantom_2d(w.n, w.pixel_mm, w.seed)
     else:
         planes = ellipsoid_phantom_3d(w.n, w.nplanes, w.pixel_mm, w.plane_mm, w.seed)
-    sino = analytic_sinogram(planes, w.nviews, w.nbins, w.bin_mm)
+    if w.tof_bins > 1:
+        sino = analytic_tof_sinogram(planes, w.nviews, w.nbins, w.bin_mm, w.tof_bins,
+                                     w.tof_bin_mm, w.tof_fwhm_mm)
+    else:
+        sino = analytic_sinogram(planes, w.nviews, w.nbins, w.bin_mm)
     total_signal = sino.sum()
     sens = w.counts / (1.1 * total_signal)
     mean_sig = sens * total_signal / sino.size

@@ -48,3 +48,15 @@ def test_psf_blur_width():
     above = np.nonzero(out >= 0.5 * out.max())[0]
     fwhm = (above[-1] - above[0] + 1) * step
     assert abs(fwhm - synth.PAPER_PSF_FWHM_MM) <= 2 * step
+
+
+def test_tof_line_integrals_add_up_to_the_plain_ones():
+    """TOF bins covering the image split each exact line integral: their sum is the chord
+    integral, and a centred disk puts its TOF profile symmetric about the line's centre."""
+    pl = synth.ellipse_phantom_2d(64, 4.0, 3)
+    a = synth.analytic_sinogram(pl, 30, 91, 4.0)
+    b = synth.analytic_tof_sinogram(pl, 30, 91, 4.0, 41, 12.0, 40.0)
+    assert np.abs(b.sum(-1) - a).max() <= 1e-12 * a.max()
+    disk = [[(0.0, 0.0, 50.0, 50.0, 0.0, 1.0)]]
+    d = synth.analytic_tof_sinogram(disk, 8, 31, 4.0, 21, 10.0, 30.0)
+    np.testing.assert_allclose(d, d[..., ::-1], rtol=0, atol=1e-12 * d.max())
