@@ -55,6 +55,8 @@ def parse():
                     help="skip the no-objective and FP32 / FP64 arithmetic measurements")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop run")
     ap.add_argument("--serve-requests", type=int, default=500)
+    ap.add_argument("--serve-slots", type=int, default=8,
+                    help="scans the server keeps resident (1: one at a time, FIFO)")
     ap.add_argument("--serve-rates", default="0.5,0.9,1.5",
                     help="arrival rates as fractions of the sequential plain capacity")
     return ap.parse_args()
@@ -521,7 +523,7 @@ def serving_measure(args, pet, torch) -> dict:
     pick = [len(ws) - 1 if rng.uniform() < 0.05 else int(rng.integers(0, len(ws) - 1)) for _ in range(n)]
     mean_service = float(np.mean([service[k] for k in pick]))
     capacity = 1.0 / mean_service
-    slots = 64
+    slots = args.serve_slots
     out = {"requests": n, "pool": f"{len(ws) - 1} mixed 2-D scans + 1 stacked 256x256x89 (5 %)",
            "stacked_requests": int(sum(1 for k in pick if k == len(ws) - 1)),
            "iterations": 20, "slots": slots, "autotune": f"pet_serve_autotune({slots})",
