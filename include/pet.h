@@ -136,6 +136,12 @@ typedef struct pet_server pet_server;
 /* Message describing the last failure on the calling thread ("" if none). */
 const char *pet_last_error(void);
 
+/* Test hook (no counterpart in the paper): host-side fault injection.  The n-th device or pinned
+ * host allocation the library makes from now on (on any thread) fails as out of memory, and
+ * the call that made it returns PET_ERR_OOM (a serving request finishes with it); n <= 0
+ * disarms the hook.  One failure per arming.  No GPU fault is involved. */
+void pet_debug_fail_alloc(int n);
+
 /* ------------------------------------------------------------------------------------------
  * Geometry (Sec. II-A/II-B).  Builds the per-view / per-ray walk tables in FP64 on the host,
  * uploads them, and computes the sensitivity p_j of Eq. pj (one backprojection of ones over all

@@ -171,8 +171,8 @@ static pet_status class_for(pet_batch *b, pet_state *s, BatchClass **out)
     c->objective.assign(c->cap, false);
     c->layout();
     for (int k = 0; k < kBufs; ++k) {
-        cudaError_t e = cudaMallocHost((void **)&c->host[k], c->bytes);
-        if (e == cudaSuccess) e = cudaMalloc((void **)&c->dev[k], c->bytes);
+        cudaError_t e = host_malloc((void **)&c->host[k], c->bytes);
+        if (e == cudaSuccess) e = dev_malloc((void **)&c->dev[k], c->bytes);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->done[k], cudaEventDisableTiming);
         if (e != cudaSuccess) {
             class_free(c);
@@ -485,6 +485,7 @@ static pet_status class_tick(pet_batch *b, BatchClass *c, cudaStream_t st, int *
 extern "C" pet_status pet_batch_step(pet_batch *b, void *stream, int *running_after)
 {
     if (!b) return fail(PET_ERR_INVALID, "pet_batch_step: NULL batch");
+    TraceRange tr("pet_batch_step");
     cudaStream_t st = as_stream(stream);
     int run = 0;
     for (BatchClass *c : b->classes) {

@@ -1,6 +1,7 @@
 // Geometry: per-view / per-ray tables of the ray-driven projector and the pixel-driven
 // backprojector (built in FP64 on the host), the subset ordering of Sec. II-B, and the
 // sensitivity p_j of Eq. pj.  Also the error plumbing of the C ABI.
+#include <atomic>
 #include <math.h>
 #include <stdio.h>
 
@@ -21,6 +22,17 @@ pet_status fail(pet_status st, const std::string &msg)
 {
     g_last_error = msg;
     return st;
+}
+
+static std::atomic<long long> g_fail_alloc{0};
+
+bool alloc_fault()
+{
+    long long n = g_fail_alloc.load();
+    while (n > 0) {
+        if (g_fail_alloc.compare_exchange_weak(n, n - 1)) return n == 1;
+    }
+    return false;
 }
 
 pet_status cuda_fail(cudaError_t e, const char *what)
@@ -51,7 +63,7 @@ pet_status geometry_scratch(const pet_geometry *gc, size_t bytes, void **out)
         if (g->d_scratch) PET_CUDA(cudaFree(g->d_scratch));
         g->d_scratch = nullptr;
         g->scratch_bytes = 0;
-        PET_CUDA(cudaMalloc(&g->d_scratch, bytes));
+        PET_CUDA(dev_malloc(&g->d_scratch, bytes));
         g->scratch_bytes = bytes;
     }
     *out = g->d_scratch;
@@ -76,6 +88,8 @@ __global__ void finish_sensitivity(const double *bp, int npix, int M, float *p, 
 using namespace pet;
 
 extern "C" const char *pet_last_error(void) { return pet::g_last_error.c_str(); }
+
+extern "C" void pet_debug_fail_alloc(int n) { pet::g_fail_alloc.store(n > 0 ? n : 0); }
 
 static pet_status build_tables(pet_geometry *g, std::vector<ViewGeo> &views,
                                std::vector<RayGeo> &rays)
@@ -230,9 +244,9 @@ static pet_status geometry_init(pet_geometry *g, cudaStream_t st)
         gd.tof_d = gd.tof_k = gd.tof_w = 0.0;
     }
     gd.tof_df = (float)gd.tof_d; gd.tof_kf = (float)gd.tof_k; gd.tof_wf = (float)gd.tof_w;
-    PET_CUDA(cudaMalloc(&g->d_views, sizeof(ViewGeo) * views.size()));
-    PET_CUDA(cudaMalloc(&g->d_rays, sizeof(RayGeo) * rays.size()));
-    PET_CUDA(cudaMalloc(&g->d_view_of_slot, sizeof(int) * g->view_of_slot.size()));
+    PET_CUDA(dev_malloc(&g->d_views, sizeof(ViewGeo) * views.size()));
+    PET_CUDA(dev_malloc(&g->d_rays, sizeof(RayGeo) * rays.size()));
+    PET_CUDA(dev_malloc(&g->d_view_of_slot, sizeof(int) * g->view_of_slot.size()));
     PET_CUDA(cudaMemcpyAsync(g->d_views, views.data(), sizeof(ViewGeo) * views.size(),
                              cudaMemcpyHostToDevice, st));
     PET_CUDA(cudaMemcpyAsync(g->d_rays, rays.data(), sizeof(RayGeo) * rays.size(),
@@ -242,18 +256,18 @@ static pet_status geometry_init(pet_geometry *g, cudaStream_t st)
     gd.views = g->d_views;
     gd.rays = g->d_rays;
     const size_t npix = (size_t)d.n * d.n;
-    PET_CUDA(cudaMalloc(&g->d_p, sizeof(float) * npix));
-    PET_CUDA(cudaMalloc(&g->d_invp, sizeof(float) * npix));
-    PET_CUDA(cudaMalloc(&g->d_invp64, sizeof(double) * npix));
+    PET_CUDA(dev_malloc(&g->d_p, sizeof(float) * npix));
+    PET_CUDA(dev_malloc(&g->d_invp, sizeof(float) * npix));
+    PET_CUDA(dev_malloc(&g->d_invp64, sizeof(double) * npix));
     const int cap = 4096;
     void *redmem = nullptr;
-    PET_CUDA(cudaMalloc(&redmem, reducer_bytes(cap, 4)));
+    PET_CUDA(dev_malloc(&redmem, reducer_bytes(cap, 4)));
     PET_CUDA(cudaMemsetAsync(redmem, 0, reducer_bytes(cap, 4), st));
     reducer_bind(g->red, redmem, cap, 4);
-    PET_CUDA(cudaMalloc(&g->d_sums, 16 * sizeof(double)));
+    PET_CUDA(dev_malloc(&g->d_sums, 16 * sizeof(double)));
     // sensitivity: one FP64 backprojection of ones over all views, single plane
     double *bp = nullptr;
-    PET_CUDA(cudaMallocAsync((void **)&bp, sizeof(double) * npix, st));
+    PET_CUDA(dev_malloc_async((void **)&bp, sizeof(double) * npix, st));
     BackArgs ba;
     ba.g = gd;
     ba.g.P = 1; ba.g.Pp = 1; ba.g.G = 1; ba.g.NG = 1;

@@ -18,6 +18,23 @@ namespace pet {
 void set_error(const std::string &msg);
 pet_status fail(pet_status st, const std::string &msg);
 pet_status cuda_fail(cudaError_t e, const char *what);
+
+// Device and pinned-host allocations of the library go through these, so that the test hook
+// pet_debug_fail_alloc can make the n-th of them fail as out of memory (host-side fault
+// injection: no GPU fault is involved).
+bool alloc_fault();
+template <class T> inline cudaError_t dev_malloc(T **p, size_t n)
+{
+    return alloc_fault() ? cudaErrorMemoryAllocation : cudaMalloc((void **)p, n);
+}
+template <class T> inline cudaError_t dev_malloc_async(T **p, size_t n, cudaStream_t st)
+{
+    return alloc_fault() ? cudaErrorMemoryAllocation : cudaMallocAsync((void **)p, n, st);
+}
+template <class T> inline cudaError_t host_malloc(T **p, size_t n)
+{
+    return alloc_fault() ? cudaErrorMemoryAllocation : cudaMallocHost((void **)p, n);
+}
 inline pet_status cuda_ok(cudaError_t e, const char *what)
 {
     return e == cudaSuccess ? PET_OK : cuda_fail(e, what);

@@ -1,9 +1,21 @@
 // Launch accounting shared by the launch wrappers (see profile.cu).
 #pragma once
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "pet_common.cuh"
 
 namespace pet {
+
+// NVTX range over a host-side phase (one subiteration, a whole reconstruction, a batch tick), for
+// timeline tools; without a tool attached a push / pop is a no-op call.
+class TraceRange {
+public:
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
 
 // RAII scope around one kernel launch: counts it and, when profiling is on, brackets it with
 // CUDA events on its stream.

@@ -202,7 +202,7 @@ static pet_status prepare(pet_server *sv, Request *r)
         cudaFree(sv->d_stage);
         sv->d_stage = nullptr;
         sv->stage_bytes = 0;
-        PET_CUDA(cudaMalloc(&sv->d_stage, need));
+        PET_CUDA(dev_malloc(&sv->d_stage, need));
         sv->stage_bytes = need;
         std::lock_guard<std::mutex> lk(sv->mu);
         sv->used += need - std::min(need, sv->stage_accounted);
@@ -220,10 +220,10 @@ static pet_status prepare(pet_server *sv, Request *r)
     r->h_img_bytes = nimg * 4;
     r->h_obj_bytes = (size_t)(r->prm.iterations + 1) * 3 * 8;
     r->h_img = reinterpret_cast<float *>(pinned_get(sv, r->h_img_bytes));
-    if (!r->h_img) PET_CUDA(cudaMallocHost((void **)&r->h_img, r->h_img_bytes));
+    if (!r->h_img) PET_CUDA(host_malloc((void **)&r->h_img, r->h_img_bytes));
     r->h_obj = reinterpret_cast<double *>(pinned_get(sv, r->h_obj_bytes));
-    if (!r->h_obj) PET_CUDA(cudaMallocHost((void **)&r->h_obj, r->h_obj_bytes));
-    PET_CUDA(cudaMallocAsync((void **)&r->d_img, nimg * 4, st));
+    if (!r->h_obj) PET_CUDA(host_malloc((void **)&r->h_obj, r->h_obj_bytes));
+    PET_CUDA(dev_malloc_async((void **)&r->d_img, nimg * 4, st));
     PET_CUDA(cudaEventCreateWithFlags(&r->ready, cudaEventDisableTiming));
     PET_CUDA(cudaStreamSynchronize(st));       // uploads done: the staging buffer is free again
     r->counts.clear();
@@ -271,6 +271,10 @@ static void prep_loop(pet_server *sv)
         lk.lock();
         --sv->preparing;
         if (st != PET_OK) {
+            // the geometry's bytes were reserved with the request; they stay reserved only if
+            // the geometry was created (it then stays in the cache)
+            if (new_geo && sv->geoms.count(key_of(r->desc)) == 0)
+                sv->used -= std::min(sv->used, geometry_bytes(r->desc));
             release_request(sv, r);
             finish(sv, r, st, msg);
         } else {

@@ -125,7 +125,7 @@ static pet_status state_alloc(pet_state *s, const pet_geometry *g, int arith, in
     s->sino_elems = sino;
     cudaStream_t as = s->alloc_stream;
     auto get = [&](void **p, size_t n) -> cudaError_t {
-        return as ? cudaMallocAsync(p, n, as) : cudaMalloc(p, n);
+        return as ? dev_malloc_async(p, n, as) : dev_malloc(p, n);
     };
     PET_CUDA(get(&s->f[0], q_bytes));
     PET_CUDA(get(&s->f[1], q_bytes));
@@ -188,8 +188,8 @@ static pet_status load_factors(pet_state *s, const float *d_mult, cudaStream_t s
     PET_TRY(to_internal_sino(gd, g->d_view_of_slot, 0, gd.V, d_mult, s->mult, 2, 0, st));
     const size_t nsino = (size_t)gd.V * gd.SB * gd.Pp, q = (size_t)gd.N * gd.N * gd.Pp;
     double *ad = nullptr, *bp = nullptr;
-    PET_CUDA(cudaMallocAsync((void **)&ad, nsino * sizeof(double), st));
-    pet_status r = cuda_ok(cudaMallocAsync((void **)&bp, q * sizeof(double), st),
+    PET_CUDA(dev_malloc_async((void **)&ad, nsino * sizeof(double), st));
+    pet_status r = cuda_ok(dev_malloc_async((void **)&bp, q * sizeof(double), st),
                            "per-voxel sensitivity");
     if (r == PET_OK) r = to_internal_sino(gd, g->d_view_of_slot, 0, gd.V, d_mult, ad, 4, 0, st);
     if (r == PET_OK) {
@@ -370,6 +370,7 @@ static pet_status tv_step(const SubiterPlan &pl, cudaStream_t st)
 // forked from `st` and joined before the update.
 static pet_status state_subiter(pet_state *s, cudaStream_t st)
 {
+    TraceRange tr("pet_subiter");
     SubiterPlan pl;
     plan_subiter(s, &pl, false);
     if (pl.mu && profile_active()) {
@@ -737,8 +738,8 @@ static pet_status state_objective_beside(pet_state *s, double *out3, cudaStream_
         PET_CUDA(cudaStreamCreateWithFlags(&s->ostream, cudaStreamNonBlocking));
         PET_CUDA(cudaEventCreateWithFlags(&s->ev_ofork, cudaEventDisableTiming));
         PET_CUDA(cudaEventCreateWithFlags(&s->ev_odone, cudaEventDisableTiming));
-        PET_CUDA(cudaMalloc(&s->fobj, s->q_bytes));
-        PET_CUDA(cudaMalloc(&s->redobj_mem, reducer_bytes(kRedCap, 2)));
+        PET_CUDA(dev_malloc(&s->fobj, s->q_bytes));
+        PET_CUDA(dev_malloc(&s->redobj_mem, reducer_bytes(kRedCap, 2)));
         PET_CUDA(cudaMemset(s->redobj_mem, 0, reducer_bytes(kRedCap, 2)));
         reducer_bind(s->red_obj, s->redobj_mem, kRedCap, 2);
     }
@@ -764,6 +765,7 @@ static pet_status state_objective_beside(pet_state *s, double *out3, cudaStream_
 // only the SM slots the subiterations leave.
 static pet_status run_reconstruct(pet_state *s, double *h_objective, cudaStream_t st0)
 {
+    TraceRange tr("pet_reconstruct");
     const int T = s->prm.iterations, M = s->g->dev.M;
     cudaStream_t st = st0;
     if (h_objective && !profile_active()) {
@@ -891,15 +893,15 @@ extern "C" pet_status pet_reconstruct_host(const pet_geometry *g, const int32_t 
         ws->counts = nullptr;
         ws->gamma = nullptr;
         ws->cap_counts = 0;
-        PET_CUDA(cudaMalloc(&ws->counts, nsino * sizeof(int32_t)));
-        PET_CUDA(cudaMalloc(&ws->gamma, nsino * sizeof(float)));
+        PET_CUDA(dev_malloc(&ws->counts, nsino * sizeof(int32_t)));
+        PET_CUDA(dev_malloc(&ws->gamma, nsino * sizeof(float)));
         ws->cap_counts = nsino;
     }
     if (ws->cap_img < nimg) {
         cudaFree(ws->img);
         ws->img = nullptr;
         ws->cap_img = 0;
-        PET_CUDA(cudaMalloc(&ws->img, nimg * sizeof(float)));
+        PET_CUDA(dev_malloc(&ws->img, nimg * sizeof(float)));
         ws->cap_img = nimg;
     }
     PET_CUDA(cudaMemcpyAsync(ws->counts, h_counts, nsino * sizeof(int32_t), cudaMemcpyHostToDevice, st));

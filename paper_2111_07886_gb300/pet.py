@@ -77,6 +77,7 @@ SIGNATURES = {
     "pet_back_subset": (_I, [_VP, _I, _VP, _VP, _VP]),
     "pet_forward_subset_f64": (_I, [_VP, _I, _VP, _VP, _VP]),
     "pet_back_subset_f64": (_I, [_VP, _I, _VP, _VP, _VP]),
+    "pet_debug_fail_alloc": (None, [ctypes.c_int]),
     "pet_state_create": (_I, [_VP, _VP, _VP, ctypes.POINTER(Params), _VP, _VP, ctypes.POINTER(_VP)]),
     "pet_state_create_attn": (_I, [_VP, _VP, _VP, _VP, ctypes.POINTER(Params), _VP, _VP,
                                    ctypes.POINTER(_VP)]),
@@ -137,6 +138,12 @@ def lib():
                 fn.argtypes = args
             _lib = L
     return _lib
+
+
+def debug_fail_alloc(n: int):
+    """Test hook: the n-th device / pinned allocation of the library from now fails as out of
+    memory (n <= 0 disarms); host-side fault injection."""
+    lib().pet_debug_fail_alloc(int(n))
 
 
 def _check(status: int):

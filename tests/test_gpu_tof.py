@@ -149,3 +149,51 @@ def test_tof_reconstruction_and_refusals():
         pet.Geometry(32, 1, 4.0, 20, 47, 4.0, 4, 1.0, subrays=4, tof_bins=9, tof_bin_mm=20.0,
                      tof_fwhm_mm=40.0)
     assert e.value.status == pet.ERR_INVALID
+
+
+def test_tof_with_attenuation_and_checkpoint():
+    """TOF and per-bin detection factors together (the clinical path: attenuation-corrected TOF
+    data): the factors of each bin repeated over its TOF bins, subiterations against the oracle;
+    a checkpoint of the TOF state resumes to the same bits."""
+    w = _work(40, 3, kind=4, iters=2, T=11, dt=30.0, fw=50.0)
+    scan = synth.make_scan(w)
+    body = [[(0.0, 0.0, 70.0, 55.0, 0.3, 1.0)]] * w.nplanes
+    chord = synth.analytic_sinogram(body, w.nviews, w.nbins, w.bin_mm)
+    mult = np.repeat(np.exp(-0.0096 * chord)[..., None], w.tof_bins, axis=-1).astype(np.float32)
+    og = oracle.geom_from(w.geometry(), scan["sens"])
+    g = pet.Geometry.from_dict(w.geometry(), scan["sens"])
+    counts, gamma = to_dev(scan["counts"], torch.int32), to_dev(scan["gamma"])
+    P, N = w.nplanes, w.n
+    for nsub in (3, 7):
+        ref, _ = oracle.reconstruct(og, scan["counts"], scan["gamma"], w.params,
+                                    np.ones((P, N, N)), nsub=nsub, mult=mult)
+        for prec, tol in ((synth.PREC_FP32_KAHAN, 1e-5), (synth.PREC_FP64, 1e-10)):
+            st = pet.State(g, counts, gamma, pet.make_params(w.params, prec),
+                           torch.ones((P, N, N), device=DEV), d_mult=to_dev(mult))
+            for _ in range(nsub):
+                st.subiter()
+            out = torch.empty((P, N, N), dtype=torch.float64, device=DEV)
+            st.read_image(out)
+            torch.cuda.synchronize()
+            assert rel_l2(out.cpu().numpy(), ref) <= tol, (nsub, prec, rel_l2(out.cpu().numpy(), ref))
+            st.close()
+    # checkpoint / resume
+    prm = pet.make_params(w.params)
+    total = w.params.iterations * w.nsubsets
+    a = pet.State(g, counts, gamma, prm, torch.ones((P, N, N), device=DEV), d_mult=to_dev(mult))
+    for _ in range(total):
+        a.subiter()
+    want = torch.empty((P, N, N), device=DEV)
+    a.read_image(want)
+    b = pet.State(g, counts, gamma, prm, torch.ones((P, N, N), device=DEV), d_mult=to_dev(mult))
+    for _ in range(4):
+        b.subiter()
+    blob = b.export()
+    c = pet.State(g, counts, gamma, prm, torch.ones((P, N, N), device=DEV), d_mult=to_dev(mult))
+    c.load(blob)
+    for _ in range(total - 4):
+        c.subiter()
+    got = torch.empty((P, N, N), device=DEV)
+    c.read_image(got)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(got.cpu().numpy(), want.cpu().numpy())
