@@ -15,8 +15,10 @@ one line per bin (the paper's 576-detector ring with 32 rays per detector pair i
 phantom blurred in image space by a Gaussian PSF of FWHM 6.59 mm before projection, scatter as
 a heavily smoothed projection scaled to SF = S/(T+S) = 0.25, randoms uniform at
 RF = R/(T+S+R) = 0.25, total counts 6.8e6 (high) / 6.8e5 (low), one Poisson realisation; the
-expected scatter + randoms form the background gamma of the reconstruction.  Attenuation is not
-modelled (the library's data model has no per-bin attenuation factors).  The paper's brain
+expected scatter + randoms form the background gamma of the reconstruction.  Uniform water
+attenuation (0.096 / cm) on the phantom's body outline attenuates the trues by
+a_i = exp(-mu x chord_i), and the reconstructions use the system matrix diag(a) A (the same
+matrix that simulated the data, as in the paper).  The paper's brain
 phantom (a clinical image) is not available: a seeded random-ellipse phantom stands in for it.
 beta = 0.1 (high) / 0.8 (low), gamma_R = 2, eps = 1e-12, t = 1e-4, f^0 = 1, lambda_0 = 1,
 J0 = 3, J1 = 1000, delta_2 = delta_1, and the a, rho, delta_1, nu_1, nu_2 of Table II and of the
@@ -83,11 +85,15 @@ def _gauss1d(x, sigma, axis):
     return np.apply_along_axis(lambda v: np.convolve(v, k, mode="same"), axis, x)
 
 
+MU_WATER_PER_MM = 0.0096
+
+
 def simulate(phantom_planes, seed: int, total_counts: float, device) -> dict:
     """Data of Sec. IV-A: trues from the PSF-blurred phantom projected by this library's own
-    system model (the paper simulates and reconstructs with the same matrix), scatter, randoms,
-    Poisson noise.  Returns counts, gamma (expected scatter + randoms), the geometry sens and
-    the unblurred pixel phantom."""
+    system model (the paper simulates and reconstructs with the same matrix) and attenuated by
+    water on the body outline, scatter, randoms, Poisson noise.  Returns counts, gamma (expected
+    scatter + randoms), the attenuation factors mult, the geometry sens and the unblurred pixel
+    phantom."""
     import torch
     f_true = synth.rasterize(phantom_planes, N, PIXEL_MM)[0]
     sigma_px = FWHM_MM / (2.0 * math.sqrt(2.0 * math.log(2.0))) / PIXEL_MM
@@ -97,8 +103,10 @@ def simulate(phantom_planes, seed: int, total_counts: float, device) -> dict:
     d_proj = torch.empty((1, VIEWS, NBINS), dtype=torch.float32, device=device)
     pet.forward_subset(g1, -1, d_img, d_proj)
     torch.cuda.synchronize()
-    trues = d_proj.cpu().double().numpy()[0]
     g1.close()
+    body = [[(cx, cy, a, b, phi, 1.0) for (cx, cy, a, b, phi, _) in pl[:1]] for pl in phantom_planes]
+    mult = np.exp(-MU_WATER_PER_MM * synth.analytic_sinogram(body, VIEWS, NBINS, PIXEL_MM)[0])
+    trues = mult * d_proj.cpu().double().numpy()[0]
     # scatter: the projection smoothed heavily along the bins (FWHM 1/4 of the field), scaled to
     # S = T SF / (1 - SF); randoms uniform, R = (T + S) RF / (1 - RF); all scaled to TC
     scat = _gauss1d(trues, NBINS / 4.0 / 2.355, 1)
@@ -111,7 +119,8 @@ def simulate(phantom_planes, seed: int, total_counts: float, device) -> dict:
     gamma = (s * (scat + rnd)).astype(np.float32)
     rng = np.random.Generator(np.random.PCG64(seed))
     counts = rng.poisson(lam).astype(np.int32)
-    return dict(counts=counts[None], gamma=gamma[None], sens=float(s), f_true=f_true)
+    return dict(counts=counts[None], gamma=gamma[None], mult=mult[None].astype(np.float32),
+                sens=float(s), f_true=f_true)
 
 
 def params(base: dict, beta: float, iterations: int):
@@ -119,12 +128,12 @@ def params(base: dict, beta: float, iterations: int):
     return dataclasses.replace(p, **base)
 
 
-def run(g, d_counts, d_gamma, prm, iterations, device, f_inf=None, rois=None):
+def run(g, d_counts, d_gamma, prm, iterations, device, f_inf=None, rois=None, d_mult=None):
     """One reconstruction, subiteration by subiteration: per iteration the GPU time of its M
     subiterations (CUDA events), Phi(f^k), and NRMSD against f_inf (global and per ROI)."""
     import torch
     f0 = torch.ones((1, N, N), dtype=torch.float32, device=device)
-    st = pet.State(g, d_counts, d_gamma, pet.make_params(prm), f0)
+    st = pet.State(g, d_counts, d_gamma, pet.make_params(prm), f0, d_mult=d_mult)
     img = torch.empty_like(f0)
     M = g.nsubsets
     out = {"phi": [st.objective()[0]], "gpu_s": [0.0], "nrmsd": [], "roi_nrmsd": {}}
@@ -179,6 +188,7 @@ def experiment(iterations: int = 60, ref_iterations: int = 1000, seed: int = 0, 
     device = device or torch.device("cuda")
     res = {"setup": {"image": [N, N], "pixel_mm": PIXEL_MM, "views": VIEWS, "bins": NBINS,
                      "psf_fwhm_mm": FWHM_MM, "SF": SF, "RF": RF, "iterations": iterations,
+                     "attenuation": f"water, {MU_WATER_PER_MM} / mm on the body outline",
                      "f_inf": f"BSREM(24), {ref_iterations} iterations", "seed": seed,
                      "time": "GPU time of the subiterations (CUDA events)"},
            "brain_standin": {}, "uniform": {}}
@@ -187,16 +197,17 @@ def experiment(iterations: int = 60, ref_iterations: int = 1000, seed: int = 0, 
         data = simulate(synth.brain_standin_2d(N, PIXEL_MM, seed), seed + 11, COUNTS[level], device)
         d_c = torch.from_numpy(data["counts"]).to(device)
         d_g = torch.from_numpy(data["gamma"]).to(device)
+        d_m = torch.from_numpy(data["mult"]).to(device)
         beta = BETA[level]
         g24 = pet.Geometry(N, 1, PIXEL_MM, VIEWS, NBINS, PIXEL_MM, 24, data["sens"])
         f_inf = run(g24, d_c, d_g, params(BRAIN[level][24]["BSREM"], beta, ref_iterations),
-                    ref_iterations, device)["image"]
+                    ref_iterations, device, d_mult=d_m)["image"]
         for M in (12, 24):
             g = g24 if M == 24 else pet.Geometry(N, 1, PIXEL_MM, VIEWS, NBINS, PIXEL_MM, M, data["sens"])
             curves = {}
             for name, base in BRAIN[level][M].items():
                 curves[name] = run(g, d_c, d_g, params(base, beta, iterations), iterations, device,
-                                   f_inf=f_inf)
+                                   f_inf=f_inf, d_mult=d_m)
             key = f"{level}_{M}"
             res["brain_standin"][key] = {"curves": curves,
                                          "vs_bsrem": speedups(curves, "BSREM", iterations)}
@@ -210,12 +221,13 @@ def experiment(iterations: int = 60, ref_iterations: int = 1000, seed: int = 0, 
     data = simulate(synth.uniform_phantom_2d(N, PIXEL_MM), seed + 23, COUNTS["high"], device)
     d_c = torch.from_numpy(data["counts"]).to(device)
     d_g = torch.from_numpy(data["gamma"]).to(device)
+    d_m = torch.from_numpy(data["mult"]).to(device)
     g24 = pet.Geometry(N, 1, PIXEL_MM, VIEWS, NBINS, PIXEL_MM, 24, data["sens"])
     f_inf = run(g24, d_c, d_g, params(UNIFORM["BSREM"], BETA["high"], ref_iterations),
-                ref_iterations, device)["image"]
+                ref_iterations, device, d_mult=d_m)["image"]
     rois = synth.uniform_phantom_rois(N, PIXEL_MM)
     curves = {name: run(g24, d_c, d_g, params(base, BETA["high"], iterations), iterations, device,
-                        f_inf=f_inf, rois=rois) for name, base in UNIFORM.items()}
+                        f_inf=f_inf, rois=rois, d_mult=d_m) for name, base in UNIFORM.items()}
     res["uniform"]["high_24"] = {"curves": curves, "vs_bsrem": speedups(curves, "BSREM", iterations)}
     res["setup"]["wall_s"] = round(time.time() - t_wall, 1)
     return res
