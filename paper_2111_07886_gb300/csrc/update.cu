@@ -691,10 +691,10 @@ int resident_blocks(const void *fn);
 template <int G, int KC>
 static const void *update_fn(int arith, int z3 = 0, int sub = 0, int tof = 0)
 {
-    if (tof) {                                   // TOF geometries: KC = 4, generic kernel
-        if (arith == AR_FP32) return (const void *)update_kernel<G, 4, AR_FP32, false, true>;
-        if (arith == AR_KAHAN) return (const void *)update_kernel<G, 4, AR_KAHAN, false, true>;
-        return (const void *)update_kernel<G, 4, AR_FP64, false, true>;
+    if (tof) {                                   // TOF geometries: generic kernel
+        if (arith == AR_FP32) return (const void *)update_kernel<G, KC, AR_FP32, false, true>;
+        if (arith == AR_KAHAN) return (const void *)update_kernel<G, KC, AR_KAHAN, false, true>;
+        return (const void *)update_kernel<G, KC, AR_FP64, false, true>;
     }
     if (sub) {                                   // sub-ray geometries: KC = 4, generic kernel
         if (arith == AR_FP32) return (const void *)update_kernel<G, 4, AR_FP32, true>;
@@ -746,10 +746,10 @@ static int persistent_grid(int nvb) { return std::max(1, std::min(nvb, sm_count(
 template <int G, int KC>
 static void update_dispatch(const UpdateArgs &a, const Batch &b, int arith, int grid, cudaStream_t st)
 {
-    if (a.g.T > 1) {                             // TOF geometries: KC = 4, generic kernel
-        if (arith == AR_FP32) update_kernel<G, 4, AR_FP32, false, true><<<grid, 256, 0, st>>>(a, b);
-        else if (arith == AR_KAHAN) update_kernel<G, 4, AR_KAHAN, false, true><<<grid, 256, 0, st>>>(a, b);
-        else update_kernel<G, 4, AR_FP64, false, true><<<grid, 256, 0, st>>>(a, b);
+    if (a.g.T > 1) {                             // TOF geometries: generic kernel
+        if (arith == AR_FP32) update_kernel<G, KC, AR_FP32, false, true><<<grid, 256, 0, st>>>(a, b);
+        else if (arith == AR_KAHAN) update_kernel<G, KC, AR_KAHAN, false, true><<<grid, 256, 0, st>>>(a, b);
+        else update_kernel<G, KC, AR_FP64, false, true><<<grid, 256, 0, st>>>(a, b);
         return;
     }
     if (a.g.R > 1) {                             // sub-ray geometries: KC = 4, generic kernel
@@ -806,9 +806,9 @@ template <int G, int KC>
 static void back_dispatch(const BackArgs &a, int arith, int grid, cudaStream_t st)
 {
     if (a.g.T > 1) {
-        if (arith == AR_FP32) back_kernel<G, 4, AR_FP32, false, true><<<grid, 256, 0, st>>>(a);
-        else if (arith == AR_KAHAN) back_kernel<G, 4, AR_KAHAN, false, true><<<grid, 256, 0, st>>>(a);
-        else back_kernel<G, 4, AR_FP64, false, true><<<grid, 256, 0, st>>>(a);
+        if (arith == AR_FP32) back_kernel<G, KC, AR_FP32, false, true><<<grid, 256, 0, st>>>(a);
+        else if (arith == AR_KAHAN) back_kernel<G, KC, AR_KAHAN, false, true><<<grid, 256, 0, st>>>(a);
+        else back_kernel<G, KC, AR_FP64, false, true><<<grid, 256, 0, st>>>(a);
         return;
     }
     if (a.g.R > 1) {
