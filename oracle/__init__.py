@@ -40,7 +40,7 @@ class Geom(ctypes.Structure):
                 ("pixel_mm", ctypes.c_double), ("bin_mm", ctypes.c_double),
                 ("sens", ctypes.c_double), ("subrays", ctypes.c_int),
                 ("tof_bins", ctypes.c_int), ("tof_bin_mm", ctypes.c_double),
-                ("tof_fwhm_mm", ctypes.c_double)]
+                ("tof_fwhm_mm", ctypes.c_double), ("ring_mm", ctypes.c_double)]
 
 
 class Params(ctypes.Structure):
@@ -107,10 +107,10 @@ def _d(a):
 
 
 def geom(n, nplanes, nviews, nbins, nsubsets, pixel_mm=1.0, bin_mm=None, sens=1.0,
-         subrays=1, tof_bins=0, tof_bin_mm=0.0, tof_fwhm_mm=0.0) -> Geom:
+         subrays=1, tof_bins=0, tof_bin_mm=0.0, tof_fwhm_mm=0.0, ring_mm=0.0) -> Geom:
     return Geom(n, nplanes, nviews, nbins, nsubsets, pixel_mm,
                 pixel_mm if bin_mm is None else bin_mm, sens, subrays, tof_bins, tof_bin_mm,
-                tof_fwhm_mm)
+                tof_fwhm_mm, ring_mm)
 
 
 def geom_from(geometry: dict, sens: float) -> Geom:
@@ -118,7 +118,7 @@ def geom_from(geometry: dict, sens: float) -> Geom:
     return Geom(g["n"], g["nplanes"], g["nviews"], g["nbins"], g["nsubsets"],
                 g["pixel_mm"], g["bin_mm"], sens, int(g.get("subrays", 1)),
                 int(g.get("tof_bins", 0)), float(g.get("tof_bin_mm", 0.0)),
-                float(g.get("tof_fwhm_mm", 0.0)))
+                float(g.get("tof_fwhm_mm", 0.0)), float(g.get("ring_mm", 0.0)))
 
 
 def ntof(g: Geom) -> int:

@@ -31,6 +31,13 @@
  * found by Siddon's method: all crossings of the ray with the grid lines are sorted, and each
  * piece between consecutive crossings is charged to the pixel that contains its midpoint.
  *
+ * Ring sampling (the paper's scanner is a ring of 576 detectors, Sec. IV-A): with ring_mm = Rd
+ * > 0 the bins are the lines of a ring of radius Rd seen in one view, equally spaced in angle:
+ * bin b sits at r_b = Rd sin(beta_b), beta_b = (b - (n_b - 1)/2) dbeta, dbeta = bin_mm / Rd (so
+ * bin_mm is the arc spacing on the ring; the radial spacing shrinks by cos beta towards the edge
+ * of the field), and spans [Rd sin(beta_b - dbeta/2), Rd sin(beta_b + dbeta/2)]: its R sub-rays
+ * are spread uniformly over that width.  ring_mm = 0: the uniform parallel-beam bins above.
+ *
  * Time of flight (the clinical reconstructions of Sec. IV-C use TOF data): with T > 1 TOF bins,
  * bin i = (v, b) splits into (v, b, t), t = 0..T-1, centred at tau_t = (t - (T-1)/2) dtau along
  * the line from its point nearest the centre, and A_{(v,b,t) j} = A_{(v,b) j} h_t(tau_j), where
@@ -67,6 +74,7 @@ typedef struct {
     int tof_bins;    /* T time-of-flight bins per bin (<= 1: no TOF) */
     double tof_bin_mm;   /* width of a TOF bin along the line */
     double tof_fwhm_mm;  /* FWHM of the Gaussian timing kernel, as a distance along the line */
+    double ring_mm;  /* detector ring radius (> 0: bins sampled like a ring's lines, below) */
 } ora_geom;
 
 typedef struct {
@@ -92,10 +100,26 @@ static void view_dir(const ora_geom *g, int v, double *c, double *s)
     *c = cc; *s = ss;
 }
 
-/* offset of bin b from the centre, in pixel units */
+/* offset of bin b from the centre, in pixel units (uniform bins, or ring sampling) */
 static double bin_offset(const ora_geom *g, int b)
 {
-    return ((double)b - 0.5 * (double)(g->nbins - 1)) * (g->bin_mm / g->pixel_mm);
+    const double k = (double)b - 0.5 * (double)(g->nbins - 1);
+    if (g->ring_mm > 0.0) return g->ring_mm * sin(k * g->bin_mm / g->ring_mm) / g->pixel_mm;
+    return k * (g->bin_mm / g->pixel_mm);
+}
+
+/* the edges of bin b's width, in pixel units */
+static void bin_edges(const ora_geom *g, int b, double *lo, double *hi)
+{
+    const double k = (double)b - 0.5 * (double)(g->nbins - 1);
+    if (g->ring_mm > 0.0) {
+        const double db = g->bin_mm / g->ring_mm;
+        *lo = g->ring_mm * sin((k - 0.5) * db) / g->pixel_mm;
+        *hi = g->ring_mm * sin((k + 0.5) * db) / g->pixel_mm;
+    } else {
+        *lo = (k - 0.5) * (g->bin_mm / g->pixel_mm);
+        *hi = (k + 0.5) * (g->bin_mm / g->pixel_mm);
+    }
 }
 
 int ora_subset_size(const ora_geom *g, int subset)
@@ -134,9 +158,12 @@ int ora_bin_pieces(const ora_geom *g, int v, int b, int *pix, double *len)
     const int R = nsub_of(g), N = g->n;
     if (R == 1) return ora_ray_pieces(g, v, b, pix, len);
     const double rho = g->bin_mm / g->pixel_mm;
+    double lo, hi;
+    bin_edges(g, b, &lo, &hi);
     int np = 0;
     for (int s = 0; s < R; ++s) {
-        const double r = bin_offset(g, b) + ((s + 0.5) / R - 0.5) * rho;
+        const double r = g->ring_mm > 0.0 ? lo + (s + 0.5) / R * (hi - lo)
+                                          : bin_offset(g, b) + ((s + 0.5) / R - 0.5) * rho;
         const int k = line_pieces(g, v, r, pix + np, len + np);
         for (int m = np; m < np + k; ++m) len[m] /= R;
         np += k;
