@@ -77,6 +77,13 @@ typedef struct {
                            Sinograms then hold [P][V][n_b][T].  At most 64; with subrays <= 1 */
     double tof_bin_mm;  /* TOF bin width along the line (> 0 with TOF) */
     double tof_fwhm_mm; /* FWHM of the timing kernel as a distance along the line (> 0 with TOF) */
+    double ring_mm;     /* 0: uniform bins bin_mm apart.  > 0: the bins of a view are the lines of
+                           a detector ring of this radius equally spaced in angle (the paper's
+                           576-detector ring, Sec. IV-A): bin b lies at r_b = ring_mm sin(beta_b),
+                           beta_b = (b - (n_b-1)/2) bin_mm / ring_mm (bin_mm is then the arc
+                           spacing on the ring), spans [ring_mm sin(beta_b - d/2),
+                           ring_mm sin(beta_b + d/2)] with d = bin_mm / ring_mm, and its subrays
+                           spread uniformly over that width.  Needs n_b bin_mm < pi ring_mm */
 } pet_geometry_desc;
 
 typedef enum {

@@ -152,7 +152,7 @@ extern "C" void pet_batch_destroy(pet_batch *b)
 static pet_status class_for(pet_batch *b, pet_state *s, BatchClass **out)
 {
     const int G = s->g->dev.G, arith = s->arith, KC = kc_of(s), z3 = s->prm.rdp_3d;
-    const int sub = s->g->dev.R > 1, vox = s->attn ? 1 : 0;
+    const int sub = s->g->dev.table, vox = s->attn ? 1 : 0;
     for (BatchClass *c : b->classes)
         if (c->G == G && c->arith == arith && c->KC == KC && c->z3 == z3 && c->sub == sub &&
             c->vox == vox) {
@@ -277,11 +277,13 @@ static pet_status class_launches(pet_batch *b, BatchClass *c, const BatchClass::
     FwdArgs fs{};
     fs.g.G = c->G;
     fs.g.K = c->KC;
-    fs.g.R = c->sub ? 2 : 1;                  // selects the sub-ray projector
+    fs.g.R = c->sub ? 2 : 1;                  // selects the sub-ray (table-driven) projector
+    fs.g.table = c->sub;
     UpdateArgs us{};
     us.g.G = c->G;
     us.g.K = c->KC;
     us.g.R = c->sub ? 2 : 1;                  // selects the sub-ray kernel (the count comes per scan)
+    us.g.table = c->sub;
     us.z3 = c->z3;
     us.vox = c->vox;
     ImageArgs is{};

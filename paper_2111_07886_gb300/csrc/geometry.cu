@@ -92,13 +92,37 @@ extern "C" const char *pet_last_error(void) { return pet::g_last_error.c_str(); 
 extern "C" void pet_debug_fail_alloc(int n) { pet::g_fail_alloc.store(n > 0 ? n : 0); }
 
 static pet_status build_tables(pet_geometry *g, std::vector<ViewGeo> &views,
-                               std::vector<RayGeo> &rays)
+                               std::vector<RayGeo> &rays, std::vector<BinGeo> &bins)
 {
     const pet_geometry_desc &d = g->desc;
     const int N = d.n, V = d.nviews, NB = d.nbins, M = d.nsubsets;
     const int R = d.subrays > 1 ? d.subrays : 1;
     const double rho = d.bin_mm / d.pixel_mm;
     const double half = 0.5 * N;
+    // bins: the line offset of bin b (pixel units) and the lines of its R sub-rays.  Uniform:
+    // r_b = (b - (NB-1)/2) rho, width rho.  Ring: r_b = Rd sin(beta_b), beta_b = (b - (NB-1)/2)
+    // dbeta, width [Rd sin(beta_b - dbeta/2), Rd sin(beta_b + dbeta/2)]; R > 1 lines spread
+    // uniformly over the width, around its middle m_b (= r_b for uniform bins).
+    const bool ring = d.ring_mm > 0.0;
+    const double Rd = ring ? d.ring_mm / d.pixel_mm : 0.0, db = ring ? d.bin_mm / d.ring_mm : 0.0;
+    std::vector<double> rc(NB), wd(NB);          // centre of the bin's lines, width
+    double wmin = 1e300;
+    bins.assign(NB, BinGeo{});
+    for (int b = 0; b < NB; ++b) {
+        const double k = (double)b - 0.5 * (NB - 1);
+        double lo, hi, rb;
+        if (ring) { lo = Rd * sin((k - 0.5) * db); hi = Rd * sin((k + 0.5) * db); rb = Rd * sin(k * db); }
+        else { rb = k * rho; lo = rb - 0.5 * rho; hi = rb + 0.5 * rho; }
+        wd[b] = ring ? hi - lo : rho;
+        wmin = std::min(wmin, wd[b]);
+        rc[b] = (R > 1 && ring) ? 0.5 * (lo + hi) : rb;
+        BinGeo bg;
+        bg.ds = wd[b] / R;
+        bg.c0 = R > 1 ? lo + 0.5 * bg.ds : rb;
+        bg.c0q = to_q32(bg.c0);
+        bg.dsq = to_q32(bg.ds);
+        bins[b] = bg;
+    }
     g->voff.assign(M + 1, 0);
     g->view_of_slot.clear();
     for (int i = 0; i < M; ++i) {
@@ -157,9 +181,21 @@ static pet_status build_tables(pet_geometry *g, std::vector<ViewGeo> &views,
         }
         vg.tau0f = (float)vg.tau0; vg.tauxf = (float)vg.taux; vg.tauyf = (float)vg.tauy;
         vg.tdrf = (float)vg.tdr; vg.tdcf = (float)vg.tdc; vg.tddf = (float)vg.tdd;
+        // table-driven bins: the pixel centre's offset along the normal (c, s), pixel units
+        vg.pnx = c;
+        vg.pny = s;
+        vg.pn0 = (0.5 - half) * (c + s);
+        vg.hp = 0.5 * (ac + as);
+        vg.islope = minor > 0.0 ? 1.0 / (major * minor) : 0.0;
+        vg.islopef = (float)vg.islope;
+        vg.pn0q = to_q32(vg.pn0); vg.pnxq = to_q32(vg.pnx); vg.pnyq = to_q32(vg.pny);
+        vg.hpq = to_q32(vg.hp);
         // candidate bins of a pixel's footprint: one line per bin, or sub-lines within
-        // (R - 1) / (2 R) bins of the bin centre on either side (first candidate floor(t - hh))
-        if (R == 1) K = std::max(K, (int)floor(2.0 * vg.h) + 1);
+        // (R - 1) / (2 R) bins of the bin centre on either side (first candidate floor(t - hh));
+        // ring bins: any bin whose width meets the footprint, from one bin before the bin
+        // coordinate of its low edge (the narrowest bins, at the edge of the field, decide)
+        if (ring) K = std::max(K, (int)floor(2.0 * (0.5 * (ac + as)) / wmin) + 3);
+        else if (R == 1) K = std::max(K, (int)floor(2.0 * vg.h) + 1);
         else K = std::max(K, (int)floor(2.0 * (vg.h + 0.5 - 0.5 / R)) + 2);
         views[u] = vg;
         // driving steps the line at offset r meets the image (+- one step of margin)
@@ -178,13 +214,13 @@ static pet_status build_tables(pet_geometry *g, std::vector<ViewGeo> &views,
             dhi = (long long)ceil(std::min(1e9, upper)) + 1;
         };
         for (int b = 0; b < NB; ++b) {
-            const double r = ((double)b - 0.5 * (NB - 1)) * rho;
+            const double r = rc[b];
             long long dlo, dhi;
             double LO0;
             range(r, dlo, dhi, LO0);
             if (R > 1) {
                 // the union of the ranges of the bin's outermost sub-lines and its centre line
-                const double e = (0.5 - 0.5 / R) * rho;
+                const double e = (0.5 - 0.5 / R) * wd[b];
                 for (double rr : {r - e, r + e}) {
                     long long l2, h2;
                     double unused;
@@ -203,11 +239,20 @@ static pet_status build_tables(pet_geometry *g, std::vector<ViewGeo> &views,
             else { rg.d0 = (int)dlo; rg.nd = (int)(dhi - dlo + 1); }
             rg.lo = LO0 + rg.d0 * B;
             rg.loq = to_q32(rg.lo);
+            rg.sh = R > 1 ? wd[b] / (2.0 * R * a) : 0.0;
+            rg.shq = to_q32(rg.sh);
             rays[(size_t)u * NB + b] = rg;
         }
     }
-    g->dev.K = R > 1 ? std::max(K, 3) : K;   // sub-ray kernels are built for 4 candidates
+    // sub-ray and ring kernels are built for 4 candidates
+    g->dev.K = (R > 1 || ring) ? std::max(K, 3) : K;
     g->dev.R = R;
+    g->dev.ring = ring ? 1 : 0;
+    g->dev.table = (R > 1 || ring) ? 1 : 0;
+    g->dev.ring_r = Rd;
+    g->dev.ring_db = db;
+    g->dev.ring_rf = (float)Rd;
+    g->dev.ring_dbf = (float)db;
     g->dev.offq = to_q32(0.5 / R);
     return PET_OK;
 }
@@ -217,7 +262,8 @@ static pet_status geometry_init(pet_geometry *g, cudaStream_t st)
     const pet_geometry_desc &d = g->desc;
     std::vector<ViewGeo> views;
     std::vector<RayGeo> rays;
-    PET_TRY(build_tables(g, views, rays));
+    std::vector<BinGeo> bins;
+    PET_TRY(build_tables(g, views, rays, bins));
     GeoDev &gd = g->dev;
     if (gd.K > 4)
         return fail(PET_ERR_INVALID, "pet_geometry_create: a pixel's footprint spans more than 4 "
@@ -247,6 +293,9 @@ static pet_status geometry_init(pet_geometry *g, cudaStream_t st)
     PET_CUDA(dev_malloc(&g->d_views, sizeof(ViewGeo) * views.size()));
     PET_CUDA(dev_malloc(&g->d_rays, sizeof(RayGeo) * rays.size()));
     PET_CUDA(dev_malloc(&g->d_view_of_slot, sizeof(int) * g->view_of_slot.size()));
+    PET_CUDA(dev_malloc(&g->d_bins, sizeof(BinGeo) * bins.size()));
+    PET_CUDA(cudaMemcpyAsync(g->d_bins, bins.data(), sizeof(BinGeo) * bins.size(),
+                             cudaMemcpyHostToDevice, st));
     PET_CUDA(cudaMemcpyAsync(g->d_views, views.data(), sizeof(ViewGeo) * views.size(),
                              cudaMemcpyHostToDevice, st));
     PET_CUDA(cudaMemcpyAsync(g->d_rays, rays.data(), sizeof(RayGeo) * rays.size(),
@@ -255,6 +304,7 @@ static pet_status geometry_init(pet_geometry *g, cudaStream_t st)
                              sizeof(int) * g->view_of_slot.size(), cudaMemcpyHostToDevice, st));
     gd.views = g->d_views;
     gd.rays = g->d_rays;
+    gd.bins = g->d_bins;
     const size_t npix = (size_t)d.n * d.n;
     PET_CUDA(dev_malloc(&g->d_p, sizeof(float) * npix));
     PET_CUDA(dev_malloc(&g->d_invp, sizeof(float) * npix));
@@ -310,6 +360,10 @@ extern "C" pet_status pet_geometry_create(const pet_geometry_desc *desc, void *s
     if (d.bin_mm < 0.36 * d.pixel_mm)
         return fail(PET_ERR_INVALID, "pet_geometry_create: bin_mm must be >= 0.36 pixel_mm "
                                      "(at most 4 rays of one view cross a pixel)");
+    if (!(d.ring_mm >= 0) || !std::isfinite(d.ring_mm) ||
+        (d.ring_mm > 0 && 0.5 * d.nbins * d.bin_mm / d.ring_mm >= 1.5707963267948966))
+        return fail(PET_ERR_INVALID, "pet_geometry_create: ring_mm must be 0 or > 0 with the bins "
+                                     "spanning less than a half circle (nbins bin_mm / ring_mm < pi)");
     if (d.tof_bins < 0 || d.tof_bins > 64 ||
         (d.tof_bins > 1 && (!(d.tof_bin_mm > 0) || !(d.tof_fwhm_mm > 0) ||
                             !std::isfinite(d.tof_bin_mm) || !std::isfinite(d.tof_fwhm_mm) ||
@@ -338,6 +392,7 @@ extern "C" void pet_geometry_destroy(pet_geometry *g)
     pet::workspace_free(g->workspace);
     cudaFree(g->d_views);
     cudaFree(g->d_rays);
+    cudaFree(g->d_bins);
     cudaFree(g->d_view_of_slot);
     cudaFree(g->d_p);
     cudaFree(g->d_invp);

@@ -350,11 +350,87 @@ template <int KC, int AR, int CAPX = 0> struct BpTable {
 // views; for views along an axis, L for each line whose forward-walk start coordinate lies in the
 // pixel's column, the forward projector's own membership test); scale carries the 1 / R.  The
 // first candidate is floor(t - h - (R - 1) / (2 R)).
+// Ring-sampled bins (g.ring): bin b's R lines lie at c0_b + s ds_b (pixel units, from the bin
+// table); the weight of bin b is the sum of their lengths in the pixel: the trapezoid
+// min(L, (hp - |r - p|) / (major minor)) of the pixel's footprint, p the pixel centre's offset
+// along the view's normal, hp its half-width; views along an axis use the forward walk's start
+// coordinates as for uniform sub-rays.  Candidates start one bin before the bin coordinate
+// asin((p - hp) / Rd) / dbeta + (NB - 1) / 2 of the footprint's low edge, rounded to the bin
+// whose width contains it (K covers the footprint over the narrowest bins).
+template <int KC, int AR>
+__device__ __forceinline__ void bp_weights_ring(const GeoDev &g, const ViewGeo &vw, int slot, int ix,
+                                                int iy, int &b0, typename ArithT<AR>::T (&w)[KC])
+{
+    using T = typename ArithT<AR>::T;
+    const int NB = g.NB, R = g.R;
+#pragma unroll
+    for (int k = 0; k < KC; ++k) w[k] = T(0);
+    if constexpr (AR == AR_FP64) {
+        const double p = vw.pn0 + (double)ix * vw.pnx + (double)iy * vw.pny;
+        const double x = fmin(1.0, fmax(-1.0, (p - vw.hp) / g.ring_r));
+        b0 = (int)floor(asin(x) / g.ring_db + 0.5 * NB) - 1;
+    } else {
+        const float p = (float)vw.pn0 + (float)ix * (float)vw.pnx + (float)iy * (float)vw.pny;
+        const float x = fminf(1.f, fmaxf(-1.f, (p - (float)vw.hp) / g.ring_rf));
+        b0 = (int)floorf(asinf(x) / g.ring_dbf + 0.5f * NB) - 1;
+    }
+    const BinGeo *bg = g.bins;
+    if (vw.axis) {
+        const int cross = vw.xdrive ? iy : ix;
+        const RayGeo *rr = g.rays + (size_t)slot * NB;
+#pragma unroll
+        for (int k = 0; k < KC; ++k) {
+            const int b = b0 + k;
+            if ((unsigned)b >= (unsigned)NB) continue;
+            int cnt = 0;
+            for (int sr = 0; sr < R; ++sr) {
+                if constexpr (AR == AR_FP64) cnt += (int)floor(rr[b].lo + (2 * sr + 1 - R) * rr[b].sh) == cross;
+                else cnt += (int)((rr[b].loq + (long long)(2 * sr + 1 - R) * rr[b].shq) >> 32) == cross;
+            }
+            w[k] = (T)cnt * (T)vw.L;
+        }
+        return;
+    }
+    if constexpr (AR == AR_FP64) {
+        const double p = vw.pn0 + (double)ix * vw.pnx + (double)iy * vw.pny;
+#pragma unroll
+        for (int k = 0; k < KC; ++k) {
+            const int b = b0 + k;
+            if ((unsigned)b >= (unsigned)NB) continue;
+            double ww = 0.0;
+            for (int sr = 0; sr < R; ++sr) {
+                const double dd = vw.hp - fabs(bg[b].c0 + sr * bg[b].ds - p);
+                ww += dd > 0.0 ? fmin(vw.L, dd * vw.islope) : 0.0;
+            }
+            w[k] = ww;
+        }
+    } else {
+        const long long pq = vw.pn0q + (long long)ix * vw.pnxq + (long long)iy * vw.pnyq;
+        const float ws = vw.islopef * (kQ32 * 256.f);
+#pragma unroll
+        for (int k = 0; k < KC; ++k) {
+            const int b = b0 + k;
+            if ((unsigned)b >= (unsigned)NB) continue;
+            float ww = 0.f;
+            for (int sr = 0; sr < R; ++sr) {
+                const long long dq = bg[b].c0q + (long long)sr * bg[b].dsq - pq;
+                const long long dd = vw.hpq - (dq < 0 ? -dq : dq);
+                ww += dd > 0 ? fminf(vw.Lf, __int2float_rn((int)(dd >> 8)) * ws) : 0.f;
+            }
+            w[k] = ww;
+        }
+    }
+}
+
 template <int KC, int AR>
 __device__ __forceinline__ void bp_weights_sub(const GeoDev &g, const ViewGeo &vw, int slot, int ix,
                                             int iy, int &b0, typename ArithT<AR>::T (&w)[KC])
 {
     using T = typename ArithT<AR>::T;
+    if (g.ring) {
+        bp_weights_ring<KC, AR>(g, vw, slot, ix, iy, b0, w);
+        return;
+    }
     const int NB = g.NB, R = g.R;
 #pragma unroll
     for (int k = 0; k < KC; ++k) w[k] = T(0);

@@ -125,9 +125,9 @@ extern "C" pet_status pet_objective_static(const pet_geometry *g, const int32_t 
     if (!g || !d_counts || !d_gamma || !d_img || !h_phi)
         return fail(PET_ERR_INVALID, "pet_objective_static: NULL argument");
     const GeoDev &gd = g->dev;
-    if (gd.R > 1 || gd.T > 1)
-        return fail(PET_ERR_INVALID, "pet_objective_static: one line per bin without TOF only (use "
-                                     "pet_objective for sub-ray and TOF geometries)");
+    if (gd.table || gd.T > 1)
+        return fail(PET_ERR_INVALID, "pet_objective_static: one line per uniform bin without TOF only "
+                                     "(use pet_objective for sub-ray, ring and TOF geometries)");
     const double nrays = (double)gd.V * gd.NB * gd.P, npix = (double)gd.N * gd.N * gd.P;
     if (nrays > 2147483647.0 || npix > 2147483647.0)
         return fail(PET_ERR_INVALID, "pet_objective_static: at most 2^31 - 1 rays x planes and "

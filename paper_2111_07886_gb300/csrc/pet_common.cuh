@@ -83,12 +83,27 @@ struct ViewGeo {
     // tau = tdr r + tdc + d tdd (r the line's offset in pixel units)
     double tau0, taux, tauy, tdr, tdc, tdd;
     float tau0f, tauxf, tauyf, tdrf, tdcf, tddf;
+    // table-driven bins (ring sampling): offset of pixel (ix, iy)'s centre along the view's
+    // normal in pixel units, pn = pn0 + ix pnx + iy pny (double and Q32.32), the pixel's
+    // half-footprint hp = (|c| + |s|) / 2 and 1 / (major minor) (pixel units)
+    long long pn0q, pnxq, pnyq, hpq;
+    double pn0, pnx, pny, hp, islope;
+    float islopef;
+};
+
+// One bin of a table-driven geometry: its first line's offset c0 and the spacing ds of its R
+// lines (pixel units, double and Q32.32): line s lies at c0 + s ds.
+struct BinGeo {
+    long long c0q, dsq;
+    double c0, ds;
 };
 
 struct RayGeo {
     long long loq;        // low cross coordinate of the first driving step, Q32.32 (grid units)
-    double lo;            // same, double
+    double lo;            // same, double (the bin's line; with sub-rays, the centre of its lines)
     int d0, nd;           // driving range [d0, d0 + nd)
+    long long shq;        // sub-rays: half the cross-coordinate spacing of the bin's lines
+    double sh;            //   (line s starts (2 s + 1 - R) sh from lo)
 };
 
 // Kernel-side view of a geometry.
@@ -97,6 +112,11 @@ struct GeoDev {
     int V, NB, M, K;          // views, bins, subsets, max candidate bins per view in the gather
     int tuneS;                // forward projector chunks per ray picked by pet_autotune (0: heuristic)
     int R;                    // sub-rays per bin (1: one line); scale includes the 1 / R
+    int ring;                 // 1: bins sampled like a detector ring's lines (table-driven)
+    int table;                // 1: table-driven bins (sub-rays or ring): the SUB kernels
+    double ring_r, ring_db;   // ring radius (pixel units) and angular bin spacing
+    float ring_rf, ring_dbf;
+    const BinGeo *bins;       // [NB] (table-driven geometries)
     int T;                    // TOF bins per bin (1: no TOF)
     int SB;                   // sinogram entries per view and plane: NB T
     double rho;               // bin spacing / pixel size
@@ -123,6 +143,7 @@ struct pet_geometry {
     std::vector<int> view_of_slot;  // original view index of each sorted slot
     pet::ViewGeo *d_views = nullptr;
     pet::RayGeo *d_rays = nullptr;
+    pet::BinGeo *d_bins = nullptr;  // table-driven geometries
     float *d_p = nullptr;           // p_j, FP32, [N*N]
     float *d_invp = nullptr;        // 1 / p_j, FP32
     double *d_invp64 = nullptr;     // 1 / p_j, FP64

@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(256, 3) fwd_kernel(const __grid_constant__ Fwd
                 for (int sr = 0; sr < nsr; ++sr)
                 for (int k = k0; k < k1; ++k) {
                     const int d = rg.d0 + k;
-                    const double lo = fma((double)k, step, rg.lo + (2 * sr + 1 - nsr) * vw.half);
+                    const double lo = fma((double)k, step, rg.lo + (2 * sr + 1 - nsr) * (SUB ? rg.sh : vw.half));
                     const double hi = lo + ast;
                     const double f0 = floor(lo), f1 = floor(hi);
                     const int r0 = (int)f0, r1 = (int)f1;
@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(256, 3) fwd_kernel(const __grid_constant__ Fwd
                 int nb = 0;
                 for (int sr = 0; sr < nsr; ++sr) {
                 unsigned base = (unsigned)(rg.d0 + k0) * dstep;
-                long long lo = rg.loq + (long long)(2 * sr + 1 - nsr) * vw.halfq + (long long)k0 * stp;
+                long long lo = rg.loq + (long long)(2 * sr + 1 - nsr) * (SUB ? rg.shq : vw.halfq) + (long long)k0 * stp;
                 for (int k = k0; k < k1; ++k) {
                     const long long hi = lo + ast;
                     const int r0 = (int)(lo >> 32), r1 = (int)(hi >> 32);
@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(256, 3) fwd_kernel(const __grid_constant__ Fwd
 #pragma unroll
                 for (int q = 0; q < 4; ++q) { sm[q] = 0ull; er[q] = 0ull; }
                 for (int sr = 0; sr < nsr; ++sr) {
-                long long lo = rg.loq + (long long)(2 * sr + 1 - nsr) * vw.halfq + (long long)k0 * stp;
+                long long lo = rg.loq + (long long)(2 * sr + 1 - nsr) * (SUB ? rg.shq : vw.halfq) + (long long)k0 * stp;
                 for (int k = k0; k < k1; ++k) {
                     const int d = rg.d0 + k;
                     const long long hi = lo + ast;
@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(256, 3) fwd_kernel(const __grid_constant__ Fwd
                 const long long stp = vw.stepq, ast = vw.absstepq;
                 const float L = vw.Lf, im = vw.inv_minorf * kQ32;
                 for (int sr = 0; sr < nsr; ++sr) {
-                long long lo = rg.loq + (long long)(2 * sr + 1 - nsr) * vw.halfq + (long long)k0 * stp;
+                long long lo = rg.loq + (long long)(2 * sr + 1 - nsr) * (SUB ? rg.shq : vw.halfq) + (long long)k0 * stp;
                 for (int k = k0; k < k1; ++k) {
                     const int d = rg.d0 + k;
                     const long long hi = lo + ast;
@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(256, 3) fwd_kernel(const __grid_constant__ Fwd
 template <int G, int AR>
 static void fwd_dispatch_mode(const FwdArgs &a, const Batch &b, int mode, int grid, cudaStream_t st)
 {
-    if (a.g.R > 1) {
+    if (a.g.table) {
         if (mode == FWD_PLAIN) fwd_kernel<G, AR, FWD_PLAIN, true><<<grid, 256, 0, st>>>(a, b);
         else if (mode == FWD_RATIO) fwd_kernel<G, AR, FWD_RATIO, true><<<grid, 256, 0, st>>>(a, b);
         else fwd_kernel<G, AR, FWD_OBJECTIVE, true><<<grid, 256, 0, st>>>(a, b);
@@ -405,7 +405,7 @@ void forward_shape(FwdArgs &a, int mode, int arith)
     a.tpv = 1;
     if (mode == FWD_OBJECTIVE) {
         // each virtual block ends in a block reduction and a grid-wide ticket: one wave of them
-        const void *fn = a.g.G == 1 ? fwd_fn_g<1>(mode, arith, a.g.R > 1) : fwd_fn_g<8>(mode, arith, a.g.R > 1);
+        const void *fn = a.g.G == 1 ? fwd_fn_g<1>(mode, arith, a.g.table) : fwd_fn_g<8>(mode, arith, a.g.table);
         const long long slots = (long long)sm_count() * resident_blocks(fn);
         long long tpv = (ntiles + slots - 1) / slots;
         if (a.red.capacity > 0) tpv = std::max(tpv, (ntiles + a.red.capacity - 1) / a.red.capacity);

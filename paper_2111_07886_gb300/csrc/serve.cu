@@ -73,12 +73,12 @@ struct SrvClass {
     std::vector<Request *> running;
 };
 
-typedef std::tuple<int, int, double, int, int, double, int, int> GeoKey;   // desc without sens
+typedef std::tuple<int, int, double, int, int, double, int, int, double> GeoKey;   // desc without sens
 
 GeoKey key_of(const pet_geometry_desc &d)
 {
     return GeoKey(d.n, d.nplanes, d.pixel_mm, d.nviews, d.nbins, d.bin_mm, d.nsubsets,
-                  d.subrays > 1 ? d.subrays : 1);
+                  d.subrays > 1 ? d.subrays : 1, d.ring_mm > 0 ? d.ring_mm : 0.0);
 }
 
 size_t geometry_bytes(const pet_geometry_desc &d)

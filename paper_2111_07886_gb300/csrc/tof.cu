@@ -54,7 +54,8 @@ __global__ void __launch_bounds__(256) tof_fwd_kernel(const __grid_constant__ Fw
             const ViewGeo &vw = g.views[slot];
             const RayGeo &rg = g.rays[(size_t)a.slot0 * NB + ray];
             // driving columns whose line point lies within the window of TOF bin t
-            const T r = (T)(2 * b - (NB - 1)) * T(0.5) * (D ? (T)g.rho : (T)(float)g.rho);
+            const T r = g.ring ? (T)g.bins[b].c0
+                               : (T)(2 * b - (NB - 1)) * T(0.5) * (D ? (T)g.rho : (T)(float)g.rho);
             const T tauA = D ? (T)vw.tdr * r + (T)vw.tdc : (T)vw.tdrf * r + (T)vw.tdcf;
             const T tdd = D ? (T)vw.tdd : (T)vw.tddf;
             const T ct = (T)(2 * t - (TT - 1)) * T(0.5) * d;

@@ -691,6 +691,11 @@ int resident_blocks(const void *fn);
 template <int G, int KC>
 static const void *update_fn(int arith, int z3 = 0, int sub = 0, int tof = 0)
 {
+    if (tof && sub) {                            // TOF on ring-sampled bins: KC = 4
+        if (arith == AR_FP32) return (const void *)update_kernel<G, 4, AR_FP32, true, true>;
+        if (arith == AR_KAHAN) return (const void *)update_kernel<G, 4, AR_KAHAN, true, true>;
+        return (const void *)update_kernel<G, 4, AR_FP64, true, true>;
+    }
     if (tof) {                                   // TOF geometries: generic kernel
         if (arith == AR_FP32) return (const void *)update_kernel<G, KC, AR_FP32, false, true>;
         if (arith == AR_KAHAN) return (const void *)update_kernel<G, KC, AR_KAHAN, false, true>;
@@ -720,7 +725,7 @@ void update_shape(UpdateArgs &a, int arith)
 {
     const int TP = 256 / a.g.NG;
     const int ntiles = (a.g.N * a.g.N + TP - 1) / TP;
-    const int sub = a.g.R > 1, tof = a.g.T > 1;
+    const int sub = a.g.table, tof = a.g.T > 1;
     const void *fn = a.g.G == 1 ? (a.g.K <= 2 ? update_fn<1, 2>(arith, 0, sub, tof) : update_fn<1, 4>(arith, 0, sub, tof))
                                 : (a.g.K <= 2 ? update_fn<8, 2>(arith, a.z3 || a.tv || a.vox, sub, tof)
                                               : update_fn<8, 4>(arith, a.z3 || a.tv || a.vox, sub, tof));
@@ -746,13 +751,19 @@ static int persistent_grid(int nvb) { return std::max(1, std::min(nvb, sm_count(
 template <int G, int KC>
 static void update_dispatch(const UpdateArgs &a, const Batch &b, int arith, int grid, cudaStream_t st)
 {
+    if (a.g.T > 1 && a.g.table) {                // TOF on ring-sampled bins: KC = 4
+        if (arith == AR_FP32) update_kernel<G, 4, AR_FP32, true, true><<<grid, 256, 0, st>>>(a, b);
+        else if (arith == AR_KAHAN) update_kernel<G, 4, AR_KAHAN, true, true><<<grid, 256, 0, st>>>(a, b);
+        else update_kernel<G, 4, AR_FP64, true, true><<<grid, 256, 0, st>>>(a, b);
+        return;
+    }
     if (a.g.T > 1) {                             // TOF geometries: generic kernel
         if (arith == AR_FP32) update_kernel<G, KC, AR_FP32, false, true><<<grid, 256, 0, st>>>(a, b);
         else if (arith == AR_KAHAN) update_kernel<G, KC, AR_KAHAN, false, true><<<grid, 256, 0, st>>>(a, b);
         else update_kernel<G, KC, AR_FP64, false, true><<<grid, 256, 0, st>>>(a, b);
         return;
     }
-    if (a.g.R > 1) {                             // sub-ray geometries: KC = 4, generic kernel
+    if (a.g.table) {                             // sub-ray / ring geometries: KC = 4, generic kernel
         if (arith == AR_FP32) update_kernel<G, 4, AR_FP32, true><<<grid, 256, 0, st>>>(a, b);
         else if (arith == AR_KAHAN) update_kernel<G, 4, AR_KAHAN, true><<<grid, 256, 0, st>>>(a, b);
         else update_kernel<G, 4, AR_FP64, true><<<grid, 256, 0, st>>>(a, b);
@@ -805,13 +816,19 @@ pet_status launch_update_batch(const UpdateArgs &shape, const Batch &b, int arit
 template <int G, int KC>
 static void back_dispatch(const BackArgs &a, int arith, int grid, cudaStream_t st)
 {
+    if (a.g.T > 1 && a.g.table) {
+        if (arith == AR_FP32) back_kernel<G, 4, AR_FP32, true, true><<<grid, 256, 0, st>>>(a);
+        else if (arith == AR_KAHAN) back_kernel<G, 4, AR_KAHAN, true, true><<<grid, 256, 0, st>>>(a);
+        else back_kernel<G, 4, AR_FP64, true, true><<<grid, 256, 0, st>>>(a);
+        return;
+    }
     if (a.g.T > 1) {
         if (arith == AR_FP32) back_kernel<G, KC, AR_FP32, false, true><<<grid, 256, 0, st>>>(a);
         else if (arith == AR_KAHAN) back_kernel<G, KC, AR_KAHAN, false, true><<<grid, 256, 0, st>>>(a);
         else back_kernel<G, KC, AR_FP64, false, true><<<grid, 256, 0, st>>>(a);
         return;
     }
-    if (a.g.R > 1) {
+    if (a.g.table) {
         if (arith == AR_FP32) back_kernel<G, 4, AR_FP32, true><<<grid, 256, 0, st>>>(a);
         else if (arith == AR_KAHAN) back_kernel<G, 4, AR_KAHAN, true><<<grid, 256, 0, st>>>(a);
         else back_kernel<G, 4, AR_FP64, true><<<grid, 256, 0, st>>>(a);

@@ -32,7 +32,7 @@ class GeometryDesc(ctypes.Structure):
                 ("nviews", ctypes.c_int), ("nbins", ctypes.c_int), ("bin_mm", ctypes.c_double),
                 ("nsubsets", ctypes.c_int), ("sens", ctypes.c_double), ("subrays", ctypes.c_int),
                 ("tof_bins", ctypes.c_int), ("tof_bin_mm", ctypes.c_double),
-                ("tof_fwhm_mm", ctypes.c_double)]
+                ("tof_fwhm_mm", ctypes.c_double), ("ring_mm", ctypes.c_double)]
 
 
 class Params(ctypes.Structure):
@@ -183,9 +183,9 @@ class Geometry:
     """pet_geometry handle (Sec. II-A/B geometry, subsets, sensitivity)."""
 
     def __init__(self, n, nplanes, pixel_mm, nviews, nbins, bin_mm, nsubsets, sens, stream=None,
-                 subrays=1, tof_bins=0, tof_bin_mm=0.0, tof_fwhm_mm=0.0):
+                 subrays=1, tof_bins=0, tof_bin_mm=0.0, tof_fwhm_mm=0.0, ring_mm=0.0):
         self.desc = GeometryDesc(n, nplanes, pixel_mm, nviews, nbins, bin_mm, nsubsets, sens, subrays,
-                                 tof_bins, tof_bin_mm, tof_fwhm_mm)
+                                 tof_bins, tof_bin_mm, tof_fwhm_mm, ring_mm)
         self.tof_bins = max(1, tof_bins)
         h = _VP()
         _check(lib().pet_geometry_create(ctypes.byref(self.desc), _stream(stream), ctypes.byref(h)))
@@ -197,7 +197,8 @@ class Geometry:
         g = geometry
         return cls(g["n"], g["nplanes"], g["pixel_mm"], g["nviews"], g["nbins"], g["bin_mm"],
                    g["nsubsets"], sens, stream, int(g.get("subrays", 1)), int(g.get("tof_bins", 0)),
-                   float(g.get("tof_bin_mm", 0.0)), float(g.get("tof_fwhm_mm", 0.0)))
+                   float(g.get("tof_bin_mm", 0.0)), float(g.get("tof_fwhm_mm", 0.0)),
+                   float(g.get("ring_mm", 0.0)))
 
     def close(self):
         if getattr(self, "handle", None):
@@ -456,7 +457,8 @@ class Server:
         g = geometry
         desc = GeometryDesc(g["n"], g["nplanes"], g["pixel_mm"], g["nviews"], g["nbins"], g["bin_mm"],
                             g["nsubsets"], sens, int(g.get("subrays", 1)), int(g.get("tof_bins", 0)),
-                            float(g.get("tof_bin_mm", 0.0)), float(g.get("tof_fwhm_mm", 0.0)))
+                            float(g.get("tof_bin_mm", 0.0)), float(g.get("tof_fwhm_mm", 0.0)),
+                            float(g.get("ring_mm", 0.0)))
         counts = np.ascontiguousarray(counts, dtype=np.int32)
         gamma = np.ascontiguousarray(gamma, dtype=np.float32)
         img0 = None if img0 is None else np.ascontiguousarray(img0, dtype=np.float32)
