@@ -9,10 +9,11 @@ Reproduces, with this library's CUDA kernels, the comparisons of Sec. IV-B on 2-
 * ROI NRMSD on the uniform phantom (Fig. 6: 4 hot spheres, 2 cold spheres, a background disk
   and all of them, high count, 24 subsets).
 
-Setup of Sec. IV-A, as far as this library's system model allows: 256 x 256 pixels of 1.17 mm,
-288 views over [0, pi), parallel-beam bins of one pixel (367 bins cover the image diagonal) with
-one line per bin (the paper's 576-detector ring with 32 rays per detector pair is not modelled),
-phantom blurred in image space by a Gaussian PSF of FWHM 6.59 mm before projection, scatter as
+Setup of Sec. IV-A: 256 x 256 pixels of 1.17 mm, 288 views over [0, pi), the bins of a ring of
+576 detectors of 4 mm (radius 366.7 mm) sampled every half detector (2 mm of arc; 155 bins cover
+the 300 mm field of view) with 32 parallel rays across each bin, the same system matrix to
+simulate and to reconstruct, phantom blurred in image space by a Gaussian PSF of FWHM 6.59 mm
+before projection, scatter as
 a heavily smoothed projection scaled to SF = S/(T+S) = 0.25, randoms uniform at
 RF = R/(T+S+R) = 0.25, total counts 6.8e6 (high) / 6.8e5 (low), one Poisson realisation; the
 expected scatter + randoms form the background gamma of the reconstruction.  Uniform water
@@ -45,7 +46,15 @@ from . import pet, synth
 FWHM_MM = 6.59
 SF = RF = 0.25
 N, PIXEL_MM, VIEWS = 256, 1.17, 288
-NBINS = 367                      # odd, >= N sqrt(2): every ray through the image has a bin
+RING_MM = 576 * 4.0 / (2.0 * math.pi)          # 576 detectors of 4 mm
+BIN_MM = math.pi * RING_MM / 576               # half a detector of arc: 2 mm
+NBINS = 155                      # odd; the outermost bins reach Rd sin(77.5 dbeta) = 150.4 mm
+SUBRAYS = 32                     # parallel rays per detector pair
+
+
+def geometry(M: int, sens: float):
+    return pet.Geometry(N, 1, PIXEL_MM, VIEWS, NBINS, BIN_MM, M, sens, subrays=SUBRAYS,
+                        ring_mm=RING_MM)
 
 # Table II (brain column) and the M1 / M2 settings of Sec. IV-B ("Comparison of
 # Preconditioners"), as (precond, overrides); delta_2 = delta_1 throughout (Sec. IV-A).
@@ -98,14 +107,15 @@ def simulate(phantom_planes, seed: int, total_counts: float, device) -> dict:
     f_true = synth.rasterize(phantom_planes, N, PIXEL_MM)[0]
     sigma_px = FWHM_MM / (2.0 * math.sqrt(2.0 * math.log(2.0))) / PIXEL_MM
     blurred = _gauss1d(_gauss1d(f_true, sigma_px, 0), sigma_px, 1)
-    g1 = pet.Geometry(N, 1, PIXEL_MM, VIEWS, NBINS, PIXEL_MM, 1, 1.0)
+    g1 = geometry(1, 1.0)
     d_img = torch.from_numpy(blurred[None].astype(np.float32)).to(device)
     d_proj = torch.empty((1, VIEWS, NBINS), dtype=torch.float32, device=device)
     pet.forward_subset(g1, -1, d_img, d_proj)
     torch.cuda.synchronize()
     g1.close()
     body = [[(cx, cy, a, b, phi, 1.0) for (cx, cy, a, b, phi, _) in pl[:1]] for pl in phantom_planes]
-    mult = np.exp(-MU_WATER_PER_MM * synth.analytic_sinogram(body, VIEWS, NBINS, PIXEL_MM)[0])
+    offs = synth.ring_offsets_mm(NBINS, BIN_MM, RING_MM)
+    mult = np.exp(-MU_WATER_PER_MM * synth.analytic_sinogram(body, VIEWS, NBINS, BIN_MM, offs)[0])
     trues = mult * d_proj.cpu().double().numpy()[0]
     # scatter: the projection smoothed heavily along the bins (FWHM 1/4 of the field), scaled to
     # S = T SF / (1 - SF); randoms uniform, R = (T + S) RF / (1 - RF); all scaled to TC
@@ -187,6 +197,7 @@ def experiment(iterations: int = 60, ref_iterations: int = 1000, seed: int = 0, 
     import torch
     device = device or torch.device("cuda")
     res = {"setup": {"image": [N, N], "pixel_mm": PIXEL_MM, "views": VIEWS, "bins": NBINS,
+                     "ring": f"radius {RING_MM:.1f} mm, {BIN_MM:.2f} mm of arc per bin, {SUBRAYS} rays per bin",
                      "psf_fwhm_mm": FWHM_MM, "SF": SF, "RF": RF, "iterations": iterations,
                      "attenuation": f"water, {MU_WATER_PER_MM} / mm on the body outline",
                      "f_inf": f"BSREM(24), {ref_iterations} iterations", "seed": seed,
@@ -199,11 +210,11 @@ def experiment(iterations: int = 60, ref_iterations: int = 1000, seed: int = 0, 
         d_g = torch.from_numpy(data["gamma"]).to(device)
         d_m = torch.from_numpy(data["mult"]).to(device)
         beta = BETA[level]
-        g24 = pet.Geometry(N, 1, PIXEL_MM, VIEWS, NBINS, PIXEL_MM, 24, data["sens"])
+        g24 = geometry(24, data["sens"])
         f_inf = run(g24, d_c, d_g, params(BRAIN[level][24]["BSREM"], beta, ref_iterations),
                     ref_iterations, device, d_mult=d_m)["image"]
         for M in (12, 24):
-            g = g24 if M == 24 else pet.Geometry(N, 1, PIXEL_MM, VIEWS, NBINS, PIXEL_MM, M, data["sens"])
+            g = g24 if M == 24 else geometry(M, data["sens"])
             curves = {}
             for name, base in BRAIN[level][M].items():
                 curves[name] = run(g, d_c, d_g, params(base, beta, iterations), iterations, device,
@@ -222,7 +233,7 @@ def experiment(iterations: int = 60, ref_iterations: int = 1000, seed: int = 0, 
     d_c = torch.from_numpy(data["counts"]).to(device)
     d_g = torch.from_numpy(data["gamma"]).to(device)
     d_m = torch.from_numpy(data["mult"]).to(device)
-    g24 = pet.Geometry(N, 1, PIXEL_MM, VIEWS, NBINS, PIXEL_MM, 24, data["sens"])
+    g24 = geometry(24, data["sens"])
     f_inf = run(g24, d_c, d_g, params(UNIFORM["BSREM"], BETA["high"], ref_iterations),
                 ref_iterations, device, d_mult=d_m)["image"]
     rois = synth.uniform_phantom_rois(N, PIXEL_MM)

@@ -29,7 +29,7 @@ __all__ = [
     "Workload", "AlgoParams", "config_2d_128", "config_stacked_256x89",
     "mixed_2d_scans", "make_scan", "ellipse_phantom_2d", "ellipsoid_phantom_3d",
     "rasterize", "random_image", "uniform_phantom_2d", "uniform_phantom_rois",
-    "brain_standin_2d", "make_scan_paper", "analytic_tof_sinogram",
+    "brain_standin_2d", "make_scan_paper", "analytic_tof_sinogram", "ring_offsets_mm",
 ]
 
 # Preconditioner kinds (Sec. III: BSREM, momentum-only M1/M2, SDP P1/P2).
@@ -271,14 +271,18 @@ def brain_standin_2d(n: int = 256, pixel_mm: float = 1.17, seed: int = 0):
     return ellipse_phantom_2d(n, pixel_mm, seed)
 
 
-def analytic_sinogram(planes, nviews: int, nbins: int, bin_mm: float) -> np.ndarray:
+def analytic_sinogram(planes, nviews: int, nbins: int, bin_mm: float, offsets_mm=None) -> np.ndarray:
     """Exact line integrals (activity x mm) of the continuous phantom along every ray,
     [P][V][n_b] float64.  For an ellipse with semi-axes (a, b), rotation phi, centre c,
     the chord along {X cos t + Y sin t = r} is 2ab sqrt(D^2 - r'^2) / D^2 with
-    D^2 = a^2 cos^2(t - phi) + b^2 sin^2(t - phi) and r' = r - <c, (cos t, sin t)>."""
+    D^2 = a^2 cos^2(t - phi) + b^2 sin^2(t - phi) and r' = r - <c, (cos t, sin t)>.  The
+    lines sit at r = (b - (n_b - 1)/2) bin_mm, or at ``offsets_mm`` (n_b values) when given."""
     theta = np.arange(nviews) * math.pi / nviews
     ct, st = np.cos(theta)[:, None], np.sin(theta)[:, None]
-    r = ((np.arange(nbins) - (nbins - 1) / 2.0) * bin_mm)[None, :]
+    if offsets_mm is None:
+        r = ((np.arange(nbins) - (nbins - 1) / 2.0) * bin_mm)[None, :]
+    else:
+        r = np.asarray(offsets_mm, np.float64)[None, :]
     out = np.zeros((len(planes), nviews, nbins))
     for p, shapes in enumerate(planes):
         for (cx, cy, a, b, phi, val) in shapes:
@@ -288,6 +292,12 @@ def analytic_sinogram(planes, nviews: int, nbins: int, bin_mm: float) -> np.ndar
             inside = np.clip(d2 - rp * rp, 0.0, None)
             out[p] += val * 2.0 * a * b * np.sqrt(inside) / d2
     return out
+
+
+def ring_offsets_mm(nbins: int, bin_mm: float, ring_mm: float) -> np.ndarray:
+    """Line offsets of a view's bins on a detector ring of radius ``ring_mm`` sampled every
+    ``bin_mm`` of arc: r_b = ring_mm sin((b - (n_b - 1)/2) bin_mm / ring_mm)."""
+    return ring_mm * np.sin((np.arange(nbins) - (nbins - 1) / 2.0) * bin_mm / ring_mm)
 
 
 def analytic_tof_sinogram(planes, nviews: int, nbins: int, bin_mm: float, tof_bins: int,
