@@ -236,8 +236,8 @@ pet_status pet_state_create(const pet_geometry *g, const int32_t *d_counts, cons
  * and p_j of Eq. pj is (A^T a)_j / M for every voxel (1/M where it is 0), computed once at
  * creation by an FP64 backprojection of a.  d_mult: float [P][V][NB] like gamma, finite and
  * >= 0 (PET_ERR_INVALID otherwise), copied into the state.  Objectives of the state
- * (pet_state_objective, the objective history) use diag(a) A.  Such states step alone and in
- * batches; the server does not take them.  Synchronises `stream`. */
+ * (pet_state_objective, the objective history) use diag(a) A.  Such states step alone, in
+ * batches and in the server (pet_request.h_mult).  Synchronises `stream`. */
 pet_status pet_state_create_attn(const pet_geometry *g, const int32_t *d_counts,
                                  const float *d_gamma, const float *d_mult,
                                  const pet_params *params, const float *d_img_init, void *stream,
@@ -361,7 +361,8 @@ pet_status pet_state_objective_history(pet_state *s, double *h_obj, void *stream
  *   arithmetic, gather width), each stepped on its own stream so that the classes advance
  *   independently and overlap on the device; the stacked (multi-plane) class runs at the higher
  *   stream priority.
- * pet_serve_submit: copies the request's host data (validated: counts >= 0, 0 < gamma < inf)
+ * pet_serve_submit: copies the request's host data (validated: counts >= 0, 0 < gamma < inf,
+ *   detection factors when given finite and >= 0)
  *   and returns a ticket; the caller may free its buffers on return.  A request larger than the
  *   whole budget fails with PET_ERR_OOM (reported by poll).
  * pet_serve_poll: PET_PENDING while queued or running; otherwise the request's final status,
@@ -385,6 +386,8 @@ typedef struct {
     const float *h_img_init;     /* [P][N][N], or NULL for f^0 = 1 */
     pet_params params;
     int with_objective;
+    const float *h_mult;         /* [P][V][n_b] per-bin detection factors (pet_state_create_attn),
+                                    finite and >= 0, or NULL for none */
 } pet_request;
 
 typedef struct {

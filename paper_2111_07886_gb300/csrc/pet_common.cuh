@@ -338,8 +338,8 @@ struct SubiterPlan {
 };
 void plan_subiter(pet_state *s, SubiterPlan *pl, bool with_objective);
 pet_status state_create_loaded(const pet_geometry *g, double sens, const int32_t *d_counts,
-                               const float *d_gamma, const float *d_img, const pet_params *p,
-                               cudaStream_t st, pet_state **out);
+                               const float *d_gamma, const float *d_mult, const float *d_img,
+                               const pet_params *p, cudaStream_t st, pet_state **out);
 size_t state_bytes(const pet_geometry *g, int precision, int iterations);
 void state_release(pet_state *s, cudaStream_t st);
 pet_status check_params(const pet_params *p);

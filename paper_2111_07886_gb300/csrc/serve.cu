@@ -45,6 +45,7 @@ struct Request {
     std::vector<int32_t> counts;
     std::vector<float> gamma;
     std::vector<float> img0;                 // empty: f^0 = 1
+    std::vector<float> mult;                 // per-bin detection factors (empty: none)
     pet_params prm{};
     int with_objective = 0;
     double t_submit = 0, t_prep = 0, t_admit = 0, t_join = 0, t_final = 0, t_done = 0;
@@ -87,7 +88,7 @@ size_t geometry_bytes(const pet_geometry_desc &d)
            (size_t)d.n * d.n * 16 + reducer_bytes(4096, 4) + 1024;
 }
 
-size_t request_bytes(const pet_geometry_desc &d, const pet_params &p)
+size_t request_bytes(const pet_geometry_desc &d, const pet_params &p, bool attn = false)
 {
     const size_t G = d.nplanes == 1 ? 1 : 8;
     const size_t Pp = (d.nplanes + G - 1) / G * G;
@@ -95,7 +96,8 @@ size_t request_bytes(const pet_geometry_desc &d, const pet_params &p)
     const size_t maxv = (d.nviews + d.nsubsets - 1) / d.nsubsets;
     return 3 * (size_t)d.n * d.n * Pp * esz + maxv * d.nbins * Pp * esz +
            (size_t)d.nviews * d.nbins * Pp * 8 + reducer_bytes(4096, 2) +
-           (size_t)d.n * d.n * d.nplanes * 4 + (size_t)(p.iterations + 1) * 24 + 4096;
+           (size_t)d.n * d.n * d.nplanes * 4 + (size_t)(p.iterations + 1) * 24 + 4096 +
+           (attn ? (size_t)d.nviews * d.nbins * Pp * 4 + (size_t)d.n * d.n * Pp * esz : 0);
 }
 
 }  // namespace
@@ -196,7 +198,8 @@ static pet_status prepare(pet_server *sv, Request *r)
         r->geom = g;
     }
     const size_t nsino = (size_t)d.nplanes * d.nviews * d.nbins, nimg = (size_t)d.nplanes * d.n * d.n;
-    const size_t need = nsino * 8 + nimg * 4 + 512;
+    const size_t sino_b = (nsino * 4 + 255) / 256 * 256;
+    const size_t need = 3 * sino_b + nimg * 4 + 512;
     if (sv->stage_bytes < need) {
         cudaStreamSynchronize(st);
         cudaFree(sv->d_stage);
@@ -211,12 +214,13 @@ static pet_status prepare(pet_server *sv, Request *r)
     char *base = reinterpret_cast<char *>(sv->d_stage);
     int32_t *dc = reinterpret_cast<int32_t *>(base);
     float *dg = reinterpret_cast<float *>(base + (nsino * 4 + 255) / 256 * 256);
-    float *di = r->img0.empty() ? nullptr
-                                : reinterpret_cast<float *>(base + 2 * ((nsino * 4 + 255) / 256 * 256));
+    float *dm = r->mult.empty() ? nullptr : reinterpret_cast<float *>(base + 2 * sino_b);
+    float *di = r->img0.empty() ? nullptr : reinterpret_cast<float *>(base + 3 * sino_b);
     PET_CUDA(cudaMemcpyAsync(dc, r->counts.data(), nsino * 4, cudaMemcpyHostToDevice, st));
     PET_CUDA(cudaMemcpyAsync(dg, r->gamma.data(), nsino * 4, cudaMemcpyHostToDevice, st));
+    if (dm) PET_CUDA(cudaMemcpyAsync(dm, r->mult.data(), nsino * 4, cudaMemcpyHostToDevice, st));
     if (di) PET_CUDA(cudaMemcpyAsync(di, r->img0.data(), nimg * 4, cudaMemcpyHostToDevice, st));
-    PET_TRY(state_create_loaded(r->geom, d.sens, dc, dg, di, &r->prm, st, &r->state));
+    PET_TRY(state_create_loaded(r->geom, d.sens, dc, dg, dm, di, &r->prm, st, &r->state));
     r->h_img_bytes = nimg * 4;
     r->h_obj_bytes = (size_t)(r->prm.iterations + 1) * 3 * 8;
     r->h_img = reinterpret_cast<float *>(pinned_get(sv, r->h_img_bytes));
@@ -232,6 +236,8 @@ static pet_status prepare(pet_server *sv, Request *r)
     r->gamma.shrink_to_fit();
     r->img0.clear();
     r->img0.shrink_to_fit();
+    r->mult.clear();
+    r->mult.shrink_to_fit();
     return PET_OK;
 }
 
@@ -246,7 +252,7 @@ static void prep_loop(pet_server *sv)
             const int slots = sv->nrunning + (int)sv->ready.size() + sv->preparing;
             if (slots >= sv->max_slots) return false;
             Request *h = sv->queue.front();
-            const size_t need = request_bytes(h->desc, h->prm) +
+            const size_t need = request_bytes(h->desc, h->prm, !h->mult.empty()) +
                                 (sv->geoms.count(key_of(h->desc)) ? 0 : geometry_bytes(h->desc));
             // admit when it fits, or when nothing else holds memory (it then fails or runs alone)
             return sv->used + need <= sv->budget || slots == 0;
@@ -255,14 +261,15 @@ static void prep_loop(pet_server *sv)
         Request *r = sv->queue.front();
         sv->queue.pop_front();
         const bool new_geo = sv->geoms.count(key_of(r->desc)) == 0;
-        const size_t need = request_bytes(r->desc, r->prm) + (new_geo ? geometry_bytes(r->desc) : 0);
+        const size_t need = request_bytes(r->desc, r->prm, !r->mult.empty()) +
+                            (new_geo ? geometry_bytes(r->desc) : 0);
         if (sv->used + need > sv->budget) {
             finish(sv, r, PET_ERR_OOM, "request needs more device memory than the server budget");
             sv->cv.notify_all();
             continue;
         }
         sv->used += need;
-        r->bytes = request_bytes(r->desc, r->prm);      // geometry bytes stay with the cache
+        r->bytes = request_bytes(r->desc, r->prm, !r->mult.empty());   // geometry bytes stay cached
         ++sv->preparing;
         r->t_prep = now_s();
         lk.unlock();
@@ -489,6 +496,10 @@ extern "C" pet_status pet_serve_submit(pet_server *sv, const pet_request *rq, ui
     for (size_t k = 0; k < nsino; ++k)
         if (rq->h_counts[k] < 0 || !(rq->h_gamma[k] > 0.f) || !isfinite(rq->h_gamma[k]))
             return fail(PET_ERR_INVALID, "pet_serve_submit: need counts >= 0 and 0 < gamma < inf");
+    if (rq->h_mult)
+        for (size_t k = 0; k < nsino; ++k)
+            if (!(rq->h_mult[k] >= 0.f) || !isfinite(rq->h_mult[k]))
+                return fail(PET_ERR_INVALID, "pet_serve_submit: need finite detection factors >= 0");
     Request *r = new Request();
     r->desc = d;
     r->prm = rq->params;
@@ -496,6 +507,7 @@ extern "C" pet_status pet_serve_submit(pet_server *sv, const pet_request *rq, ui
     r->counts.assign(rq->h_counts, rq->h_counts + nsino);
     r->gamma.assign(rq->h_gamma, rq->h_gamma + nsino);
     if (rq->h_img_init) r->img0.assign(rq->h_img_init, rq->h_img_init + nimg);
+    if (rq->h_mult) r->mult.assign(rq->h_mult, rq->h_mult + nsino);
     std::lock_guard<std::mutex> lk(sv->mu);
     if (sv->stop) { delete r; return fail(PET_ERR_INVALID, "pet_serve_submit: server stopping"); }
     r->ticket = sv->next_ticket++;

@@ -445,24 +445,26 @@ static int arith_of(int precision)
 // load it from device buffers in the C-ABI layouts (d_img may be NULL: f^0 = 1).  The data were
 // validated by the caller.  sens: this scan's sensitivity (may differ from the geometry's).
 pet_status pet::state_create_loaded(const pet_geometry *g, double sens, const int32_t *d_counts,
-                                    const float *d_gamma, const float *d_img,
+                                    const float *d_gamma, const float *d_mult, const float *d_img,
                                     const pet_params *p, cudaStream_t st, pet_state **out)
 {
     *out = nullptr;
     PET_TRY(check_params(p));
     pet_state *s = new pet_state();
     s->alloc_stream = st;                       // stream-ordered memory: no device-wide syncs
-    pet_status r = state_alloc(s, g, arith_of(p->precision), p->iterations);
+    pet_status r = state_alloc(s, g, arith_of(p->precision), p->iterations, false, d_mult != nullptr);
     if (r == PET_OK) {
         s->sens_ratio = sens / g->desc.sens;
         if (d_img) {
-            r = state_load(s, d_counts, d_gamma, nullptr, p, d_img, st, false);
+            r = state_load(s, d_counts, d_gamma, d_mult, p, d_img, st, false);
         } else {
             // f^0 = 1: fill the internal image, then load data
             s->prm = *p;
             const GeoDev &gd = g->dev;
             r = to_internal_sino(gd, g->d_view_of_slot, 0, gd.V, d_counts, s->counts, 0, 0, st);
             if (r == PET_OK) r = to_internal_sino(gd, g->d_view_of_slot, 0, gd.V, d_gamma, s->gamma, 1, 0, st);
+            s->attn = d_mult != nullptr;
+            if (r == PET_OK && d_mult) r = load_factors(s, d_mult, st);
             if (r == PET_OK) r = fill_internal_ones(gd, s->f[0], s->arith == AR_FP64, st);
             s->cur = 0;
             s->k = s->i = s->J = 0;

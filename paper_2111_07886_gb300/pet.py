@@ -46,7 +46,8 @@ class Params(ctypes.Structure):
 
 class Request(ctypes.Structure):
     _fields_ = [("geom", GeometryDesc), ("h_counts", ctypes.c_void_p), ("h_gamma", ctypes.c_void_p),
-                ("h_img_init", ctypes.c_void_p), ("params", Params), ("with_objective", ctypes.c_int)]
+                ("h_img_init", ctypes.c_void_p), ("params", Params), ("with_objective", ctypes.c_int),
+                ("h_mult", ctypes.c_void_p)]
 
 
 class ServeStats(ctypes.Structure):
@@ -452,7 +453,8 @@ class Server:
         self.shapes = {}
 
     def submit(self, geometry: dict, sens: float, counts, gamma, params: Params, img0=None,
-               with_objective: bool = True) -> int:
+               with_objective: bool = True, mult=None) -> int:
+        """mult: per-bin detection factors ([P][V][n_b] float32, host) or None."""
         import numpy as np
         g = geometry
         desc = GeometryDesc(g["n"], g["nplanes"], g["pixel_mm"], g["nviews"], g["nbins"], g["bin_mm"],
@@ -462,8 +464,10 @@ class Server:
         counts = np.ascontiguousarray(counts, dtype=np.int32)
         gamma = np.ascontiguousarray(gamma, dtype=np.float32)
         img0 = None if img0 is None else np.ascontiguousarray(img0, dtype=np.float32)
+        mult = None if mult is None else np.ascontiguousarray(mult, dtype=np.float32)
         req = Request(desc, counts.ctypes.data, gamma.ctypes.data,
-                      None if img0 is None else img0.ctypes.data, params, 1 if with_objective else 0)
+                      None if img0 is None else img0.ctypes.data, params, 1 if with_objective else 0,
+                      None if mult is None else mult.ctypes.data)
         t = ctypes.c_uint64()
         _check(lib().pet_serve_submit(self.handle, ctypes.byref(req), ctypes.byref(t)))
         self.shapes[t.value] = ((g["nplanes"], g["n"], g["n"]), params.iterations + 1)

@@ -147,3 +147,50 @@ def test_attn_refusals_and_checkpoint():
     c = pet.State(g, counts, gamma, prm, f0, d_mult=to_dev(scan["mult"]))
     c.load(blob)
     assert c.subiters == 1
+
+
+def test_attn_served_equals_alone():
+    """A scan with detection factors served (pet_request.h_mult) beside a plain one gives the
+    bits of the same scan stepped alone, and its objective history is the diag(a) A one."""
+    import time
+    w = _work(48, 1, 30, 69, 5, iters=3, seed=13)
+    scan = synth.make_scan_paper(w)
+    g = pet.Geometry.from_dict(w.geometry(), scan["sens"])
+    counts, gamma = to_dev(scan["counts"], torch.int32), to_dev(scan["gamma"])
+    st = pet.State(g, counts, gamma, pet.make_params(w.params), torch.ones((1, 48, 48), device=DEV),
+                   d_mult=to_dev(scan["mult"]))
+    for _ in range(w.params.iterations * w.nsubsets):
+        st.subiter()
+    want = torch.empty((1, 48, 48), device=DEV)
+    st.read_image(want)
+    torch.cuda.synchronize()
+    og = oracle.geom_from(w.geometry(), scan["sens"])
+    _, obj_ref = oracle.reconstruct(og, scan["counts"], scan["gamma"], w.params, np.ones((1, 48, 48)),
+                                    with_objective=True, mult=scan["mult"])
+    server = pet.Server(hbm_budget_bytes=1 << 30, max_slots=4)
+    t_plain = server.submit(w.geometry(), scan["sens"], scan["counts"], scan["gamma"],
+                            pet.make_params(w.params))
+    t_attn = server.submit(w.geometry(), scan["sens"], scan["counts"], scan["gamma"],
+                           pet.make_params(w.params), mult=scan["mult"])
+    res = {}
+    deadline = time.time() + 120
+    while len(res) < 2 and time.time() < deadline:
+        for t in (t_plain, t_attn):
+            if t not in res:
+                r = server.poll(t)
+                if r is not None:
+                    res[t] = r
+        time.sleep(0.005)
+    server.close()
+    img, obj, _ = res[t_attn]
+    np.testing.assert_array_equal(img, want.cpu().numpy())
+    assert np.max(np.abs(np.array(obj) - obj_ref) / np.abs(obj_ref)) <= 1e-6
+    assert rel_l2(res[t_plain][0], want.cpu().numpy()) > 1e-2
+    bad = scan["mult"].copy()
+    bad[0, 0, 0] = -1.0
+    server = pet.Server(hbm_budget_bytes=1 << 30, max_slots=2)
+    with pytest.raises(pet.PetError) as e:
+        server.submit(w.geometry(), scan["sens"], scan["counts"], scan["gamma"],
+                      pet.make_params(w.params), mult=bad)
+    assert e.value.status == pet.ERR_INVALID
+    server.close()
