@@ -156,9 +156,8 @@ void pet_debug_fail_alloc(int n);
  * (limits: 1 <= n <= 8192, 1 <= nplanes <= 2048, nbins >= 4, 1 <= nsubsets <= nviews,
  * bin_mm >= 0.36 pixel_mm, 0 <= subrays <= 64, 0 <= tof_bins <= 64 (TOF with subrays <= 1),
  * at most 4 bins per view in a pixel's footprint, fewer than 4e9 image or sinogram elements).
- * With TOF bins every sinogram argument and result of the library is [P][V][n_b][T]; TOF
- * scans run through pet_subiter / pet_reconstruct and the single-step calls (not in batches or
- * the server).
+ * With TOF bins every sinogram argument and result of the library is [P][V][n_b][T] (also the
+ * server's request data).
  * ---------------------------------------------------------------------------------------- */
 pet_status pet_geometry_create(const pet_geometry_desc *desc, void *stream, pet_geometry **out);
 void pet_geometry_destroy(pet_geometry *g);

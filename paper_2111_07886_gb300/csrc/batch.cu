@@ -39,6 +39,7 @@ struct BatchClass {
     int z3 = 0;                               // 3-D prior (the generic update and mu kernels)
     int sub = 0;                              // sub-ray geometry (the sub-ray update kernel)
     int vox = 0;                              // detection factors: p per voxel (generic update)
+    int tof = 0;                              // TOF geometries (the TOF projector and gather)
     int cap = 0;                              // scan slots of this class
     std::vector<pet_state *> slot;            // nullptr = empty
     std::vector<bool> objective;              // per slot: plan objectives
@@ -152,10 +153,10 @@ extern "C" void pet_batch_destroy(pet_batch *b)
 static pet_status class_for(pet_batch *b, pet_state *s, BatchClass **out)
 {
     const int G = s->g->dev.G, arith = s->arith, KC = kc_of(s), z3 = s->prm.rdp_3d;
-    const int sub = s->g->dev.table, vox = s->attn ? 1 : 0;
+    const int sub = s->g->dev.table, vox = s->attn ? 1 : 0, tof = s->g->dev.T > 1 ? 1 : 0;
     for (BatchClass *c : b->classes)
         if (c->G == G && c->arith == arith && c->KC == KC && c->z3 == z3 && c->sub == sub &&
-            c->vox == vox) {
+            c->vox == vox && c->tof == tof) {
             *out = c;
             return PET_OK;
         }
@@ -166,6 +167,7 @@ static pet_status class_for(pet_batch *b, pet_state *s, BatchClass **out)
     c->z3 = z3;
     c->sub = sub;
     c->vox = vox;
+    c->tof = tof;
     c->cap = b->capacity;
     c->slot.assign(c->cap, nullptr);
     c->objective.assign(c->cap, false);
@@ -190,8 +192,6 @@ extern "C" pet_status pet_batch_add(pet_batch *b, pet_state *s, int with_objecti
     if (!b || !s) return fail(PET_ERR_INVALID, "pet_batch_add: NULL argument");
     if (s->prm.regularizer == PET_REG_TV)
         return fail(PET_ERR_INVALID, "pet_batch_add: the TV variant runs through pet_subiter / pet_reconstruct");
-    if (s->g->dev.T > 1)
-        return fail(PET_ERR_INVALID, "pet_batch_add: TOF scans run through pet_subiter / pet_reconstruct");
     for (BatchClass *c : b->classes)
         for (pet_state *x : c->slot)
             if (x == s) return fail(PET_ERR_INVALID, "pet_batch_add: state already in the batch");
@@ -279,11 +279,13 @@ static pet_status class_launches(pet_batch *b, BatchClass *c, const BatchClass::
     fs.g.K = c->KC;
     fs.g.R = c->sub ? 2 : 1;                  // selects the sub-ray (table-driven) projector
     fs.g.table = c->sub;
+    fs.g.T = c->tof ? 2 : 1;                  // selects the TOF projector (the count comes per scan)
     UpdateArgs us{};
     us.g.G = c->G;
     us.g.K = c->KC;
     us.g.R = c->sub ? 2 : 1;                  // selects the sub-ray kernel (the count comes per scan)
     us.g.table = c->sub;
+    us.g.T = c->tof ? 2 : 1;                  // selects the TOF gather
     us.z3 = c->z3;
     us.vox = c->vox;
     ImageArgs is{};

@@ -191,6 +191,8 @@ pet_status launch_forward(const FwdArgs &a, int mode, int arith, cudaStream_t st
 void forward_shape(FwdArgs &a, int mode, int arith);      // fills S, R, tpv, nvb
 // time-of-flight geometries (g.T > 1; launch_forward / forward_shape forward to these)
 pet_status launch_forward_tof(const FwdArgs &a, int mode, int arith, cudaStream_t st);
+pet_status launch_forward_tof_batch(const FwdArgs &shape, const Batch &b, int mode, int arith,
+                                    cudaStream_t st);
 void forward_shape_tof(FwdArgs &a, int mode, int arith);
 pet_status launch_forward_batch(const FwdArgs &shape, const Batch &b, int mode, int arith,
                                 cudaStream_t st);

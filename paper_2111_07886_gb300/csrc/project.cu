@@ -436,6 +436,7 @@ pet_status launch_forward(const FwdArgs &a0, int mode, int arith, cudaStream_t s
 pet_status launch_forward_batch(const FwdArgs &shape, const Batch &b, int mode, int arith,
                                 cudaStream_t st)
 {
+    if (shape.g.T > 1) return launch_forward_tof_batch(shape, b, mode, arith, st);
     LaunchScope ls(mode == FWD_RATIO ? PET_K_FORWARD_RATIO
                    : (mode == FWD_OBJECTIVE ? PET_K_OBJ_FORWARD : PET_K_OTHER), st);
     if (shape.g.G == 1) fwd_dispatch<1>(shape, b, mode, arith, b.grid, st);

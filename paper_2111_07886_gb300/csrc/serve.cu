@@ -74,12 +74,17 @@ struct SrvClass {
     std::vector<Request *> running;
 };
 
-typedef std::tuple<int, int, double, int, int, double, int, int, double> GeoKey;   // desc without sens
+// desc without sens
+typedef std::tuple<int, int, double, int, int, double, int, int, double, int, double, double> GeoKey;
+
+static int tof_of(const pet_geometry_desc &d) { return d.tof_bins > 1 ? d.tof_bins : 1; }
 
 GeoKey key_of(const pet_geometry_desc &d)
 {
+    const bool tof = d.tof_bins > 1;
     return GeoKey(d.n, d.nplanes, d.pixel_mm, d.nviews, d.nbins, d.bin_mm, d.nsubsets,
-                  d.subrays > 1 ? d.subrays : 1, d.ring_mm > 0 ? d.ring_mm : 0.0);
+                  d.subrays > 1 ? d.subrays : 1, d.ring_mm > 0 ? d.ring_mm : 0.0, tof_of(d),
+                  tof ? d.tof_bin_mm : 0.0, tof ? d.tof_fwhm_mm : 0.0);
 }
 
 size_t geometry_bytes(const pet_geometry_desc &d)
@@ -94,10 +99,11 @@ size_t request_bytes(const pet_geometry_desc &d, const pet_params &p, bool attn 
     const size_t Pp = (d.nplanes + G - 1) / G * G;
     const size_t esz = p.precision == PET_PREC_FP64 ? 8 : 4;
     const size_t maxv = (d.nviews + d.nsubsets - 1) / d.nsubsets;
-    return 3 * (size_t)d.n * d.n * Pp * esz + maxv * d.nbins * Pp * esz +
-           (size_t)d.nviews * d.nbins * Pp * 8 + reducer_bytes(4096, 2) +
+    const size_t SB = (size_t)d.nbins * tof_of(d);   // sinogram entries per view and plane
+    return 3 * (size_t)d.n * d.n * Pp * esz + maxv * SB * Pp * esz +
+           (size_t)d.nviews * SB * Pp * 8 + reducer_bytes(4096, 2) +
            (size_t)d.n * d.n * d.nplanes * 4 + (size_t)(p.iterations + 1) * 24 + 4096 +
-           (attn ? (size_t)d.nviews * d.nbins * Pp * 4 + (size_t)d.n * d.n * Pp * esz : 0);
+           (attn ? (size_t)d.nviews * SB * Pp * 4 + (size_t)d.n * d.n * Pp * esz : 0);
 }
 
 }  // namespace
@@ -197,7 +203,8 @@ static pet_status prepare(pet_server *sv, Request *r)
         if (sv->autotune > 0) ++sv->tuned;
         r->geom = g;
     }
-    const size_t nsino = (size_t)d.nplanes * d.nviews * d.nbins, nimg = (size_t)d.nplanes * d.n * d.n;
+    const size_t nsino = (size_t)d.nplanes * d.nviews * d.nbins * tof_of(d);
+    const size_t nimg = (size_t)d.nplanes * d.n * d.n;
     const size_t sino_b = (nsino * 4 + 255) / 256 * 256;
     const size_t need = 3 * sino_b + nimg * 4 + 512;
     if (sv->stage_bytes < need) {
@@ -487,12 +494,11 @@ extern "C" pet_status pet_serve_submit(pet_server *sv, const pet_request *rq, ui
         d.nsubsets > d.nviews || !(d.pixel_mm > 0) || !(d.bin_mm > 0) || !(d.sens > 0) ||
         d.subrays < 0 || d.subrays > 64)
         return fail(PET_ERR_INVALID, "pet_serve_submit: invalid geometry description");
-    if (d.tof_bins > 1)
-        return fail(PET_ERR_INVALID, "pet_serve_submit: TOF scans run through pet_reconstruct");
     PET_TRY(check_params(&rq->params));
     if (rq->params.regularizer == PET_REG_TV)
         return fail(PET_ERR_INVALID, "pet_serve_submit: the TV variant runs through pet_reconstruct");
-    const size_t nsino = (size_t)d.nplanes * d.nviews * d.nbins, nimg = (size_t)d.nplanes * d.n * d.n;
+    const size_t nsino = (size_t)d.nplanes * d.nviews * d.nbins * tof_of(d);
+    const size_t nimg = (size_t)d.nplanes * d.n * d.n;
     for (size_t k = 0; k < nsino; ++k)
         if (rq->h_counts[k] < 0 || !(rq->h_gamma[k] > 0.f) || !isfinite(rq->h_gamma[k]))
             return fail(PET_ERR_INVALID, "pet_serve_submit: need counts >= 0 and 0 < gamma < inf");

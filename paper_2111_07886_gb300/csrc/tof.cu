@@ -5,7 +5,8 @@
 // the ray where h_t can be non-zero (|tau - tau_t| <= the kernel's window), with the same
 // column-by-column walk and exact lengths as the non-TOF projector, each length weighted by h_t
 // at its pixel's centre.  Epilogues as in fwd_kernel: plain, ratio (with the per-bin detection
-// factors), or the objective's FP64 sums.  Outputs are [nviews][NB][T][Pp].  Single scans only.
+// factors), or the objective's FP64 sums.  Outputs are [nviews][NB][T][Pp].  One scan, or a batch
+// of TOF scans (per-scan arguments and virtual blocks, as in fwd_kernel).
 #include "kernels.cuh"
 #include "profile.cuh"
 
@@ -18,33 +19,48 @@ namespace pet {
 constexpr int TOF_TAB = 2048;
 
 template <int G, int AR, int MODE>
-__global__ void __launch_bounds__(256) tof_fwd_kernel(const __grid_constant__ FwdArgs a)
+__global__ void __launch_bounds__(256) tof_fwd_kernel(const __grid_constant__ FwdArgs one,
+                                                      const Batch bt)
 {
     using T = typename ArithT<AR>::T;
     constexpr bool D = AR == AR_FP64;
-    const GeoDev &g = a.g;
-    const int NG = g.NG, NB = g.NB, N = g.N, Pp = g.Pp, TT = g.T;
-    const long long items = (long long)a.nviews * NB * TT * NG;
-    const T d = D ? (T)g.tof_d : (T)g.tof_df, kk = D ? (T)g.tof_k : (T)g.tof_kf;
-    const T W = (D ? (T)g.tof_w : (T)g.tof_wf) + T(1);   // + 1: pixel centres vs the line
     __shared__ float2 tab[D ? 1 : TOF_TAB];
-    const float Wt = g.tof_wf, dt_ = (2.f * Wt) / (float)(TOF_TAB - 1), idt = 1.f / dt_;
-    if constexpr (!D) {
-        const float k = g.tof_kf, hd = 0.5f * g.tof_df;
-        const float dphi = 1.1283791670955126f * k;   // d/du of erfc(x k) / 2 = -k e^{-x^2 k^2} / sqrt(pi)
-        for (int i = threadIdx.x; i < TOF_TAB; i += blockDim.x) {
-            const float u = -Wt + (float)i * dt_;
-            const float z0 = (-hd - u) * k, z1 = (hd - u) * k;
-            // h(u) = Phi(sqrt2 z1) - Phi(sqrt2 z0); h'(u) = k / sqrt(pi) (e^{-z0^2} - e^{-z1^2})
-            tab[i] = make_float2(tof_h<float>(z0, z1),
-                                 0.5f * dphi * (expf(-z0 * z0) - expf(-z1 * z1)));
+    __shared__ float tab_key[3];                       // the TOF kernel the table holds
+    __shared__ FwdArgs sh_args;
+    if (threadIdx.x == 0) tab_key[0] = tab_key[1] = tab_key[2] = -1.f;
+    __syncthreads();
+    const int total = total_vblocks(one, bt);
+    for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
+        int vloc, nv;
+        const FwdArgs &a = scan_args(one, bt, vb, vloc, nv, sh_args);
+        const GeoDev &g = a.g;
+        const int NG = g.NG, NB = g.NB, N = g.N, Pp = g.Pp, TT = g.T;
+        const long long items = (long long)a.nviews * NB * TT * NG;
+        const T d = D ? (T)g.tof_d : (T)g.tof_df, kk = D ? (T)g.tof_k : (T)g.tof_kf;
+        const T W = (D ? (T)g.tof_w : (T)g.tof_wf) + T(1);   // + 1: pixel centres vs the line
+        const float Wt = g.tof_wf, dt_ = (2.f * Wt) / (float)(TOF_TAB - 1), idt = 1.f / dt_;
+        if constexpr (!D) {
+            // (re)build the table when this scan's kernel differs from the one it holds
+            // (block-uniform: every thread reads the same arguments)
+            if (tab_key[0] != g.tof_df || tab_key[1] != g.tof_kf || tab_key[2] != g.tof_wf) {
+                __syncthreads();
+                const float k = g.tof_kf, hd = 0.5f * g.tof_df;
+                const float dphi = 1.1283791670955126f * k;   // 2 k / sqrt(pi)
+                for (int i = threadIdx.x; i < TOF_TAB; i += blockDim.x) {
+                    const float u = -Wt + (float)i * dt_;
+                    const float z0 = (-hd - u) * k, z1 = (hd - u) * k;
+                    // h(u) = Phi(sqrt2 z1) - Phi(sqrt2 z0); h'(u) = k / sqrt(pi) (e^{-z0^2} - e^{-z1^2})
+                    tab[i] = make_float2(tof_h<float>(z0, z1),
+                                         0.5f * dphi * (expf(-z0 * z0) - expf(-z1 * z1)));
+                }
+                __syncthreads();
+                if (threadIdx.x == 0) { tab_key[0] = g.tof_df; tab_key[1] = g.tof_kf; tab_key[2] = g.tof_wf; }
+                __syncthreads();
+            }
         }
-        __syncthreads();
-    }
-    for (int vb = blockIdx.x; vb < a.nvb; vb += gridDim.x) {
         double obj[2] = {0.0, 0.0};
         for (int k = 0; k < a.tpv; ++k) {
-            const long long it = ((long long)vb * a.tpv + k) * 256 + threadIdx.x;
+            const long long it = ((long long)vloc * a.tpv + k) * 256 + threadIdx.x;
             if (it >= items) continue;
             const int grp = (int)(it % NG);
             const long long rt = it / NG;
@@ -166,7 +182,7 @@ __global__ void __launch_bounds__(256) tof_fwd_kernel(const __grid_constant__ Fw
                 }
             }
         }
-        if constexpr (MODE == FWD_OBJECTIVE) grid_reduce<2>(obj, a.red, a.result, vb, a.nvb);
+        if constexpr (MODE == FWD_OBJECTIVE) grid_reduce<2>(obj, a.red, a.result, vloc, nv);
     }
 }
 
@@ -206,19 +222,19 @@ void forward_shape_tof(FwdArgs &a, int mode, int arith)
 }
 
 template <int G, int AR>
-static void tof_launch_mode(const FwdArgs &a, int mode, int grid, cudaStream_t st)
+static void tof_launch_mode(const FwdArgs &a, const Batch &b, int mode, int grid, cudaStream_t st)
 {
-    if (mode == FWD_PLAIN) tof_fwd_kernel<G, AR, FWD_PLAIN><<<grid, 256, 0, st>>>(a);
-    else if (mode == FWD_RATIO) tof_fwd_kernel<G, AR, FWD_RATIO><<<grid, 256, 0, st>>>(a);
-    else tof_fwd_kernel<G, AR, FWD_OBJECTIVE><<<grid, 256, 0, st>>>(a);
+    if (mode == FWD_PLAIN) tof_fwd_kernel<G, AR, FWD_PLAIN><<<grid, 256, 0, st>>>(a, b);
+    else if (mode == FWD_RATIO) tof_fwd_kernel<G, AR, FWD_RATIO><<<grid, 256, 0, st>>>(a, b);
+    else tof_fwd_kernel<G, AR, FWD_OBJECTIVE><<<grid, 256, 0, st>>>(a, b);
 }
 
 template <int G>
-static void tof_launch(const FwdArgs &a, int mode, int arith, int grid, cudaStream_t st)
+static void tof_launch(const FwdArgs &a, const Batch &b, int mode, int arith, int grid, cudaStream_t st)
 {
-    if (arith == AR_FP64) tof_launch_mode<G, AR_FP64>(a, mode, grid, st);
-    else if (arith == AR_FP32) tof_launch_mode<G, AR_FP32>(a, mode, grid, st);
-    else tof_launch_mode<G, AR_KAHAN>(a, mode, grid, st);
+    if (arith == AR_FP64) tof_launch_mode<G, AR_FP64>(a, b, mode, grid, st);
+    else if (arith == AR_FP32) tof_launch_mode<G, AR_FP32>(a, b, mode, grid, st);
+    else tof_launch_mode<G, AR_KAHAN>(a, b, mode, grid, st);
 }
 
 pet_status launch_forward_tof(const FwdArgs &a0, int mode, int arith, cudaStream_t st)
@@ -229,10 +245,24 @@ pet_status launch_forward_tof(const FwdArgs &a0, int mode, int arith, cudaStream
     const int grid = std::max(1, std::min(a.nvb, sm_count() * 8));
     LaunchScope ls(mode == FWD_RATIO ? PET_K_FORWARD_RATIO
                    : (mode == FWD_OBJECTIVE ? PET_K_OBJ_FORWARD : PET_K_OTHER), st);
-    if (a.g.G == 1) tof_launch<1>(a, mode, arith, grid, st);
-    else tof_launch<8>(a, mode, arith, grid, st);
+    const Batch b{nullptr, nullptr, 0, grid};
+    if (a.g.G == 1) tof_launch<1>(a, b, mode, arith, grid, st);
+    else tof_launch<8>(a, b, mode, arith, grid, st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "tof_fwd_kernel launch");
+    return PET_OK;
+}
+
+// Batched launch: every scan of the batch has TOF bins and the plane-group size of `shape`.
+pet_status launch_forward_tof_batch(const FwdArgs &shape, const Batch &b, int mode, int arith,
+                                    cudaStream_t st)
+{
+    LaunchScope ls(mode == FWD_RATIO ? PET_K_FORWARD_RATIO
+                   : (mode == FWD_OBJECTIVE ? PET_K_OBJ_FORWARD : PET_K_OTHER), st);
+    if (shape.g.G == 1) tof_launch<1>(shape, b, mode, arith, b.grid, st);
+    else tof_launch<8>(shape, b, mode, arith, b.grid, st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "tof_fwd_kernel batch launch");
     return PET_OK;
 }
 

@@ -115,10 +115,12 @@ def test_tof_subiterations(N, P, kind):
             st.close()
 
 
-def test_tof_reconstruction_and_refusals():
+def test_tof_reconstruction_batch_serve_and_refusals():
     """64^2, 10 iterations of SDP-P2 with 21 TOF bins: image relL2 <= 1e-4 and the objective
-    history within 1e-6 of the oracle; batches and the server refuse TOF scans; TOF with
-    sub-rays is refused."""
+    history within 1e-6 of the oracle; in a graph-replayed batch beside a TOF scan of another
+    timing resolution, and through the server, it gives its bits alone; TOF with sub-rays is
+    refused."""
+    import time
     w = synth.Workload("tof64", 64, 1, 4.0, 60, 91, 4.0, 6, 1e6, "ellipses2d",
                        synth.AlgoParams(iterations=10, beta=0.5), seed=9, tof_bins=21,
                        tof_bin_mm=18.0, tof_fwhm_mm=50.0)
@@ -135,16 +137,53 @@ def test_tof_reconstruction_and_refusals():
     gap = np.max(np.abs(np.array(obj) - obj_ref) / np.abs(obj_ref))
     assert gap <= 1e-6, gap
     assert obj_ref[-1] < obj_ref[0]
-    st = pet.State(g, counts, gamma, pet.make_params(w.params), torch.ones((1, 64, 64), device=DEV))
-    batch = pet.Batch(capacity=2)
-    with pytest.raises(pet.PetError) as e:
-        batch.add(st)
-    assert e.value.status == pet.ERR_INVALID
+    # alone, subiteration by subiteration (the bits batches and the server must give)
+    w2 = synth.Workload("tof64b", 64, 1, 4.0, 60, 91, 4.0, 6, 1e6, "ellipses2d",
+                        synth.AlgoParams(iterations=10, beta=0.5), seed=10, tof_bins=15,
+                        tof_bin_mm=25.0, tof_fwhm_mm=70.0)
+    scan2 = synth.make_scan(w2)
+    runs = [(w, scan), (w2, scan2)]
+    alone, states = [], []
+    for ww, sc in runs:
+        gg = pet.Geometry.from_dict(ww.geometry(), sc["sens"])
+        c, gm = to_dev(sc["counts"], torch.int32), to_dev(sc["gamma"])
+        st = pet.State(gg, c, gm, pet.make_params(ww.params), torch.ones((1, 64, 64), device=DEV))
+        for _ in range(ww.params.iterations * ww.nsubsets):
+            st.subiter()
+        out = torch.empty((1, 64, 64), device=DEV)
+        st.read_image(out)
+        torch.cuda.synchronize()
+        alone.append(out.cpu().numpy())
+        states.append((gg, pet.State(gg, c, gm, pet.make_params(ww.params),
+                                     torch.ones((1, 64, 64), device=DEV))))
+    stream = torch.cuda.Stream()
+    batch = pet.Batch(capacity=2, use_graph=True)
+    for gg, st in states:
+        batch.add(st, with_objective=True, stream=stream)
+    while batch.step(stream=stream) > 0:
+        pass
+    stream.synchronize()
+    for (gg, st), want in zip(states, alone):
+        out = torch.empty((1, 64, 64), device=DEV)
+        st.read_image(out)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(out.cpu().numpy(), want)
     server = pet.Server(hbm_budget_bytes=1 << 30, max_slots=2)
-    with pytest.raises(pet.PetError) as e:
-        server.submit(w.geometry(), scan["sens"], scan["counts"], scan["gamma"], pet.make_params(w.params))
-    assert e.value.status == pet.ERR_INVALID
+    tickets = [server.submit(ww.geometry(), sc["sens"], sc["counts"], sc["gamma"],
+                             pet.make_params(ww.params)) for ww, sc in runs]
+    res = {}
+    deadline = time.time() + 120
+    while len(res) < 2 and time.time() < deadline:
+        for t in tickets:
+            if t not in res:
+                r = server.poll(t)
+                if r is not None:
+                    res[t] = r
+        time.sleep(0.005)
     server.close()
+    for t, want in zip(tickets, alone):
+        np.testing.assert_array_equal(res[t][0], want)
+    assert np.max(np.abs(np.array(res[tickets[0]][1]) - obj_ref) / np.abs(obj_ref)) <= 1e-6
     with pytest.raises(pet.PetError) as e:
         pet.Geometry(32, 1, 4.0, 20, 47, 4.0, 4, 1.0, subrays=4, tof_bins=9, tof_bin_mm=20.0,
                      tof_fwhm_mm=40.0)
