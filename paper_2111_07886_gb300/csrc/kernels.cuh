@@ -203,6 +203,14 @@ __device__ __forceinline__ f2x vrsqrt(f2x a)
     return vpk(x, y);
 }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream serialization may
+// start before the previous kernel of its stream has finished; grid_dependency_wait() blocks
+// until that kernel has completed and its memory operations are visible (a no-op for a kernel
+// launched without the attribute).  grid_dependents_launch() lets such a dependent kernel be
+// scheduled before this one completes.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dependents_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // one 8-plane FP32 group (32-byte aligned) as four pairs, through the read-only path
 __device__ __forceinline__ void load8x(const float *__restrict__ p, f2x (&v)[4])
 {

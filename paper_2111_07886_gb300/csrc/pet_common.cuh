@@ -187,7 +187,12 @@ struct FwdArgs {
 enum FwdMode { FWD_PLAIN = 0, FWD_RATIO = 1, FWD_OBJECTIVE = 2 };
 enum Arith { AR_FP32 = 0, AR_KAHAN = 1, AR_FP64 = 2 };
 
-pet_status launch_forward(const FwdArgs &a, int mode, int arith, cudaStream_t st);
+// after_kernel: the launch directly follows a kernel of the same stream that produces the
+// image (a subiteration's update); the projection is then launched with programmatic stream
+// serialization, so that its blocks are scheduled while that kernel's last blocks finish and
+// wait (griddepcontrol.wait) for its completion before their first memory access.
+pet_status launch_forward(const FwdArgs &a, int mode, int arith, cudaStream_t st,
+                          bool after_kernel = false);
 void forward_shape(FwdArgs &a, int mode, int arith);      // fills S, R, tpv, nvb
 // time-of-flight geometries (g.T > 1; launch_forward / forward_shape forward to these)
 pet_status launch_forward_tof(const FwdArgs &a, int mode, int arith, cudaStream_t st);

@@ -35,6 +35,7 @@ namespace pet {
 template <int G, int AR, int MODE, bool SUB = false>
 __global__ void __launch_bounds__(256, 3) fwd_kernel(const __grid_constant__ FwdArgs one, const Batch bt)
 {
+    grid_dependency_wait();                      // before any memory access
     using T = typename ArithT<AR>::T;
     __shared__ T comb_s[256 * G];
     __shared__ T comb_e[256 * G];
@@ -310,27 +311,51 @@ __global__ void __launch_bounds__(256, 3) fwd_kernel(const __grid_constant__ Fwd
     }
 }
 
-template <int G, int AR>
-static void fwd_dispatch_mode(const FwdArgs &a, const Batch &b, int mode, int grid, cudaStream_t st)
+// One launch of a forward-projection instantiation; `pdl`: with programmatic stream
+// serialization (the kernel waits for the previous kernel of the stream before its first
+// memory access).
+template <typename K>
+static void fwd_launch(K kernel, int grid, cudaStream_t st, bool pdl, const FwdArgs &a, const Batch &b)
 {
-    if (a.g.table) {
-        if (mode == FWD_PLAIN) fwd_kernel<G, AR, FWD_PLAIN, true><<<grid, 256, 0, st>>>(a, b);
-        else if (mode == FWD_RATIO) fwd_kernel<G, AR, FWD_RATIO, true><<<grid, 256, 0, st>>>(a, b);
-        else fwd_kernel<G, AR, FWD_OBJECTIVE, true><<<grid, 256, 0, st>>>(a, b);
+    if (!pdl) {
+        kernel<<<grid, 256, 0, st>>>(a, b);
         return;
     }
-    if (mode == FWD_PLAIN) fwd_kernel<G, AR, FWD_PLAIN><<<grid, 256, 0, st>>>(a, b);
-    else if (mode == FWD_RATIO) fwd_kernel<G, AR, FWD_RATIO><<<grid, 256, 0, st>>>(a, b);
-    else fwd_kernel<G, AR, FWD_OBJECTIVE><<<grid, 256, 0, st>>>(a, b);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, a, b);
+}
+
+template <int G, int AR>
+static void fwd_dispatch_mode(const FwdArgs &a, const Batch &b, int mode, int grid, cudaStream_t st,
+                              bool pdl)
+{
+    if (a.g.table) {
+        if (mode == FWD_PLAIN) fwd_launch(fwd_kernel<G, AR, FWD_PLAIN, true>, grid, st, pdl, a, b);
+        else if (mode == FWD_RATIO) fwd_launch(fwd_kernel<G, AR, FWD_RATIO, true>, grid, st, pdl, a, b);
+        else fwd_launch(fwd_kernel<G, AR, FWD_OBJECTIVE, true>, grid, st, pdl, a, b);
+        return;
+    }
+    if (mode == FWD_PLAIN) fwd_launch(fwd_kernel<G, AR, FWD_PLAIN>, grid, st, pdl, a, b);
+    else if (mode == FWD_RATIO) fwd_launch(fwd_kernel<G, AR, FWD_RATIO>, grid, st, pdl, a, b);
+    else fwd_launch(fwd_kernel<G, AR, FWD_OBJECTIVE>, grid, st, pdl, a, b);
 }
 
 template <int G>
 static void fwd_dispatch(const FwdArgs &a, const Batch &b, int mode, int arith, int grid,
-                         cudaStream_t st)
+                         cudaStream_t st, bool pdl = false)
 {
-    if (arith == AR_FP32) fwd_dispatch_mode<G, AR_FP32>(a, b, mode, grid, st);
-    else if (arith == AR_KAHAN) fwd_dispatch_mode<G, AR_KAHAN>(a, b, mode, grid, st);
-    else fwd_dispatch_mode<G, AR_FP64>(a, b, mode, grid, st);
+    if (arith == AR_FP32) fwd_dispatch_mode<G, AR_FP32>(a, b, mode, grid, st, pdl);
+    else if (arith == AR_KAHAN) fwd_dispatch_mode<G, AR_KAHAN>(a, b, mode, grid, st, pdl);
+    else fwd_dispatch_mode<G, AR_FP64>(a, b, mode, grid, st, pdl);
 }
 
 template <int G, int AR>
@@ -414,7 +439,8 @@ void forward_shape(FwdArgs &a, int mode, int arith)
     a.nvb = (int)((ntiles + a.tpv - 1) / a.tpv);
 }
 
-pet_status launch_forward(const FwdArgs &a0, int mode, int arith, cudaStream_t st)
+pet_status launch_forward(const FwdArgs &a0, int mode, int arith, cudaStream_t st,
+                          bool after_kernel)
 {
     if (a0.g.T > 1) return launch_forward_tof(a0, mode, arith, st);
     FwdArgs a = a0;
@@ -425,8 +451,8 @@ pet_status launch_forward(const FwdArgs &a0, int mode, int arith, cudaStream_t s
     Batch b{nullptr, nullptr, 0, grid};
     LaunchScope ls(mode == FWD_RATIO ? PET_K_FORWARD_RATIO
                    : (mode == FWD_OBJECTIVE ? PET_K_OBJ_FORWARD : PET_K_OTHER), st);
-    if (a.g.G == 1) fwd_dispatch<1>(a, b, mode, arith, grid, st);
-    else fwd_dispatch<8>(a, b, mode, arith, grid, st);
+    if (a.g.G == 1) fwd_dispatch<1>(a, b, mode, arith, grid, st, after_kernel);
+    else fwd_dispatch<8>(a, b, mode, arith, grid, st, after_kernel);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "fwd_kernel launch");
     return PET_OK;

@@ -392,7 +392,9 @@ static pet_status state_subiter(pet_state *s, cudaStream_t st)
         PET_TRY(launch_mu_sum(pl.mu_args, pl.arith, s->side));
         PET_CUDA(cudaEventRecord(s->ev_join, s->side));
     }
-    PET_TRY(launch_forward(pl.fwd, FWD_RATIO, pl.arith, st));
+    // the projection follows the previous subiteration's update on `st` (or the host's own
+    // work, where the launch attribute has no effect): see launch_forward
+    PET_TRY(launch_forward(pl.fwd, FWD_RATIO, pl.arith, st, true));
     if (pl.mu) PET_CUDA(cudaStreamWaitEvent(st, s->ev_join, 0));
     PET_TRY(launch_update(pl.upd, pl.arith, st));
     return tv_step(pl, st);

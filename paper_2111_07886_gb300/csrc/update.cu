@@ -218,6 +218,7 @@ __global__ void __launch_bounds__(256, G == 1 ? UPDATE_G1_BLOCKS : 3) update_ker
 {
     using T = typename ArithT<AR>::T;
     __shared__ BpTable<KC, AR> tb;
+    grid_dependents_launch();                    // as in update_kernel_x8
     const int total = total_vblocks(one, bt);
     __shared__ UpdateArgs sh_args;
     for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
@@ -345,6 +346,9 @@ __global__ void __launch_bounds__(256, UPDATE_X8_BLOCKS) update_kernel_x8(
     // 16 KB of (pixel, view) entries: the rest of the SM's shared memory stays L1 for the gather
     using Table = BpTable<KC, AR, 1024 / (KC > 2 ? 2 : 1)>;
     __shared__ Table tb;
+    // the next subiteration's projection (launched after this kernel with programmatic stream
+    // serialization) may be scheduled as this kernel's blocks retire; it waits for completion
+    grid_dependents_launch();
     const int total = total_vblocks(one, bt);
     __shared__ UpdateArgs sh_args;
     for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
