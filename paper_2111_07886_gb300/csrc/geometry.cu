@@ -334,6 +334,7 @@ static pet_status geometry_init(pet_geometry *g, cudaStream_t st)
         if (e != cudaSuccess) s = cuda_fail(e, "finish_sensitivity");
     }
     cudaFreeAsync(bp, st);
+    if (s == PET_OK) s = build_bp_table(g, st);
     cudaError_t e = cudaStreamSynchronize(st);
     if (s != PET_OK) return s;
     if (e != cudaSuccess) return cuda_fail(e, "pet_geometry_create");
@@ -400,6 +401,7 @@ extern "C" void pet_geometry_destroy(pet_geometry *g)
     cudaFree(g->d_scratch);
     cudaFree(g->red.partials);
     cudaFree(g->d_sums);
+    cudaFree(g->d_bptab);
     delete g;
 }
 

@@ -211,6 +211,16 @@ __device__ __forceinline__ f2x vrsqrt(f2x a)
 __device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void grid_dependents_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
+// 16-byte asynchronous copy global -> shared (cp.async, cached in L2 only), its commit and the
+// wait for all of this thread's copies
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // one 8-plane FP32 group (32-byte aligned) as four pairs, through the read-only path
 __device__ __forceinline__ void load8x(const float *__restrict__ p, f2x (&v)[4])
 {

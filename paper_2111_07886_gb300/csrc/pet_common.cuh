@@ -154,6 +154,11 @@ struct pet_geometry {
     pet::Reducer red{};
     double *d_sums = nullptr;       // small FP64 scalar area
     void *workspace = nullptr;      // reconstruction workspace reused by pet_reconstruct*
+    // precomputed (pixel, view) backprojection entries of the packed update kernel (8-plane
+    // groups, uniform bins, no TOF): per subset, [pixel tile][view][pixel of the tile], the
+    // kernel's shared-memory order; nullptr: the kernel computes them per tile
+    void *d_bptab = nullptr;
+    std::vector<size_t> bptab_off;  // byte offset of each subset's block
 };
 
 namespace pet {
@@ -220,6 +225,8 @@ struct UpdateArgs {
     void *fout;                // f^{k,i}
     const void *invp;          // [N*N], or [N*N][Pp] when vox (float or double)
     int vox;                   // 1: p differs per voxel (a scan with per-bin detection factors)
+    const void *bptab;         // the subset's precomputed (pixel, view) entries (pet_geometry::
+                               // d_bptab), or NULL: computed in the kernel
     double invp_scale;         // multiplies invp (a scan whose sens differs from the geometry's)
     void *nu_frozen;           // [N*N][Pp]
     int nu_mode;               // 0: nu = 1, 1: from f, 2: from f and stored, 3: frozen
@@ -245,6 +252,11 @@ void update_shape(UpdateArgs &a, int arith);               // fills tpv, nvb
 GeoDev update_geo(const GeoDev &g);                        // plane grouping of the update kernel
 pet_status launch_update_batch(const UpdateArgs &shape, const Batch &b, int arith,
                                cudaStream_t st);
+// the geometry's precomputed backprojection entries (d_bptab; left empty where the packed
+// update kernel does not run or a subset's views do not fit its table), and an upper bound
+// of their size from the description alone (memory accounting before creation)
+pet_status build_bp_table(pet_geometry *g, cudaStream_t st);
+size_t bp_table_bytes_bound(const pet_geometry_desc &d);
 
 struct ImageArgs {
     GeoDev g;

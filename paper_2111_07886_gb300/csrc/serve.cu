@@ -90,7 +90,7 @@ GeoKey key_of(const pet_geometry_desc &d)
 size_t geometry_bytes(const pet_geometry_desc &d)
 {
     return (size_t)d.nviews * (sizeof(ViewGeo) + sizeof(RayGeo) * d.nbins + sizeof(int)) +
-           (size_t)d.n * d.n * 16 + reducer_bytes(4096, 4) + 1024;
+           (size_t)d.n * d.n * 16 + reducer_bytes(4096, 4) + 1024 + bp_table_bytes_bound(d);
 }
 
 size_t request_bytes(const pet_geometry_desc &d, const pet_params &p, bool attn = false)

@@ -308,6 +308,9 @@ void pet::plan_subiter(pet_state *s, SubiterPlan *pl, bool with_objective)
     ua.invp = s->attn ? (const void *)s->invp_vox
                       : (s->arith == AR_FP64 ? (const void *)g->d_invp64 : (const void *)g->d_invp);
     ua.vox = s->attn ? 1 : 0;
+    ua.bptab = g->d_bptab && s->arith != AR_FP64 ? static_cast<const char *>(g->d_bptab) +
+                                                       g->bptab_off[s->i]
+                                                 : nullptr;
     ua.invp_scale = 1.0 / s->sens_ratio;
     ua.nu_frozen = s->nu_frozen;
     ua.nu_mode = nu_mode;

@@ -372,10 +372,21 @@ __global__ void __launch_bounds__(256, UPDATE_X8_BLOCKS) update_kernel_x8(
         const float *w = reinterpret_cast<const float *>(a.w) + grp * 8;
         const float *invp = reinterpret_cast<const float *>(a.invp);
         const int ntiles = (npix + TP - 1) / TP;
+        // the subset's precomputed entries (one contiguous block per tile) when its views fit
+        // the table: copied with cp.async while the stencil runs
+        const char *ptab = (a.bptab && a.nviews <= VC) ? static_cast<const char *>(a.bptab) : nullptr;
+        const int tbytes = a.nviews * TP * (int)sizeof(typename Table::E);
         float part = 0.f;
         for (int tile = vloc * a.tpv; tile < min(ntiles, (vloc + 1) * a.tpv); ++tile) {
             const int j0 = tile * TP, j = j0 + pl;
             const bool active = pl < TP && j < npix;
+            if (ptab) {
+                __syncthreads();                 // the previous tile's gather is done with tb
+                const char *src = ptab + (size_t)tile * tbytes;
+                for (int o = threadIdx.x * 16; o < tbytes; o += 256 * 16)
+                    cp_async16(reinterpret_cast<char *>(tb.e) + o, src + o);
+                cp_async_commit();
+            }
             f2x A[4], B[4];
             if (active) {
                 const int ix = j % N, iy = j / N;
@@ -466,9 +477,14 @@ __global__ void __launch_bounds__(256, UPDATE_X8_BLOCKS) update_kernel_x8(
             for (int k = 0; k < 4; ++k) { sm[k] = 0ull; er[k] = 0ull; }
             for (int u0 = 0; u0 < a.nviews; u0 += VC) {
                 const int nvc = min(VC, a.nviews - u0);
-                __syncthreads();
-                bp_fill<KC, AR>(g, a.slot0, u0, nvc, j0, TP, tb);
-                __syncthreads();
+                if (ptab) {
+                    cp_async_wait_all();
+                    __syncthreads();
+                } else {
+                    __syncthreads();
+                    bp_fill<KC, AR>(g, a.slot0, u0, nvc, j0, TP, tb);
+                    __syncthreads();
+                }
                 if (!active) continue;
                 for (int uu = 0; uu < nvc; ++uu) {
                     const typename Table::E ent = tb.e[uu * TP + pl];
@@ -725,6 +741,76 @@ static const void *update_fn(int arith, int z3 = 0, int sub = 0, int tof = 0)
 // Pixel tiles per virtual block: each virtual block ends in a block reduction and a grid-wide
 // ticket, so the tiles are grouped into one wave of virtual blocks over the resident block
 // slots (and never more virtual blocks than the reducer has partial sums for).
+// Entries of update_kernel_x8's (pixel, view) table for one subset, computed once per geometry:
+// entry e = (tile t, view u, pixel pl of the tile) is bp_entry(pixel t TP + pl, view u), in the
+// kernel's shared-memory order, so that one tile's entries are one contiguous block.  bp_entry
+// has no arithmetic that differs between the FP32 kernels (the FP32 and FP32 + Kahan tables are
+// the same bits as those the kernel computes).
+template <int KC>
+__global__ void __launch_bounds__(256) bp_table_kernel(const __grid_constant__ GeoDev g, int slot0,
+                                                      int nviews, int TP, long long nent, void *out)
+{
+    using E = typename BpTable<KC, AR_KAHAN, 1024 / (KC > 2 ? 2 : 1)>::E;
+    const long long per = (long long)nviews * TP;
+    const int npix = g.N * g.N;
+    for (long long e = blockIdx.x * 256LL + threadIdx.x; e < nent; e += (long long)gridDim.x * 256) {
+        const long long tile = e / per;
+        const int r = (int)(e - tile * per);
+        const int uu = r / TP, pl = r - uu * TP;
+        const long long j = tile * TP + pl;
+        const bool in = j < npix;
+        reinterpret_cast<E *>(out)[e] = bp_entry<KC, AR_KAHAN, 1024 / (KC > 2 ? 2 : 1)>(
+            g, slot0, uu, in, in ? (int)(j % g.N) : 0, in ? (int)(j / g.N) : 0);
+    }
+}
+
+// The packed update kernel runs for 8-plane groups with uniform bins and without TOF; its table
+// holds 1024 (KC = 2) or 512 (KC = 4) entries of 16 or 32 bytes.
+size_t bp_table_bytes_bound(const pet_geometry_desc &d)
+{
+    if (d.nplanes <= 1 || d.subrays > 1 || d.ring_mm > 0 || d.tof_bins > 1) return 0;
+    const long long NG = (d.nplanes + 7) / 8, TP = 256 / NG;
+    const long long npix = (long long)d.n * d.n, ntiles = (npix + TP - 1) / TP;
+    const long long vmax = (d.nviews + d.nsubsets - 1) / d.nsubsets;
+    if (TP < 1 || vmax * TP > 1024) return 0;
+    return (size_t)(ntiles * d.nviews * TP * 32);
+}
+
+pet_status build_bp_table(pet_geometry *g, cudaStream_t st)
+{
+    const GeoDev &gd = g->dev;
+    g->bptab_off.clear();
+    if (gd.G != 8 || gd.table || gd.T > 1) return PET_OK;
+    const int KC = gd.K <= 2 ? 2 : 4;
+    const int CAP = KC > 2 ? 512 : 1024;
+    const int TP = 256 / gd.NG;
+    if (TP < 1) return PET_OK;
+    const size_t esz = KC > 2 ? sizeof(BpTable<4, AR_KAHAN, 512>::E) : sizeof(BpTable<2, AR_KAHAN, 1024>::E);
+    const long long ntiles = ((long long)gd.N * gd.N + TP - 1) / TP;
+    std::vector<size_t> off(gd.M);
+    size_t total = 0;
+    for (int i = 0; i < gd.M; ++i) {
+        const int nv = g->voff[i + 1] - g->voff[i];
+        if (nv * TP > CAP) return PET_OK;           // the kernel computes this geometry's entries
+        off[i] = total;
+        total += (size_t)ntiles * nv * TP * esz;
+    }
+    if (total == 0) return PET_OK;
+    PET_CUDA(dev_malloc(&g->d_bptab, total));
+    for (int i = 0; i < gd.M; ++i) {
+        const int nv = g->voff[i + 1] - g->voff[i];
+        const long long nent = ntiles * nv * TP;
+        const int grid = (int)std::min<long long>((nent + 255) / 256, (long long)sm_count() * 16);
+        char *out = static_cast<char *>(g->d_bptab) + off[i];
+        if (KC == 2) bp_table_kernel<2><<<grid, 256, 0, st>>>(gd, g->voff[i], nv, TP, nent, out);
+        else bp_table_kernel<4><<<grid, 256, 0, st>>>(gd, g->voff[i], nv, TP, nent, out);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "bp_table_kernel launch");
+    }
+    g->bptab_off = off;
+    return PET_OK;
+}
+
 void update_shape(UpdateArgs &a, int arith)
 {
     const int TP = 256 / a.g.NG;
