@@ -374,15 +374,15 @@ __global__ void __launch_bounds__(256, UPDATE_X8_BLOCKS) update_kernel_x8(
         const int ntiles = (npix + TP - 1) / TP;
         // the subset's precomputed entries (one contiguous block per tile) when its views fit
         // the table: copied with cp.async while the stencil runs
-        const char *ptab = (a.bptab && a.nviews <= VC) ? static_cast<const char *>(a.bptab) : nullptr;
-        const int tbytes = a.nviews * TP * (int)sizeof(typename Table::E);
+        const bool pre = a.bptab && a.nviews <= VC;
         float part = 0.f;
         for (int tile = vloc * a.tpv; tile < min(ntiles, (vloc + 1) * a.tpv); ++tile) {
             const int j0 = tile * TP, j = j0 + pl;
             const bool active = pl < TP && j < npix;
-            if (ptab) {
+            if (pre) {
                 __syncthreads();                 // the previous tile's gather is done with tb
-                const char *src = ptab + (size_t)tile * tbytes;
+                const int tbytes = a.nviews * TP * (int)sizeof(typename Table::E);
+                const char *src = static_cast<const char *>(a.bptab) + (size_t)tile * tbytes;
                 for (int o = threadIdx.x * 16; o < tbytes; o += 256 * 16)
                     cp_async16(reinterpret_cast<char *>(tb.e) + o, src + o);
                 cp_async_commit();
@@ -477,7 +477,7 @@ __global__ void __launch_bounds__(256, UPDATE_X8_BLOCKS) update_kernel_x8(
             for (int k = 0; k < 4; ++k) { sm[k] = 0ull; er[k] = 0ull; }
             for (int u0 = 0; u0 < a.nviews; u0 += VC) {
                 const int nvc = min(VC, a.nviews - u0);
-                if (ptab) {
+                if (pre) {
                     cp_async_wait_all();
                     __syncthreads();
                 } else {
