@@ -155,7 +155,7 @@ void pet_debug_fail_alloc(int n);
  * views) on the device.  With nplanes > 1, uniform bins (subrays <= 1, ring_mm = 0) and no TOF
  * it also stores the backprojection's (pixel, view) entries for the FP32 update (16 or 32 bytes
  * per pixel and view: 302 MB for 256 x 256 pixels and 288 views), unless a subset has more
- * views than the update's table holds.  Synchronises `stream` before returning.
+ * views than half the update's table holds.  Synchronises `stream` before returning.
  * PET_ERR_INVALID for a bad desc
  * (limits: 1 <= n <= 8192, 1 <= nplanes <= 2048, nbins >= 4, 1 <= nsubsets <= nviews,
  * bin_mm >= 0.36 pixel_mm, 0 <= subrays <= 64, 0 <= tof_bins <= 64 (TOF with subrays <= 1),

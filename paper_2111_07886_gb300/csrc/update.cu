@@ -372,21 +372,23 @@ __global__ void __launch_bounds__(256, UPDATE_X8_BLOCKS) update_kernel_x8(
         const float *w = reinterpret_cast<const float *>(a.w) + grp * 8;
         const float *invp = reinterpret_cast<const float *>(a.invp);
         const int ntiles = (npix + TP - 1) / TP;
-        // the subset's precomputed entries (one contiguous block per tile) when its views fit
-        // the table: copied with cp.async while the stencil runs
-        const bool pre = a.bptab && a.nviews <= VC;
+        // the subset's precomputed entries (one contiguous block per tile) when two tiles' entries
+        // fit the table: double-buffered, the next tile's block copied with cp.async while this
+        // tile is gathered and the next one's stencil runs (one barrier per tile)
+        const bool pre = a.bptab && 2 * a.nviews * TP <= Table::CAP;
+        const int t0 = vloc * a.tpv, t1 = min(ntiles, (vloc + 1) * a.tpv);
+        auto copy_tile = [&](int tile) {
+            const int tbytes = a.nviews * TP * (int)sizeof(typename Table::E);
+            const char *src = static_cast<const char *>(a.bptab) + (size_t)tile * tbytes;
+            char *dst = reinterpret_cast<char *>(tb.e) + ((tile - t0) & 1) * tbytes;
+            for (int o = threadIdx.x * 16; o < tbytes; o += 256 * 16) cp_async16(dst + o, src + o);
+            cp_async_commit();
+        };
+        if (pre && t0 < t1) copy_tile(t0);
         float part = 0.f;
-        for (int tile = vloc * a.tpv; tile < min(ntiles, (vloc + 1) * a.tpv); ++tile) {
+        for (int tile = t0; tile < t1; ++tile) {
             const int j0 = tile * TP, j = j0 + pl;
             const bool active = pl < TP && j < npix;
-            if (pre) {
-                __syncthreads();                 // the previous tile's gather is done with tb
-                const int tbytes = a.nviews * TP * (int)sizeof(typename Table::E);
-                const char *src = static_cast<const char *>(a.bptab) + (size_t)tile * tbytes;
-                for (int o = threadIdx.x * 16; o < tbytes; o += 256 * 16)
-                    cp_async16(reinterpret_cast<char *>(tb.e) + o, src + o);
-                cp_async_commit();
-            }
             f2x A[4], B[4];
             if (active) {
                 const int ix = j % N, iy = j / N;
@@ -478,16 +480,18 @@ __global__ void __launch_bounds__(256, UPDATE_X8_BLOCKS) update_kernel_x8(
             for (int u0 = 0; u0 < a.nviews; u0 += VC) {
                 const int nvc = min(VC, a.nviews - u0);
                 if (pre) {
-                    cp_async_wait_all();
-                    __syncthreads();
+                    cp_async_wait_all();             // this tile's block (this thread's part)
+                    __syncthreads();                 // all parts; the previous gather is done
+                    if (tile + 1 < t1) copy_tile(tile + 1);
                 } else {
                     __syncthreads();
                     bp_fill<KC, AR>(g, a.slot0, u0, nvc, j0, TP, tb);
                     __syncthreads();
                 }
                 if (!active) continue;
+                const typename Table::E *te = tb.e + (pre ? ((tile - t0) & 1) * a.nviews * TP : 0);
                 for (int uu = 0; uu < nvc; ++uu) {
-                    const typename Table::E ent = tb.e[uu * TP + pl];
+                    const typename Table::E ent = te[uu * TP + pl];
                     const float *row = w + ent.off;
 #pragma unroll
                     for (int kb = 0; kb < KC; kb += 2) {
@@ -765,14 +769,14 @@ __global__ void __launch_bounds__(256) bp_table_kernel(const __grid_constant__ G
 }
 
 // The packed update kernel runs for 8-plane groups with uniform bins and without TOF; its table
-// holds 1024 (KC = 2) or 512 (KC = 4) entries of 16 or 32 bytes.
+// holds 1024 (KC = 2) or 512 (KC = 4) entries of 16 or 32 bytes, two tiles' worth when copied.
 size_t bp_table_bytes_bound(const pet_geometry_desc &d)
 {
     if (d.nplanes <= 1 || d.subrays > 1 || d.ring_mm > 0 || d.tof_bins > 1) return 0;
     const long long NG = (d.nplanes + 7) / 8, TP = 256 / NG;
     const long long npix = (long long)d.n * d.n, ntiles = (npix + TP - 1) / TP;
     const long long vmax = (d.nviews + d.nsubsets - 1) / d.nsubsets;
-    if (TP < 1 || vmax * TP > 1024) return 0;
+    if (TP < 1 || 2 * vmax * TP > 1024) return 0;
     return (size_t)(ntiles * d.nviews * TP * 32);
 }
 
@@ -791,7 +795,7 @@ pet_status build_bp_table(pet_geometry *g, cudaStream_t st)
     size_t total = 0;
     for (int i = 0; i < gd.M; ++i) {
         const int nv = g->voff[i + 1] - g->voff[i];
-        if (nv * TP > CAP) return PET_OK;           // the kernel computes this geometry's entries
+        if (2 * nv * TP > CAP) return PET_OK;       // the kernel computes this geometry's entries
         off[i] = total;
         total += (size_t)ntiles * nv * TP * esz;
     }
