@@ -149,6 +149,12 @@ const char *pet_last_error(void);
  * disarms the hook.  One failure per arming.  No GPU fault is involved. */
 void pet_debug_fail_alloc(int n);
 
+/* Test hook (no counterpart in the paper): enable = 0 makes geometries created from now on (on
+ * any thread) skip the precomputed backprojection entries described at pet_geometry_create,
+ * so that their FP32 update computes the entries per tile; a nonzero value restores the
+ * default.  Both give the same results, bit for bit; the hook lets a test show it. */
+void pet_debug_bp_table(int enable);
+
 /* ------------------------------------------------------------------------------------------
  * Geometry (Sec. II-A/II-B).  Builds the per-view / per-ray walk tables in FP64 on the host,
  * uploads them, and computes the sensitivity p_j of Eq. pj (one backprojection of ones over all

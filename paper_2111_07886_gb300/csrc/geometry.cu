@@ -25,6 +25,7 @@ pet_status fail(pet_status st, const std::string &msg)
 }
 
 static std::atomic<long long> g_fail_alloc{0};
+static std::atomic<int> g_bp_table{1};   // pet_debug_bp_table
 
 bool alloc_fault()
 {
@@ -90,6 +91,7 @@ using namespace pet;
 extern "C" const char *pet_last_error(void) { return pet::g_last_error.c_str(); }
 
 extern "C" void pet_debug_fail_alloc(int n) { pet::g_fail_alloc.store(n > 0 ? n : 0); }
+extern "C" void pet_debug_bp_table(int enable) { pet::g_bp_table.store(enable ? 1 : 0); }
 
 static pet_status build_tables(pet_geometry *g, std::vector<ViewGeo> &views,
                                std::vector<RayGeo> &rays, std::vector<BinGeo> &bins)
@@ -334,7 +336,7 @@ static pet_status geometry_init(pet_geometry *g, cudaStream_t st)
         if (e != cudaSuccess) s = cuda_fail(e, "finish_sensitivity");
     }
     cudaFreeAsync(bp, st);
-    if (s == PET_OK) s = build_bp_table(g, st);
+    if (s == PET_OK && g_bp_table.load()) s = build_bp_table(g, st);
     cudaError_t e = cudaStreamSynchronize(st);
     if (s != PET_OK) return s;
     if (e != cudaSuccess) return cuda_fail(e, "pet_geometry_create");

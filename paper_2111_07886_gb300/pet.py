@@ -79,6 +79,7 @@ SIGNATURES = {
     "pet_forward_subset_f64": (_I, [_VP, _I, _VP, _VP, _VP]),
     "pet_back_subset_f64": (_I, [_VP, _I, _VP, _VP, _VP]),
     "pet_debug_fail_alloc": (None, [ctypes.c_int]),
+    "pet_debug_bp_table": (None, [ctypes.c_int]),
     "pet_state_create": (_I, [_VP, _VP, _VP, ctypes.POINTER(Params), _VP, _VP, ctypes.POINTER(_VP)]),
     "pet_state_create_attn": (_I, [_VP, _VP, _VP, _VP, ctypes.POINTER(Params), _VP, _VP,
                                    ctypes.POINTER(_VP)]),
@@ -145,6 +146,12 @@ def debug_fail_alloc(n: int):
     """Test hook: the n-th device / pinned allocation of the library from now fails as out of
     memory (n <= 0 disarms); host-side fault injection."""
     lib().pet_debug_fail_alloc(int(n))
+
+
+def debug_bp_table(enable: bool):
+    """Test hook: geometries created from now on skip (False) or build (True, the default) the
+    precomputed backprojection entries of the FP32 update; the results are the same bits."""
+    lib().pet_debug_bp_table(1 if enable else 0)
 
 
 def _check(status: int):
