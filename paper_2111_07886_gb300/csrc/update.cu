@@ -742,9 +742,6 @@ static const void *update_fn(int arith, int z3 = 0, int sub = 0, int tof = 0)
     return (const void *)update_kernel<G, KC, AR_FP64>;
 }
 
-// Pixel tiles per virtual block: each virtual block ends in a block reduction and a grid-wide
-// ticket, so the tiles are grouped into one wave of virtual blocks over the resident block
-// slots (and never more virtual blocks than the reducer has partial sums for).
 // Entries of update_kernel_x8's (pixel, view) table for one subset, computed once per geometry:
 // entry e = (tile t, view u, pixel pl of the tile) is bp_entry(pixel t TP + pl, view u), in the
 // kernel's shared-memory order, so that one tile's entries are one contiguous block.  bp_entry
@@ -800,21 +797,29 @@ pet_status build_bp_table(pet_geometry *g, cudaStream_t st)
         total += (size_t)ntiles * nv * TP * esz;
     }
     if (total == 0) return PET_OK;
-    PET_CUDA(dev_malloc(&g->d_bptab, total));
+    void *tab = nullptr;
+    PET_CUDA(dev_malloc(&tab, total));
     for (int i = 0; i < gd.M; ++i) {
         const int nv = g->voff[i + 1] - g->voff[i];
         const long long nent = ntiles * nv * TP;
         const int grid = (int)std::min<long long>((nent + 255) / 256, (long long)sm_count() * 16);
-        char *out = static_cast<char *>(g->d_bptab) + off[i];
+        char *out = static_cast<char *>(tab) + off[i];
         if (KC == 2) bp_table_kernel<2><<<grid, 256, 0, st>>>(gd, g->voff[i], nv, TP, nent, out);
         else bp_table_kernel<4><<<grid, 256, 0, st>>>(gd, g->voff[i], nv, TP, nent, out);
         cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return cuda_fail(e, "bp_table_kernel launch");
+        if (e != cudaSuccess) {
+            cudaFree(tab);
+            return cuda_fail(e, "bp_table_kernel launch");
+        }
     }
+    g->d_bptab = tab;                                // set together with the offsets
     g->bptab_off = off;
     return PET_OK;
 }
 
+// Pixel tiles per virtual block: each virtual block ends in a block reduction and a grid-wide
+// ticket, so the tiles are grouped into one wave of virtual blocks over the resident block
+// slots (and never more virtual blocks than the reducer has partial sums for).
 void update_shape(UpdateArgs &a, int arith)
 {
     const int TP = 256 / a.g.NG;
